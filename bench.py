@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark of the directional splitting solver on one GB300.
+
+Workload: the sheared-flow stationary problem on the unit square, 2048 x 2048
+nodes, beta = (1, 0.5 + 0.3 sin 2 pi x), mu = 1e-3, sigma = 1, f = 8 seeded
+Gaussians of width 0.02 (synthetic data), solved from u = 0 until the relative
+update |u_{j+1} - u_j| / |u_{j+1}| <= 1e-8.
+
+One step = one such solve.  value = line unknowns solved per second (both curve
+families, every split step) over the timed steps; ms_per_step = time to 1e-8.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32]
+  python bench.py --impl reference     # the FP64 CPU oracle on the same workload
+
+With N > 1 (torchrun) every rank solves its own copy of the problem (the
+path has no exchange step between independent problems): weak scaling, no
+collective on the data path; the barrier and the max-over-ranks time only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "line-DOF/s (2D ADR directional splitting, time-to-1e-8 relative update)"
+UNIT = "line-DOF/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 arithmetic peak of one GB300: 152 SMs x 2 FP64 FMA/clk (4 flop) x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+# Algorithmic traffic and FP64 work per unit of each sweep kernel (unit = one
+# curve node for the curve solves, one grid node for the maps).  Bytes count
+# every array the kernel must touch once; flops count the kernel's FP64
+# arithmetic per unit (fma = 2, divide = 1).
+KERNELS = ["curve solve B", "curve->grid map B", "curve solve G", "curve->grid map G"]
+BYTES_PER_UNIT = [48.0, 81.0, 32.0, 89.0]
+FLOPS_PER_UNIT = [80.0, 16.0, 52.0, 20.0]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        load = [r for r in rows if num(r[4]) >= 50] or rows
+        sm = [num(r[1]) for r in load]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in load:
+            for k, name in enumerate(names):
+                if r[6 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": num(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load)}
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, value, device):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(ws, value, device):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- oracle legs
+
+def oracle_sample(n, budget_s=12.0, min_steps=1):
+    """Time split steps of the FP64 CPU oracle on the same workload (setup
+    excluded) for about budget_s seconds.  Returns (line-DOF/s, steps, secs)."""
+    from oracle import oracle as O
+    from paper_2411_11041_gb300 import workloads as W
+    prob = W.sheared(n=n)
+    o = O.Oracle(prob)
+    unknowns = 0
+    for fam in (0, 1):
+        off = o.lines(fam)["off"]
+        unknowns += int(np.maximum(np.diff(off) - 2, 0).sum())
+    dt = o.default_dt()
+    u = np.zeros((n, n))
+    steps, t0 = 0, time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < budget_s:
+        _, u = o.split_step(0.5, dt, u)
+        steps += 1
+    secs = time.perf_counter() - t0
+    return unknowns * steps / secs, steps, secs, unknowns
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2411_11041_gb300 import workloads as W
+    prob = W.sheared(n=args.n)
+    o = O.Oracle(prob)
+    unknowns = 0
+    for fam in (0, 1):
+        off = o.lines(fam)["off"]
+        unknowns += int(np.maximum(np.diff(off) - 2, 0).sum())
+    dt = o.default_dt()
+    u = np.zeros((args.n, args.n))
+    for _ in range(args.warmup):
+        _, u = o.split_step(0.5, dt, u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, u = o.split_step(0.5, dt, u)
+    secs = time.perf_counter() - t0
+    val = unknowns * args.steps / secs
+    sample = (f"{args.steps} split steps (one B and one G sweep each) of the {args.n}^2 "
+              "sheared problem per timed run, setup excluded; a full solve takes the "
+              "same per-step work times the iteration count")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"sheared{args.n}", "nodes": args.n * args.n,
+                                        "step": "one split step (oracle sample)"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our leg
+
+def run_ours(args):
+    import torch
+
+    from paper_2411_11041_gb300 import ADR_FP32_REFINE, ADR_FP64, Solver
+    from paper_2411_11041_gb300 import workloads as W
+    ws, rank, local = dist_setup(args)
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
+    prob = W.sheared(n=args.n)
+    solver = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec)
+    unknowns = solver.line_unknowns()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        solver.solve_stationary()
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, dofs, status = [], 0.0, []
+    e0.record(stream)
+    for _ in range(args.steps):
+        u, _, st, code = solver.solve_stationary()
+        iters.append(st["iters"])
+        dofs += st["line_dofs"]
+        status.append(code)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ws, ms, dev)
+    dofs_all = sum_over_ranks(ws, dofs, dev)
+    value = dofs_all / (ms_max / 1e3)
+    # per-kernel device time in the solve's launch configuration (CUDA events)
+    kms = solver.time_kernels(reps=20)
+    units = [unknowns[0], prob.nx * prob.ny, unknowns[1], prob.nx * prob.ny]
+    k = int(np.argmax(kms))
+    hbm, hbm_kind = peaks()
+    gbs = BYTES_PER_UNIT[k] * units[k] / (kms[k] * 1e-3) / 1e9
+    tflops = FLOPS_PER_UNIT[k] * units[k] / (kms[k] * 1e-3) / 1e12
+    if tflops / FP64_PEAK_TFLOPS >= gbs / hbm:
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "FP64 FMA issue peak derived from 152 SMs x 2 FMA/clk x 2.07 GHz",
+                "hbm_frac": gbs / hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": None, "peak_kind": hbm_kind}
+    roof.update({"kernel": KERNELS[k], "kernel_ms": kms[k], "units_per_launch": units[k],
+                 "all_kernels_ms": dict(zip(KERNELS, kms))})
+    launches = int(sum(5 * it + 3 for it in iters))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == ADR_FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"sheared{args.n}", "nodes": prob.nx * prob.ny,
+                   "mu": prob.mu, "sigma": prob.sigma, "tol": args.tol, "prec": args.prec,
+                   "line_unknowns_per_step": unknowns, "iters_per_solve": iters,
+                   "step": "one stationary solve to tol from u=0",
+                   "l2": "working set > 129 MB L2 (curve data and maps ~1 GB)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roof, "gpu_launches": launches, "clocks": clk,
+    }
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, prob, dev, prec)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, nst, secs, unk = oracle_sample(args.n)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{nst} split steps of the {args.n}^2 sheared problem "
+                                          f"({secs:.1f} s, setup excluded), single thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(args, prob, dev, prec):
+    """Public-API end to end: pinned host inputs -> device, adr_create,
+    adr_solve_stationary, result -> host, every step."""
+    import torch
+
+    from paper_2411_11041_gb300 import Solver
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k))).pin_memory()
+           for k in ("mask", "beta1", "beta2", "f")}
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    d2h = prob.nx * prob.ny * 8
+    host_out = torch.empty((prob.ny, prob.nx), dtype=torch.float64).pin_memory()
+
+    class P:
+        pass
+
+    def one():
+        q = P()
+        q.nx, q.ny, q.x0, q.y0, q.x1, q.y1 = prob.nx, prob.ny, prob.x0, prob.y0, prob.x1, prob.y1
+        q.mu, q.sigma = prob.mu, prob.sigma
+        for k, t in pin.items():
+            setattr(q, k, t.to(dev, non_blocking=True))
+        s = Solver(q, device=dev, tol=args.tol, max_iter=200000, prec=prec)
+        u, _, st, _ = s.solve_stationary()
+        host_out.copy_(u)
+        s.close()
+        return st["line_dofs"]
+
+    one()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    dofs = 0.0
+    for _ in range(args.steps):
+        dofs += one()
+    torch.cuda.synchronize(dev)
+    secs = time.perf_counter() - t0
+    return {"value": dofs / secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": secs / args.steps * 1e3,
+            "includes": "H2D of mask/beta/f from pinned memory, adr_create (geometry setup), "
+                        "adr_solve_stationary, D2H of u"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

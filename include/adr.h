@@ -1,0 +1,199 @@
+/*
+ * adr.h -- C ABI of the GB300 (sm_103a) directional diffusion splitting
+ * solver for 2D advection-diffusion-reaction problems
+ * (Drebotiy & Shynkarenko, arXiv 2411.11041).
+ *
+ * Problem (§2, eqs. BVP1 and Parabolic1):
+ *     u_t - mu Lap u + beta . grad u + sigma u = f   in Omega,  u = 0 on its boundary,
+ * and its stationary limit.  The library reduces every split substep
+ * (§5, eq. SemiDiscrSplit) to independent 1D linear-FEM problems along the
+ * integral curves of beta (family B) and of gamma = (beta2, -beta1) (family G)
+ * (§6, eqs. SemiDiscrSplit1Dbeta / SemiDiscrSplit1Dgamma).  It carries values
+ * between the two families through the grid: curve -> grid by the
+ * min/max-crossing rule of §6, grid -> curve by bilinear interpolation (§6.1).
+ *
+ * Conventions used by every call below:
+ *  - Grids are row-major [ny][nx] arrays over the NODES of a uniform grid on
+ *    [x0,x1] x [y0,y1], boundary nodes included (spacing hx = (x1-x0)/(nx-1)).
+ *  - Every array argument is a DEVICE pointer (CUDA global memory) unless it
+ *    is documented as a host pointer.  The caller owns it.  The library never
+ *    frees or retains caller memory past the call, except that a handle keeps
+ *    private copies of what adr_create derives from its inputs.
+ *  - `stream` is a cudaStream_t passed as void*; all device work of a handle is
+ *    ordered on it.  NULL means the legacy default stream.
+ *  - Functions never abort and never throw across the ABI.  They return an
+ *    adr_status; adr_last_error() gives a message for the calling thread.
+ *  - Domain: a grid cell is active when its 4 corner nodes have mask != 0;
+ *    Omega_h is the union of active cells.  A node is interior when its 4
+ *    cells are active; every other node of Omega_h carries u = 0.
+ */
+#ifndef ADR_H
+#define ADR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ADR_OK = 0,
+    ADR_EINVAL = 1,   /* invalid argument (sizes, mu/sigma <= 0, |beta| = 0, empty mask ...) */
+    ADR_ENOMEM = 2,   /* device or host allocation failed */
+    ADR_ECUDA = 3,    /* a CUDA call failed (message in adr_last_error) */
+    ADR_ENOCONV = 4,  /* max_iter reached before tol; outputs hold the last iterate */
+    ADR_EGEOM = 5,    /* curve tracing failed (closed integral curve or |beta| = 0 on a curve) */
+    ADR_ETIMEOUT = 6  /* reserved: a bounded device wait gave up */
+} adr_status;
+
+typedef enum {
+    ADR_FP64 = 0,        /* every step in FP64 */
+    ADR_FP32_REFINE = 1  /* line solves in FP32 + one FP64-residual refinement step */
+} adr_precision;
+
+typedef enum {
+    ADR_INIT_ZERO = 0,     /* u_0 = 0 */
+    ADR_INIT_USER = 1,     /* u_0 = caller array (non-interior nodes ignored) */
+    ADR_INIT_PAPER_U0 = 2, /* s(u_0, v) = <l, v>  (§5, eq. u0stationary) */
+    ADR_INIT_LEARNED = 3   /* reserved for a learned initial state */
+} adr_init;
+
+/* Grid of nx x ny nodes on [x0,x1] x [y0,y1]; nx, ny >= 3. */
+typedef struct {
+    int nx, ny;
+    double x0, y0, x1, y1;
+} adr_grid;
+
+/* Options of a handle.  theta: time-scheme weight, (0,1] (§4 eq. SemiDiscr;
+ * 0.5 = Crank-Nicolson).  dt: pseudo-time step of the stationary iteration
+ * (<= 0 selects 2/sqrt(lmin*lmax), lmin = sigma, lmax = 12 mu/h^2 +
+ * 2 sqrt(3) max|beta|/h).  tol: stop when |u_{j+1}-u_j|_2/|u_{j+1}|_2 <= tol over
+ * interior nodes (tol <= 0 runs exactly max_iter steps and succeeds).
+ * max_iter: cap (>= 0). */
+typedef struct {
+    int prec;        /* adr_precision */
+    double theta;
+    double dt;
+    double tol;
+    int max_iter;
+    int init;        /* adr_init */
+    int reserved0;   /* must be 0 */
+    int reserved1;   /* must be 0 */
+} adr_opts;
+
+/* Result statistics (host struct filled by the solve calls). */
+typedef struct {
+    int iters;          /* split steps performed */
+    double rel_update;  /* last relative update */
+    double ms;          /* device time of the solve (CUDA events on the stream) */
+    double line_dofs;   /* line unknowns solved in total (both families, all steps) */
+    double dt;          /* pseudo step used */
+} adr_stats;
+
+typedef struct adr_problem adr_problem; /* opaque handle */
+
+/* Fill opts with the defaults: FP64, theta 0.5, dt auto, tol 1e-10,
+ * max_iter 100000, zero initial state. */
+void adr_default_opts(adr_opts* opts);
+
+/*
+ * adr_create -- build a problem handle (§2 eq. BVP1 data; §6 geometry).
+ * grid:  host pointer.  mask: device uint8 [ny][nx].  mu, sigma > 0
+ * (constants, §2).  beta1, beta2, f: device double [ny][nx] nodal values.  A
+ * field that is the same at every node of Omega_h gives straight line
+ * families; any other field gives RK4-traced curves seeded on the inflow
+ * boundary (eqs. cauchyStartSets, CauchyBeta, CauchyGamma).  opts: host
+ * pointer (copied).  On success *out owns its device buffers until
+ * adr_destroy.  Inputs may be freed after the call returns.
+ * Errors: ADR_EINVAL (bad sizes/coefficients, |beta| = 0 or non-finite data on
+ * Omega_h, empty mask), ADR_EGEOM, ADR_ENOMEM, ADR_ECUDA.
+ */
+adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, double sigma,
+                      const double* beta1, const double* beta2, const double* f,
+                      const adr_opts* opts, void* stream, adr_problem** out);
+
+/*
+ * adr_solve_stationary -- solve BVP1 as the large-time limit of Parabolic1
+ * (§2) with the split scheme (§5 eq. SemiDiscrSplit, reduced to the curves as
+ * in §6) until the relative update is <= opts.tol or opts.max_iter steps ran.
+ * u_init: device [ny][nx], read only when opts.init == ADR_INIT_USER (else may
+ * be NULL).  u_out: device [ny][nx] <- the solution: for theta = 0.5 the
+ * midpoint (u_j + u_{j+1/2})/2 of the last step, else u_{j+1}.
+ * u_iter_out: nullable device [ny][nx] <- u_{j+1}.  stats: nullable host.
+ * The call returns after the solve has finished on the stream.
+ * Errors: ADR_ENOCONV (outputs written), ADR_EINVAL, ADR_ECUDA.
+ */
+adr_status adr_solve_stationary(adr_problem* prob, const double* u_init, double* u_out,
+                                double* u_iter_out, adr_stats* stats);
+
+/*
+ * adr_step_parabolic -- advance Parabolic1 (§2) by nsteps steps of dt.
+ * mode 0: the paper's scheme, one split step per time step (§5 eq.
+ *         SemiDiscrSplit with dt and opts.theta).
+ * mode 1: implicit Euler in time; each slice
+ *         -mu Lap u + beta.grad u + (sigma + 1/dt) u = f + u_n/dt
+ *         is solved by the stationary iteration (opts.theta, opts.dt as the
+ *         pseudo step, opts.tol, opts.max_iter), warm-started from u_n.
+ * u_inout: device [ny][nx], the state, overwritten (non-interior nodes set
+ * to 0).  stats: nullable host (iters = split steps over all slices).
+ * Errors: ADR_EINVAL, ADR_ENOCONV (a slice hit max_iter; stepping continues),
+ * ADR_ECUDA.
+ */
+adr_status adr_step_parabolic(adr_problem* prob, double dt, int nsteps, int mode,
+                              double* u_inout, adr_stats* stats);
+
+/* Release a handle and its device buffers (NULL is a no-op). */
+void adr_destroy(adr_problem* prob);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* adr_last_error(void);
+
+/*
+ * Geometry inspection (setup results, for tests and tools).  Host outputs.
+ * adr_num_lines / adr_num_line_nodes: counts of family fam (0 = B, 1 = G).
+ * adr_get_lines: off[n_lines+1] (int32), xi/eta[n_nodes] index coordinates
+ * (x = x0 + xi*hx), h[n_lines] element length; any pointer may be NULL.
+ * adr_get_crossings: per grid node the 4 crossings used by the curve->grid map
+ * (row left, row right, column down, column up): seg[4*nx*ny] global index of
+ * the segment's first curve node (-1 boundary, -2 non-interior node),
+ * t[4*nx*ny] position in the segment, pos[4*nx*ny] coordinate along the grid
+ * line.  Errors: ADR_EINVAL.
+ */
+int adr_num_lines(const adr_problem* prob, int fam);
+int adr_num_line_nodes(const adr_problem* prob, int fam);
+adr_status adr_get_lines(const adr_problem* prob, int fam, int* off, double* xi, double* eta,
+                         double* h);
+adr_status adr_get_crossings(const adr_problem* prob, int fam, int* seg, double* t, double* pos);
+
+/*
+ * adr_split_step -- one split step u -> (u_half, u_next) of eq. SemiDiscrSplit
+ * with the handle's theta and the given dt (device arrays [ny][nx]; u_half
+ * may be NULL).  The building block of both solve calls, exported so that
+ * callers can drive their own time loop.  Errors: ADR_EINVAL, ADR_ECUDA.
+ */
+adr_status adr_split_step(adr_problem* prob, double dt, const double* u, double* u_half,
+                          double* u_next);
+
+/*
+ * adr_paper_u0 -- the paper's initial state for advection-dominated problems
+ * (§5 eq. u0stationary): one steady solve s_i(u0, w) = <l_i, w> on every B
+ * curve, mapped to the grid.  u0: device [ny][nx].  Errors: ADR_ECUDA.
+ */
+adr_status adr_paper_u0(adr_problem* prob, double* u0);
+
+/*
+ * adr_time_kernels -- device time of the four sweep kernels of one split step
+ * (B curve solve, B curve->grid map, G curve solve, G map), each launched reps
+ * times back to back on the handle's stream in the launch configuration of
+ * the solve, timed with CUDA events on that stream.  They run on the handle's
+ * current grid state (work buffers only; no caller memory is touched).
+ * ms_out: host double[4], average milliseconds per launch.  Errors:
+ * ADR_EINVAL, ADR_ECUDA.
+ */
+adr_status adr_time_kernels(adr_problem* prob, int reps, double* ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADR_H */

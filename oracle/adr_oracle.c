@@ -1160,7 +1160,8 @@ static void relative_update(const orc_problem* p, const double* u, const double*
  * |u_{j+1} - u_j| / |u_{j+1}| (interior nodes, 2-norm) is <= tol.
  * Output: for theta = 1/2 the midpoint (u_j + u_{j+1/2}) / 2 of the last step
  * (the fixed point of the Crank-Nicolson split step sits there), otherwise
- * u_{j+1}; u_iter_out (nullable) receives u_{j+1}. */
+ * u_{j+1}; u_iter_out (nullable) receives u_{j+1}.  tol <= 0 runs exactly
+ * max_iter steps and reports success. */
 int orc_solve_stationary(const orc_problem* p, double theta, double dt, double tol,
                          int max_iter, int init, const double* u_init, double sig,
                          const double* f_extra, double fx_scale, double* u_out,
@@ -1181,13 +1182,14 @@ int orc_solve_stationary(const orc_problem* p, double theta, double dt, double t
     for (j = 0; j < max_iter; ++j) {
         orc_split_step(p, theta, dt, sig, f_extra, fx_scale, u, uh, un);
         relative_update(p, u, un, &rel);
-        if (rel <= tol) {
+        if (tol > 0.0 && rel <= tol) {
             status = ORC_OK;
             break;
         }
         if (j + 1 < max_iter) memcpy(u, un, N * sizeof(double));
     }
     int done = (j < max_iter) ? j + 1 : max_iter;
+    if (tol <= 0.0) status = ORC_OK; /* a fixed number of steps was asked for */
     if (max_iter <= 0) memcpy(un, u, N * sizeof(double)), memcpy(uh, u, N * sizeof(double));
     for (size_t k = 0; k < N; ++k)
         u_out[k] = (theta == 0.5) ? 0.5 * (u[k] + uh[k]) : un[k];

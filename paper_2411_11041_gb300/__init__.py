@@ -1,0 +1,258 @@
+"""Python binding of the GB300 directional diffusion splitting library.
+
+Thin ctypes marshalling over ``libadr.so`` (C ABI in ``include/adr.h``): the
+functions below carry the C names and only move pointers, sizes and structs.
+Every step of the method runs in the library's CUDA kernels; there is no CPU
+path, and importing the binding fails loudly when the library is missing.
+
+Device memory and streams come from PyTorch: arrays are CUDA tensors
+(float64 grids ``[ny][nx]``, uint8 masks) and the stream is torch's current
+CUDA stream unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libadr.so")
+
+ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_ENOCONV, ADR_EGEOM, ADR_ETIMEOUT = range(7)
+ADR_FP64, ADR_FP32_REFINE = 0, 1
+ADR_INIT_ZERO, ADR_INIT_USER, ADR_INIT_PAPER_U0, ADR_INIT_LEARNED = 0, 1, 2, 3
+STATUS_NAMES = {0: "ADR_OK", 1: "ADR_EINVAL", 2: "ADR_ENOMEM", 3: "ADR_ECUDA", 4: "ADR_ENOCONV",
+                5: "ADR_EGEOM", 6: "ADR_ETIMEOUT"}
+
+
+class adr_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
+                ("x1", C.c_double), ("y1", C.c_double)]
+
+
+class adr_opts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("theta", C.c_double), ("dt", C.c_double),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("init", C.c_int),
+                ("reserved0", C.c_int), ("reserved1", C.c_int)]
+
+
+class adr_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rel_update", C.c_double), ("ms", C.c_double),
+                ("line_dofs", C.c_double), ("dt", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AdrError(RuntimeError):
+    def __init__(self, status, what):
+        msg = lib().adr_last_error().decode(errors="replace")
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libadr.so (built by ``paper_2411_11041_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2411_11041_gb300/build.py "
+                              "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+        L.adr_default_opts.argtypes = [C.POINTER(adr_opts)]
+        L.adr_default_opts.restype = None
+        L.adr_last_error.restype = C.c_char_p
+        L.adr_create.argtypes = [C.POINTER(adr_grid), vp, C.c_double, C.c_double, vp, vp, vp,
+                                 C.POINTER(adr_opts), vp, C.POINTER(vp)]
+        L.adr_solve_stationary.argtypes = [vp, vp, vp, vp, C.POINTER(adr_stats)]
+        L.adr_step_parabolic.argtypes = [vp, C.c_double, C.c_int, C.c_int, vp,
+                                         C.POINTER(adr_stats)]
+        L.adr_destroy.argtypes = [vp]
+        L.adr_destroy.restype = None
+        L.adr_num_lines.argtypes = [vp, C.c_int]
+        L.adr_num_line_nodes.argtypes = [vp, C.c_int]
+        L.adr_get_lines.argtypes = [vp, C.c_int, ip, dp, dp, dp]
+        L.adr_get_crossings.argtypes = [vp, C.c_int, ip, dp, dp]
+        L.adr_split_step.argtypes = [vp, C.c_double, vp, vp, vp]
+        L.adr_paper_u0.argtypes = [vp, vp]
+        L.adr_time_kernels.argtypes = [vp, C.c_int, dp]
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["adr_default_opts", "adr_create", "adr_solve_stationary", "adr_step_parabolic",
+            "adr_destroy", "adr_last_error", "adr_num_lines", "adr_num_line_nodes",
+            "adr_get_lines", "adr_get_crossings", "adr_split_step", "adr_paper_u0",
+            "adr_time_kernels"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(status, what, allow=()):
+    if status != ADR_OK and status not in allow:
+        raise AdrError(status, what)
+    return status
+
+
+def default_opts(**kw) -> adr_opts:
+    o = adr_opts()
+    lib().adr_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+# ------------------------------------------------------------ C-named calls
+
+def adr_create(grid: adr_grid, mask, mu, sigma, beta1, beta2, f, opts: adr_opts, stream=None):
+    h = C.c_void_p()
+    st = lib().adr_create(C.byref(grid), _ptr(mask), float(mu), float(sigma), _ptr(beta1),
+                          _ptr(beta2), _ptr(f), C.byref(opts), _stream_ptr(stream), C.byref(h))
+    _check(st, "adr_create")
+    return h
+
+
+def adr_solve_stationary(h, u_init, u_out, u_iter_out=None):
+    s = adr_stats()
+    st = lib().adr_solve_stationary(h, _ptr(u_init), _ptr(u_out), _ptr(u_iter_out), C.byref(s))
+    _check(st, "adr_solve_stationary", allow=(ADR_ENOCONV,))
+    return st, s
+
+
+def adr_step_parabolic(h, dt, nsteps, mode, u_inout):
+    s = adr_stats()
+    st = lib().adr_step_parabolic(h, float(dt), int(nsteps), int(mode), _ptr(u_inout), C.byref(s))
+    _check(st, "adr_step_parabolic", allow=(ADR_ENOCONV,))
+    return st, s
+
+
+def adr_split_step(h, dt, u, u_half, u_next):
+    _check(lib().adr_split_step(h, float(dt), _ptr(u), _ptr(u_half), _ptr(u_next)),
+           "adr_split_step")
+
+
+def adr_paper_u0(h, u0):
+    _check(lib().adr_paper_u0(h, _ptr(u0)), "adr_paper_u0")
+
+
+def adr_time_kernels(h, reps):
+    ms = (C.c_double * 4)()
+    _check(lib().adr_time_kernels(h, int(reps), ms), "adr_time_kernels")
+    return list(ms)
+
+
+def adr_destroy(h):
+    lib().adr_destroy(h)
+
+
+# ---------------------------------------------------------- convenience
+
+class Solver:
+    """One problem handle on a CUDA device.
+
+    ``prob`` is any object with ``nx, ny, x0, y0, x1, y1, mu, sigma`` and nodal
+    arrays ``mask, beta1, beta2, f`` (numpy or torch).  Inputs are copied to
+    the device once; the handle owns everything it derives from them.
+    """
+
+    def __init__(self, prob, device="cuda:0", stream=None, **opts):
+        torch = _torch()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream
+        self.nx, self.ny = int(prob.nx), int(prob.ny)
+        self.opts = default_opts(**opts)
+        def dev(a, dt):
+            if isinstance(a, torch.Tensor):
+                return a.to(device=self.device, dtype=dt).contiguous()
+            return torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(self.device)
+        mask = dev(prob.mask, torch.uint8)
+        b1, b2, f = (dev(a, torch.float64) for a in (prob.beta1, prob.beta2, prob.f))
+        grid = adr_grid(self.nx, self.ny, prob.x0, prob.y0, prob.x1, prob.y1)
+        with torch.cuda.device(self.device):
+            self.h = adr_create(grid, mask, prob.mu, prob.sigma, b1, b2, f, self.opts, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            adr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _grid(self):
+        return self.torch.zeros((self.ny, self.nx), dtype=self.torch.float64, device=self.device)
+
+    def solve_stationary(self, u_init=None, want_iter=False):
+        out = self._grid()
+        it = self._grid() if want_iter else None
+        st, s = adr_solve_stationary(self.h, u_init, out, it)
+        return out, it, s.as_dict(), st
+
+    def step_parabolic(self, u, dt, nsteps, mode):
+        st, s = adr_step_parabolic(self.h, dt, nsteps, mode, u)
+        return s.as_dict(), st
+
+    def split_step(self, u, dt):
+        uh, un = self._grid(), self._grid()
+        adr_split_step(self.h, dt, u, uh, un)
+        return uh, un
+
+    def paper_u0(self):
+        out = self._grid()
+        adr_paper_u0(self.h, out)
+        return out
+
+    def time_kernels(self, reps=20):
+        """Average device ms of [B solve, B map, G solve, G map] per launch."""
+        return adr_time_kernels(self.h, reps)
+
+    def line_unknowns(self):
+        """Unknowns of one sweep of each family (curve nodes minus the ends)."""
+        out = []
+        for fam in (0, 1):
+            off = self.lines(fam)["off"]
+            out.append(int(np.maximum(np.diff(off) - 2, 0).sum()))
+        return out
+
+    def lines(self, fam):
+        L = lib()
+        nl, nn = L.adr_num_lines(self.h, fam), L.adr_num_line_nodes(self.h, fam)
+        off = np.zeros(nl + 1, np.int32)
+        xi, eta, hh = np.zeros(nn), np.zeros(nn), np.zeros(max(nl, 1))
+        _check(L.adr_get_lines(self.h, fam, off.ctypes.data_as(C.POINTER(C.c_int)),
+                               xi.ctypes.data_as(C.POINTER(C.c_double)),
+                               eta.ctypes.data_as(C.POINTER(C.c_double)),
+                               hh.ctypes.data_as(C.POINTER(C.c_double))), "adr_get_lines")
+        return dict(off=off, xi=xi, eta=eta, h=hh[:nl])
+
+    def crossings(self, fam):
+        n = 4 * self.nx * self.ny
+        seg, t, pos = np.zeros(n, np.int32), np.zeros(n), np.zeros(n)
+        _check(lib().adr_get_crossings(self.h, fam, seg.ctypes.data_as(C.POINTER(C.c_int)),
+                                       t.ctypes.data_as(C.POINTER(C.c_double)),
+                                       pos.ctypes.data_as(C.POINTER(C.c_double))),
+               "adr_get_crossings")
+        s = (self.ny, self.nx, 4)
+        return seg.reshape(s), t.reshape(s), pos.reshape(s)

@@ -1,0 +1,487 @@
+// C ABI of the directional splitting solver: handle lifecycle, the outer
+// iteration as one CUDA graph with a device-side WHILE loop, and the
+// parabolic time stepping.  See include/adr.h for the contract.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "adr_internal.cuh"
+
+namespace adr {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+adr_status cuda_fail(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return ADR_ECUDA;
+}
+
+// launchers defined in sweep.cu
+adr_status launch_line_sweep_ex(Problem* p, int fam, double theta, double dt, double sig,
+                                const double* u_even, const double* u_odd, bool use_state,
+                                const double* fextra, double fx_scale, int paper_u0);
+adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out_odd,
+                              int parity_shift, const double* prev_even, const double* prev_odd,
+                              bool use_state, bool norms);
+int grid_map_blocks(const Problem* p);
+adr_status launch_check_ex(Problem* p, double tol, int max_iter,
+                           cudaGraphConditionalHandle handle, bool use_cond);
+adr_status launch_finish(Problem* p, double* out, double* iter_out, bool midpoint);
+
+}  // namespace adr
+
+using namespace adr;
+
+// The handle: the problem plus the cached solve graph.
+struct adr_problem {
+    Problem p;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // parameters the cached graph was captured with
+    double g_theta = 0, g_dt = 0, g_sig = 0, g_scale = 0, g_tol = 0;
+    int g_max_iter = -1;
+    const double* g_fextra = nullptr;
+    double line_unknowns[2] = {0, 0};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+#define TRY(x)                       \
+    do {                             \
+        adr_status _s = (x);         \
+        if (_s != ADR_OK) return _s; \
+    } while (0)
+
+namespace {
+
+double default_dt(const Problem& p, double sig)
+{
+    double hs = p.gv.hs;
+    double lmax = 12.0 * p.mu / (hs * hs) + 2.0 * std::sqrt(3.0) * p.bmax / hs;
+    return 2.0 / std::sqrt(sig * lmax);
+}
+
+void drop_graph(adr_problem* h)
+{
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    h->g_max_iter = -1;
+}
+
+// Capture one split step (B sweep, B map, G sweep, G map + norms, check) as
+// the body of a conditional WHILE node; the check kernel clears the
+// condition once the relative update reaches tol or max_iter steps ran.
+adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
+                       const double* fextra, double fx_scale, double tol, int max_iter)
+{
+    Problem* p = &h->p;
+    drop_graph(h);
+    ADR_CUDA_TRY(cudaGraphCreate(&h->graph, 0));
+    cudaGraphConditionalHandle cond;
+    ADR_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    ADR_CUDA_TRY(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t user = p->stream;
+    p->stream = h->cap_stream;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
+    adr_status s = ADR_OK;
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+    if (s == ADR_OK)
+        s = launch_line_sweep_ex(p, 0, theta, dt, sig, p->ubuf[0], p->ubuf[1], true, fextra,
+                                 fx_scale, 0);
+    if (s == ADR_OK)
+        s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, true, false);
+    if (s == ADR_OK)
+        s = launch_line_sweep_ex(p, 1, theta, dt, sig, p->ubuf[2], p->ubuf[2], true, nullptr, 0.0,
+                                 0);
+    if (s == ADR_OK)
+        s = launch_grid_map_ex(p, 1, p->ubuf[0], p->ubuf[1], 1, p->ubuf[0], p->ubuf[1], true, true);
+    if (s == ADR_OK) s = launch_check_ex(p, tol, max_iter, cond, true);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &out);
+    p->stream = user;
+    if (s != ADR_OK) return s;
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    ADR_CUDA_TRY(cudaGraphInstantiate(&h->exec, h->graph, 0));
+    h->g_theta = theta;
+    h->g_dt = dt;
+    h->g_sig = sig;
+    h->g_fextra = fextra;
+    h->g_scale = fx_scale;
+    h->g_tol = tol;
+    h->g_max_iter = max_iter;
+    return ADR_OK;
+}
+
+// Outer iteration from the state in ubuf[0]; results into out / iter_out.
+adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
+                         const double* fextra, double fx_scale, double tol, int max_iter,
+                         bool midpoint, double* out, double* iter_out, adr_stats* stats,
+                         bool* converged)
+{
+    Problem* p = &h->p;
+    TRY(launch_state_reset(p));
+    ADR_CUDA_TRY(cudaEventRecord(h->ev0, p->stream));
+    if (max_iter > 0) {
+        if (!h->exec || h->g_theta != theta || h->g_dt != dt || h->g_sig != sig ||
+            h->g_fextra != fextra || h->g_scale != fx_scale || h->g_tol != tol ||
+            h->g_max_iter != max_iter)
+            TRY(build_graph(h, theta, dt, sig, fextra, fx_scale, tol, max_iter));
+        ADR_CUDA_TRY(cudaGraphLaunch(h->exec, p->stream));
+    }
+    TRY(launch_finish(p, out, iter_out, midpoint));
+    ADR_CUDA_TRY(cudaEventRecord(h->ev1, p->stream));
+    IterState st;
+    ADR_CUDA_TRY(cudaMemcpyAsync(&st, p->state, sizeof st, cudaMemcpyDeviceToHost, p->stream));
+    ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    *converged = st.converged != 0;
+    if (stats) {
+        stats->iters += st.iter;
+        stats->rel_update = st.rel;
+        stats->ms += ms;
+        stats->line_dofs += (double)st.iter * (h->line_unknowns[0] + h->line_unknowns[1]);
+        stats->dt = dt;
+    }
+    return ADR_OK;
+}
+
+adr_status init_state(adr_problem* h, int init, const double* u_init)
+{
+    Problem* p = &h->p;
+    if (init == ADR_INIT_USER) {
+        if (!u_init) {
+            set_error("opts.init == ADR_INIT_USER needs u_init");
+            return ADR_EINVAL;
+        }
+        return launch_mask_copy(p, u_init, p->ubuf[0]);
+    }
+    if (init == ADR_INIT_PAPER_U0) {
+        TRY(launch_line_sweep_ex(p, 0, 1.0, 1.0, p->sigma, nullptr, nullptr, false, nullptr, 0.0, 1));
+        return launch_grid_map_ex(p, 0, p->ubuf[0], p->ubuf[0], 0, nullptr, nullptr, false, false);
+    }
+    if (init == ADR_INIT_ZERO) return launch_mask_copy(p, nullptr, p->ubuf[0]);
+    set_error("unsupported opts.init");
+    return ADR_EINVAL;
+}
+
+adr_status check_opts(const adr_opts* o)
+{
+    if (!o) return ADR_OK;
+    if (o->prec != ADR_FP64 && o->prec != ADR_FP32_REFINE) {
+        set_error("opts.prec must be ADR_FP64 or ADR_FP32_REFINE");
+        return ADR_EINVAL;
+    }
+    if (!(o->theta > 0.0 && o->theta <= 1.0)) {
+        set_error("opts.theta must lie in (0, 1]");
+        return ADR_EINVAL;
+    }
+    if (o->max_iter < 0 || !std::isfinite(o->dt) || std::isnan(o->tol)) {
+        set_error("opts.max_iter must be >= 0 and dt, tol finite");
+        return ADR_EINVAL;
+    }
+    if (o->init < ADR_INIT_ZERO || o->init > ADR_INIT_PAPER_U0) {
+        set_error("unsupported opts.init");
+        return ADR_EINVAL;
+    }
+    return ADR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void adr_default_opts(adr_opts* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->prec = ADR_FP64;
+    o->theta = 0.5;
+    o->dt = 0.0;
+    o->tol = 1e-10;
+    o->max_iter = 100000;
+    o->init = ADR_INIT_ZERO;
+}
+
+const char* adr_last_error(void) { return g_err.c_str(); }
+
+adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, double sigma,
+                      const double* beta1, const double* beta2, const double* f,
+                      const adr_opts* opts, void* stream, adr_problem** out)
+{
+    g_err.clear();
+    if (!out) {
+        set_error("out is NULL");
+        return ADR_EINVAL;
+    }
+    *out = nullptr;
+    if (!grid || !mask || !beta1 || !beta2 || !f) {
+        set_error("NULL argument");
+        return ADR_EINVAL;
+    }
+    if (grid->nx < 3 || grid->ny < 3 || !(grid->x1 > grid->x0) || !(grid->y1 > grid->y0) ||
+        (long long)grid->nx * grid->ny > 0x7fffffffLL) {
+        set_error("grid needs nx, ny >= 3, x1 > x0, y1 > y0 and nx*ny < 2^31");
+        return ADR_EINVAL;
+    }
+    if (!(mu > 0.0) || !(sigma > 0.0) || !std::isfinite(mu) || !std::isfinite(sigma)) {
+        set_error("mu and sigma must be positive constants");
+        return ADR_EINVAL;
+    }
+    TRY(check_opts(opts));
+    adr_problem* h = new (std::nothrow) adr_problem;
+    if (!h) {
+        set_error("out of host memory");
+        return ADR_ENOMEM;
+    }
+    Problem* p = &h->p;
+    p->grid = *grid;
+    if (opts) p->opts = *opts;
+    else adr_default_opts(&p->opts);
+    p->mu = mu;
+    p->sigma = sigma;
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->N = grid->nx * grid->ny;
+    adr_status s = ADR_OK;
+    auto fail = [&](adr_status st) {
+        adr_destroy(h);
+        return st;
+    };
+    size_t N = p->N;
+    if ((s = dev_alloc(p, &p->beta1, N)) || (s = dev_alloc(p, &p->beta2, N)) ||
+        (s = dev_alloc(p, &p->f, N)))
+        return fail(s);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(p->beta1, beta1, N * 8, cudaMemcpyDeviceToDevice, p->stream)) ||
+        (e = cudaMemcpyAsync(p->beta2, beta2, N * 8, cudaMemcpyDeviceToDevice, p->stream)) ||
+        (e = cudaMemcpyAsync(p->f, f, N * 8, cudaMemcpyDeviceToDevice, p->stream)))
+        return fail(cuda_fail(e, "cudaMemcpyAsync"));
+    if ((s = build_geometry(p, mask))) return fail(s);
+    for (int k = 0; k < 3; ++k)
+        if ((s = dev_alloc(p, &p->ubuf[k], N))) return fail(s);
+    p->n_partial_blocks = grid_map_blocks(p);
+    if ((s = dev_alloc(p, &p->partial, 2 * (size_t)p->n_partial_blocks)) ||
+        (s = dev_alloc(p, &p->state, 1)) || (s = dev_alloc(p, &p->fextra, N)))
+        return fail(s);
+    for (int fam = 0; fam < 2; ++fam) {
+        std::vector<int> off(p->fam[fam].n_lines + 1);
+        if ((e = cudaMemcpy(off.data(), p->fam[fam].off, off.size() * sizeof(int),
+                            cudaMemcpyDeviceToHost)))
+            return fail(cuda_fail(e, "cudaMemcpy"));
+        double u = 0;
+        for (int l = 0; l < p->fam[fam].n_lines; ++l) u += std::max(0, off[l + 1] - off[l] - 2);
+        h->line_unknowns[fam] = u;
+    }
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreate(&h->ev0)) || (e = cudaEventCreate(&h->ev1)))
+        return fail(cuda_fail(e, "stream/event create"));
+    if ((e = cudaStreamSynchronize(p->stream))) return fail(cuda_fail(e, "adr_create"));
+    *out = h;
+    return ADR_OK;
+}
+
+void adr_destroy(adr_problem* h)
+{
+    if (!h) return;
+    if (h->p.stream) cudaStreamSynchronize(h->p.stream);
+    else cudaDeviceSynchronize();
+    drop_graph(h);
+    for (void* q : h->p.owned) cudaFree(q);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+adr_status adr_solve_stationary(adr_problem* h, const double* u_init, double* u_out,
+                                double* u_iter_out, adr_stats* stats)
+{
+    g_err.clear();
+    if (!h || !u_out) {
+        set_error("NULL handle or output");
+        return ADR_EINVAL;
+    }
+    Problem* p = &h->p;
+    const adr_opts& o = p->opts;
+    if (stats) memset(stats, 0, sizeof *stats);
+    double dt = o.dt > 0 ? o.dt : default_dt(*p, p->sigma);
+    TRY(init_state(h, o.init, u_init));
+    bool conv = false;
+    TRY(run_iteration(h, o.theta, dt, p->sigma, nullptr, 0.0, o.tol, o.max_iter,
+                      o.theta == 0.5, u_out, u_iter_out, stats, &conv));
+    if (!conv && o.tol > 0.0) {
+        set_error("max_iter reached before tol");
+        return ADR_ENOCONV;
+    }
+    return ADR_OK;
+}
+
+adr_status adr_step_parabolic(adr_problem* h, double dt, int nsteps, int mode, double* u,
+                              adr_stats* stats)
+{
+    g_err.clear();
+    if (!h || !u || !(dt > 0.0) || nsteps < 0 || (mode != 0 && mode != 1)) {
+        set_error("bad arguments to adr_step_parabolic");
+        return ADR_EINVAL;
+    }
+    Problem* p = &h->p;
+    const adr_opts& o = p->opts;
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (nsteps == 0) return launch_mask_copy(p, u, u);
+    bool conv = false;
+    if (mode == 0) {
+        TRY(launch_mask_copy(p, u, p->ubuf[0]));
+        TRY(run_iteration(h, o.theta, dt, p->sigma, nullptr, 0.0, -1.0, nsteps, false, u, nullptr,
+                          stats, &conv));
+        return ADR_OK;
+    }
+    double sig = p->sigma + 1.0 / dt;
+    double pdt = o.dt > 0 ? o.dt : default_dt(*p, sig);
+    adr_status result = ADR_OK;
+    for (int k = 0; k < nsteps; ++k) {
+        TRY(launch_mask_copy(p, u, p->fextra));
+        TRY(launch_mask_copy(p, u, p->ubuf[0]));
+        TRY(run_iteration(h, o.theta, pdt, sig, p->fextra, 1.0 / dt, o.tol, o.max_iter,
+                          o.theta == 0.5, u, nullptr, stats, &conv));
+        if (!conv && o.tol > 0.0) result = ADR_ENOCONV;
+    }
+    if (result != ADR_OK) set_error("a time slice reached max_iter before tol");
+    return result;
+}
+
+adr_status adr_split_step(adr_problem* h, double dt, const double* u, double* u_half,
+                          double* u_next)
+{
+    g_err.clear();
+    if (!h || !u || !u_next) {
+        set_error("NULL argument");
+        return ADR_EINVAL;
+    }
+    Problem* p = &h->p;
+    double* half = u_half ? u_half : p->ubuf[2];
+    double th = p->opts.theta;
+    TRY(launch_line_sweep_ex(p, 0, th, dt, p->sigma, u, u, false, nullptr, 0.0, 0));
+    TRY(launch_grid_map_ex(p, 0, half, half, 0, nullptr, nullptr, false, false));
+    TRY(launch_line_sweep_ex(p, 1, th, dt, p->sigma, half, half, false, nullptr, 0.0, 0));
+    TRY(launch_grid_map_ex(p, 1, u_next, u_next, 0, nullptr, nullptr, false, false));
+    ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return ADR_OK;
+}
+
+adr_status adr_paper_u0(adr_problem* h, double* u0)
+{
+    g_err.clear();
+    if (!h || !u0) {
+        set_error("NULL argument");
+        return ADR_EINVAL;
+    }
+    Problem* p = &h->p;
+    TRY(launch_line_sweep_ex(p, 0, 1.0, 1.0, p->sigma, nullptr, nullptr, false, nullptr, 0.0, 1));
+    TRY(launch_grid_map_ex(p, 0, u0, u0, 0, nullptr, nullptr, false, false));
+    ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return ADR_OK;
+}
+
+int adr_num_lines(const adr_problem* h, int fam)
+{
+    return (h && (fam == 0 || fam == 1)) ? h->p.fam[fam].n_lines : -1;
+}
+
+int adr_num_line_nodes(const adr_problem* h, int fam)
+{
+    return (h && (fam == 0 || fam == 1)) ? h->p.fam[fam].n_nodes : -1;
+}
+
+adr_status adr_get_lines(const adr_problem* h, int fam, int* off, double* xi, double* eta,
+                         double* hh)
+{
+    if (!h || (fam != 0 && fam != 1)) {
+        set_error("bad handle or family");
+        return ADR_EINVAL;
+    }
+    const Family& F = h->p.fam[fam];
+    if (off) ADR_CUDA_TRY(cudaMemcpy(off, F.off, sizeof(int) * (F.n_lines + 1), cudaMemcpyDeviceToHost));
+    if (xi) ADR_CUDA_TRY(cudaMemcpy(xi, F.xi, sizeof(double) * F.n_nodes, cudaMemcpyDeviceToHost));
+    if (eta) ADR_CUDA_TRY(cudaMemcpy(eta, F.eta, sizeof(double) * F.n_nodes, cudaMemcpyDeviceToHost));
+    if (hh) ADR_CUDA_TRY(cudaMemcpy(hh, F.h, sizeof(double) * F.n_lines, cudaMemcpyDeviceToHost));
+    return ADR_OK;
+}
+
+adr_status adr_get_crossings(const adr_problem* h, int fam, int* seg, double* t, double* pos)
+{
+    if (!h || (fam != 0 && fam != 1)) {
+        set_error("bad handle or family");
+        return ADR_EINVAL;
+    }
+    const Family& F = h->p.fam[fam];
+    size_t n = 4 * (size_t)h->p.N;
+    if (seg) ADR_CUDA_TRY(cudaMemcpy(seg, F.cg, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    if (t) ADR_CUDA_TRY(cudaMemcpy(t, F.ct, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (pos) ADR_CUDA_TRY(cudaMemcpy(pos, F.cpos, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return ADR_OK;
+}
+
+adr_status adr_time_kernels(adr_problem* h, int reps, double* ms_out)
+{
+    g_err.clear();
+    if (!h || reps < 1 || !ms_out) {
+        set_error("bad arguments to adr_time_kernels");
+        return ADR_EINVAL;
+    }
+    Problem* p = &h->p;
+    const adr_opts& o = p->opts;
+    double dt = o.dt > 0 ? o.dt : default_dt(*p, p->sigma);
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; ++k) ADR_CUDA_TRY(cudaEventCreate(&ev[k]));
+    adr_status s = ADR_OK;
+    for (int stage = 0; stage < 4 && s == ADR_OK; ++stage) {
+        cudaEventRecord(ev[stage], p->stream);
+        for (int r = 0; r < reps && s == ADR_OK; ++r) {
+            switch (stage) {
+            case 0:
+                s = launch_line_sweep_ex(p, 0, o.theta, dt, p->sigma, p->ubuf[0], p->ubuf[0], false,
+                                         nullptr, 0.0, 0);
+                break;
+            case 1:
+                s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, false, false);
+                break;
+            case 2:
+                s = launch_line_sweep_ex(p, 1, o.theta, dt, p->sigma, p->ubuf[2], p->ubuf[2], false,
+                                         nullptr, 0.0, 0);
+                break;
+            default:
+                s = launch_grid_map_ex(p, 1, p->ubuf[1], p->ubuf[1], 0, p->ubuf[0], p->ubuf[0], false,
+                                       true);
+            }
+        }
+    }
+    cudaEventRecord(ev[4], p->stream);
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (s == ADR_OK && e != cudaSuccess) s = cuda_fail(e, "adr_time_kernels");
+    for (int k = 0; k < 4 && s == ADR_OK; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+        ms_out[k] = ms / reps;
+    }
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    return s;
+}
+
+}  // extern "C"

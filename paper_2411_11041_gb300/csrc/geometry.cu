@@ -1,0 +1,1092 @@
+// Setup kernels: domain, curve families B and G, and the curve -> grid
+// crossing structure (§6).  Run once per problem.  This file is compiled with
+// -fmad=false so that every coordinate follows plain IEEE operations in the
+// written order; the integer decisions that depend on them (node counts,
+// snapped grid coordinates, chosen crossings) are then reproducible.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "adr_internal.cuh"
+
+namespace adr {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(long long n, int t = kThreads)
+{
+    long long b = (n + t - 1) / t;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// status bits raised by setup kernels
+enum : int { kErrInvalid = 1, kErrGeom = 2, kErrCapacity = 4 };
+
+__device__ __forceinline__ double snap(double v)
+{
+    double r = rint(v);
+    return fabs(v - r) <= kSnapTol ? r : v;
+}
+
+__device__ __forceinline__ int cell_on(const GridView& g, int i, int r)
+{
+    if (i < 0 || r < 0 || i >= g.nx - 1 || r >= g.ny - 1) return 0;
+    return g.cell[(size_t)r * (g.nx - 1) + i];
+}
+
+// interior of Omega_h: every cell whose closure holds the point is active
+__device__ int interior_point(const GridView& g, double xi, double eta)
+{
+    if (!isfinite(xi) || !isfinite(eta)) return 0;
+    if (xi < -1.0 || eta < -1.0 || xi > g.nx || eta > g.ny) return 0;
+    double fx = floor(xi), fy = floor(eta);
+    int i0 = (int)fx, i1 = (int)fx, r0 = (int)fy, r1 = (int)fy;
+    if (xi == fx) i0 = (int)fx - 1;
+    if (eta == fy) r0 = (int)fy - 1;
+    for (int r = r0; r <= r1; ++r)
+        for (int i = i0; i <= i1; ++i)
+            if (!cell_on(g, i, r)) return 0;
+    return 1;
+}
+
+// bilinear interpolation (§6.1), cell i = min(floor(xi), nx-2), clamped at 0
+__device__ double bilin(const GridView& g, const double* a, double xi, double eta)
+{
+    int i = (int)floor(xi), r = (int)floor(eta);
+    if (i > g.nx - 2) i = g.nx - 2;
+    if (i < 0) i = 0;
+    if (r > g.ny - 2) r = g.ny - 2;
+    if (r < 0) r = 0;
+    double lx = xi - i, ly = eta - r;
+    const double* r0 = a + (size_t)r * g.nx;
+    const double* r1 = r0 + g.nx;
+    double p11 = r0[i], p12 = r0[i + 1], p21 = r1[i], p22 = r1[i + 1];
+    return (1.0 - ly) * (1.0 - lx) * p11 + (1.0 - ly) * lx * p12 + ly * (1.0 - lx) * p21 +
+           ly * lx * p22;
+}
+
+// unit direction of family fam at physical offset (X, Y): b (B) or p (G), §3
+__device__ int direction(const GridView& g, int fam, double X, double Y, double* dx, double* dy)
+{
+    double xi = X / g.hx, eta = Y / g.hy;
+    double b1 = bilin(g, g.beta1, xi, eta), b2 = bilin(g, g.beta2, xi, eta);
+    double nb = sqrt(b1 * b1 + b2 * b2);
+    if (!(nb > 0.0)) return -1;
+    if (fam == 0) {
+        *dx = b1 / nb;
+        *dy = b2 / nb;
+    } else {
+        *dx = b2 / nb;
+        *dy = -b1 / nb;
+    }
+    return 0;
+}
+
+// classical RK4 step of x' = dir(x) over arc length ds (eqs. CauchyBeta/CauchyGamma)
+__device__ int rk4(const GridView& g, int fam, double X, double Y, double ds, double* Xo,
+                   double* Yo)
+{
+    double k1x, k1y, k2x, k2y, k3x, k3y, k4x, k4y;
+    if (direction(g, fam, X, Y, &k1x, &k1y)) return -1;
+    if (direction(g, fam, X + 0.5 * ds * k1x, Y + 0.5 * ds * k1y, &k2x, &k2y)) return -1;
+    if (direction(g, fam, X + 0.5 * ds * k2x, Y + 0.5 * ds * k2y, &k3x, &k3y)) return -1;
+    if (direction(g, fam, X + ds * k3x, Y + ds * k3y, &k4x, &k4y)) return -1;
+    *Xo = X + ds / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
+    *Yo = Y + ds / 6.0 * (k1y + 2.0 * k2y + 2.0 * k3y + k4y);
+    return 0;
+}
+
+__device__ __forceinline__ int elements_for(const GridView& g, double L)
+{
+    int n = (int)ceil(L / g.hs - kNodeTol);
+    return n < 1 ? 1 : n;
+}
+
+// ------------------------------------------------------------- domain
+
+__global__ void k_cells(const uint8_t* mask, int nx, int ny, uint8_t* cell)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long nc = (long long)(nx - 1) * (ny - 1);
+    if (k >= nc) return;
+    int r = (int)(k / (nx - 1)), i = (int)(k % (nx - 1));
+    size_t a = (size_t)r * nx + i;
+    cell[k] = (mask[a] && mask[a + 1] && mask[a + nx] && mask[a + nx + 1]) ? 1 : 0;
+}
+
+__global__ void k_ntype(GridView g, uint8_t* ntype, int* counts /* [0] interior, [1] in */)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= (long long)g.nx * g.ny) return;
+    int r = (int)(k / g.nx), i = (int)(k % g.nx);
+    int c00 = cell_on(g, i - 1, r - 1), c10 = cell_on(g, i, r - 1);
+    int c01 = cell_on(g, i - 1, r), c11 = cell_on(g, i, r);
+    uint8_t t = kOutside;
+    if (c00 || c10 || c01 || c11) t = (c00 && c10 && c01 && c11) ? kInterior : kDirichlet;
+    ntype[k] = t;
+    if (t == kInterior) atomicAdd(&counts[0], 1);
+    if (t != kOutside) atomicMin(&counts[2], (int)k);  // first node of Omega_h
+}
+
+// field checks over Omega_h: finite data, |beta| > 0, constant field, max |beta|
+__global__ void k_fields(GridView g, int first, int* status, int* nonconst,
+                         unsigned long long* bmax_bits)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= (long long)g.nx * g.ny) return;
+    if (g.ntype[k] == kOutside) return;
+    double b1 = g.beta1[k], b2 = g.beta2[k];
+    double nb = sqrt(b1 * b1 + b2 * b2);
+    if (!(nb > 0.0) || !isfinite(nb) || !isfinite(g.f[k])) atomicOr(status, kErrInvalid);
+    if (b1 != g.beta1[first] || b2 != g.beta2[first]) atomicOr(nonconst, 1);
+    if (isfinite(nb)) atomicMax(bmax_bits, (unsigned long long)__double_as_longlong(nb));
+}
+
+// -------------------------------------------------- straight curve families
+// For a constant field the curves are the lines p.(x - x_ref) = k h_s (B) and
+// b.(x - x_ref) = k h_s (G), x_ref = (x0, y0), cut into the maximal pieces
+// inside Omega_h; s is arc length along the line direction.
+
+struct LineParams {
+    double dx, dy, nxv, nyv;
+    long long kmin, kmax;
+};
+
+__global__ void k_line_params(GridView g, int fam, int first, LineParams* out)
+{
+    double b1 = g.beta1[first], b2 = g.beta2[first];
+    double nb = sqrt(b1 * b1 + b2 * b2);
+    double bx = b1 / nb, by = b2 / nb, px = by, py = -bx;
+    LineParams P;
+    P.dx = fam == 0 ? bx : px;
+    P.dy = fam == 0 ? by : py;
+    P.nxv = fam == 0 ? px : bx;
+    P.nyv = fam == 0 ? py : by;
+    double qc[4] = {0.0, P.nxv * g.W, P.nyv * g.H, P.nxv * g.W + P.nyv * g.H};
+    double qmin = qc[0], qmax = qc[0];
+    for (int c = 1; c < 4; ++c) {
+        if (qc[c] < qmin) qmin = qc[c];
+        if (qc[c] > qmax) qmax = qc[c];
+    }
+    P.kmin = (long long)ceil(qmin / g.hs - 1e-9);
+    P.kmax = (long long)floor(qmax / g.hs + 1e-9);
+    *out = P;
+}
+
+// Walks the pieces of line k between consecutive grid-line crossings and
+// emits the maximal runs of interior pieces.  FILL = false counts, true writes.
+template <bool FILL>
+__device__ void straight_line(const GridView& g, const LineParams& P, long long k, int* n_lines,
+                              int* n_nodes, int line0, int node0, int* off, double* h,
+                              double* xs, double* es)
+{
+    double dx = P.dx, dy = P.dy;
+    double ox = k * g.hs * P.nxv, oy = k * g.hs * P.nyv;
+    double slo = -INFINITY, shi = INFINITY;
+    double lim[2] = {g.W, g.H}, o[2] = {ox, oy}, d[2] = {dx, dy}, hh[2] = {g.hx, g.hy};
+    double top[2] = {(double)(g.nx - 1), (double)(g.ny - 1)};
+    for (int a = 0; a < 2; ++a) {
+        if (d[a] == 0.0) {
+            double c = snap(o[a] / hh[a]);
+            if (c < 0.0 || c > top[a]) return;
+        } else {
+            double s0 = (0.0 - o[a]) / d[a], s1 = (lim[a] - o[a]) / d[a];
+            if (s0 > s1) {
+                double t = s0;
+                s0 = s1;
+                s1 = t;
+            }
+            if (s0 > slo) slo = s0;
+            if (s1 < shi) shi = s1;
+        }
+    }
+    if (!(shi > slo)) return;
+    // breakpoint generators: grid lines g*hh crossed inside (slo, shi), in s order
+    long long gcur[2], gend[2];
+    int gstep[2];
+    for (int a = 0; a < 2; ++a) {
+        gstep[a] = 0;
+        if (d[a] == 0.0) continue;
+        double c0 = (o[a] + slo * d[a]) / hh[a], c1 = (o[a] + shi * d[a]) / hh[a];
+        double lo = c0 < c1 ? c0 : c1, hi = c0 < c1 ? c1 : c0;
+        long long ga = (long long)ceil(lo - 1e-9), gb = (long long)floor(hi + 1e-9);
+        if (ga > gb) continue;
+        if (d[a] > 0) {
+            gcur[a] = ga;
+            gend[a] = gb;
+            gstep[a] = 1;
+        } else {
+            gcur[a] = gb;
+            gend[a] = ga;
+            gstep[a] = -1;
+        }
+    }
+    auto next_of = [&](int a) -> double {
+        while (gstep[a] != 0) {
+            double s = (gcur[a] * hh[a] - o[a]) / d[a];
+            if (s > slo && s < shi) return s;
+            if (gcur[a] == gend[a]) {
+                gstep[a] = 0;
+                break;
+            }
+            gcur[a] += gstep[a];
+        }
+        return INFINITY;
+    };
+    auto advance = [&](int a) {
+        if (gcur[a] == gend[a]) gstep[a] = 0;
+        else gcur[a] += gstep[a];
+    };
+    int lines = 0, nodes = 0;
+    auto emit = [&](double sa, double sb) {
+        double L = sb - sa;
+        int n = elements_for(g, L);
+        if (FILL) {
+            int base = node0 + nodes;
+            for (int j = 0; j <= n; ++j) {
+                double s = (j == n) ? sb : sa + j * (L / n);
+                xs[base + j] = snap((ox + s * dx) / g.hx);
+                es[base + j] = snap((oy + s * dy) / g.hy);
+            }
+            off[line0 + lines] = base;
+            h[line0 + lines] = L / n;
+        }
+        lines += 1;
+        nodes += n + 1;
+    };
+    double prev = slo, run_a = 0.0, run_b = 0.0;
+    int open = 0;
+    for (;;) {
+        double sa = next_of(0), sb = next_of(1);
+        double nxt;
+        int which;
+        if (sa <= sb && sa < shi) {
+            nxt = sa;
+            which = 0;
+        } else if (sb < shi) {
+            nxt = sb;
+            which = 1;
+        } else {
+            nxt = shi;
+            which = 2;
+        }
+        double s0 = prev, s1 = nxt;
+        if (s1 - s0 > 1e-9 * g.hs) {
+            double sm = 0.5 * (s0 + s1);
+            double xi = snap((ox + sm * dx) / g.hx), eta = snap((oy + sm * dy) / g.hy);
+            if (interior_point(g, xi, eta)) {
+                if (!open) {
+                    run_a = s0;
+                    open = 1;
+                }
+                run_b = s1;
+            } else if (open) {
+                emit(run_a, run_b);
+                open = 0;
+            }
+        }
+        if (which == 2) break;
+        advance(which);
+        prev = nxt;
+    }
+    if (open) emit(run_a, run_b);
+    *n_lines = lines;
+    *n_nodes = nodes;
+}
+
+__global__ void k_straight_count(GridView g, const LineParams* P, long long* cl, long long* cn)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long nk = P->kmax - P->kmin + 1;
+    if (t >= nk) return;
+    int nl = 0, nn = 0;
+    straight_line<false>(g, *P, P->kmin + t, &nl, &nn, 0, 0, nullptr, nullptr, nullptr,
+                         nullptr);
+    cl[t] = nl;
+    cn[t] = nn;
+}
+
+__global__ void k_straight_fill(GridView g, const LineParams* P, const long long* cl,
+                                const long long* cn, int* off, double* h, double* xs, double* es)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long nk = P->kmax - P->kmin + 1;
+    if (t >= nk) return;
+    int nl = 0, nn = 0;
+    straight_line<true>(g, *P, P->kmin + t, &nl, &nn, (int)cl[t], (int)cn[t], off, h, xs, es);
+}
+
+// exclusive scan of a small int64 array by one block; out[n] = total
+__global__ void k_scan(const long long* in, long long* out, long long n)
+{
+    __shared__ long long buf[1024];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < n; base += 1024) {
+        long long i = base + threadIdx.x;
+        long long v = i < n ? in[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int s = 1; s < 1024; s <<= 1) {
+            long long add = threadIdx.x >= s ? buf[threadIdx.x - s] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (i < n) out[i] = carry + buf[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += buf[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+// ---------------------------------------------------- traced curve families
+// Seeds on the inflow part of the boundary (eq. cauchyStartSets): the staircase
+// boundary is walked loop by loop counter-clockwise (domain on the left), each
+// loop from its lowest-leftmost bottom edge; edge e carries the transverse
+// measure max(0, -n_e . dir) |e| with dir from the nodal mean of beta on e;
+// seeds sit where the running measure reaches (k + 1/2) h_s.
+
+__device__ int hedge_dir(const GridView& g, int i, int r)
+{
+    int up = cell_on(g, i, r), dn = cell_on(g, i, r - 1);
+    return up && !dn ? 1 : (dn && !up ? -1 : 0);
+}
+__device__ int vedge_dir(const GridView& g, int i, int r)
+{
+    int lf = cell_on(g, i - 1, r), rt = cell_on(g, i, r);
+    return lf && !rt ? 1 : (rt && !lf ? -1 : 0);
+}
+__device__ int out_edge(const GridView& g, int i, int r, int d)
+{
+    switch (d) {
+    case 0: return i <= g.nx - 2 && hedge_dir(g, i, r) == 1;
+    case 1: return r <= g.ny - 2 && vedge_dir(g, i, r) == 1;
+    case 2: return i >= 1 && hedge_dir(g, i - 1, r) == -1;
+    default: return r >= 1 && vedge_dir(g, i, r - 1) == -1;
+    }
+}
+__device__ const int kDXI[4] = {1, 0, -1, 0};
+__device__ const int kDETA[4] = {0, 1, 0, -1};
+
+__global__ void k_count_bedges(GridView g, int* count)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= (long long)g.nx * g.ny) return;
+    int r = (int)(k / g.nx), i = (int)(k % g.nx);
+    int c = 0;
+    if (i < g.nx - 1 && hedge_dir(g, i, r)) c++;
+    if (r < g.ny - 1 && vedge_dir(g, i, r)) c++;
+    if (c) atomicAdd(count, c);
+}
+
+// single thread: walk the loops and place the seeds (X0, Y0 physical offsets)
+__global__ void k_seeds(GridView g, int fam, uint8_t* vis_h, uint8_t* vis_v, long long total,
+                        double* sx, double* sy, int cap, int* nseeds, int* status)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int nx = g.nx, ny = g.ny;
+    double cum = 0.0;
+    long long k = 0;
+    int ns = 0;
+    for (int r0 = 0; r0 < ny; ++r0)
+        for (int i0 = 0; i0 < nx - 1; ++i0) {
+            if (hedge_dir(g, i0, r0) != 1 || vis_h[(size_t)r0 * (nx - 1) + i0]) continue;
+            int i = i0, r = r0, d = 0;
+            long long steps = 0;
+            for (;;) {
+                uint8_t* mark;
+                if (d == 0) mark = &vis_h[(size_t)r * (nx - 1) + i];
+                else if (d == 2) mark = &vis_h[(size_t)r * (nx - 1) + i - 1];
+                else if (d == 1) mark = &vis_v[(size_t)r * nx + i];
+                else mark = &vis_v[(size_t)(r - 1) * nx + i];
+                if (*mark) break;
+                *mark = 1;
+                // the edge from (i, r) in direction d
+                int ib = i + kDXI[d], rb = r + kDETA[d];
+                size_t A = (size_t)r * nx + i, B = (size_t)rb * nx + ib;
+                double m1 = 0.5 * (g.beta1[A] + g.beta1[B]), m2 = 0.5 * (g.beta2[A] + g.beta2[B]);
+                double nm = sqrt(m1 * m1 + m2 * m2);
+                if (!(nm > 0.0)) {
+                    atomicOr(status, kErrGeom);
+                    *nseeds = 0;
+                    return;
+                }
+                double vx = fam == 0 ? m1 / nm : m2 / nm, vy = fam == 0 ? m2 / nm : -m1 / nm;
+                double nxo = (double)kDETA[d], nyo = (double)(-kDXI[d]);
+                double len = (d & 1) ? g.hy : g.hx;
+                double w = -(nxo * vx + nyo * vy) * len;
+                if (w > 0.0) {
+                    while ((k + 0.5) * g.hs < cum + w) {
+                        double phi = ((k + 0.5) * g.hs - cum) / w;
+                        if (ns < cap) {
+                            sx[ns] = (i + phi * kDXI[d]) * g.hx;
+                            sy[ns] = (r + phi * kDETA[d]) * g.hy;
+                        }
+                        ns++;
+                        k++;
+                    }
+                    cum += w;
+                }
+                i = ib;
+                r = rb;
+                int nd = -1;
+                int pref[3] = {(d + 1) & 3, d, (d + 3) & 3};
+                for (int q = 0; q < 3; ++q)
+                    if (out_edge(g, i, r, pref[q])) {
+                        nd = pref[q];
+                        break;
+                    }
+                if (nd < 0 || ++steps > total + 4) break;
+                d = nd;
+            }
+        }
+    if (ns > cap) {
+        atomicOr(status, kErrCapacity);
+        ns = cap;
+    }
+    *nseeds = ns;
+}
+
+// trace one curve: number of full RK4 steps M, length L and exit point
+__device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mout, double* L,
+                         double* Xe, double* Ye)
+{
+    double ds = g.hs / kTraceStepsPerH;
+    double cap_len = 10.0 * 2.0 * (g.W + g.H);
+    long long npts = 0;
+    for (;;) {
+        npts++;
+        double Xn, Yn;
+        if (rk4(g, fam, X, Y, ds, &Xn, &Yn)) return -1;
+        if (interior_point(g, snap(Xn / g.hx), snap(Yn / g.hy))) {
+            X = Xn;
+            Y = Yn;
+            if (npts * ds > cap_len) return -1;
+            continue;
+        }
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < kBisectIters; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (rk4(g, fam, X, Y, mid * ds, &Xn, &Yn)) return -1;
+            if (interior_point(g, snap(Xn / g.hx), snap(Yn / g.hy))) lo = mid;
+            else hi = mid;
+        }
+        double XE = X, YE = Y;
+        if (lo > 0.0 && rk4(g, fam, X, Y, lo * ds, &XE, &YE)) return -1;
+        *Mout = (int)(npts - 1);
+        *L = (npts - 1) * ds + lo * ds;
+        *Xe = XE;
+        *Ye = YE;
+        return 0;
+    }
+}
+
+__global__ void k_trace_count(GridView g, int fam, const double* sx, const double* sy,
+                              const int* nseeds, int* M, double* L, double* XE, double* YE,
+                              long long* cn, int* status)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= *nseeds) return;
+    int m = 0;
+    double len = 0, xe = 0, ye = 0;
+    if (trace_len(g, fam, sx[s], sy[s], &m, &len, &xe, &ye)) {
+        atomicOr(status, kErrGeom);
+        m = 0;
+        len = 0.0;
+        xe = sx[s];
+        ye = sy[s];
+    }
+    M[s] = m;
+    L[s] = len;
+    XE[s] = xe;
+    YE[s] = ye;
+    cn[s] = elements_for(g, len) + 1;
+}
+
+// re-trace the M RK4 steps and place n+1 nodes uniformly in arc length
+__global__ void k_trace_fill(GridView g, int fam, const double* sx, const double* sy,
+                             const int* nseeds, const int* M, const double* L, const double* XE,
+                             const double* YE, const long long* noff, int* off, double* h,
+                             double* xs, double* es)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= *nseeds) return;
+    double ds = g.hs / kTraceStepsPerH;
+    double len = L[s];
+    int m = M[s];
+    int n = elements_for(g, len);
+    int base = (int)noff[s];
+    off[s] = base;
+    h[s] = len / n;
+    double Xq = sx[s], Yq = sy[s];  // P_q
+    double Xn = Xq, Yn = Yq;        // P_{q+1}
+    int q = -1;                     // index of the segment held in (P_q, P_{q+1})
+    for (int j = 0; j <= n; ++j) {
+        double X, Y;
+        if (j == n) {
+            X = XE[s];
+            Y = YE[s];
+        } else {
+            double sj = j * (len / n);
+            int qj = (int)floor(sj / ds);
+            if (qj > m) qj = m;
+            while (q < qj) {
+                q++;
+                Xq = Xn;
+                Yq = Yn;
+                if (q < m) {
+                    rk4(g, fam, Xq, Yq, ds, &Xn, &Yn);
+                } else {
+                    Xn = XE[s];
+                    Yn = YE[s];
+                }
+            }
+            if (q == -1) {
+                q = 0;
+                if (m > 0) rk4(g, fam, Xq, Yq, ds, &Xn, &Yn);
+                else {
+                    Xn = XE[s];
+                    Yn = YE[s];
+                }
+            }
+            double s0 = q * ds, s1 = (q < m) ? (q + 1) * ds : len;
+            double fr = (s1 > s0) ? (sj - s0) / (s1 - s0) : 0.0;
+            X = Xq + fr * (Xn - Xq);
+            Y = Yq + fr * (Yn - Yq);
+        }
+        xs[base + j] = snap(X / g.hx);
+        es[base + j] = snap(Y / g.hy);
+    }
+}
+
+// --------------------------------------------------------- node data
+
+__global__ void k_node_data(GridView g, int n_nodes, const double* xs, const double* es,
+                            double* bnorm, double* fval)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_nodes) return;
+    double b1 = bilin(g, g.beta1, xs[k], es[k]);
+    double b2 = bilin(g, g.beta2, xs[k], es[k]);
+    bnorm[k] = sqrt(b1 * b1 + b2 * b2);
+    fval[k] = bilin(g, g.f, xs[k], es[k]);
+}
+
+__global__ void k_line_of_node(int n_lines, const int* off, int* lon, int* maxlen)
+{
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_lines) return;
+    int a = off[l], b = off[l + 1];
+    for (int k = a; k < b; ++k) lon[k] = l;
+    atomicMax(maxlen, b - a);
+}
+
+// ------------------------------------------------- curve -> grid crossings
+// §6: every grid line is cut into segments by the grid nodes; each segment
+// keeps its crossing with the smallest and with the largest coordinate (ties:
+// smaller curve-segment index, then smaller t).  Built with atomics in three
+// rounds (position, segment index, t); the result does not depend on order.
+
+struct Slots {
+    unsigned long long* minpos;  // bits of a non-negative double
+    unsigned long long* maxpos;
+    int* ming;
+    int* maxg;
+    unsigned long long* mint;
+    unsigned long long* maxt;
+};
+
+__device__ __forceinline__ unsigned long long dbits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v + 0.0);
+}
+
+template <int ROUND>
+__device__ void record(const Slots& S, size_t base, int nseg, double pos, int g, double t)
+{
+    double fp = floor(pos);
+    int e0 = (int)fp, e1 = (int)fp;
+    if (pos == fp) e0 = (int)fp - 1;
+    unsigned long long pb = dbits(pos), tb = dbits(t);
+    for (int e = e0; e <= e1; ++e) {
+        if (e < 0 || e >= nseg) continue;
+        size_t s = base + e;
+        if (ROUND == 0) {
+            atomicMin(&S.minpos[s], pb);
+            atomicMax(&S.maxpos[s], pb);
+        } else if (ROUND == 1) {
+            if (S.minpos[s] == pb) atomicMin(&S.ming[s], g);
+            if (S.maxpos[s] == pb) atomicMin(&S.maxg[s], g);
+        } else {
+            if (S.minpos[s] == pb && S.ming[s] == g) atomicMin(&S.mint[s], tb);
+            if (S.maxpos[s] == pb && S.maxg[s] == g) atomicMin(&S.maxt[s], tb);
+        }
+    }
+}
+
+template <int ROUND>
+__global__ void k_cross(GridView g, int n_nodes, const int* lon, const double* xs,
+                        const double* es, Slots rows, Slots cols)
+{
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi + 1 >= n_nodes || lon[gi] != lon[gi + 1]) return;
+    int nx = g.nx, ny = g.ny;
+    double xa = xs[gi], xb = xs[gi + 1], ea = es[gi], eb = es[gi + 1];
+    if (ea == eb) {
+        if (ea == floor(ea) && ea >= 0 && ea <= ny - 1) {
+            size_t base = (size_t)ea * (nx - 1);
+            record<ROUND>(rows, base, nx - 1, xa, gi, 0.0);
+            record<ROUND>(rows, base, nx - 1, xb, gi, 1.0);
+        }
+    } else {
+        double lo = ea < eb ? ea : eb, hi = ea < eb ? eb : ea;
+        for (long long r = (long long)ceil(lo); r <= (long long)floor(hi); ++r) {
+            if (r < 0 || r > ny - 1) continue;
+            double t, pos;
+            if (r == ea) {
+                t = 0.0;
+                pos = xa;
+            } else if (r == eb) {
+                t = 1.0;
+                pos = xb;
+            } else {
+                t = (r - ea) / (eb - ea);
+                pos = snap(xa + t * (xb - xa));
+            }
+            record<ROUND>(rows, (size_t)r * (nx - 1), nx - 1, pos, gi, t);
+        }
+    }
+    if (xa == xb) {
+        if (xa == floor(xa) && xa >= 0 && xa <= nx - 1) {
+            size_t base = (size_t)xa * (ny - 1);
+            record<ROUND>(cols, base, ny - 1, ea, gi, 0.0);
+            record<ROUND>(cols, base, ny - 1, eb, gi, 1.0);
+        }
+    } else {
+        double lo = xa < xb ? xa : xb, hi = xa < xb ? xb : xa;
+        for (long long i = (long long)ceil(lo); i <= (long long)floor(hi); ++i) {
+            if (i < 0 || i > nx - 1) continue;
+            double t, pos;
+            if (i == xa) {
+                t = 0.0;
+                pos = ea;
+            } else if (i == xb) {
+                t = 1.0;
+                pos = eb;
+            } else {
+                t = (i - xa) / (xb - xa);
+                pos = snap(ea + t * (eb - ea));
+            }
+            record<ROUND>(cols, (size_t)i * (ny - 1), ny - 1, pos, gi, t);
+        }
+    }
+}
+
+__global__ void k_slots_init(Slots s, size_t n)
+{
+    size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    s.minpos[k] = ~0ull;
+    s.maxpos[k] = 0ull;
+    s.ming[k] = 0x7fffffff;
+    s.maxg[k] = 0x7fffffff;
+    s.mint[k] = ~0ull;
+    s.maxt[k] = ~0ull;
+}
+
+// nearest crossing on each side of every interior node (a non-interior grid
+// node met first stands for the boundary, value 0)
+__global__ void k_node_desc(GridView g, Slots rows, Slots cols, int* cg, double* ct,
+                            double* cw, double* cpos)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int nx = g.nx, ny = g.ny;
+    if (k >= (long long)nx * ny) return;
+    int r = (int)(k / nx), i = (int)(k % nx);
+    if (g.ntype[k] != kInterior) {
+        for (int q = 0; q < 4; ++q) {
+            cg[4 * k + q] = -2;
+            ct[4 * k + q] = 0.0;
+            cpos[4 * k + q] = 0.0;
+        }
+        cw[2 * k] = cw[2 * k + 1] = 0.0;
+        return;
+    }
+    int G[4];
+    double T[4], Pp[4];
+    size_t rb = (size_t)r * (nx - 1), cb = (size_t)i * (ny - 1);
+    for (int e = i - 1;; --e) {
+        if (rows.minpos[rb + e] != ~0ull) {
+            G[0] = rows.maxg[rb + e];
+            T[0] = __longlong_as_double((long long)rows.maxt[rb + e]);
+            Pp[0] = __longlong_as_double((long long)rows.maxpos[rb + e]);
+            break;
+        }
+        if (g.ntype[(size_t)r * nx + e] != kInterior) {
+            G[0] = -1;
+            T[0] = 0.0;
+            Pp[0] = e;
+            break;
+        }
+    }
+    for (int e = i;; ++e) {
+        if (rows.minpos[rb + e] != ~0ull) {
+            G[1] = rows.ming[rb + e];
+            T[1] = __longlong_as_double((long long)rows.mint[rb + e]);
+            Pp[1] = __longlong_as_double((long long)rows.minpos[rb + e]);
+            break;
+        }
+        if (g.ntype[(size_t)r * nx + e + 1] != kInterior) {
+            G[1] = -1;
+            T[1] = 0.0;
+            Pp[1] = e + 1;
+            break;
+        }
+    }
+    for (int e = r - 1;; --e) {
+        if (cols.minpos[cb + e] != ~0ull) {
+            G[2] = cols.maxg[cb + e];
+            T[2] = __longlong_as_double((long long)cols.maxt[cb + e]);
+            Pp[2] = __longlong_as_double((long long)cols.maxpos[cb + e]);
+            break;
+        }
+        if (g.ntype[(size_t)e * nx + i] != kInterior) {
+            G[2] = -1;
+            T[2] = 0.0;
+            Pp[2] = e;
+            break;
+        }
+    }
+    for (int e = r;; ++e) {
+        if (cols.minpos[cb + e] != ~0ull) {
+            G[3] = cols.ming[cb + e];
+            T[3] = __longlong_as_double((long long)cols.mint[cb + e]);
+            Pp[3] = __longlong_as_double((long long)cols.minpos[cb + e]);
+            break;
+        }
+        if (g.ntype[(size_t)(e + 1) * nx + i] != kInterior) {
+            G[3] = -1;
+            T[3] = 0.0;
+            Pp[3] = e + 1;
+            break;
+        }
+    }
+    for (int q = 0; q < 4; ++q) {
+        cg[4 * k + q] = G[q];
+        ct[4 * k + q] = T[q];
+        cpos[4 * k + q] = Pp[q];
+    }
+    cw[2 * k] = (Pp[1] == Pp[0]) ? 0.0 : (i - Pp[0]) / (Pp[1] - Pp[0]);
+    cw[2 * k + 1] = (Pp[3] == Pp[2]) ? 0.0 : (r - Pp[2]) / (Pp[3] - Pp[2]);
+}
+
+// longest-first order of the curves (work balance of the sweep kernels):
+// counting sort by length, ties by curve index
+__global__ void k_len_hist(int n_lines, const int* off, int* hist)
+{
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_lines) return;
+    atomicAdd(&hist[off[l + 1] - off[l]], 1);
+}
+__global__ void k_len_order(int n_lines, const int* off, const long long* start, int maxlen,
+                            int* order)
+{
+    // one thread per length bucket keeps index order inside the bucket
+    int len = blockIdx.x * blockDim.x + threadIdx.x;
+    if (len > maxlen) return;
+    long long pos = start[maxlen - len];
+    for (int l = 0; l < n_lines; ++l)
+        if (off[l + 1] - off[l] == len) order[pos++] = l;
+}
+
+__global__ void k_reverse_hist(const int* hist, long long* rev, int maxlen)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > maxlen) return;
+    rev[k] = hist[maxlen - k];
+}
+
+template <typename T>
+adr_status alloc_tmp(std::vector<void*>& tmp, T** p, size_t n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        return ADR_ENOMEM;
+    }
+    tmp.push_back(q);
+    *p = static_cast<T*>(q);
+    return ADR_OK;
+}
+
+struct TmpGuard {
+    std::vector<void*> v;
+    ~TmpGuard()
+    {
+        for (void* q : v) cudaFree(q);
+    }
+};
+
+#define TRY(x)                         \
+    do {                               \
+        adr_status _s = (x);           \
+        if (_s != ADR_OK) return _s;   \
+    } while (0)
+
+adr_status finish_family(Problem* p, int fam, TmpGuard& tg)
+{
+    Family& F = p->fam[fam];
+    cudaStream_t st = p->stream;
+    const GridView& g = p->gv;
+    int N = p->N;
+    TRY(dev_alloc(p, &F.bnorm, F.n_nodes));
+    TRY(dev_alloc(p, &F.fval, F.n_nodes));
+    TRY(dev_alloc(p, &F.v, F.n_nodes + 1));
+    TRY(dev_alloc(p, &F.scr, 3 * (size_t)F.n_nodes + 3));
+    TRY(dev_alloc(p, &F.cg, 4 * (size_t)N));
+    TRY(dev_alloc(p, &F.ct, 4 * (size_t)N));
+    TRY(dev_alloc(p, &F.cw, 2 * (size_t)N));
+    TRY(dev_alloc(p, &F.cpos, 4 * (size_t)N));
+    TRY(dev_alloc(p, &F.order, F.n_lines + 1));
+    k_node_data<<<blocks_for(F.n_nodes), kThreads, 0, st>>>(g, F.n_nodes, F.xi, F.eta, F.bnorm,
+                                                          F.fval);
+    int* lon;
+    int* maxlen;
+    TRY(alloc_tmp(tg.v, &lon, F.n_nodes + 1));
+    TRY(alloc_tmp(tg.v, &maxlen, 1));
+    ADR_CUDA_TRY(cudaMemsetAsync(maxlen, 0, sizeof(int), st));
+    k_line_of_node<<<blocks_for(F.n_lines), kThreads, 0, st>>>(F.n_lines, F.off, lon, maxlen);
+    ADR_CUDA_TRY(cudaMemcpyAsync(&F.max_nodes, maxlen, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    // curves sorted longest first
+    int ml = F.max_nodes;
+    int* hist;
+    long long *rev, *start;
+    TRY(alloc_tmp(tg.v, &hist, ml + 1));
+    TRY(alloc_tmp(tg.v, &rev, ml + 2));
+    TRY(alloc_tmp(tg.v, &start, ml + 2));
+    ADR_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (ml + 1), st));
+    k_len_hist<<<blocks_for(F.n_lines), kThreads, 0, st>>>(F.n_lines, F.off, hist);
+    k_reverse_hist<<<blocks_for(ml + 1), kThreads, 0, st>>>(hist, rev, ml);
+    k_scan<<<1, 1024, 0, st>>>(rev, start, ml + 1);
+    k_len_order<<<blocks_for(ml + 1, 64), 64, 0, st>>>(F.n_lines, F.off, start, ml, F.order);
+    // crossing slots
+    size_t nr = (size_t)p->grid.ny * (p->grid.nx - 1), nc = (size_t)p->grid.nx * (p->grid.ny - 1);
+    Slots R, C;
+    TRY(alloc_tmp(tg.v, &R.minpos, nr));
+    TRY(alloc_tmp(tg.v, &R.maxpos, nr));
+    TRY(alloc_tmp(tg.v, &R.ming, nr));
+    TRY(alloc_tmp(tg.v, &R.maxg, nr));
+    TRY(alloc_tmp(tg.v, &R.mint, nr));
+    TRY(alloc_tmp(tg.v, &R.maxt, nr));
+    TRY(alloc_tmp(tg.v, &C.minpos, nc));
+    TRY(alloc_tmp(tg.v, &C.maxpos, nc));
+    TRY(alloc_tmp(tg.v, &C.ming, nc));
+    TRY(alloc_tmp(tg.v, &C.maxg, nc));
+    TRY(alloc_tmp(tg.v, &C.mint, nc));
+    TRY(alloc_tmp(tg.v, &C.maxt, nc));
+    k_slots_init<<<blocks_for((long long)nr), kThreads, 0, st>>>(R, nr);
+    k_slots_init<<<blocks_for((long long)nc), kThreads, 0, st>>>(C, nc);
+    int nb = blocks_for(F.n_nodes);
+    k_cross<0><<<nb, kThreads, 0, st>>>(g, F.n_nodes, lon, F.xi, F.eta, R, C);
+    k_cross<1><<<nb, kThreads, 0, st>>>(g, F.n_nodes, lon, F.xi, F.eta, R, C);
+    k_cross<2><<<nb, kThreads, 0, st>>>(g, F.n_nodes, lon, F.xi, F.eta, R, C);
+    k_node_desc<<<blocks_for(N), kThreads, 0, st>>>(g, R, C, F.cg, F.ct, F.cw, F.cpos);
+    ADR_CUDA_TRY(cudaGetLastError());
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    return ADR_OK;
+}
+
+adr_status build_straight(Problem* p, int fam, int first, TmpGuard& tg)
+{
+    Family& F = p->fam[fam];
+    cudaStream_t st = p->stream;
+    LineParams* P;
+    TRY(alloc_tmp(tg.v, &P, 1));
+    k_line_params<<<1, 1, 0, st>>>(p->gv, fam, first, P);
+    LineParams hp;
+    ADR_CUDA_TRY(cudaMemcpyAsync(&hp, P, sizeof hp, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    long long nk = hp.kmax - hp.kmin + 1;
+    if (nk < 1) {
+        set_error("no curve crosses the domain");
+        return ADR_EGEOM;
+    }
+    long long *cl, *cn, *ol, *on;
+    TRY(alloc_tmp(tg.v, &cl, nk));
+    TRY(alloc_tmp(tg.v, &cn, nk));
+    TRY(alloc_tmp(tg.v, &ol, nk + 1));
+    TRY(alloc_tmp(tg.v, &on, nk + 1));
+    k_straight_count<<<blocks_for(nk, 64), 64, 0, st>>>(p->gv, P, cl, cn);
+    k_scan<<<1, 1024, 0, st>>>(cl, ol, nk);
+    k_scan<<<1, 1024, 0, st>>>(cn, on, nk);
+    long long tl = 0, tn = 0;
+    ADR_CUDA_TRY(cudaMemcpyAsync(&tl, ol + nk, sizeof tl, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaMemcpyAsync(&tn, on + nk, sizeof tn, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (tl < 1 || tn > 0x7fffffffLL) {
+        set_error(tl < 1 ? "no curve inside the domain" : "too many curve nodes");
+        return tl < 1 ? ADR_EGEOM : ADR_EINVAL;
+    }
+    F.n_lines = (int)tl;
+    F.n_nodes = (int)tn;
+    TRY(dev_alloc(p, &F.off, F.n_lines + 1));
+    TRY(dev_alloc(p, &F.h, F.n_lines));
+    TRY(dev_alloc(p, &F.xi, F.n_nodes));
+    TRY(dev_alloc(p, &F.eta, F.n_nodes));
+    k_straight_fill<<<blocks_for(nk, 64), 64, 0, st>>>(p->gv, P, ol, on, F.off, F.h, F.xi, F.eta);
+    int nn = F.n_nodes;
+    ADR_CUDA_TRY(cudaMemcpyAsync(F.off + F.n_lines, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
+    ADR_CUDA_TRY(cudaGetLastError());
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    return ADR_OK;
+}
+
+adr_status build_curved(Problem* p, int fam, int* status_d, TmpGuard& tg)
+{
+    Family& F = p->fam[fam];
+    cudaStream_t st = p->stream;
+    const GridView& g = p->gv;
+    int nx = p->grid.nx, ny = p->grid.ny;
+    int* cnt;
+    TRY(alloc_tmp(tg.v, &cnt, 2));
+    ADR_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
+    k_count_bedges<<<blocks_for((long long)nx * ny), kThreads, 0, st>>>(g, cnt);
+    int nbe = 0;
+    ADR_CUDA_TRY(cudaMemcpyAsync(&nbe, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    double hmax = p->gv.hx > p->gv.hy ? p->gv.hx : p->gv.hy;
+    int cap = (int)(nbe * ceil(hmax / p->gv.hs)) + 4;
+    uint8_t *vh, *vv;
+    TRY(alloc_tmp(tg.v, &vh, (size_t)ny * (nx - 1)));
+    TRY(alloc_tmp(tg.v, &vv, (size_t)nx * (ny - 1)));
+    ADR_CUDA_TRY(cudaMemsetAsync(vh, 0, (size_t)ny * (nx - 1), st));
+    ADR_CUDA_TRY(cudaMemsetAsync(vv, 0, (size_t)nx * (ny - 1), st));
+    double *sx, *sy;
+    TRY(alloc_tmp(tg.v, &sx, cap));
+    TRY(alloc_tmp(tg.v, &sy, cap));
+    k_seeds<<<1, 1, 0, st>>>(g, fam, vh, vv, nbe, sx, sy, cap, cnt + 1, status_d);
+    int ns = 0;
+    ADR_CUDA_TRY(cudaMemcpyAsync(&ns, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (ns < 1) {
+        set_error("no inflow boundary for a curve family");
+        return ADR_EGEOM;
+    }
+    int* M;
+    double *L, *XE, *YE;
+    long long *cn, *on;
+    TRY(alloc_tmp(tg.v, &M, ns));
+    TRY(alloc_tmp(tg.v, &L, ns));
+    TRY(alloc_tmp(tg.v, &XE, ns));
+    TRY(alloc_tmp(tg.v, &YE, ns));
+    TRY(alloc_tmp(tg.v, &cn, ns));
+    TRY(alloc_tmp(tg.v, &on, ns + 1));
+    k_trace_count<<<blocks_for(ns, 64), 64, 0, st>>>(g, fam, sx, sy, cnt + 1, M, L, XE, YE, cn,
+                                                     status_d);
+    k_scan<<<1, 1024, 0, st>>>(cn, on, ns);
+    long long tn = 0;
+    ADR_CUDA_TRY(cudaMemcpyAsync(&tn, on + ns, sizeof tn, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (tn > 0x7fffffffLL) {
+        set_error("too many curve nodes");
+        return ADR_EINVAL;
+    }
+    F.n_lines = ns;
+    F.n_nodes = (int)tn;
+    TRY(dev_alloc(p, &F.off, F.n_lines + 1));
+    TRY(dev_alloc(p, &F.h, F.n_lines));
+    TRY(dev_alloc(p, &F.xi, F.n_nodes));
+    TRY(dev_alloc(p, &F.eta, F.n_nodes));
+    k_trace_fill<<<blocks_for(ns, 64), 64, 0, st>>>(g, fam, sx, sy, cnt + 1, M, L, XE, YE, on,
+                                                    F.off, F.h, F.xi, F.eta);
+    int nn = F.n_nodes;
+    ADR_CUDA_TRY(cudaMemcpyAsync(F.off + F.n_lines, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
+    ADR_CUDA_TRY(cudaGetLastError());
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    return ADR_OK;
+}
+
+}  // namespace
+
+adr_status build_geometry(Problem* p, const uint8_t* mask)
+{
+    cudaStream_t st = p->stream;
+    int nx = p->grid.nx, ny = p->grid.ny;
+    size_t N = (size_t)nx * ny, NC = (size_t)(nx - 1) * (ny - 1);
+    TmpGuard tg;
+    TRY(dev_alloc(p, &p->cell, NC));
+    TRY(dev_alloc(p, &p->ntype, N));
+    k_cells<<<blocks_for((long long)NC), kThreads, 0, st>>>(mask, nx, ny, p->cell);
+    GridView& g = p->gv;
+    g.nx = nx;
+    g.ny = ny;
+    g.W = p->grid.x1 - p->grid.x0;
+    g.H = p->grid.y1 - p->grid.y0;
+    g.hx = g.W / (nx - 1);
+    g.hy = g.H / (ny - 1);
+    g.hs = g.hx < g.hy ? g.hx : g.hy;
+    g.cell = p->cell;
+    g.ntype = p->ntype;
+    g.beta1 = p->beta1;
+    g.beta2 = p->beta2;
+    g.f = p->f;
+    int* info;  // [0] interior count, [1] status, [2] first node, [3] nonconst
+    unsigned long long* bmax;
+    TRY(alloc_tmp(tg.v, &info, 4));
+    TRY(alloc_tmp(tg.v, &bmax, 1));
+    int init[4] = {0, 0, 0x7fffffff, 0};
+    ADR_CUDA_TRY(cudaMemcpyAsync(info, init, sizeof init, cudaMemcpyHostToDevice, st));
+    ADR_CUDA_TRY(cudaMemsetAsync(bmax, 0, sizeof(unsigned long long), st));
+    k_ntype<<<blocks_for((long long)N), kThreads, 0, st>>>(g, p->ntype, info);
+    int hinfo[4];
+    ADR_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hinfo[2] == 0x7fffffff) {
+        set_error("empty domain: no grid cell has four corners in the mask");
+        return ADR_EINVAL;
+    }
+    int first = hinfo[2];
+    p->n_interior = hinfo[0];
+    k_fields<<<blocks_for((long long)N), kThreads, 0, st>>>(g, first, info + 1, info + 3, bmax);
+    unsigned long long hb = 0;
+    ADR_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaMemcpyAsync(&hb, bmax, sizeof hb, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hinfo[1] & kErrInvalid) {
+        set_error("beta is zero or data is not finite at a node of the domain");
+        return ADR_EINVAL;
+    }
+    p->const_beta = hinfo[3] == 0;
+    double bm;
+    long long bits = (long long)hb;
+    memcpy(&bm, &bits, sizeof bm);
+    p->bmax = bm;
+    for (int fam = 0; fam < 2; ++fam) {
+        adr_status s = p->const_beta ? build_straight(p, fam, first, tg)
+                                     : build_curved(p, fam, info + 1, tg);
+        if (s != ADR_OK) return s;
+        ADR_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, st));
+        ADR_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hinfo[1] & kErrGeom) {
+            set_error("curve tracing failed (closed integral curve or |beta| = 0 on a curve)");
+            return ADR_EGEOM;
+        }
+        if (hinfo[1] & kErrCapacity) {
+            set_error("internal: seed capacity exceeded");
+            return ADR_EGEOM;
+        }
+        s = finish_family(p, fam, tg);
+        if (s != ADR_OK) return s;
+    }
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+}  // namespace adr

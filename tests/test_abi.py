@@ -1,0 +1,64 @@
+"""The C-ABI library loads without a GPU and exports every declared call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(adr_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libadr():
+    from paper_2411_11041_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_library_exports_every_declared_call(libadr):
+    names = declared_functions()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(libadr, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    import paper_2411_11041_gb300 as P
+    assert sorted(P.EXPORTED) == [n for n in declared_functions() if n in P.EXPORTED]
+    for n in P.EXPORTED:
+        assert n in declared_functions()
+
+
+def test_default_opts_without_gpu(libadr):
+    import paper_2411_11041_gb300 as P
+    o = P.default_opts()
+    assert o.theta == 0.5 and o.tol == 1e-10 and o.prec == P.ADR_FP64
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu(libadr):
+    import paper_2411_11041_gb300 as P
+    g = P.adr_grid(2, 5, 0.0, 0.0, 1.0, 1.0)
+    o = P.default_opts()
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    st = P.lib().adr_create(ctypes.byref(g), dummy, 1.0, 1.0, dummy, dummy, dummy, ctypes.byref(o),
+                            None, ctypes.byref(h))
+    assert st == P.ADR_EINVAL and b"nx" in P.lib().adr_last_error()
+    g = P.adr_grid(8, 8, 0.0, 0.0, 1.0, 1.0)
+    st = P.lib().adr_create(ctypes.byref(g), dummy, -1.0, 1.0, dummy, dummy, dummy, ctypes.byref(o),
+                            None, ctypes.byref(h))
+    assert st == P.ADR_EINVAL
+    o.theta = 0.0
+    st = P.lib().adr_create(ctypes.byref(g), dummy, 1.0, 1.0, dummy, dummy, dummy, ctypes.byref(o),
+                            None, ctypes.byref(h))
+    assert st == P.ADR_EINVAL and b"theta" in P.lib().adr_last_error()

@@ -1,0 +1,175 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, on seeded inputs.
+
+Tolerance (FP64 mode): max |u_gpu - u_oracle| / max |u_oracle| <= 1e-12 over
+the grid.  Geometry (curve counts, node counts, chosen crossings) must agree
+exactly; coordinates to 1e-12 in index units.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_11041_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_11041_gb300 import build
+    build.build()
+    return torch
+
+
+def relerr(a, b):
+    a = a.cpu().numpy() if hasattr(a, "cpu") else a
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def _const(n, beta, mask="square", mu=0.1, sigma=1.0, nx=None, seed=0):
+    nx = nx or n
+    rng = np.random.default_rng(seed)
+    X, Y = W.node_coords(nx, n)
+    f = np.exp(-((X - 0.4) ** 2 + (Y - 0.55) ** 2) / 0.05) + 0.3 * rng.random((n, nx))
+    m = W.make_mask(mask, nx, n) if nx == n else np.ones((n, nx), np.uint8)
+    return W.Problem(nx, n, mu, sigma, np.full((n, nx), beta[0]), np.full((n, nx), beta[1]), f, m)
+
+
+def _data2d(n):
+    X, Y = W.node_coords(n, n)
+    return W.Problem(n, n, 1.0, 1.0, -5.0 * (Y + 1.0), 5.0 * (X + 1.0), np.full((n, n), 5.0),
+                     W.make_mask("square", n, n), name="data2d")
+
+
+PROBLEMS = {
+    "manufactured33": lambda: W.manufactured(n=33),
+    "aligned17": lambda: W.manufactured(n=17, beta=(1.0, 0.0)),
+    "rect_ragged": lambda: _const(19, (0.8, -0.35), nx=45),
+    "L_mask": lambda: _const(41, (0.3, 1.0), mask="L"),
+    "disc_mask": lambda: _const(47, (-0.9, 0.2), mask="disc", mu=1e-3),
+    "steep": lambda: _const(64, (0.02, 1.0), mu=1e-4),
+    "long_lines": lambda: _const(300, (1.0, 0.37), mu=1e-2),
+    "sheared65": lambda: W.sheared(n=65),
+    "data2d": lambda: _data2d(33),
+    "tiny3": lambda: _const(3, (1.0, 0.5)),
+}
+
+
+@pytest.fixture(scope="module")
+def pairs(torch_cuda):
+    from paper_2411_11041_gb300 import Solver
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            p = PROBLEMS[name]()
+            cache[name] = (p, O.Oracle(p), Solver(p, tol=0.0, max_iter=0))
+        return cache[name]
+    return get
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_geometry_matches_oracle(pairs, name):
+    p, o, s = pairs(name)
+    for fam in (0, 1):
+        Lo, Lg = o.lines(fam), s.lines(fam)
+        assert np.array_equal(Lo["off"], Lg["off"]), f"family {fam} curve layout differs"
+        assert np.abs(Lo["xi"] - Lg["xi"]).max(initial=0) <= 1e-12
+        assert np.abs(Lo["eta"] - Lg["eta"]).max(initial=0) <= 1e-12
+        np.testing.assert_allclose(Lg["h"], Lo["h"], rtol=1e-13)
+        so, to, po = o.crossings(fam)
+        sg, tg, pg = s.crossings(fam)
+        assert np.array_equal(so, sg), f"family {fam} crossings differ"
+        assert np.abs(to - tg).max() <= 1e-12 and np.abs(po - pg).max() <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_split_step_matches_oracle(pairs, torch_cuda, name):
+    from paper_2411_11041_gb300 import Solver
+    p, o, s = pairs(name)
+    torch = torch_cuda
+    u = np.random.default_rng(11).normal(size=(p.ny, p.nx)) * o.interior()
+    ug = torch.tensor(u, device="cuda:0")
+    for theta, dt in ((0.5, o.default_dt()), (0.5, 0.3), (1.0, 0.01)):
+        sv = s if theta == 0.5 else Solver(p, theta=theta)
+        uh, un = sv.split_step(ug, dt)
+        ouh, oun = o.split_step(theta, dt, u)
+        assert relerr(uh, ouh) <= TOL64, (theta, dt)
+        assert relerr(un, oun) <= TOL64, (theta, dt)
+
+
+@pytest.mark.parametrize("name", ["manufactured33", "L_mask", "sheared65", "data2d", "tiny3",
+                                  "long_lines"])
+def test_fixed_step_count_solve_matches_oracle(torch_cuda, name):
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    p = PROBLEMS[name]()
+    o = O.Oracle(p)
+    for init in (0, 2):
+        s = Solver(p, tol=0.0, max_iter=37, init=init)
+        u, uit, stats, st = s.solve_stationary(want_iter=True)
+        ref, refit, it, rel, ost = o.solve_stationary(tol=0.0, max_iter=37, init=init)
+        assert st == ADR_OK and ost == O.OK  # tol <= 0: exactly max_iter steps
+        assert stats["iters"] == it == 37
+        assert relerr(u, ref) <= TOL64 and relerr(uit, refit) <= TOL64
+        assert abs(stats["rel_update"] - rel) <= 1e-9 * rel + 1e-13
+
+
+@pytest.mark.parametrize("name", ["manufactured33", "aligned17", "disc_mask", "sheared65"])
+def test_converged_solve_matches_oracle(torch_cuda, name):
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    p = PROBLEMS[name]()
+    o = O.Oracle(p)
+    s = Solver(p, tol=1e-10, max_iter=20000)
+    u, uit, stats, st = s.solve_stationary(want_iter=True)
+    ref, refit, it, rel, ost = o.solve_stationary(tol=1e-10, max_iter=20000)
+    assert st == ADR_OK and ost == O.OK
+    assert stats["iters"] == it
+    assert stats["rel_update"] <= 1e-10
+    assert relerr(u, ref) <= TOL64 and relerr(uit, refit) <= TOL64
+
+
+def test_user_init_and_paper_u0(torch_cuda):
+    from paper_2411_11041_gb300 import Solver
+    torch = torch_cuda
+    p = W.sheared(n=65)
+    o = O.Oracle(p)
+    s = Solver(p)
+    assert relerr(s.paper_u0(), o.paper_u0()) <= TOL64
+    u0 = np.random.default_rng(3).normal(size=(65, 65))
+    s2 = Solver(p, tol=0.0, max_iter=9, init=1)
+    u, _, _, _ = s2.solve_stationary(u_init=torch.tensor(u0, device="cuda:0"))
+    ref = o.solve_stationary(tol=0.0, max_iter=9, init=1, u_init=u0)[0]
+    assert relerr(u, ref) <= TOL64
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_parabolic_matches_oracle(torch_cuda, mode):
+    from paper_2411_11041_gb300 import Solver
+    torch = torch_cuda
+    p = W.parabolic(n=65)
+    o = O.Oracle(p)
+    s = Solver(p, tol=1e-9, max_iter=5000)
+    u = torch.tensor(p.u0, device="cuda:0")
+    stats, st = s.step_parabolic(u, 1e-3, 4, mode)
+    ref, tot, ost = o.step_parabolic(p.u0, 1e-3, 4, mode, tol=1e-9, max_iter=5000)
+    assert stats["iters"] == tot
+    assert relerr(u, ref) <= TOL64
+
+
+def test_sheared_2048_two_steps_match_oracle(torch_cuda):
+    """Full-size sheared workload (2048^2 nodes, traced curves), two split
+    steps from zero, every grid value compared."""
+    from paper_2411_11041_gb300 import Solver
+    p = W.sheared(n=2048)
+    o = O.Oracle(p)
+    s = Solver(p, tol=0.0, max_iter=2)
+    u, uit, stats, st = s.solve_stationary(want_iter=True)
+    ref, refit, it, rel, ost = o.solve_stationary(tol=0.0, max_iter=2)
+    assert stats["iters"] == 2
+    assert relerr(u, ref) <= TOL64 and relerr(uit, refit) <= TOL64
