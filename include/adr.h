@@ -193,6 +193,42 @@ adr_status adr_paper_u0(adr_problem* prob, double* u0);
  */
 adr_status adr_time_kernels(adr_problem* prob, int reps, double* ms_out);
 
+/*
+ * adr_cross_substep_noalloc -- one cross-flow substep (G family: curve solve
+ * with m_i and the curve -> grid map) that allocates nothing.  The paper has no
+ * counterpart; this call exists for callers that cannot call cudaMalloc: code
+ * running under a memory pool or caching allocator owned by someone else
+ * (a host framework that forbids raw device allocations), and latency-bound
+ * callers that must not let an allocation synchronise the device mid-loop.
+ * They keep the curve data and crossings in their own memory (for example
+ * copies of adr_get_lines / adr_get_crossings of family 1, made once by a
+ * setup step that could allocate) and pass them in with the input and output.
+ *
+ * u_in -> u_out (device double [ny][nx]): u_out = G_G(u^i + dt d) where on
+ * every G curve (M + theta dt mu K) d = -mu K u^i, u^i the bilinear samples of
+ * u_in.  off[n_lines+1] (device int32, off[n_lines] == n_nodes), h[n_lines],
+ * xi/eta[n_nodes]: the family-1 curves as adr_get_lines reports them.
+ * seg/t/pos[4*nx*ny]: the family-1 crossings as adr_get_crossings reports them
+ * (seg = -2 marks a non-interior node, which gets 0).  stream: cudaStream_t or
+ * NULL.  The call only launches work; it returns before the kernels finish.
+ *
+ * Work space: a fixed array of 4 x 524288 doubles (16 MiB) in device memory,
+ * reserved by every GPU that loads the library until the process exits.
+ * n_nodes > 524288 is rejected with ADR_EINVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the one array and it keeps the last call's contents; a call
+ * writes every entry it reads, so nothing needs clearing, but calls whose
+ * kernels may overlap on the GPU (different streams, no ordering between
+ * them) race on it and must be serialised by the caller.  Curves with offsets
+ * outside [0, n_nodes] are skipped.  Errors: ADR_EINVAL, ADR_ECUDA.
+ */
+adr_status adr_cross_substep_noalloc(int nx, int ny, double mu, double theta, double dt,
+                                     const double* u_in, int n_lines, int n_nodes, const int* off,
+                                     const double* h, const double* xi, const double* eta,
+                                     const int* seg, const double* t, const double* pos,
+                                     double* u_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,7 @@ UNITS = {
     "geometry.cu": ["-fmad=false"],
     "sweep.cu": [],
     "api.cu": [],
+    "noalloc.cu": [],
 }
 
 
