@@ -44,8 +44,12 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # every array the kernel must touch once; flops count the kernel's FP64
 # arithmetic per unit (fma = 2, divide = 1).
 KERNELS = ["curve solve B", "curve->grid map B", "curve solve G", "curve->grid map G"]
-BYTES_PER_UNIT = [48.0, 81.0, 32.0, 89.0]
-FLOPS_PER_UNIT = [80.0, 16.0, 52.0, 20.0]
+#   curve solve B: cell 4 + lambda 16 + F 8 + S row 24 + factors 32 + rp 8 + v 8 + u 8 B;
+#                  gather 9 + rhs 6 + elimination 3 + upward 2 + back 4 + update 2 flop
+#   curve solve G: the same without F and S rows (S = mu K is constant per curve)
+#   maps: crossings 16 + t 32 + w 16 + v 8 + type 1 + out 8 (+ u_j 8 for the norms) B
+BYTES_PER_UNIT = [108.0, 81.0, 76.0, 89.0]
+FLOPS_PER_UNIT = [26.0, 16.0, 24.0, 20.0]
 
 
 def parse():

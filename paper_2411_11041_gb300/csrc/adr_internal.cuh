@@ -30,6 +30,17 @@ struct GridView {
     const double* f;
 };
 
+// Work items of the curve solve: a block of BS threads takes BS/T curves of
+// the same block size T.
+constexpr int kItemSets = 3;
+struct ItemSet {
+    int BS = 0;
+    int count = 0;
+    int* T = nullptr;         // [count] block size of the item's curves
+    int* curve = nullptr;     // [count * BS/32] curve indices (-1 empty)
+    double* lanec = nullptr;  // [count * (2 log2 BS + 2) * BS] reduced-system constants
+};
+
 // One curve family in structure-of-arrays form.  Curves are stored back to
 // back: curve l owns nodes off[l] .. off[l+1]-1 (both ends on the boundary).
 struct Family {
@@ -44,7 +55,24 @@ struct Family {
     double* bnorm = nullptr;  // [n_nodes] |beta| at the nodes
     double* fval = nullptr;   // [n_nodes] f at the nodes
     double* v = nullptr;      // [n_nodes] curve values u + dt d of the current substep
-    double* scr = nullptr;    // [3*n_nodes] tridiagonal work space
+    // per-row data of the curve solve in slot layout (row (t, j) of a curve at
+    // soff[curve] + j*T + t, T the curve's block size)
+    int n_slots = 0;
+    int* soff = nullptr;      // [n_lines+1]
+    int* gcell = nullptr;     // [n_slots] bilinear cell r*nx + i of the row's node
+    double* glx = nullptr;    // [n_slots] bilinear weights lambda_x, lambda_y
+    double* gly = nullptr;
+    double* Fl = nullptr;     // [n_slots] load F = M f (B)
+    double* srow = nullptr;   // [3*n_slots] S sub/diag/super (B)
+    double* fac = nullptr;    // [4*n_slots] elimination factors cp, vp, ip, lp
+    ItemSet iset[3];          // BS = 256, 512, 1024
+    int* mg = nullptr;        // [4*N] curve -> grid map: segment of each crossing
+    double* mc = nullptr;     // [8*N] combined weights of the map
+    // factorisation currently held in fac/lanec (theta dt, sigma, steady flag)
+    bool prep_valid = false;
+    double prep_td = 0, prep_sig = 0;
+    int prep_paper = 0;
+    bool load_plain = false;  // Fl holds M f without extra load
     // curve -> grid map, per grid node: 4 crossings (row L, row R, col D, col U)
     int* cg = nullptr;        // [4*N] first node of the crossed segment (-1 boundary)
     double* ct = nullptr;     // [4*N] position in that segment
@@ -69,6 +97,7 @@ struct Problem {
     GridView gv{};
     int N = 0;             // nx*ny
     int n_interior = 0;
+    int n_sm = 0;
     bool const_beta = false;
     double bmax = 0;
     Family fam[2];
@@ -89,6 +118,11 @@ struct Problem {
 // error helpers
 void set_error(const std::string& msg);
 adr_status cuda_fail(cudaError_t e, const char* what);
+#define TRY_S(x)                      \
+    do {                              \
+        adr_status _st = (x);         \
+        if (_st != ADR_OK) return _st; \
+    } while (0)
 #define ADR_CUDA_TRY(call)                                      \
     do {                                                        \
         cudaError_t _e = (call);                                \
@@ -114,6 +148,13 @@ adr_status dev_alloc(Problem* p, T** ptr, size_t count)
 adr_status build_geometry(Problem* p, const uint8_t* mask);
 
 // sweeps (sweep.cu)
+adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off);
+adr_status launch_map_coef(Problem* p, int fam);
+int grid_map_blocks(const Problem* p);
+adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper);
+adr_status load_family(Problem* p, const double* fextra, double fx_scale);
+adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_even,
+                             const double* u_odd, bool use_state, int paper);
 adr_status launch_mask_copy(Problem* p, const double* in, double* out);
 adr_status launch_state_reset(Problem* p);
 

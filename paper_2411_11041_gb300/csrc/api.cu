@@ -24,13 +24,9 @@ adr_status cuda_fail(cudaError_t e, const char* what)
 }
 
 // launchers defined in sweep.cu
-adr_status launch_line_sweep_ex(Problem* p, int fam, double theta, double dt, double sig,
-                                const double* u_even, const double* u_odd, bool use_state,
-                                const double* fextra, double fx_scale, int paper_u0);
 adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out_odd,
                               int parity_shift, const double* prev_even, const double* prev_odd,
                               bool use_state, bool norms);
-int grid_map_blocks(const Problem* p);
 adr_status launch_check_ex(Problem* p, double tol, int max_iter,
                            cudaGraphConditionalHandle handle, bool use_cond);
 adr_status launch_finish(Problem* p, double* out, double* iter_out, bool midpoint);
@@ -96,20 +92,18 @@ adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
     cudaGraphNode_t node;
     ADR_CUDA_TRY(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &np));
     cudaGraph_t body = np.conditional.phGraph_out[0];
+    TRY(prepare_family(p, 0, theta * dt, sig, 0));
+    TRY(prepare_family(p, 1, theta * dt, sig, 0));
     cudaStream_t user = p->stream;
     p->stream = h->cap_stream;
     cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed);
     adr_status s = ADR_OK;
     if (e != cudaSuccess) s = cuda_fail(e, "cudaStreamBeginCaptureToGraph");
-    if (s == ADR_OK)
-        s = launch_line_sweep_ex(p, 0, theta, dt, sig, p->ubuf[0], p->ubuf[1], true, fextra,
-                                 fx_scale, 0);
+    if (s == ADR_OK) s = launch_line_solve(p, 0, dt, p->ubuf[0], p->ubuf[1], true, 0);
     if (s == ADR_OK)
         s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, true, false);
-    if (s == ADR_OK)
-        s = launch_line_sweep_ex(p, 1, theta, dt, sig, p->ubuf[2], p->ubuf[2], true, nullptr, 0.0,
-                                 0);
+    if (s == ADR_OK) s = launch_line_solve(p, 1, dt, p->ubuf[2], p->ubuf[2], true, 0);
     if (s == ADR_OK)
         s = launch_grid_map_ex(p, 1, p->ubuf[0], p->ubuf[1], 1, p->ubuf[0], p->ubuf[1], true, true);
     if (s == ADR_OK) s = launch_check_ex(p, tol, max_iter, cond, true);
@@ -139,6 +133,9 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
     TRY(launch_state_reset(p));
     ADR_CUDA_TRY(cudaEventRecord(h->ev0, p->stream));
     if (max_iter > 0) {
+        TRY(prepare_family(p, 0, theta * dt, sig, 0));
+        TRY(prepare_family(p, 1, theta * dt, sig, 0));
+        TRY(load_family(p, fextra, fx_scale));
         if (!h->exec || h->g_theta != theta || h->g_dt != dt || h->g_sig != sig ||
             h->g_fextra != fextra || h->g_scale != fx_scale || h->g_tol != tol ||
             h->g_max_iter != max_iter)
@@ -174,7 +171,9 @@ adr_status init_state(adr_problem* h, int init, const double* u_init)
         return launch_mask_copy(p, u_init, p->ubuf[0]);
     }
     if (init == ADR_INIT_PAPER_U0) {
-        TRY(launch_line_sweep_ex(p, 0, 1.0, 1.0, p->sigma, nullptr, nullptr, false, nullptr, 0.0, 1));
+        TRY(prepare_family(p, 0, 1.0, p->sigma, 1));
+        TRY(load_family(p, nullptr, 0.0));
+        TRY(launch_line_solve(p, 0, 1.0, nullptr, nullptr, false, 1));
         return launch_grid_map_ex(p, 0, p->ubuf[0], p->ubuf[0], 0, nullptr, nullptr, false, false);
     }
     if (init == ADR_INIT_ZERO) return launch_mask_copy(p, nullptr, p->ubuf[0]);
@@ -259,6 +258,11 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
     p->sigma = sigma;
     p->stream = static_cast<cudaStream_t>(stream);
     p->N = grid->nx * grid->ny;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    }
     adr_status s = ADR_OK;
     auto fail = [&](adr_status st) {
         adr_destroy(h);
@@ -288,6 +292,7 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
         double u = 0;
         for (int l = 0; l < p->fam[fam].n_lines; ++l) u += std::max(0, off[l + 1] - off[l] - 2);
         h->line_unknowns[fam] = u;
+        if ((s = setup_groups(p, fam, off))) return fail(s);
     }
     if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) ||
         (e = cudaEventCreate(&h->ev0)) || (e = cudaEventCreate(&h->ev1)))
@@ -377,9 +382,12 @@ adr_status adr_split_step(adr_problem* h, double dt, const double* u, double* u_
     Problem* p = &h->p;
     double* half = u_half ? u_half : p->ubuf[2];
     double th = p->opts.theta;
-    TRY(launch_line_sweep_ex(p, 0, th, dt, p->sigma, u, u, false, nullptr, 0.0, 0));
+    TRY(prepare_family(p, 0, th * dt, p->sigma, 0));
+    TRY(prepare_family(p, 1, th * dt, p->sigma, 0));
+    TRY(load_family(p, nullptr, 0.0));
+    TRY(launch_line_solve(p, 0, dt, u, u, false, 0));
     TRY(launch_grid_map_ex(p, 0, half, half, 0, nullptr, nullptr, false, false));
-    TRY(launch_line_sweep_ex(p, 1, th, dt, p->sigma, half, half, false, nullptr, 0.0, 0));
+    TRY(launch_line_solve(p, 1, dt, half, half, false, 0));
     TRY(launch_grid_map_ex(p, 1, u_next, u_next, 0, nullptr, nullptr, false, false));
     ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
     return ADR_OK;
@@ -393,7 +401,9 @@ adr_status adr_paper_u0(adr_problem* h, double* u0)
         return ADR_EINVAL;
     }
     Problem* p = &h->p;
-    TRY(launch_line_sweep_ex(p, 0, 1.0, 1.0, p->sigma, nullptr, nullptr, false, nullptr, 0.0, 1));
+    TRY(prepare_family(p, 0, 1.0, p->sigma, 1));
+    TRY(load_family(p, nullptr, 0.0));
+    TRY(launch_line_solve(p, 0, 1.0, nullptr, nullptr, false, 1));
     TRY(launch_grid_map_ex(p, 0, u0, u0, 0, nullptr, nullptr, false, false));
     ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
     return ADR_OK;
@@ -448,6 +458,9 @@ adr_status adr_time_kernels(adr_problem* h, int reps, double* ms_out)
     Problem* p = &h->p;
     const adr_opts& o = p->opts;
     double dt = o.dt > 0 ? o.dt : default_dt(*p, p->sigma);
+    TRY(prepare_family(p, 0, o.theta * dt, p->sigma, 0));
+    TRY(prepare_family(p, 1, o.theta * dt, p->sigma, 0));
+    TRY(load_family(p, nullptr, 0.0));
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) ADR_CUDA_TRY(cudaEventCreate(&ev[k]));
     adr_status s = ADR_OK;
@@ -456,15 +469,13 @@ adr_status adr_time_kernels(adr_problem* h, int reps, double* ms_out)
         for (int r = 0; r < reps && s == ADR_OK; ++r) {
             switch (stage) {
             case 0:
-                s = launch_line_sweep_ex(p, 0, o.theta, dt, p->sigma, p->ubuf[0], p->ubuf[0], false,
-                                         nullptr, 0.0, 0);
+                s = launch_line_solve(p, 0, dt, p->ubuf[0], p->ubuf[0], false, 0);
                 break;
             case 1:
                 s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, false, false);
                 break;
             case 2:
-                s = launch_line_sweep_ex(p, 1, o.theta, dt, p->sigma, p->ubuf[2], p->ubuf[2], false,
-                                         nullptr, 0.0, 0);
+                s = launch_line_solve(p, 1, dt, p->ubuf[2], p->ubuf[2], false, 0);
                 break;
             default:
                 s = launch_grid_map_ex(p, 1, p->ubuf[1], p->ubuf[1], 0, p->ubuf[0], p->ubuf[0], false,

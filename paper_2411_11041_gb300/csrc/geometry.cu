@@ -384,72 +384,99 @@ __global__ void k_count_bedges(GridView g, int* count)
     if (c) atomicAdd(count, c);
 }
 
-// single thread: walk the loops and place the seeds (X0, Y0 physical offsets)
-__global__ void k_seeds(GridView g, int fam, uint8_t* vis_h, uint8_t* vis_v, long long total,
-                        double* sx, double* sy, int cap, int* nseeds, int* status)
+// loop starts: the +x boundary edges of every row, in (row, column) order;
+// one thread per row counts, then writes its row's edges at its offset
+__global__ void k_row_cand_count(GridView g, long long* cnt)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.ny) return;
+    long long c = 0;
+    for (int i = 0; i < g.nx - 1; ++i) c += hedge_dir(g, i, r) == 1;
+    cnt[r] = c;
+}
+__global__ void k_row_cand_fill(GridView g, const long long* start, int* cand)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.ny) return;
+    long long pos = start[r];
+    for (int i = 0; i < g.nx - 1; ++i)
+        if (hedge_dir(g, i, r) == 1) cand[pos++] = r * (g.nx - 1) + i;
+}
+
+// one thread per family (block f): walk the loops from the candidate starts
+// and place the seeds (X0, Y0 physical offsets) at sx/sy + f*cap
+__global__ void k_seeds(GridView g, const int* cand, long long ncand, uint8_t* vis_h_all,
+                        uint8_t* vis_v_all, long long total, double* sx_all, double* sy_all,
+                        int cap, int* nseeds, int* status)
+{
+    if (threadIdx.x != 0) return;
+    int fam = blockIdx.x;
     int nx = g.nx, ny = g.ny;
+    uint8_t* vis_h = vis_h_all + (size_t)fam * ny * (nx - 1);
+    uint8_t* vis_v = vis_v_all + (size_t)fam * nx * (ny - 1);
+    double* sx = sx_all + (size_t)fam * cap;
+    double* sy = sy_all + (size_t)fam * cap;
     double cum = 0.0;
     long long k = 0;
     int ns = 0;
-    for (int r0 = 0; r0 < ny; ++r0)
-        for (int i0 = 0; i0 < nx - 1; ++i0) {
-            if (hedge_dir(g, i0, r0) != 1 || vis_h[(size_t)r0 * (nx - 1) + i0]) continue;
-            int i = i0, r = r0, d = 0;
-            long long steps = 0;
-            for (;;) {
-                uint8_t* mark;
-                if (d == 0) mark = &vis_h[(size_t)r * (nx - 1) + i];
-                else if (d == 2) mark = &vis_h[(size_t)r * (nx - 1) + i - 1];
-                else if (d == 1) mark = &vis_v[(size_t)r * nx + i];
-                else mark = &vis_v[(size_t)(r - 1) * nx + i];
-                if (*mark) break;
-                *mark = 1;
-                // the edge from (i, r) in direction d
-                int ib = i + kDXI[d], rb = r + kDETA[d];
-                size_t A = (size_t)r * nx + i, B = (size_t)rb * nx + ib;
-                double m1 = 0.5 * (g.beta1[A] + g.beta1[B]), m2 = 0.5 * (g.beta2[A] + g.beta2[B]);
-                double nm = sqrt(m1 * m1 + m2 * m2);
-                if (!(nm > 0.0)) {
-                    atomicOr(status, kErrGeom);
-                    *nseeds = 0;
-                    return;
-                }
-                double vx = fam == 0 ? m1 / nm : m2 / nm, vy = fam == 0 ? m2 / nm : -m1 / nm;
-                double nxo = (double)kDETA[d], nyo = (double)(-kDXI[d]);
-                double len = (d & 1) ? g.hy : g.hx;
-                double w = -(nxo * vx + nyo * vy) * len;
-                if (w > 0.0) {
-                    while ((k + 0.5) * g.hs < cum + w) {
-                        double phi = ((k + 0.5) * g.hs - cum) / w;
-                        if (ns < cap) {
-                            sx[ns] = (i + phi * kDXI[d]) * g.hx;
-                            sy[ns] = (r + phi * kDETA[d]) * g.hy;
-                        }
-                        ns++;
-                        k++;
-                    }
-                    cum += w;
-                }
-                i = ib;
-                r = rb;
-                int nd = -1;
-                int pref[3] = {(d + 1) & 3, d, (d + 3) & 3};
-                for (int q = 0; q < 3; ++q)
-                    if (out_edge(g, i, r, pref[q])) {
-                        nd = pref[q];
-                        break;
-                    }
-                if (nd < 0 || ++steps > total + 4) break;
-                d = nd;
+    for (long long c = 0; c < ncand; ++c) {
+        int e0 = cand[c];
+        int r0 = e0 / (nx - 1), i0 = e0 % (nx - 1);
+        if (vis_h[(size_t)r0 * (nx - 1) + i0]) continue;
+        int i = i0, r = r0, d = 0;
+        long long steps = 0;
+        for (;;) {
+            uint8_t* mark;
+            if (d == 0) mark = &vis_h[(size_t)r * (nx - 1) + i];
+            else if (d == 2) mark = &vis_h[(size_t)r * (nx - 1) + i - 1];
+            else if (d == 1) mark = &vis_v[(size_t)r * nx + i];
+            else mark = &vis_v[(size_t)(r - 1) * nx + i];
+            if (*mark) break;
+            *mark = 1;
+            // the edge from (i, r) in direction d
+            int ib = i + kDXI[d], rb = r + kDETA[d];
+            size_t A = (size_t)r * nx + i, B = (size_t)rb * nx + ib;
+            double m1 = 0.5 * (g.beta1[A] + g.beta1[B]), m2 = 0.5 * (g.beta2[A] + g.beta2[B]);
+            double nm = sqrt(m1 * m1 + m2 * m2);
+            if (!(nm > 0.0)) {
+                atomicOr(status, kErrGeom);
+                nseeds[fam] = 0;
+                return;
             }
+            double vx = fam == 0 ? m1 / nm : m2 / nm, vy = fam == 0 ? m2 / nm : -m1 / nm;
+            double nxo = (double)kDETA[d], nyo = (double)(-kDXI[d]);
+            double len = (d & 1) ? g.hy : g.hx;
+            double w = -(nxo * vx + nyo * vy) * len;
+            if (w > 0.0) {
+                while ((k + 0.5) * g.hs < cum + w) {
+                    double phi = ((k + 0.5) * g.hs - cum) / w;
+                    if (ns < cap) {
+                        sx[ns] = (i + phi * kDXI[d]) * g.hx;
+                        sy[ns] = (r + phi * kDETA[d]) * g.hy;
+                    }
+                    ns++;
+                    k++;
+                }
+                cum += w;
+            }
+            i = ib;
+            r = rb;
+            int nd = -1;
+            int pref[3] = {(d + 1) & 3, d, (d + 3) & 3};
+            for (int q = 0; q < 3; ++q)
+                if (out_edge(g, i, r, pref[q])) {
+                    nd = pref[q];
+                    break;
+                }
+            if (nd < 0 || ++steps > total + 4) break;
+            d = nd;
         }
+    }
     if (ns > cap) {
         atomicOr(status, kErrCapacity);
         ns = cap;
     }
-    *nseeds = ns;
+    nseeds[fam] = ns;
 }
 
 // trace one curve: number of full RK4 steps M, length L and exit point
@@ -486,12 +513,29 @@ __device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mo
     }
 }
 
-__global__ void k_trace_count(GridView g, int fam, const double* sx, const double* sy,
+// seed t of the combined launch: family 0 takes t < nseeds[0], family 1 the
+// rest; per-seed arrays of family f live at offset f*cap
+__device__ __forceinline__ bool seed_of(const int* nseeds, int cap, int t, int* fam, int* s)
+{
+    if (t < nseeds[0]) {
+        *fam = 0;
+        *s = t;
+        return true;
+    }
+    if (t < nseeds[0] + nseeds[1]) {
+        *fam = 1;
+        *s = cap + (t - nseeds[0]);
+        return true;
+    }
+    return false;
+}
+
+__global__ void k_trace_count(GridView g, int cap, const double* sx, const double* sy,
                               const int* nseeds, int* M, double* L, double* XE, double* YE,
                               long long* cn, int* status)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= *nseeds) return;
+    int fam, s;
+    if (!seed_of(nseeds, cap, blockIdx.x * blockDim.x + threadIdx.x, &fam, &s)) return;
     int m = 0;
     double len = 0, xe = 0, ye = 0;
     if (trace_len(g, fam, sx[s], sy[s], &m, &len, &xe, &ye)) {
@@ -509,23 +553,40 @@ __global__ void k_trace_count(GridView g, int fam, const double* sx, const doubl
 }
 
 // re-trace the M RK4 steps and place n+1 nodes uniformly in arc length
-__global__ void k_trace_fill(GridView g, int fam, const double* sx, const double* sy,
+struct FillOut {
+    int* off;
+    double* h;
+    double* xs;
+    double* es;
+};
+
+__global__ void k_trace_fill(GridView g, int cap, const double* sx, const double* sy,
                              const int* nseeds, const int* M, const double* L, const double* XE,
-                             const double* YE, const long long* noff, int* off, double* h,
-                             double* xs, double* es)
+                             const double* YE, const long long* noff, FillOut o0, FillOut o1)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= *nseeds) return;
+    int fam, s;
+    if (!seed_of(nseeds, cap, blockIdx.x * blockDim.x + threadIdx.x, &fam, &s)) return;
+    const FillOut& o = fam == 0 ? o0 : o1;
+    int* off = o.off;
+    double* h = o.h;
+    double* xs = o.xs;
+    double* es = o.es;
+    int li = fam == 0 ? s : s - cap;  // curve index inside its family
     double ds = g.hs / kTraceStepsPerH;
     double len = L[s];
     int m = M[s];
     int n = elements_for(g, len);
     int base = (int)noff[s];
-    off[s] = base;
-    h[s] = len / n;
-    double Xq = sx[s], Yq = sy[s];  // P_q
-    double Xn = Xq, Yn = Yq;        // P_{q+1}
-    int q = -1;                     // index of the segment held in (P_q, P_{q+1})
+    off[li] = base;
+    h[li] = len / n;
+    // (Xa, Ya) = P_q, (Xb, Yb) = P_{q+1}; P_0 is the seed, P_{m+1} the exit point
+    int q = 0;
+    double Xa = sx[s], Ya = sy[s], Xb, Yb;
+    if (m > 0) rk4(g, fam, Xa, Ya, ds, &Xb, &Yb);
+    else {
+        Xb = XE[s];
+        Yb = YE[s];
+    }
     for (int j = 0; j <= n; ++j) {
         double X, Y;
         if (j == n) {
@@ -537,27 +598,18 @@ __global__ void k_trace_fill(GridView g, int fam, const double* sx, const double
             if (qj > m) qj = m;
             while (q < qj) {
                 q++;
-                Xq = Xn;
-                Yq = Yn;
-                if (q < m) {
-                    rk4(g, fam, Xq, Yq, ds, &Xn, &Yn);
-                } else {
-                    Xn = XE[s];
-                    Yn = YE[s];
-                }
-            }
-            if (q == -1) {
-                q = 0;
-                if (m > 0) rk4(g, fam, Xq, Yq, ds, &Xn, &Yn);
+                Xa = Xb;
+                Ya = Yb;
+                if (q < m) rk4(g, fam, Xa, Ya, ds, &Xb, &Yb);
                 else {
-                    Xn = XE[s];
-                    Yn = YE[s];
+                    Xb = XE[s];
+                    Yb = YE[s];
                 }
             }
             double s0 = q * ds, s1 = (q < m) ? (q + 1) * ds : len;
             double fr = (s1 > s0) ? (sj - s0) / (s1 - s0) : 0.0;
-            X = Xq + fr * (Xn - Xq);
-            Y = Yq + fr * (Yn - Yq);
+            X = Xa + fr * (Xb - Xa);
+            Y = Ya + fr * (Yb - Ya);
         }
         xs[base + j] = snap(X / g.hx);
         es[base + j] = snap(Y / g.hy);
@@ -848,7 +900,6 @@ adr_status finish_family(Problem* p, int fam, TmpGuard& tg)
     TRY(dev_alloc(p, &F.bnorm, F.n_nodes));
     TRY(dev_alloc(p, &F.fval, F.n_nodes));
     TRY(dev_alloc(p, &F.v, F.n_nodes + 1));
-    TRY(dev_alloc(p, &F.scr, 3 * (size_t)F.n_nodes + 3));
     TRY(dev_alloc(p, &F.cg, 4 * (size_t)N));
     TRY(dev_alloc(p, &F.ct, 4 * (size_t)N));
     TRY(dev_alloc(p, &F.cw, 2 * (size_t)N));
@@ -898,6 +949,9 @@ adr_status finish_family(Problem* p, int fam, TmpGuard& tg)
     k_cross<1><<<nb, kThreads, 0, st>>>(g, F.n_nodes, lon, F.xi, F.eta, R, C);
     k_cross<2><<<nb, kThreads, 0, st>>>(g, F.n_nodes, lon, F.xi, F.eta, R, C);
     k_node_desc<<<blocks_for(N), kThreads, 0, st>>>(g, R, C, F.cg, F.ct, F.cw, F.cpos);
+    TRY(dev_alloc(p, &F.mg, 4 * (size_t)N));
+    TRY(dev_alloc(p, &F.mc, 8 * (size_t)N));
+    TRY(launch_map_coef(p, fam));
     ADR_CUDA_TRY(cudaGetLastError());
     ADR_CUDA_TRY(cudaStreamSynchronize(st));
     return ADR_OK;
@@ -948,68 +1002,92 @@ adr_status build_straight(Problem* p, int fam, int first, TmpGuard& tg)
     return ADR_OK;
 }
 
-adr_status build_curved(Problem* p, int fam, int* status_d, TmpGuard& tg)
+adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
 {
-    Family& F = p->fam[fam];
     cudaStream_t st = p->stream;
     const GridView& g = p->gv;
     int nx = p->grid.nx, ny = p->grid.ny;
-    int* cnt;
-    TRY(alloc_tmp(tg.v, &cnt, 2));
-    ADR_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
+    int* cnt;  // [0] boundary edges, [1..2] seeds per family
+    TRY(alloc_tmp(tg.v, &cnt, 3));
+    ADR_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(int), st));
     k_count_bedges<<<blocks_for((long long)nx * ny), kThreads, 0, st>>>(g, cnt);
+    // loop-start candidates in (row, column) order
+    long long *rc, *rs;
+    TRY(alloc_tmp(tg.v, &rc, ny));
+    TRY(alloc_tmp(tg.v, &rs, ny + 1));
+    k_row_cand_count<<<blocks_for(ny, 64), 64, 0, st>>>(g, rc);
+    k_scan<<<1, 1024, 0, st>>>(rc, rs, ny);
     int nbe = 0;
+    long long ncand = 0;
     ADR_CUDA_TRY(cudaMemcpyAsync(&nbe, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaMemcpyAsync(&ncand, rs + ny, sizeof ncand, cudaMemcpyDeviceToHost, st));
     ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    int* cand;
+    TRY(alloc_tmp(tg.v, &cand, ncand + 1));
+    k_row_cand_fill<<<blocks_for(ny, 64), 64, 0, st>>>(g, rs, cand);
     double hmax = p->gv.hx > p->gv.hy ? p->gv.hx : p->gv.hy;
     int cap = (int)(nbe * ceil(hmax / p->gv.hs)) + 4;
+    size_t nh = (size_t)ny * (nx - 1), nv = (size_t)nx * (ny - 1);
     uint8_t *vh, *vv;
-    TRY(alloc_tmp(tg.v, &vh, (size_t)ny * (nx - 1)));
-    TRY(alloc_tmp(tg.v, &vv, (size_t)nx * (ny - 1)));
-    ADR_CUDA_TRY(cudaMemsetAsync(vh, 0, (size_t)ny * (nx - 1), st));
-    ADR_CUDA_TRY(cudaMemsetAsync(vv, 0, (size_t)nx * (ny - 1), st));
+    TRY(alloc_tmp(tg.v, &vh, 2 * nh));
+    TRY(alloc_tmp(tg.v, &vv, 2 * nv));
+    ADR_CUDA_TRY(cudaMemsetAsync(vh, 0, 2 * nh, st));
+    ADR_CUDA_TRY(cudaMemsetAsync(vv, 0, 2 * nv, st));
     double *sx, *sy;
-    TRY(alloc_tmp(tg.v, &sx, cap));
-    TRY(alloc_tmp(tg.v, &sy, cap));
-    k_seeds<<<1, 1, 0, st>>>(g, fam, vh, vv, nbe, sx, sy, cap, cnt + 1, status_d);
-    int ns = 0;
-    ADR_CUDA_TRY(cudaMemcpyAsync(&ns, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(alloc_tmp(tg.v, &sx, 2 * (size_t)cap));
+    TRY(alloc_tmp(tg.v, &sy, 2 * (size_t)cap));
+    k_seeds<<<2, 32, 0, st>>>(g, cand, ncand, vh, vv, nbe, sx, sy, cap, cnt + 1, status_d);
+    int ns[2] = {0, 0};
+    ADR_CUDA_TRY(cudaMemcpyAsync(ns, cnt + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     ADR_CUDA_TRY(cudaStreamSynchronize(st));
-    if (ns < 1) {
+    if (ns[0] < 1 || ns[1] < 1) {
         set_error("no inflow boundary for a curve family");
         return ADR_EGEOM;
     }
     int* M;
     double *L, *XE, *YE;
     long long *cn, *on;
-    TRY(alloc_tmp(tg.v, &M, ns));
-    TRY(alloc_tmp(tg.v, &L, ns));
-    TRY(alloc_tmp(tg.v, &XE, ns));
-    TRY(alloc_tmp(tg.v, &YE, ns));
-    TRY(alloc_tmp(tg.v, &cn, ns));
-    TRY(alloc_tmp(tg.v, &on, ns + 1));
-    k_trace_count<<<blocks_for(ns, 64), 64, 0, st>>>(g, fam, sx, sy, cnt + 1, M, L, XE, YE, cn,
-                                                     status_d);
-    k_scan<<<1, 1024, 0, st>>>(cn, on, ns);
-    long long tn = 0;
-    ADR_CUDA_TRY(cudaMemcpyAsync(&tn, on + ns, sizeof tn, cudaMemcpyDeviceToHost, st));
+    size_t n2 = 2 * (size_t)cap;
+    TRY(alloc_tmp(tg.v, &M, n2));
+    TRY(alloc_tmp(tg.v, &L, n2));
+    TRY(alloc_tmp(tg.v, &XE, n2));
+    TRY(alloc_tmp(tg.v, &YE, n2));
+    TRY(alloc_tmp(tg.v, &cn, n2));
+    TRY(alloc_tmp(tg.v, &on, n2 + 2));
+    int tot = ns[0] + ns[1];
+    k_trace_count<<<blocks_for(tot, 64), 64, 0, st>>>(g, cap, sx, sy, cnt + 1, M, L, XE, YE, cn,
+                                                      status_d);
+    k_scan<<<1, 1024, 0, st>>>(cn, on, ns[0]);
+    k_scan<<<1, 1024, 0, st>>>(cn + cap, on + cap, ns[1]);
+    long long tn[2] = {0, 0};
+    ADR_CUDA_TRY(cudaMemcpyAsync(&tn[0], on + ns[0], sizeof(long long), cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaMemcpyAsync(&tn[1], on + cap + ns[1], sizeof(long long), cudaMemcpyDeviceToHost,
+                                 st));
     ADR_CUDA_TRY(cudaStreamSynchronize(st));
-    if (tn > 0x7fffffffLL) {
-        set_error("too many curve nodes");
-        return ADR_EINVAL;
+    FillOut fo[2];
+    for (int fam = 0; fam < 2; ++fam) {
+        if (tn[fam] > 0x7fffffffLL) {
+            set_error("too many curve nodes");
+            return ADR_EINVAL;
+        }
+        Family& F = p->fam[fam];
+        F.n_lines = ns[fam];
+        F.n_nodes = (int)tn[fam];
+        TRY(dev_alloc(p, &F.off, F.n_lines + 1));
+        TRY(dev_alloc(p, &F.h, F.n_lines));
+        TRY(dev_alloc(p, &F.xi, F.n_nodes));
+        TRY(dev_alloc(p, &F.eta, F.n_nodes));
+        fo[fam] = {F.off, F.h, F.xi, F.eta};
     }
-    F.n_lines = ns;
-    F.n_nodes = (int)tn;
-    TRY(dev_alloc(p, &F.off, F.n_lines + 1));
-    TRY(dev_alloc(p, &F.h, F.n_lines));
-    TRY(dev_alloc(p, &F.xi, F.n_nodes));
-    TRY(dev_alloc(p, &F.eta, F.n_nodes));
-    k_trace_fill<<<blocks_for(ns, 64), 64, 0, st>>>(g, fam, sx, sy, cnt + 1, M, L, XE, YE, on,
-                                                    F.off, F.h, F.xi, F.eta);
-    int nn = F.n_nodes;
-    ADR_CUDA_TRY(cudaMemcpyAsync(F.off + F.n_lines, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
+    k_trace_fill<<<blocks_for(tot, 64), 64, 0, st>>>(g, cap, sx, sy, cnt + 1, M, L, XE, YE, on,
+                                                     fo[0], fo[1]);
+    for (int fam = 0; fam < 2; ++fam) {
+        int nn = p->fam[fam].n_nodes;
+        ADR_CUDA_TRY(cudaMemcpyAsync(p->fam[fam].off + p->fam[fam].n_lines, &nn, sizeof(int),
+                                     cudaMemcpyHostToDevice, st));
+        ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     ADR_CUDA_TRY(cudaGetLastError());
-    ADR_CUDA_TRY(cudaStreamSynchronize(st));
     return ADR_OK;
 }
 
@@ -1068,20 +1146,24 @@ adr_status build_geometry(Problem* p, const uint8_t* mask)
     long long bits = (long long)hb;
     memcpy(&bm, &bits, sizeof bm);
     p->bmax = bm;
+    adr_status s = ADR_OK;
+    if (p->const_beta) {
+        for (int fam = 0; fam < 2 && s == ADR_OK; ++fam) s = build_straight(p, fam, first, tg);
+    } else {
+        s = build_curved_both(p, info + 1, tg);
+    }
+    if (s != ADR_OK) return s;
+    ADR_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hinfo[1] & kErrGeom) {
+        set_error("curve tracing failed (closed integral curve or |beta| = 0 on a curve)");
+        return ADR_EGEOM;
+    }
+    if (hinfo[1] & kErrCapacity) {
+        set_error("internal: seed capacity exceeded");
+        return ADR_EGEOM;
+    }
     for (int fam = 0; fam < 2; ++fam) {
-        adr_status s = p->const_beta ? build_straight(p, fam, first, tg)
-                                     : build_curved(p, fam, info + 1, tg);
-        if (s != ADR_OK) return s;
-        ADR_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, st));
-        ADR_CUDA_TRY(cudaStreamSynchronize(st));
-        if (hinfo[1] & kErrGeom) {
-            set_error("curve tracing failed (closed integral curve or |beta| = 0 on a curve)");
-            return ADR_EGEOM;
-        }
-        if (hinfo[1] & kErrCapacity) {
-            set_error("internal: seed capacity exceeded");
-            return ADR_EGEOM;
-        }
         s = finish_family(p, fam, tg);
         if (s != ADR_OK) return s;
     }

@@ -10,206 +10,359 @@
 //  k_check       one block: convergence test and the CUDA-graph loop condition.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "adr_internal.cuh"
 
 namespace adr {
 namespace {
 
-constexpr int kLineWarps = 4;  // warps (curves) per block of the line kernel
+constexpr int kCmax = 8;       // rows per thread held in registers by the curve solve
 constexpr int kGridThreads = 256;
 
-struct LineArgs {
+// ---------------------------------------------------------------- curves
+// The curve systems (M + theta dt S) are fixed for a given (theta dt, sigma),
+// so their partitioned elimination is factored once (k_curve_prep) and every
+// split step only carries the right-hand side through it (k_curve_solve).
+//
+// One block of T threads per curve (T = 32..1024 chosen per curve so that a
+// thread owns at most kCmax rows).  Thread t owns rows [t c, t c + c) of the
+// curve's m unknowns, c = ceil(m / T) (row q <-> curve node q+1).  Downward
+// elimination inside a chunk writes every row as
+//     x_q + cp_q x_{q+1} + vp_q x_{s-1} = rp_q,   rp_q = r_q ip_q - lp_q rp_{q-1},
+// an upward pass gives the chunk's first unknown in terms of the chunk ends,
+// the chunk ends G_t = x_{e_t - 1} satisfy a T-equation tridiagonal system
+// solved by cyclic reduction in shared memory (multipliers factored once),
+// and back substitution gives every x_q.
+//
+// Per-row data live in a chunk-interleaved "slot" layout: row (t, j) of a
+// curve is stored at soff[curve] + j T + t, so that the j-th row of all
+// threads is one coalesced access.
+
+struct CurveArgs {
     int nx, ny;
-    const double* u_even;  // grid state read by the gather: u_even or u_odd by
-    const double* u_odd;   // the parity of the step counter
-    const double* fextra;  // nullable: extra nodal load (B family only)
-    double fx_scale;
+    const double* u_even;  // grid state of the gather (by step parity)
+    const double* u_odd;
     const IterState* state;
-    int n_lines;
-    const int* order;
-    const int* off;
+    const int* off;        // curve -> first node
+    const int* soff;       // curve -> first slot
     const double* h;
-    const double* xi;
+    int* gcell;            // per slot: bilinear cell r*nx + i of the row's node
+    double* glx;           // per slot: lambda_x, lambda_y of the row's node
+    double* gly;
+    const double* bnorm;   // per node
+    const double* fval;    // per node
+    const double* xi;      // per node (setup of the gather descriptors)
     const double* eta;
-    const double* bnorm;
-    const double* fval;
-    double* v;
-    double* scr;  // 3 planes of n_nodes
-    int n_nodes;
-    double mu, sig, theta, dt;
-    int paper_u0;  // 1: steady solve S u0 = F, values out
+    const double* fextra;  // load kernel only
+    double fx_scale;
+    double* Fl;            // per slot: load F (B)
+    double* srow;          // 3 planes per slot: S sub/diag/super (B)
+    double* fac;           // 4 planes per slot: cp, vp, ip, lp
+    double* v;             // per node: curve values
+    int n_slots;
+    double mu, sig, td, dt;
+    int paper;             // steady solve S u0 = F (no mass term, values out)
 };
 
-__device__ __forceinline__ double gather(const double* __restrict__ u, int nx, int ny, double xi,
-                                         double eta)
+// Work items: a block of BS threads takes BS/T curves of the same block size
+// T (a power of two, 32 <= T <= BS); sub-block k of the item owns curve
+// item_curve[item*(BS/32) + k] (-1: empty).  T is uniform per block, so every
+// __syncthreads below is reached by the whole block.
+template <int BS>
+struct Items {
+    static constexpr int LMAX = BS == 256 ? 8 : BS == 512 ? 9 : 10;
+    static constexpr int NF = 2 * LMAX + 2;  // per-thread constants: cpL, k1[LMAX], k2[LMAX], 1/B
+    static constexpr int MAXC = BS / 32;
+};
+
+struct BlockChunk {
+    int line, base, n, m, c, s, cnt, so, T, lt;
+    bool active;
+};
+
+template <int BS>
+__device__ __forceinline__ void item_chunk(const CurveArgs& a, const int* item_T,
+                                           const int* item_curve, BlockChunk& b)
 {
-    int i = (int)floor(xi), r = (int)floor(eta);
-    i = i > nx - 2 ? nx - 2 : (i < 0 ? 0 : i);
-    r = r > ny - 2 ? ny - 2 : (r < 0 ? 0 : r);
-    double lx = xi - i, ly = eta - r;
-    const double* r0 = u + (size_t)r * nx + i;
+    b.T = item_T[blockIdx.x];
+    int L = __ffs(b.T) - 1;
+    int sb = threadIdx.x >> L;
+    b.lt = threadIdx.x & (b.T - 1);
+    b.line = item_curve[blockIdx.x * Items<BS>::MAXC + sb];
+    b.active = b.line >= 0;
+    b.base = b.n = b.m = b.c = b.s = b.cnt = b.so = 0;
+    if (!b.active) return;
+    b.base = a.off[b.line];
+    b.n = a.off[b.line + 1] - b.base - 1;
+    b.m = b.n - 1;
+    b.c = b.m > 0 ? (b.m + b.T - 1) / b.T : 0;
+    b.s = b.lt * b.c;
+    b.cnt = b.m > 0 ? max(0, min(b.m, b.s + b.c) - b.s) : 0;
+    b.so = a.soff[b.line];
+}
+
+__device__ __forceinline__ double gather_at(const double* __restrict__ u, int nx, int cell,
+                                            double lx, double ly)
+{
+    const double* r0 = u + cell;
     double p11 = __ldg(r0), p12 = __ldg(r0 + 1), p21 = __ldg(r0 + nx), p22 = __ldg(r0 + nx + 1);
     double b = p11 + lx * (p12 - p11);
     double t = p21 + lx * (p22 - p21);
     return b + ly * (t - b);
 }
 
-template <int FAM>
-__device__ __forceinline__ void node_vals(const LineArgs& a, const double* __restrict__ u, int base,
-                                          int n, int k, double& uk, double& bk, double& fk)
+// gather descriptors of every row's node, in slot layout (setup)
+template <int BS>
+__global__ void __launch_bounds__(BS) k_curve_gdesc(CurveArgs a, const int* item_T,
+                                                    const int* item_curve)
 {
-    int g = base + k;
-    if (k == 0 || k == n || a.paper_u0) uk = 0.0;
-    else uk = gather(u, a.nx, a.ny, __ldg(a.xi + g), __ldg(a.eta + g));
-    if (FAM == 0) {
-        bk = __ldg(a.bnorm + g);
-        fk = __ldg(a.fval + g);
-        if (a.fextra) fk += a.fx_scale * gather(a.fextra, a.nx, a.ny, __ldg(a.xi + g), __ldg(a.eta + g));
-    } else {
-        bk = 0.0;
-        fk = 0.0;
+    BlockChunk b;
+    item_chunk<BS>(a, item_T, item_curve, b);
+    for (int j = 0; j < b.cnt; ++j) {
+        int node = b.base + b.s + j + 1;
+        double x = a.xi[node], y = a.eta[node];
+        int i = (int)floor(x), r = (int)floor(y);
+        i = i > a.nx - 2 ? a.nx - 2 : (i < 0 ? 0 : i);
+        r = r > a.ny - 2 ? a.ny - 2 : (r < 0 ? 0 : r);
+        size_t sl = b.so + (size_t)j * b.T + b.lt;
+        a.gcell[sl] = r * a.nx + i;
+        a.glx[sl] = x - i;
+        a.gly[sl] = y - r;
     }
 }
 
-template <int FAM>
-__global__ void __launch_bounds__(32 * kLineWarps) k_line_sweep(LineArgs a)
+// load F = M f on the B curves (f + fx_scale * fextra when an extra load is given)
+template <int BS>
+__global__ void __launch_bounds__(BS) k_curve_load(CurveArgs a, const int* item_T,
+                                                   const int* item_curve)
 {
-    if (a.state && a.state->done) return;
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= a.n_lines) return;
-    const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
-    int line = a.order[warp];
-    int base = a.off[line];
-    int n = a.off[line + 1] - base - 1;  // elements
-    double* __restrict__ v = a.v;
-    if (n < 2) {
-        if (lane <= n) v[base + lane] = 0.0;
-        return;
+    BlockChunk b;
+    item_chunk<BS>(a, item_T, item_curve, b);
+    if (b.cnt == 0) return;
+    const double Mo = a.h[b.line] / 6.0;
+    auto fat = [&](int k) {
+        int g = b.base + k;
+        double f = a.fval[g];
+        if (a.fextra) {
+            double x = a.xi[g], y = a.eta[g];
+            int i = (int)floor(x), r = (int)floor(y);
+            i = i > a.nx - 2 ? a.nx - 2 : (i < 0 ? 0 : i);
+            r = r > a.ny - 2 ? a.ny - 2 : (r < 0 ? 0 : r);
+            f += a.fx_scale * gather_at(a.fextra, a.nx, r * a.nx + i, x - i, y - r);
+        }
+        return f;
+    };
+    double f0 = fat(b.s), f1 = fat(b.s + 1);
+    for (int j = 0; j < b.cnt; ++j) {
+        double f2 = fat(b.s + j + 2);
+        a.Fl[b.so + (size_t)j * b.T + b.lt] = Mo * (f0 + 4.0 * f1 + f2);
+        f0 = f1;
+        f1 = f2;
     }
-    const int m = n - 1;  // unknowns = rows 0..m-1  (row q <-> node q+1)
-    const int c = (m + 31) >> 5;
-    const int s = lane * c;
-    const int e = min(m, s + c);
-    const bool has = s < m;
-    const double h = a.h[line];
-    const double Mo = h / 6.0, Md = 2.0 * h / 3.0, Ko = -1.0 / h, Kd = 2.0 / h;
-    const double td = a.paper_u0 ? 1.0 : a.theta * a.dt;
-    const double mw = a.paper_u0 ? 0.0 : 1.0;  // weight of the mass term in the system matrix
-    double* __restrict__ cpS = a.scr;
-    double* __restrict__ vpS = a.scr + a.n_nodes;
-    double* __restrict__ rpS = a.scr + 2 * (size_t)a.n_nodes;
+}
 
-    double cpL = 0, vpL = 0, rpL = 0;  // last row of this lane's chunk
+template <int BS, int FAM>
+__global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_T,
+                                                   const int* item_curve, double* lanec)
+{
+    constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
+    __shared__ double sA[BS], sB[BS], sC[BS];
+    BlockChunk b;
+    item_chunk<BS>(a, item_T, item_curve, b);
+    const int tid = threadIdx.x, lt = b.lt, T = b.T, L = __ffs(T) - 1, m = b.m, base = b.base;
+    const bool has = b.cnt > 0;
+    const size_t NS = a.n_slots;
+    double cpL = 0, vpL = 0;
     if (has) {
-        double u0, b0, f0, u1, b1, f1, u2, b2, f2;
-        node_vals<FAM>(a, u, base, n, s, u0, b0, f0);
-        node_vals<FAM>(a, u, base, n, s + 1, u1, b1, f1);
-        double cpp = 0, vpp = 0, rpp = 0;
-        for (int q = s; q < e; ++q) {
-            node_vals<FAM>(a, u, base, n, q + 2, u2, b2, f2);
-            double Ssub, Sdia, Ssup, F;
+        const double h = a.h[b.line];
+        const double Mo = h / 6.0, Md = 2.0 * h / 3.0, Ko = -1.0 / h, Kd = 2.0 / h;
+        const double mw = a.paper ? 0.0 : 1.0, td = a.td;
+        double b0 = 0, b1 = 0, b2 = 0;
+        if (FAM == 0) {
+            b0 = a.bnorm[base + b.s];
+            b1 = a.bnorm[base + b.s + 1];
+        }
+        double cpp = 0, vpp = 0;
+        for (int j = 0; j < b.cnt; ++j) {
+            const int q = b.s + j;
+            const size_t sl = b.so + (size_t)j * T + lt;
+            double Ssub, Sdia, Ssup;
             if (FAM == 0) {
+                b2 = a.bnorm[base + q + 2];
                 double Csub = -(b0 * (1.0 / 6.0) + b1 * (1.0 / 3.0));
                 double Cdia = (b0 - b2) * (1.0 / 6.0);
                 double Csup = b1 * (1.0 / 3.0) + b2 * (1.0 / 6.0);
                 Ssub = a.mu * Ko + Csub + a.sig * Mo;
                 Sdia = a.mu * Kd + Cdia + a.sig * Md;
                 Ssup = a.mu * Ko + Csup + a.sig * Mo;
-                F = Mo * (f0 + 4.0 * f1 + f2);
+                a.srow[sl] = Ssub;
+                a.srow[NS + sl] = Sdia;
+                a.srow[2 * NS + sl] = Ssup;
+                b0 = b1;
+                b1 = b2;
             } else {
                 Ssub = a.mu * Ko;
                 Sdia = a.mu * Kd;
                 Ssup = Ssub;
-                F = 0.0;
             }
-            double r = F - (Ssub * u0 + Sdia * u1 + Ssup * u2);
             double A = (q == 0) ? 0.0 : mw * Mo + td * Ssub;
             double B = mw * Md + td * Sdia;
             double C = (q == m - 1) ? 0.0 : mw * Mo + td * Ssup;
-            double cp, vp, rp;
-            if (q == s) {
-                double inv = 1.0 / B;
-                cp = C * inv;
-                vp = A * inv;
-                rp = r * inv;
+            double ip, cp, vp, lp;
+            if (j == 0) {
+                ip = 1.0 / B;
+                cp = C * ip;
+                vp = A * ip;
+                lp = 0.0;
             } else {
-                double inv = 1.0 / (B - A * cpp);
-                cp = C * inv;
-                vp = -A * vpp * inv;
-                rp = (r - A * rpp) * inv;
+                ip = 1.0 / (B - A * cpp);
+                cp = C * ip;
+                vp = -A * vpp * ip;
+                lp = A * ip;
             }
-            int g = base + q;
-            cpS[g] = cp;
-            vpS[g] = vp;
-            rpS[g] = rp;
-            v[g + 1] = u1;  // state on the curve; the increment is added below
+            a.fac[sl] = cp;
+            a.fac[NS + sl] = vp;
+            a.fac[2 * NS + sl] = ip;
+            a.fac[3 * NS + sl] = lp;
             cpp = cp;
             vpp = vp;
-            rpp = rp;
-            u0 = u1;
-            b0 = b1;
-            f0 = f1;
-            u1 = u2;
-            b1 = b2;
-            f1 = f2;
         }
         cpL = cpp;
         vpL = vpp;
-        rpL = rpp;
     }
-    // upward sweep: x_s = rho - kap * G_j - nu * G_{j-1}
-    double rho = 0.0, kap = -1.0, nu = 0.0;
-    if (has) {
-        for (int q = e - 2; q >= s; --q) {
-            int g = base + q;
-            double cp = cpS[g];
-            rho = rpS[g] - cp * rho;
-            kap = -cp * kap;
-            nu = vpS[g] - cp * nu;
-        }
-    } else {
-        kap = 0.0;
+    // fixed part of the upward pass: x_s = rho - kap G_t - nu G_{t-1}
+    double kap = has ? -1.0 : 0.0, nu = 0.0;
+    for (int j = b.cnt - 2; j >= 0; --j) {
+        const size_t sl = b.so + (size_t)j * T + lt;
+        double cp = a.fac[sl];
+        kap = -cp * kap;
+        nu = a.fac[NS + sl] - cp * nu;
     }
-    double rhoN = __shfl_down_sync(0xffffffffu, rho, 1);
-    double kapN = __shfl_down_sync(0xffffffffu, kap, 1);
-    double nuN = __shfl_down_sync(0xffffffffu, nu, 1);
-    if (lane == 31) rhoN = kapN = nuN = 0.0;
-    // reduced system over the chunk ends G_j (one equation per lane)
+    sA[tid] = kap;
+    sB[tid] = nu;
+    __syncthreads();
+    double kapN = lt + 1 < T ? sA[tid + 1] : 0.0;
+    double nuN = lt + 1 < T ? sB[tid + 1] : 0.0;
+    __syncthreads();
     double A = has ? vpL : 0.0;
     double B = has ? 1.0 - cpL * nuN : 1.0;
     double C = has ? -cpL * kapN : 0.0;
-    double R = has ? rpL - cpL * rhoN : 0.0;
+    double* Lc = lanec + (size_t)blockIdx.x * NF * BS;
+    Lc[tid] = cpL;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        double Am = __shfl_up_sync(0xffffffffu, A, d), Bm = __shfl_up_sync(0xffffffffu, B, d);
-        double Cm = __shfl_up_sync(0xffffffffu, C, d), Rm = __shfl_up_sync(0xffffffffu, R, d);
-        double Ap = __shfl_down_sync(0xffffffffu, A, d), Bp = __shfl_down_sync(0xffffffffu, B, d);
-        double Cp = __shfl_down_sync(0xffffffffu, C, d), Rp = __shfl_down_sync(0xffffffffu, R, d);
-        double k1 = lane >= d ? A / Bm : 0.0;
-        double k2 = lane + d < 32 ? C / Bp : 0.0;
-        double nA = lane >= d ? -Am * k1 : 0.0;
-        double nC = lane + d < 32 ? -Cp * k2 : 0.0;
-        B = B - (lane >= d ? Cm * k1 : 0.0) - (lane + d < 32 ? Ap * k2 : 0.0);
-        R = R - (lane >= d ? Rm * k1 : 0.0) - (lane + d < 32 ? Rp * k2 : 0.0);
+    for (int l = 0; l < LMAX; ++l) {
+        const int d = 1 << l;
+        sA[tid] = A;
+        sB[tid] = B;
+        sC[tid] = C;
+        __syncthreads();
+        bool use = l < L;
+        bool lo = use && lt >= d, hi = use && lt + d < T;
+        double Am = lo ? sA[tid - d] : 0.0, Bm = lo ? sB[tid - d] : 1.0, Cm = lo ? sC[tid - d] : 0.0;
+        double Ap = hi ? sA[tid + d] : 0.0, Bp = hi ? sB[tid + d] : 1.0, Cp = hi ? sC[tid + d] : 0.0;
+        __syncthreads();
+        double k1 = lo ? A / Bm : 0.0, k2 = hi ? C / Bp : 0.0;
+        double nA = lo ? -Am * k1 : (use ? 0.0 : A), nC = hi ? -Cp * k2 : (use ? 0.0 : C);
+        B = B - (lo ? Cm * k1 : 0.0) - (hi ? Ap * k2 : 0.0);
         A = nA;
         C = nC;
+        Lc[(1 + l) * BS + tid] = k1;
+        Lc[(1 + LMAX + l) * BS + tid] = k2;
     }
-    double G = R / B;
-    double Gm = __shfl_up_sync(0xffffffffu, G, 1);
-    if (lane == 0) Gm = 0.0;
-    if (has) {
-        const double w = a.paper_u0 ? 1.0 : a.dt;
-        double x = G;
-        int g = base + e - 1;
-        v[g + 1] = (a.paper_u0 ? 0.0 : v[g + 1]) + w * x;
-        for (int q = e - 2; q >= s; --q) {
-            g = base + q;
-            x = rpS[g] - cpS[g] * x - vpS[g] * Gm;
-            v[g + 1] = (a.paper_u0 ? 0.0 : v[g + 1]) + w * x;
+    Lc[(NF - 1) * BS + tid] = 1.0 / B;
+}
+
+template <int BS, int FAM>
+__global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item_T,
+                                                    const int* item_curve, const double* lanec)
+{
+    constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
+    if (a.state && a.state->done) return;
+    __shared__ double sR[2][BS];
+    const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
+    double* __restrict__ v = a.v;
+    BlockChunk b;
+    item_chunk<BS>(a, item_T, item_curve, b);
+    const int tid = threadIdx.x, lt = b.lt, T = b.T, L = __ffs(T) - 1;
+    if (b.active && b.n < 2 && lt <= b.n) v[b.base + lt] = 0.0;
+    const int base = b.base, n = b.n, s = b.s, cnt = b.cnt;
+    const size_t NS = a.n_slots, so = b.so;
+    const bool paper = a.paper != 0;
+    auto uslot = [&](int sl) -> double {
+        return gather_at(u, a.nx, __ldg(a.gcell + sl), __ldg(a.glx + sl), __ldg(a.gly + sl));
+    };
+    double rp[kCmax], ur[kCmax];
+    double rpp = 0.0;
+    const int so32 = (int)so;
+    const double* __restrict__ cpP = a.fac;
+    const double* __restrict__ vpP = a.fac + NS;
+    if (cnt > 0) {
+        const double muh = a.mu / a.h[b.line];
+        // node s (row s-1: the previous thread's last row) and node s+1 (own row 0)
+        double u0 = (paper || s == 0) ? 0.0 : uslot(so32 + (b.c - 1) * T + (lt - 1));
+        double u1 = paper ? 0.0 : uslot(so32 + lt);
+#pragma unroll
+        for (int j = 0; j < kCmax; ++j) {
+            if (j < cnt) {
+                const int sl = so32 + j * T + lt;
+                double u2;  // node s+j+2 = row s+j+1
+                if (paper) u2 = 0.0;
+                else if (j + 1 < cnt) u2 = uslot(sl + T);
+                else if (s + cnt < b.m) u2 = uslot(so32 + lt + 1);  // next thread's row 0
+                else u2 = 0.0;                                      // the curve's end node
+                double r;
+                if (FAM == 0)
+                    r = __ldg(a.Fl + sl) - (__ldg(a.srow + sl) * u0 + __ldg(a.srow + NS + sl) * u1 +
+                                            __ldg(a.srow + 2 * NS + sl) * u2);
+                else
+                    r = muh * ((u0 + u2) - 2.0 * u1);
+                rpp = r * __ldg(a.fac + 2 * NS + sl) - __ldg(a.fac + 3 * NS + sl) * rpp;
+                rp[j] = rpp;
+                ur[j] = u1;
+                u0 = u1;
+                u1 = u2;
+            }
         }
     }
-    if (lane == 0) {
+    // upward pass over the chunk: rho for its first row
+    double rho = 0.0;
+#pragma unroll
+    for (int j = kCmax - 2; j >= 0; --j)
+        if (j <= cnt - 2) rho = rp[j] - __ldg(cpP + so32 + j * T + lt) * rho;
+    sR[0][tid] = rho;
+    __syncthreads();
+    double rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.0;
+    const double* Lc = lanec + (size_t)blockIdx.x * NF * BS;
+    double R = cnt > 0 ? rpp - Lc[tid] * rhoN : 0.0;
+    int buf = 1;
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l) {
+        const int d = 1 << l;
+        sR[buf][tid] = R;
+        __syncthreads();
+        if (l < L) {
+            double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
+            double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
+            R = R - Lc[(1 + l) * BS + tid] * Rm - Lc[(1 + LMAX + l) * BS + tid] * Rp;
+        }
+        buf ^= 1;
+    }
+    double G = R * Lc[(NF - 1) * BS + tid];
+    sR[buf][tid] = G;
+    __syncthreads();
+    double Gm = lt > 0 ? sR[buf][tid - 1] : 0.0;
+    const double w = paper ? 1.0 : a.dt;
+    double x = G;
+#pragma unroll
+    for (int j = kCmax - 1; j >= 0; --j) {
+        if (j < cnt) {
+            const int sl = so32 + j * T + lt;
+            if (j < cnt - 1) x = rp[j] - __ldg(cpP + sl) * x - __ldg(vpP + sl) * Gm;
+            v[base + s + j + 1] = (paper ? 0.0 : ur[j]) + w * x;
+        }
+    }
+    if (b.active && n >= 2 && lt == 0) {
         v[base] = 0.0;
         v[base + n] = 0.0;
     }
@@ -218,9 +371,8 @@ __global__ void __launch_bounds__(32 * kLineWarps) k_line_sweep(LineArgs a)
 struct GridArgs {
     int nx, ny;
     const uint8_t* ntype;
-    const int* cg;
-    const double* ct;
-    const double* cw;
+    const int* mg;     // [4 N] first node of each crossed segment (boundary: 0 with zero weights)
+    const double* mc;  // [8 N] weights of v[g], v[g+1] for the 4 crossings
     const double* v;
     double* out_even;  // written buffer by parity of the step counter (or fixed)
     double* out_odd;
@@ -231,11 +383,24 @@ struct GridArgs {
     double* partial;   // [2 * gridDim.x] sums of (u - u_prev)^2 and u^2
 };
 
-__device__ __forceinline__ double cross_val(const double* __restrict__ v, int g, double t)
+// combined weights of the curve -> grid map (setup): the row value
+// (1-w) vL + w vR and the column value, each crossing v = (1-t) v[g] + t v[g+1],
+// averaged, written as 8 products with the curve values
+__global__ void k_map_coef(long long N, const uint8_t* ntype, const int* cg, const double* ct,
+                           const double* cw, int* mg, double* mc)
 {
-    if (g < 0) return 0.0;
-    double a = __ldg(v + g), b = __ldg(v + g + 1);
-    return a + t * (b - a);
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    for (int q = 0; q < 4; ++q) {
+        int g = cg[4 * k + q];
+        double t = ct[4 * k + q];
+        double w = cw[2 * k + (q >> 1)];
+        double side = (q & 1) ? w : 1.0 - w;  // left/down: 1-w, right/up: w
+        bool ok = ntype[k] == kInterior && g >= 0;
+        mg[4 * k + q] = ok ? g : 0;
+        mc[8 * k + 2 * q] = ok ? 0.5 * side * (1.0 - t) : 0.0;
+        mc[8 * k + 2 * q + 1] = ok ? 0.5 * side * t : 0.0;
+    }
 }
 
 template <bool NORMS>
@@ -245,25 +410,28 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_map(GridArgs a)
     int it = a.state ? a.state->iter : 0;
     double* __restrict__ out = ((it + a.parity_shift) & 1) ? a.out_odd : a.out_even;
     const double* __restrict__ prev = (it & 1) ? a.prev_odd : a.prev_even;
-    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long N = (long long)a.nx * a.ny;
+    const double* __restrict__ v = a.v;
+    const long long N = (long long)a.nx * a.ny;
     double dd = 0.0, uu = 0.0;
-    if (k < N) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
+         k += (long long)gridDim.x * blockDim.x) {
         double val = 0.0;
         if (a.ntype[k] == kInterior) {
-            int4 g = *reinterpret_cast<const int4*>(a.cg + 4 * k);
-            double2 t01 = *reinterpret_cast<const double2*>(a.ct + 4 * k);
-            double2 t23 = *reinterpret_cast<const double2*>(a.ct + 4 * k + 2);
-            double2 w = *reinterpret_cast<const double2*>(a.cw + 2 * k);
-            double vL = cross_val(a.v, g.x, t01.x), vR = cross_val(a.v, g.y, t01.y);
-            double vD = cross_val(a.v, g.z, t23.x), vU = cross_val(a.v, g.w, t23.y);
-            double row = vL + w.x * (vR - vL);
-            double col = vD + w.y * (vU - vD);
-            val = 0.5 * (row + col);
+            int4 g = *reinterpret_cast<const int4*>(a.mg + 4 * k);
+            const double2* c = reinterpret_cast<const double2*>(a.mc + 8 * k);
+            double2 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
+            val = c0.x * __ldg(v + g.x);
+            val = fma(c0.y, __ldg(v + g.x + 1), val);
+            val = fma(c1.x, __ldg(v + g.y), val);
+            val = fma(c1.y, __ldg(v + g.y + 1), val);
+            val = fma(c2.x, __ldg(v + g.z), val);
+            val = fma(c2.y, __ldg(v + g.z + 1), val);
+            val = fma(c3.x, __ldg(v + g.w), val);
+            val = fma(c3.y, __ldg(v + g.w + 1), val);
             if (NORMS) {
                 double dlt = val - prev[k];
-                dd = dlt * dlt;
-                uu = val * val;
+                dd = fma(dlt, dlt, dd);
+                uu = fma(val, val, uu);
             }
         }
         out[k] = val;
@@ -365,39 +533,185 @@ __global__ void k_reset(IterState* st)
 
 }  // namespace
 
-adr_status launch_line_sweep_ex(Problem* p, int fam, double theta, double dt, double sig,
-                                const double* u_even, const double* u_odd, bool use_state,
-                                const double* fextra, double fx_scale, int paper_u0)
+static CurveArgs curve_args(Problem* p, int fam)
 {
     Family& F = p->fam[fam];
-    LineArgs a;
+    CurveArgs a{};
     a.nx = p->grid.nx;
     a.ny = p->grid.ny;
-    a.u_even = u_even;
-    a.u_odd = u_odd;
-    a.fextra = fam == 0 ? fextra : nullptr;
-    a.fx_scale = fx_scale;
-    a.state = use_state ? p->state : nullptr;
-    a.n_lines = F.n_lines;
-    a.order = F.order;
     a.off = F.off;
+    a.soff = F.soff;
     a.h = F.h;
-    a.xi = F.xi;
-    a.eta = F.eta;
+    a.gcell = F.gcell;
+    a.glx = F.glx;
+    a.gly = F.gly;
     a.bnorm = F.bnorm;
     a.fval = F.fval;
+    a.xi = F.xi;
+    a.eta = F.eta;
+    a.Fl = F.Fl;
+    a.srow = F.srow;
+    a.fac = F.fac;
     a.v = F.v;
-    a.scr = F.scr;
-    a.n_nodes = F.n_nodes;
+    a.n_slots = F.n_slots;
     a.mu = p->mu;
+    return a;
+}
+
+// split the curves of a family into work items, assign slots and build the
+// gather descriptors (host orchestration, at setup).  A curve of m unknowns
+// gets the smallest block size T >= 32 (power of two) with T * kCmax >= m;
+// items of BS = 256 threads hold 256/T curves of one T, curves with T > 256
+// go to items of BS = 1024.  Items are ordered longest curves first.
+adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
+{
+    Family& F = p->fam[fam];
+    std::vector<int> order(F.n_lines), Tof(F.n_lines);
+    ADR_CUDA_TRY(cudaMemcpy(order.data(), F.order, sizeof(int) * F.n_lines, cudaMemcpyDeviceToHost));
+    std::vector<int> byT[11];  // index log2(T)
+    for (int l : order) {
+        int m = off[l + 1] - off[l] - 2;
+        int T = 32, lg = 5;
+        while (T < 1024 && (long long)T * kCmax < m) {
+            T *= 2;
+            lg++;
+        }
+        if ((long long)T * kCmax < m) {
+            set_error("a curve has more than 16384 unknowns");
+            return ADR_EINVAL;
+        }
+        byT[lg].push_back(l);
+        Tof[l] = T;
+    }
+    std::vector<int> soff(F.n_lines + 1, 0);
+    long long tot = 0;
+    for (int l = 0; l < F.n_lines; ++l) {
+        soff[l] = (int)tot;
+        int m = off[l + 1] - off[l] - 2;
+        if (m > 0) tot += (long long)Tof[l] * ((m + Tof[l] - 1) / Tof[l]);
+        if (tot > 0x7fffffffLL) {
+            set_error("too many curve rows");
+            return ADR_EINVAL;
+        }
+    }
+    soff[F.n_lines] = (int)tot;
+    F.n_slots = (int)tot + 1;
+    size_t NS = F.n_slots;
+    TRY_S(dev_alloc(p, &F.soff, F.n_lines + 1));
+    ADR_CUDA_TRY(cudaMemcpy(F.soff, soff.data(), sizeof(int) * soff.size(), cudaMemcpyHostToDevice));
+    TRY_S(dev_alloc(p, &F.gcell, NS));
+    TRY_S(dev_alloc(p, &F.glx, NS));
+    TRY_S(dev_alloc(p, &F.gly, NS));
+    TRY_S(dev_alloc(p, &F.fac, 4 * NS));
+    if (fam == 0) {
+        TRY_S(dev_alloc(p, &F.Fl, NS));
+        TRY_S(dev_alloc(p, &F.srow, 3 * NS));
+    }
+    CurveArgs a = curve_args(p, fam);
+    cudaStream_t st = p->stream;
+    for (int k = 0; k < kItemSets; ++k) {
+        const int BS = 256 << k, maxc = BS / 32, nf = 2 * (8 + k) + 2;
+        std::vector<int> iT, icv;
+        for (int lg = 8 + k; lg >= (k == 0 ? 5 : 8 + k); --lg) {
+            const std::vector<int>& L = byT[lg];
+            int T = 1 << lg, per = BS / T;
+            for (size_t q = 0; q < L.size(); q += per) {
+                iT.push_back(T);
+                for (int r = 0; r < maxc; ++r)
+                    icv.push_back((r < per && q + r < L.size()) ? L[q + r] : -1);
+            }
+        }
+        ItemSet& I = F.iset[k];
+        I.BS = BS;
+        I.count = (int)iT.size();
+        if (I.count == 0) continue;
+        TRY_S(dev_alloc(p, &I.T, I.count));
+        TRY_S(dev_alloc(p, &I.curve, (size_t)I.count * maxc));
+        TRY_S(dev_alloc(p, &I.lanec, (size_t)I.count * nf * BS));
+        ADR_CUDA_TRY(cudaMemcpy(I.T, iT.data(), sizeof(int) * iT.size(), cudaMemcpyHostToDevice));
+        ADR_CUDA_TRY(cudaMemcpy(I.curve, icv.data(), sizeof(int) * icv.size(), cudaMemcpyHostToDevice));
+        if (BS == 256) k_curve_gdesc<256><<<I.count, 256, 0, st>>>(a, I.T, I.curve);
+        else if (BS == 512) k_curve_gdesc<512><<<I.count, 512, 0, st>>>(a, I.T, I.curve);
+        else k_curve_gdesc<1024><<<I.count, 1024, 0, st>>>(a, I.T, I.curve);
+    }
+    ADR_CUDA_TRY(cudaGetLastError());
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    return ADR_OK;
+}
+
+adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper)
+{
+    Family& F = p->fam[fam];
+    if (F.prep_valid && F.prep_td == td && F.prep_sig == sig && F.prep_paper == paper) return ADR_OK;
+    CurveArgs a = curve_args(p, fam);
+    a.td = td;
     a.sig = sig;
-    a.theta = theta;
+    a.paper = paper;
+    cudaStream_t st = p->stream;
+#define ADR_PREP(BS_, I_)                                                                      \
+    if (I_.count) {                                                                            \
+        if (fam == 0) k_curve_prep<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec); \
+        else k_curve_prep<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec);         \
+    }
+    ADR_PREP(256, F.iset[0])
+    ADR_PREP(512, F.iset[1])
+    ADR_PREP(1024, F.iset[2])
+#undef ADR_PREP
+    ADR_CUDA_TRY(cudaGetLastError());
+    F.prep_valid = true;
+    F.prep_td = td;
+    F.prep_sig = sig;
+    F.prep_paper = paper;
+    return ADR_OK;
+}
+
+adr_status load_family(Problem* p, const double* fextra, double fx_scale)
+{
+    Family& F = p->fam[0];
+    if (!fextra && F.load_plain) return ADR_OK;
+    CurveArgs a = curve_args(p, 0);
+    a.fextra = fextra;
+    a.fx_scale = fx_scale;
+    cudaStream_t st = p->stream;
+    const ItemSet &I0 = F.iset[0], &I1 = F.iset[1], &I2 = F.iset[2];
+    if (I0.count) k_curve_load<256><<<I0.count, 256, 0, st>>>(a, I0.T, I0.curve);
+    if (I1.count) k_curve_load<512><<<I1.count, 512, 0, st>>>(a, I1.T, I1.curve);
+    if (I2.count) k_curve_load<1024><<<I2.count, 1024, 0, st>>>(a, I2.T, I2.curve);
+    ADR_CUDA_TRY(cudaGetLastError());
+    F.load_plain = fextra == nullptr;
+    return ADR_OK;
+}
+
+adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_even,
+                             const double* u_odd, bool use_state, int paper)
+{
+    Family& F = p->fam[fam];
+    CurveArgs a = curve_args(p, fam);
+    a.u_even = u_even;
+    a.u_odd = u_odd;
+    a.state = use_state ? p->state : nullptr;
     a.dt = dt;
-    a.paper_u0 = paper_u0;
-    int threads = 32 * kLineWarps;
-    int blocks = (F.n_lines + kLineWarps - 1) / kLineWarps;
-    if (fam == 0) k_line_sweep<0><<<blocks, threads, 0, p->stream>>>(a);
-    else k_line_sweep<1><<<blocks, threads, 0, p->stream>>>(a);
+    a.paper = paper;
+    cudaStream_t st = p->stream;
+#define ADR_SOLVE(BS_, I_)                                                                      \
+    if (I_.count) {                                                                             \
+        if (fam == 0) k_curve_solve<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec); \
+        else k_curve_solve<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec);         \
+    }
+    ADR_SOLVE(1024, F.iset[2])
+    ADR_SOLVE(512, F.iset[1])
+    ADR_SOLVE(256, F.iset[0])
+#undef ADR_SOLVE
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+adr_status launch_map_coef(Problem* p, int fam)
+{
+    Family& F = p->fam[fam];
+    long long N = p->N;
+    k_map_coef<<<(int)((N + 255) / 256), 256, 0, p->stream>>>(N, p->ntype, F.cg, F.ct, F.cw, F.mg,
+                                                            F.mc);
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }
@@ -411,9 +725,8 @@ adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out
     a.nx = p->grid.nx;
     a.ny = p->grid.ny;
     a.ntype = p->ntype;
-    a.cg = F.cg;
-    a.ct = F.ct;
-    a.cw = F.cw;
+    a.mg = F.mg;
+    a.mc = F.mc;
     a.v = F.v;
     a.out_even = out_even;
     a.out_odd = out_odd;
@@ -422,14 +735,20 @@ adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out
     a.state = use_state ? p->state : nullptr;
     a.parity_shift = parity_shift;
     a.partial = p->partial;
-    int blocks = (int)((p->N + kGridThreads - 1) / kGridThreads);
+    int blocks = grid_map_blocks(p);
     if (norms) k_grid_map<true><<<blocks, kGridThreads, 0, p->stream>>>(a);
     else k_grid_map<false><<<blocks, kGridThreads, 0, p->stream>>>(a);
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }
 
-int grid_map_blocks(const Problem* p) { return (int)((p->N + kGridThreads - 1) / kGridThreads); }
+// grid-stride map: at most 8 blocks of 256 threads per SM
+int grid_map_blocks(const Problem* p)
+{
+    long long need = (p->N + kGridThreads - 1) / kGridThreads;
+    long long cap = 8LL * (p->n_sm > 0 ? p->n_sm : 152);
+    return (int)(need < cap ? need : cap);
+}
 
 adr_status launch_check_ex(Problem* p, double tol, int max_iter,
                            cudaGraphConditionalHandle handle, bool use_cond)
