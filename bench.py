@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--other-prec", action=argparse.BooleanOptionalAction, default=True)
     return ap.parse_args()
 
 
@@ -290,6 +291,29 @@ def run_ours(args):
     roof.update({"kernel": KERNELS[k], "kernel_ms": kms[k], "units_per_launch": units[k],
                  "all_kernels_ms": dict(zip(KERNELS, kms))})
     launches = int(sum(5 * it + 3 for it in iters))
+    # the other precision mode on the same workload: time to tol and agreement
+    other = {}
+    if args.other_prec:
+        oprec = ADR_FP32_REFINE if prec == ADR_FP64 else ADR_FP64
+        s2 = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=oprec)
+        s2.solve_stationary()
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        reps, it2, d2 = 3, [], 0.0
+        for _ in range(reps):
+            u2, _, st2, _ = s2.solve_stationary()
+            it2.append(st2["iters"])
+            d2 += st2["line_dofs"]
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms2 = f0.elapsed_time(f1)
+        diff = float((u2 - u).abs().max() / u.abs().max())
+        other = {"prec": "fp32+refine" if oprec == ADR_FP32_REFINE else "fp64",
+                 "ms_per_step": ms2 / reps, "value": d2 / (ms2 / 1e3), "iters_per_solve": it2,
+                 "kernels_ms": dict(zip(KERNELS, s2.time_kernels(reps=20))),
+                 "max_rel_diff_vs_this_mode": diff}
+        s2.close()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -303,6 +327,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "roofline": roof, "gpu_launches": launches, "clocks": clk,
     }
+    if other:
+        line["other_precision"] = other
     if not args.no_e2e:
         line["e2e"] = e2e(args, prob, dev, prec)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

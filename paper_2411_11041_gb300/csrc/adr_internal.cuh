@@ -39,6 +39,7 @@ struct ItemSet {
     int* T = nullptr;         // [count] block size of the item's curves
     int* curve = nullptr;     // [count * BS/32] curve indices (-1 empty)
     double* lanec = nullptr;  // [count * (2 log2 BS + 2) * BS] reduced-system constants
+    float* lanec32 = nullptr; // the same in FP32 (reduced-precision mode)
 };
 
 // One curve family in structure-of-arrays form.  Curves are stored back to
@@ -65,6 +66,7 @@ struct Family {
     double* Fl = nullptr;     // [n_slots] load F = M f (B)
     double* srow = nullptr;   // [3*n_slots] S sub/diag/super (B)
     double* fac = nullptr;    // [4*n_slots] elimination factors cp, vp, ip, lp
+    float* fac32 = nullptr;   // [4*n_slots] the same in FP32 (reduced-precision mode)
     ItemSet iset[3];          // BS = 256, 512, 1024
     int* mg = nullptr;        // [4*N] curve -> grid map: segment of each crossing
     double* mc = nullptr;     // [8*N] combined weights of the map

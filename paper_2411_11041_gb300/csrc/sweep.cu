@@ -59,6 +59,7 @@ struct CurveArgs {
     double* Fl;            // per slot: load F (B)
     double* srow;          // 3 planes per slot: S sub/diag/super (B)
     double* fac;           // 4 planes per slot: cp, vp, ip, lp
+    float* fac32;          // the same factors rounded to FP32 (reduced-precision mode)
     double* v;             // per node: curve values
     int n_slots;
     double mu, sig, td, dt;
@@ -164,7 +165,8 @@ __global__ void __launch_bounds__(BS) k_curve_load(CurveArgs a, const int* item_
 
 template <int BS, int FAM>
 __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_T,
-                                                   const int* item_curve, double* lanec)
+                                                   const int* item_curve, double* lanec,
+                                                   float* lanec32)
 {
     constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
     __shared__ double sA[BS], sB[BS], sC[BS];
@@ -225,6 +227,12 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
             a.fac[NS + sl] = vp;
             a.fac[2 * NS + sl] = ip;
             a.fac[3 * NS + sl] = lp;
+            if (a.fac32) {
+                a.fac32[sl] = (float)cp;
+                a.fac32[NS + sl] = (float)vp;
+                a.fac32[2 * NS + sl] = (float)ip;
+                a.fac32[3 * NS + sl] = (float)lp;
+            }
             cpp = cp;
             vpp = vp;
         }
@@ -271,6 +279,10 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
         Lc[(1 + LMAX + l) * BS + tid] = k2;
     }
     Lc[(NF - 1) * BS + tid] = 1.0 / B;
+    if (lanec32) {
+        float* L32 = lanec32 + (size_t)blockIdx.x * NF * BS;
+        for (int f = 0; f < NF; ++f) L32[f * BS + tid] = (float)Lc[f * BS + tid];
+    }
 }
 
 template <int BS, int FAM>
@@ -362,6 +374,173 @@ __global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item
             v[base + s + j + 1] = (paper ? 0.0 : ur[j]) + w * x;
         }
     }
+    if (b.active && n >= 2 && lt == 0) {
+        v[base] = 0.0;
+        v[base + n] = 0.0;
+    }
+}
+
+// ----------------------------------------------- FP32 solve + FP64 refinement
+// Reduced-precision mode: x0 = A32^-1 r with the FP32-rounded factors, the
+// residual rho = r - A x0 in FP64 (A's entries rebuilt in FP64), x1 = A32^-1 rho,
+// x = x0 + x1.  The right-hand side, the residual and the state update stay in
+// FP64; only the two eliminations run in FP32.
+
+// one FP32 pass of the partitioned elimination over the calling thread's rows;
+// every thread of the block must call it (it synchronises); returns in x the
+// thread's solution rows and in *gprev the previous thread's last unknown
+template <int BS>
+__device__ __forceinline__ void elim32(const float (&rhs)[kCmax], float (&x)[kCmax], int cnt,
+                                       int so32, int T, int lt, int L, const float* __restrict__ f32,
+                                       size_t NS, const float* __restrict__ L32, float (*sR)[BS],
+                                       float* gprev)
+{
+    constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
+    const int tid = threadIdx.x;
+    float rp[kCmax];
+    float rpp = 0.f;
+#pragma unroll
+    for (int j = 0; j < kCmax; ++j)
+        if (j < cnt) {
+            const int sl = so32 + j * T + lt;
+            rpp = rhs[j] * __ldg(f32 + 2 * NS + sl) - __ldg(f32 + 3 * NS + sl) * rpp;
+            rp[j] = rpp;
+        }
+    float rho = 0.f;
+#pragma unroll
+    for (int j = kCmax - 2; j >= 0; --j)
+        if (j <= cnt - 2) rho = rp[j] - __ldg(f32 + so32 + j * T + lt) * rho;
+    __syncthreads();  // sR may still be read by a previous pass
+    sR[0][tid] = rho;
+    __syncthreads();
+    float rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.f;
+    float R = cnt > 0 ? rpp - L32[tid] * rhoN : 0.f;
+    int buf = 1;
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l) {
+        const int d = 1 << l;
+        sR[buf][tid] = R;
+        __syncthreads();
+        if (l < L) {
+            float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
+            float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
+            R = R - L32[(1 + l) * BS + tid] * Rm - L32[(1 + LMAX + l) * BS + tid] * Rp;
+        }
+        buf ^= 1;
+    }
+    float G = R * L32[(NF - 1) * BS + tid];
+    sR[buf][tid] = G;
+    __syncthreads();
+    float Gm = lt > 0 ? sR[buf][tid - 1] : 0.f;
+    *gprev = Gm;
+    float xx = G;
+#pragma unroll
+    for (int j = kCmax - 1; j >= 0; --j) {
+        x[j] = 0.f;
+        if (j < cnt) {
+            const int sl = so32 + j * T + lt;
+            if (j < cnt - 1) xx = rp[j] - __ldg(f32 + sl) * xx - __ldg(f32 + NS + sl) * Gm;
+            x[j] = xx;
+        }
+    }
+}
+
+template <int BS, int FAM>
+__global__ void __launch_bounds__(BS) k_curve_solve_ref(CurveArgs a, const int* item_T,
+                                                        const int* item_curve, const float* lanec32)
+{
+    constexpr int NF = Items<BS>::NF;
+    if (a.state && a.state->done) return;
+    __shared__ float sR[2][BS];
+    __shared__ double sX[BS];
+    const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
+    double* __restrict__ v = a.v;
+    BlockChunk b;
+    item_chunk<BS>(a, item_T, item_curve, b);
+    const int tid = threadIdx.x, lt = b.lt, T = b.T, L = __ffs(T) - 1;
+    if (b.active && b.n < 2 && lt <= b.n) v[b.base + lt] = 0.0;
+    const int base = b.base, n = b.n, s = b.s, cnt = b.cnt, m = b.m;
+    const size_t NS = a.n_slots;
+    const int so32 = (int)b.so;
+    const bool paper = a.paper != 0;
+    const float* L32 = lanec32 + (size_t)blockIdx.x * NF * BS;
+    auto uslot = [&](int sl) -> double {
+        return gather_at(u, a.nx, __ldg(a.gcell + sl), __ldg(a.glx + sl), __ldg(a.gly + sl));
+    };
+    double r64[kCmax], ur[kCmax];
+    float r32[kCmax];
+    double muh = 0.0, h = 1.0;
+    if (cnt > 0) {
+        h = a.h[b.line];
+        muh = a.mu / h;
+        double u0 = (paper || s == 0) ? 0.0 : uslot(so32 + (b.c - 1) * T + (lt - 1));
+        double u1 = paper ? 0.0 : uslot(so32 + lt);
+#pragma unroll
+        for (int j = 0; j < kCmax; ++j) {
+            r64[j] = 0.0;
+            ur[j] = 0.0;
+            r32[j] = 0.f;
+            if (j < cnt) {
+                const int sl = so32 + j * T + lt;
+                double u2;
+                if (paper) u2 = 0.0;
+                else if (j + 1 < cnt) u2 = uslot(sl + T);
+                else if (s + cnt < m) u2 = uslot(so32 + lt + 1);
+                else u2 = 0.0;
+                double r;
+                if (FAM == 0)
+                    r = __ldg(a.Fl + sl) - (__ldg(a.srow + sl) * u0 + __ldg(a.srow + NS + sl) * u1 +
+                                            __ldg(a.srow + 2 * NS + sl) * u2);
+                else
+                    r = muh * ((u0 + u2) - 2.0 * u1);
+                r64[j] = r;
+                r32[j] = (float)r;
+                ur[j] = u1;
+                u0 = u1;
+                u1 = u2;
+            }
+        }
+    }
+    float x0[kCmax], x1[kCmax], g0;
+    elim32<BS>(r32, x0, cnt, so32, T, lt, L, a.fac32, NS, L32, sR, &g0);
+    // neighbours of the chunk in x0: x_{s-1} = g0 (previous thread), x_e from the next thread
+    sX[tid] = cnt > 0 ? (double)x0[0] : 0.0;
+    __syncthreads();
+    double xe = (lt + 1 < T) ? sX[tid + 1] : 0.0;
+    // FP64 residual rho = r - A x0 on the chunk's rows
+    {
+        const double Mo = h / 6.0, Md = 2.0 * h / 3.0, mw = paper ? 0.0 : 1.0, td = a.td;
+        double xm = (double)g0;
+#pragma unroll
+        for (int j = 0; j < kCmax; ++j) {
+            if (j < cnt) {
+                const int q = s + j, sl = so32 + j * T + lt;
+                double Ssub, Sdia, Ssup;
+                if (FAM == 0) {
+                    Ssub = __ldg(a.srow + sl);
+                    Sdia = __ldg(a.srow + NS + sl);
+                    Ssup = __ldg(a.srow + 2 * NS + sl);
+                } else {
+                    Ssub = -muh;
+                    Sdia = 2.0 * muh;
+                    Ssup = -muh;
+                }
+                double A = (q == 0) ? 0.0 : mw * Mo + td * Ssub;
+                double B = mw * Md + td * Sdia;
+                double C = (q == m - 1) ? 0.0 : mw * Mo + td * Ssup;
+                double xc = (double)x0[j];
+                double xn = (j + 1 < cnt) ? (double)x0[j + 1] : xe;
+                double rho = r64[j] - (A * xm + B * xc + C * xn);
+                r32[j] = (float)rho;
+                xm = xc;
+            }
+        }
+    }
+    elim32<BS>(r32, x1, cnt, so32, T, lt, L, a.fac32, NS, L32, sR, &g0);
+    const double w = paper ? 1.0 : a.dt;
+#pragma unroll
+    for (int j = 0; j < kCmax; ++j)
+        if (j < cnt) v[base + s + j + 1] = (paper ? 0.0 : ur[j]) + w * ((double)x0[j] + (double)x1[j]);
     if (b.active && n >= 2 && lt == 0) {
         v[base] = 0.0;
         v[base + n] = 0.0;
@@ -552,6 +731,7 @@ static CurveArgs curve_args(Problem* p, int fam)
     a.Fl = F.Fl;
     a.srow = F.srow;
     a.fac = F.fac;
+    a.fac32 = F.fac32;
     a.v = F.v;
     a.n_slots = F.n_slots;
     a.mu = p->mu;
@@ -603,6 +783,7 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
     TRY_S(dev_alloc(p, &F.glx, NS));
     TRY_S(dev_alloc(p, &F.gly, NS));
     TRY_S(dev_alloc(p, &F.fac, 4 * NS));
+    if (p->opts.prec == ADR_FP32_REFINE) TRY_S(dev_alloc(p, &F.fac32, 4 * NS));
     if (fam == 0) {
         TRY_S(dev_alloc(p, &F.Fl, NS));
         TRY_S(dev_alloc(p, &F.srow, 3 * NS));
@@ -628,6 +809,7 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
         TRY_S(dev_alloc(p, &I.T, I.count));
         TRY_S(dev_alloc(p, &I.curve, (size_t)I.count * maxc));
         TRY_S(dev_alloc(p, &I.lanec, (size_t)I.count * nf * BS));
+        if (p->opts.prec == ADR_FP32_REFINE) TRY_S(dev_alloc(p, &I.lanec32, (size_t)I.count * nf * BS));
         ADR_CUDA_TRY(cudaMemcpy(I.T, iT.data(), sizeof(int) * iT.size(), cudaMemcpyHostToDevice));
         ADR_CUDA_TRY(cudaMemcpy(I.curve, icv.data(), sizeof(int) * icv.size(), cudaMemcpyHostToDevice));
         if (BS == 256) k_curve_gdesc<256><<<I.count, 256, 0, st>>>(a, I.T, I.curve);
@@ -648,10 +830,12 @@ adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper)
     a.sig = sig;
     a.paper = paper;
     cudaStream_t st = p->stream;
-#define ADR_PREP(BS_, I_)                                                                      \
-    if (I_.count) {                                                                            \
-        if (fam == 0) k_curve_prep<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec); \
-        else k_curve_prep<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec);         \
+#define ADR_PREP(BS_, I_)                                                                          \
+    if (I_.count) {                                                                                \
+        if (fam == 0)                                                                              \
+            k_curve_prep<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32); \
+        else                                                                                       \
+            k_curve_prep<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32); \
     }
     ADR_PREP(256, F.iset[0])
     ADR_PREP(512, F.iset[1])
@@ -692,11 +876,20 @@ adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_eve
     a.state = use_state ? p->state : nullptr;
     a.dt = dt;
     a.paper = paper;
+    a.td = F.prep_td;
+    const bool ref = p->opts.prec == ADR_FP32_REFINE;
     cudaStream_t st = p->stream;
-#define ADR_SOLVE(BS_, I_)                                                                      \
-    if (I_.count) {                                                                             \
-        if (fam == 0) k_curve_solve<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec); \
-        else k_curve_solve<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec);         \
+#define ADR_SOLVE(BS_, I_)                                                                          \
+    if (I_.count) {                                                                                 \
+        if (ref) {                                                                                  \
+            if (fam == 0)                                                                           \
+                k_curve_solve_ref<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec32); \
+            else                                                                                    \
+                k_curve_solve_ref<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec32); \
+        } else {                                                                                    \
+            if (fam == 0) k_curve_solve<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec); \
+            else k_curve_solve<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec);     \
+        }                                                                                           \
     }
     ADR_SOLVE(1024, F.iset[2])
     ADR_SOLVE(512, F.iset[1])

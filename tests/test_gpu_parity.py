@@ -173,3 +173,48 @@ def test_sheared_2048_two_steps_match_oracle(torch_cuda):
     ref, refit, it, rel, ost = o.solve_stationary(tol=0.0, max_iter=2)
     assert stats["iters"] == 2
     assert relerr(u, ref) <= TOL64 and relerr(uit, refit) <= TOL64
+
+
+# ------------------------------------------------------------ FP32 + FP64 refinement
+TOL_REF = 1e-5
+
+
+@pytest.mark.parametrize("name", ["manufactured33", "L_mask", "disc_mask", "long_lines", "sheared65",
+                                  "data2d", "tiny3", "steep"])
+def test_refine_split_step_matches_oracle(torch_cuda, name):
+    from paper_2411_11041_gb300 import ADR_FP32_REFINE, Solver
+    torch = torch_cuda
+    p = PROBLEMS[name]()
+    o = O.Oracle(p)
+    s = Solver(p, prec=ADR_FP32_REFINE)
+    u = np.random.default_rng(11).normal(size=(p.ny, p.nx)) * o.interior()
+    for dt in (o.default_dt(), 0.3):
+        uh, un = s.split_step(torch.tensor(u, device="cuda:0"), dt)
+        ouh, oun = o.split_step(0.5, dt, u)
+        assert relerr(uh, ouh) <= TOL_REF and relerr(un, oun) <= TOL_REF
+
+
+@pytest.mark.parametrize("name", ["manufactured33", "sheared65", "disc_mask"])
+def test_refine_converged_solve_matches_oracle(torch_cuda, name):
+    from paper_2411_11041_gb300 import ADR_FP32_REFINE, ADR_OK, Solver
+    p = PROBLEMS[name]()
+    o = O.Oracle(p)
+    s = Solver(p, tol=1e-8, max_iter=20000, prec=ADR_FP32_REFINE)
+    u, _, stats, st = s.solve_stationary()
+    ref, _, it, _, ost = o.solve_stationary(tol=1e-8, max_iter=20000)
+    assert st == ADR_OK and ost == O.OK
+    assert abs(stats["iters"] - it) <= 1
+    assert relerr(u, ref) <= TOL_REF
+
+
+def test_refine_paper_u0_and_parabolic(torch_cuda):
+    from paper_2411_11041_gb300 import ADR_FP32_REFINE, Solver
+    torch = torch_cuda
+    p = W.parabolic(n=65)
+    o = O.Oracle(p)
+    s = Solver(p, tol=1e-9, max_iter=5000, prec=ADR_FP32_REFINE)
+    assert relerr(s.paper_u0(), o.paper_u0()) <= TOL_REF
+    u = torch.tensor(p.u0, device="cuda:0")
+    s.step_parabolic(u, 1e-3, 3, 1)
+    ref, _, _ = o.step_parabolic(p.u0, 1e-3, 3, 1, tol=1e-9, max_iter=5000)
+    assert relerr(u, ref) <= TOL_REF
