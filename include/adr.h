@@ -194,6 +194,33 @@ adr_status adr_paper_u0(adr_problem* prob, double* u0);
 adr_status adr_time_kernels(adr_problem* prob, int reps, double* ms_out);
 
 /*
+ * Batches (many independent problems of uneven size and shape): every split
+ * step of all active problems runs as one persistent launch per sweep stage,
+ * over one list of work items (curves of all problems, longest first), and the
+ * whole outer loop of the batch is one CUDA graph whose WHILE condition stays
+ * set while any problem is active.  Each problem keeps its own options (dt,
+ * theta, tol, max_iter, init) and convergence test; a converged problem drops
+ * out of the later launches.  All handles must share the precision mode.
+ *
+ * adr_batch_create: probs (host array of n handles, not owned; they must
+ * outlive the batch and must not be used concurrently with it).  stream: the
+ * batch's cudaStream_t (or NULL).  Errors: ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA.
+ * adr_batch_solve: u_init (nullable host array of n device grids, read for
+ * handles with init == ADR_INIT_USER), u_out (host array of n device grids
+ * [ny][nx] of the respective handles), stats (nullable host array of n;
+ * ms = device time of the whole batch).  Returns ADR_ENOCONV if a problem hit
+ * max_iter (all outputs written).
+ * adr_solve_batch: create, solve from the handles' initial states, destroy.
+ */
+typedef struct adr_batch adr_batch;
+adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_batch** out);
+adr_status adr_batch_solve(adr_batch* batch, const double* const* u_init, double* const* u_out,
+                           adr_stats* stats);
+void adr_batch_destroy(adr_batch* batch);
+adr_status adr_solve_batch(adr_problem* const* probs, int n, double* const* u_out,
+                           adr_stats* stats);
+
+/*
  * adr_cross_substep_noalloc -- one cross-flow substep (G family: curve solve
  * with m_i and the curve -> grid map) that allocates nothing.  The paper has no
  * counterpart; this call exists for callers that cannot call cudaMalloc: code

@@ -81,6 +81,11 @@ def lib():
         L.adr_split_step.argtypes = [vp, C.c_double, vp, vp, vp]
         L.adr_paper_u0.argtypes = [vp, vp]
         L.adr_time_kernels.argtypes = [vp, C.c_int, dp]
+        L.adr_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.POINTER(vp)]
+        L.adr_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(adr_stats)]
+        L.adr_batch_destroy.argtypes = [vp]
+        L.adr_batch_destroy.restype = None
+        L.adr_solve_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(adr_stats)]
         _lib = L
     return _lib
 
@@ -88,7 +93,8 @@ def lib():
 EXPORTED = ["adr_default_opts", "adr_create", "adr_solve_stationary", "adr_step_parabolic",
             "adr_destroy", "adr_last_error", "adr_num_lines", "adr_num_line_nodes",
             "adr_get_lines", "adr_get_crossings", "adr_split_step", "adr_paper_u0",
-            "adr_time_kernels"]
+            "adr_time_kernels", "adr_batch_create", "adr_batch_solve", "adr_batch_destroy",
+            "adr_solve_batch"]
 
 
 def _torch():
@@ -157,6 +163,41 @@ def adr_time_kernels(h, reps):
     ms = (C.c_double * 4)()
     _check(lib().adr_time_kernels(h, int(reps), ms), "adr_time_kernels")
     return list(ms)
+
+
+def _ptr_array(items):
+    arr = (C.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = None if t is None else (t.value if isinstance(t, C.c_void_p) else t.data_ptr())
+    return arr
+
+
+def adr_batch_create(handles, stream=None):
+    b = C.c_void_p()
+    _check(lib().adr_batch_create(_ptr_array(handles), len(handles), _stream_ptr(stream),
+                                  C.byref(b)), "adr_batch_create")
+    return b
+
+
+def adr_batch_solve(b, u_init, u_out):
+    n = len(u_out)
+    stats = (adr_stats * n)()
+    st = lib().adr_batch_solve(b, None if u_init is None else _ptr_array(u_init), _ptr_array(u_out),
+                               stats)
+    _check(st, "adr_batch_solve", allow=(ADR_ENOCONV,))
+    return st, [x.as_dict() for x in stats]
+
+
+def adr_batch_destroy(b):
+    lib().adr_batch_destroy(b)
+
+
+def adr_solve_batch(handles, u_out):
+    n = len(handles)
+    stats = (adr_stats * n)()
+    st = lib().adr_solve_batch(_ptr_array(handles), n, _ptr_array(u_out), stats)
+    _check(st, "adr_solve_batch", allow=(ADR_ENOCONV,))
+    return st, [x.as_dict() for x in stats]
 
 
 def adr_destroy(h):
@@ -256,3 +297,28 @@ class Solver:
                "adr_get_crossings")
         s = (self.ny, self.nx, 4)
         return seg.reshape(s), t.reshape(s), pos.reshape(s)
+
+
+class Batch:
+    """Many Solver handles solved together: one persistent launch per sweep
+    stage and one CUDA graph for the whole outer loop."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        self.b = adr_batch_create([s.h for s in self.solvers], stream)
+
+    def solve(self, u_init=None):
+        outs = [s._grid() for s in self.solvers]
+        st, stats = adr_batch_solve(self.b, u_init, outs)
+        return outs, stats, st
+
+    def close(self):
+        if getattr(self, "b", None):
+            adr_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -158,6 +158,12 @@ adr_status load_family(Problem* p, const double* fextra, double fx_scale);
 adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_even,
                              const double* u_odd, bool use_state, int paper);
 adr_status launch_mask_copy(Problem* p, const double* in, double* out);
+// batches of problems (sweep.cu)
+struct BatchDev;
+adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const double* tols,
+                            const int* max_iters, BatchDev** out);
+adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHandle cond);
+void batch_dev_destroy(BatchDev* b);
 adr_status launch_state_reset(Problem* p);
 
 }  // namespace adr

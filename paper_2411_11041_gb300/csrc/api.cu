@@ -495,4 +495,203 @@ adr_status adr_time_kernels(adr_problem* h, int reps, double* ms_out)
     return s;
 }
 
+// ---------------------------------------------------------------- batches
+
+}  // extern "C"
+
+struct adr_batch {
+    std::vector<adr_problem*> hs;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    BatchDev* dev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<double> dts;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+// run f with every handle's stream set to the batch stream
+template <typename F>
+adr_status on_batch_stream(adr_batch* b, F f)
+{
+    std::vector<cudaStream_t> saved;
+    for (adr_problem* h : b->hs) {
+        saved.push_back(h->p.stream);
+        h->p.stream = b->stream;
+    }
+    adr_status s = f();
+    for (size_t i = 0; i < b->hs.size(); ++i) b->hs[i]->p.stream = saved[i];
+    return s;
+}
+
+adr_status prepare_batch(adr_batch* b)
+{
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        Problem* p = &b->hs[i]->p;
+        double td = p->opts.theta * b->dts[i];
+        TRY(prepare_family(p, 0, td, p->sigma, 0));
+        TRY(prepare_family(p, 1, td, p->sigma, 0));
+        TRY(load_family(p, nullptr, 0.0));
+    }
+    return ADR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void adr_batch_destroy(adr_batch* b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    batch_dev_destroy(b->dev);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+}
+
+adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_batch** out)
+{
+    g_err.clear();
+    if (!out || !probs || n < 1) {
+        set_error("adr_batch_create needs n >= 1 handles and an output");
+        return ADR_EINVAL;
+    }
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!probs[i] || probs[i]->p.opts.prec != probs[0]->p.opts.prec) {
+            set_error("adr_batch_create: NULL handle or mixed precision modes");
+            return ADR_EINVAL;
+        }
+    adr_batch* b = new (std::nothrow) adr_batch;
+    if (!b) {
+        set_error("out of host memory");
+        return ADR_ENOMEM;
+    }
+    auto fail = [&](adr_status st) {
+        adr_batch_destroy(b);
+        return st;
+    };
+    b->hs.assign(probs, probs + n);
+    b->stream = static_cast<cudaStream_t>(stream);
+    std::vector<double> tols(n);
+    std::vector<int> maxit(n);
+    for (int i = 0; i < n; ++i) {
+        const Problem& p = probs[i]->p;
+        b->dts.push_back(p.opts.dt > 0 ? p.opts.dt : default_dt(p, p.sigma));
+        tols[i] = p.opts.tol;
+        maxit[i] = p.opts.max_iter;
+    }
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreate(&b->ev0)) || (e = cudaEventCreate(&b->ev1)))
+        return fail(cuda_fail(e, "batch stream/events"));
+    std::vector<Problem*> ps(n);
+    for (int i = 0; i < n; ++i) ps[i] = &probs[i]->p;
+    adr_status s = batch_dev_create(ps.data(), n, b->dts.data(), tols.data(), maxit.data(), &b->dev);
+    if (s) return fail(s);
+    s = on_batch_stream(b, [&] { return prepare_batch(b); });
+    if (s) return fail(s);
+    // the batch loop as one graph: WHILE(any problem active) { batched split step }
+    if ((e = cudaGraphCreate(&b->graph, 0))) return fail(cuda_fail(e, "cudaGraphCreate"));
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, b->graph, 1, cudaGraphCondAssignDefault)))
+        return fail(cuda_fail(e, "cudaGraphConditionalHandleCreate"));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &np)))
+        return fail(cuda_fail(e, "cudaGraphAddNode"));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed)))
+        return fail(cuda_fail(e, "cudaStreamBeginCaptureToGraph"));
+    s = batch_dev_step(b->dev, b->cap_stream, cond);
+    cudaGraph_t cap = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &cap);
+    if (s) return fail(s);
+    if (e) return fail(cuda_fail(e, "cudaStreamEndCapture"));
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0))) return fail(cuda_fail(e, "cudaGraphInstantiate"));
+    if ((e = cudaStreamSynchronize(b->stream))) return fail(cuda_fail(e, "adr_batch_create"));
+    *out = b;
+    return ADR_OK;
+}
+
+adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* const* u_out,
+                           adr_stats* stats)
+{
+    g_err.clear();
+    if (!b || !u_out) {
+        set_error("NULL batch or output array");
+        return ADR_EINVAL;
+    }
+    const int n = (int)b->hs.size();
+    for (int i = 0; i < n; ++i)
+        if (!u_out[i]) {
+            set_error("NULL output grid in adr_batch_solve");
+            return ADR_EINVAL;
+        }
+    std::vector<IterState> st(n);
+    float ms = 0.f;
+    adr_status s = on_batch_stream(b, [&]() -> adr_status {
+        for (int i = 0; i < n; ++i) {
+            adr_problem* h = b->hs[i];
+            TRY(init_state(h, h->p.opts.init, u_init ? u_init[i] : nullptr));
+            TRY(launch_state_reset(&h->p));
+        }
+        TRY(prepare_batch(b));
+        ADR_CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
+        ADR_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+        for (int i = 0; i < n; ++i)
+            TRY(launch_finish(&b->hs[i]->p, u_out[i], nullptr, b->hs[i]->p.opts.theta == 0.5));
+        ADR_CUDA_TRY(cudaEventRecord(b->ev1, b->stream));
+        for (int i = 0; i < n; ++i)
+            ADR_CUDA_TRY(cudaMemcpyAsync(&st[i], b->hs[i]->p.state, sizeof(IterState),
+                                         cudaMemcpyDeviceToHost, b->stream));
+        ADR_CUDA_TRY(cudaStreamSynchronize(b->stream));
+        cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+        return ADR_OK;
+    });
+    if (s) return s;
+    bool all = true;
+    for (int i = 0; i < n; ++i) {
+        adr_problem* h = b->hs[i];
+        if (!st[i].converged && h->p.opts.tol > 0.0) all = false;
+        if (stats) {
+            stats[i].iters = st[i].iter;
+            stats[i].rel_update = st[i].rel;
+            stats[i].ms = ms;
+            stats[i].line_dofs = (double)st[i].iter * (h->line_unknowns[0] + h->line_unknowns[1]);
+            stats[i].dt = b->dts[i];
+        }
+    }
+    if (!all) {
+        set_error("a problem of the batch reached max_iter before tol");
+        return ADR_ENOCONV;
+    }
+    return ADR_OK;
+}
+
+adr_status adr_solve_batch(adr_problem* const* probs, int n, double* const* u_out, adr_stats* stats)
+{
+    adr_batch* b = nullptr;
+    void* stream = (n > 0 && probs && probs[0]) ? (void*)probs[0]->p.stream : nullptr;
+    adr_status s = adr_batch_create(probs, n, stream, &b);
+    if (s) return s;
+    s = adr_batch_solve(b, nullptr, u_out, stats);
+    std::string keep = g_err;
+    adr_batch_destroy(b);
+    g_err = keep;
+    return s;
+}
+
 }  // extern "C"

@@ -10,6 +10,8 @@
 //  k_check       one block: convergence test and the CUDA-graph loop condition.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <string>
 #include <vector>
 
 #include "adr_internal.cuh"
@@ -60,6 +62,8 @@ struct CurveArgs {
     double* srow;          // 3 planes per slot: S sub/diag/super (B)
     double* fac;           // 4 planes per slot: cp, vp, ip, lp
     float* fac32;          // the same factors rounded to FP32 (reduced-precision mode)
+    const double* lanecs[3];   // reduced-system constants of the item sets (batched launches)
+    const float* lanec32s[3];
     double* v;             // per node: curve values
     int n_slots;
     double mu, sig, td, dt;
@@ -82,15 +86,16 @@ struct BlockChunk {
     bool active;
 };
 
-template <int BS>
-__device__ __forceinline__ void item_chunk(const CurveArgs& a, const int* item_T,
-                                           const int* item_curve, BlockChunk& b)
+// chunk of the calling thread inside a work item of block size T whose curves
+// are curves[0 .. BS/T-1]
+__device__ __forceinline__ void item_chunk_of(const CurveArgs& a, int T, const int* curves,
+                                              BlockChunk& b)
 {
-    b.T = item_T[blockIdx.x];
+    b.T = T;
     int L = __ffs(b.T) - 1;
     int sb = threadIdx.x >> L;
     b.lt = threadIdx.x & (b.T - 1);
-    b.line = item_curve[blockIdx.x * Items<BS>::MAXC + sb];
+    b.line = curves[sb];
     b.active = b.line >= 0;
     b.base = b.n = b.m = b.c = b.s = b.cnt = b.so = 0;
     if (!b.active) return;
@@ -101,6 +106,13 @@ __device__ __forceinline__ void item_chunk(const CurveArgs& a, const int* item_T
     b.s = b.lt * b.c;
     b.cnt = b.m > 0 ? max(0, min(b.m, b.s + b.c) - b.s) : 0;
     b.so = a.soff[b.line];
+}
+
+template <int BS>
+__device__ __forceinline__ void item_chunk(const CurveArgs& a, const int* item_T,
+                                           const int* item_curve, BlockChunk& b)
+{
+    item_chunk_of(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC, b);
 }
 
 __device__ __forceinline__ double gather_at(const double* __restrict__ u, int nx, int cell,
@@ -285,17 +297,17 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
     }
 }
 
+// curve solve of one work item (block size T, curves[0 .. BS/T-1], reduced-
+// system constants Lc); the whole block calls it
 template <int BS, int FAM>
-__global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item_T,
-                                                    const int* item_curve, const double* lanec)
+__device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, const int* curves,
+                                                 const double* Lc, double (*sR)[BS])
 {
     constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
-    if (a.state && a.state->done) return;
-    __shared__ double sR[2][BS];
     const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
     double* __restrict__ v = a.v;
     BlockChunk b;
-    item_chunk<BS>(a, item_T, item_curve, b);
+    item_chunk_of(a, Titem, curves, b);
     const int tid = threadIdx.x, lt = b.lt, T = b.T, L = __ffs(T) - 1;
     if (b.active && b.n < 2 && lt <= b.n) v[b.base + lt] = 0.0;
     const int base = b.base, n = b.n, s = b.s, cnt = b.cnt;
@@ -345,7 +357,6 @@ __global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item
     sR[0][tid] = rho;
     __syncthreads();
     double rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.0;
-    const double* Lc = lanec + (size_t)blockIdx.x * NF * BS;
     double R = cnt > 0 ? rpp - Lc[tid] * rhoN : 0.0;
     int buf = 1;
 #pragma unroll
@@ -378,6 +389,16 @@ __global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item
         v[base] = 0.0;
         v[base + n] = 0.0;
     }
+}
+
+template <int BS, int FAM>
+__global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item_T,
+                                                    const int* item_curve, const double* lanec)
+{
+    if (a.state && a.state->done) return;
+    __shared__ double sR[2][BS];
+    curve_solve_body<BS, FAM>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
+                              lanec + (size_t)blockIdx.x * Items<BS>::NF * BS, sR);
 }
 
 // ----------------------------------------------- FP32 solve + FP64 refinement
@@ -446,24 +467,20 @@ __device__ __forceinline__ void elim32(const float (&rhs)[kCmax], float (&x)[kCm
 }
 
 template <int BS, int FAM>
-__global__ void __launch_bounds__(BS) k_curve_solve_ref(CurveArgs a, const int* item_T,
-                                                        const int* item_curve, const float* lanec32)
+__device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Titem,
+                                                     const int* curves, const float* L32,
+                                                     float (*sR)[BS], double* sX)
 {
-    constexpr int NF = Items<BS>::NF;
-    if (a.state && a.state->done) return;
-    __shared__ float sR[2][BS];
-    __shared__ double sX[BS];
     const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
     double* __restrict__ v = a.v;
     BlockChunk b;
-    item_chunk<BS>(a, item_T, item_curve, b);
+    item_chunk_of(a, Titem, curves, b);
     const int tid = threadIdx.x, lt = b.lt, T = b.T, L = __ffs(T) - 1;
     if (b.active && b.n < 2 && lt <= b.n) v[b.base + lt] = 0.0;
     const int base = b.base, n = b.n, s = b.s, cnt = b.cnt, m = b.m;
     const size_t NS = a.n_slots;
     const int so32 = (int)b.so;
     const bool paper = a.paper != 0;
-    const float* L32 = lanec32 + (size_t)blockIdx.x * NF * BS;
     auto uslot = [&](int sl) -> double {
         return gather_at(u, a.nx, __ldg(a.gcell + sl), __ldg(a.glx + sl), __ldg(a.gly + sl));
     };
@@ -547,6 +564,51 @@ __global__ void __launch_bounds__(BS) k_curve_solve_ref(CurveArgs a, const int* 
     }
 }
 
+template <int BS, int FAM>
+__global__ void __launch_bounds__(BS) k_curve_solve_ref(CurveArgs a, const int* item_T,
+                                                        const int* item_curve, const float* lanec32)
+{
+    if (a.state && a.state->done) return;
+    __shared__ float sR[2][BS];
+    __shared__ double sX[BS];
+    curve_solve_ref_body<BS, FAM>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
+                                  lanec32 + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sX);
+}
+
+// ------------------------------------------------------------ batched problems
+// A batch keeps one CurveArgs per (problem, family) in a device table and one
+// list of work items over all problems, longest curves first.  The persistent
+// kernels below loop over that list with a grid of a few blocks per SM; an
+// item whose problem has converged is skipped.
+struct BatchItem {
+    int prob;     // problem index
+    int T;        // block size of the item's curves
+    int local;    // item index inside its problem's item set (reduced-system constants)
+    int curves[8];
+};
+
+template <int BS, int FAM, bool REF>
+__global__ void __launch_bounds__(BS) k_curve_solve_batch(const CurveArgs* __restrict__ table,
+                                                          const BatchItem* __restrict__ items,
+                                                          int n_items, int set)
+{
+    __shared__ double sR[2][BS];
+    __shared__ float sRf[2][BS];
+    __shared__ double sX[BS];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem& I = items[it];
+        const CurveArgs& a = table[2 * I.prob + FAM];
+        if (a.state->done) continue;  // uniform: one problem per item
+        if (REF)
+            curve_solve_ref_body<BS, FAM>(a, I.T, I.curves,
+                                          a.lanec32s[set] + (size_t)I.local * Items<BS>::NF * BS, sRf, sX);
+        else
+            curve_solve_body<BS, FAM>(a, I.T, I.curves,
+                                      a.lanecs[set] + (size_t)I.local * Items<BS>::NF * BS, sR);
+        __syncthreads();  // shared arrays are reused by the next item
+    }
+}
+
 struct GridArgs {
     int nx, ny;
     const uint8_t* ntype;
@@ -582,18 +644,18 @@ __global__ void k_map_coef(long long N, const uint8_t* ntype, const int* cg, con
     }
 }
 
+// curve -> grid map over nodes first, first + stride, ... of one problem;
+// returns the partial sums of the norms of the calling thread
 template <bool NORMS>
-__global__ void __launch_bounds__(kGridThreads) k_grid_map(GridArgs a)
+__device__ __forceinline__ void grid_map_body(const GridArgs& a, long long first, long long stride,
+                                              double& dd, double& uu)
 {
-    if (a.state && a.state->done) return;
     int it = a.state ? a.state->iter : 0;
     double* __restrict__ out = ((it + a.parity_shift) & 1) ? a.out_odd : a.out_even;
     const double* __restrict__ prev = (it & 1) ? a.prev_odd : a.prev_even;
     const double* __restrict__ v = a.v;
     const long long N = (long long)a.nx * a.ny;
-    double dd = 0.0, uu = 0.0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
-         k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = first; k < N; k += stride) {
         double val = 0.0;
         if (a.ntype[k] == kInterior) {
             int4 g = *reinterpret_cast<const int4*>(a.mg + 4 * k);
@@ -615,27 +677,111 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_map(GridArgs a)
         }
         out[k] = val;
     }
-    if (NORMS) {
-        __shared__ double sd[kGridThreads / 32], su[kGridThreads / 32];
-        for (int o = 16; o > 0; o >>= 1) {
-            dd += __shfl_down_sync(0xffffffffu, dd, o);
-            uu += __shfl_down_sync(0xffffffffu, uu, o);
+}
+
+// block sum of (dd, uu) into dst[0..1]
+__device__ __forceinline__ void block_sum2(double dd, double uu, double* dst)
+{
+    __shared__ double sd[kGridThreads / 32], su[kGridThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        dd += __shfl_down_sync(0xffffffffu, dd, o);
+        uu += __shfl_down_sync(0xffffffffu, uu, o);
+    }
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sd[w] = dd;
+        su[w] = uu;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double td = 0, tu = 0;
+        for (int q = 0; q < kGridThreads / 32; ++q) {
+            td += sd[q];
+            tu += su[q];
         }
-        int w = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0) {
-            sd[w] = dd;
-            su[w] = uu;
+        dst[0] = td;
+        dst[1] = tu;
+    }
+}
+
+template <bool NORMS>
+__global__ void __launch_bounds__(kGridThreads) k_grid_map(GridArgs a)
+{
+    if (a.state && a.state->done) return;
+    double dd = 0.0, uu = 0.0;
+    grid_map_body<NORMS>(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                         (long long)gridDim.x * blockDim.x, dd, uu);
+    if (NORMS) block_sum2(dd, uu, a.partial + 2 * blockIdx.x);
+}
+
+// batched map: block b works for problem blk_prob[b] as its local block
+// blk_local[b] of nblk[p] (table entries 2p + fam); partial sums per local block
+template <bool NORMS>
+__global__ void __launch_bounds__(kGridThreads) k_grid_map_batch(const GridArgs* __restrict__ table,
+                                                                int fam, const int* blk_prob,
+                                                                const int* blk_local, const int* nblk)
+{
+    int p = blk_prob[blockIdx.x], lb = blk_local[blockIdx.x];
+    const GridArgs& a = table[2 * p + fam];
+    if (a.state->done) return;
+    double dd = 0.0, uu = 0.0;
+    grid_map_body<NORMS>(a, (long long)lb * blockDim.x + threadIdx.x,
+                         (long long)nblk[p] * blockDim.x, dd, uu);
+    if (NORMS) block_sum2(dd, uu, a.partial + 2 * lb);
+}
+
+// batched convergence test: block p reduces problem p's partial sums; the last
+// block to finish clears the graph condition when every problem is done
+__global__ void k_check_batch(IterState* const* states, const double* const* partials,
+                              const int* nblk, int n_prob, const double* tols, const int* max_iters,
+                              unsigned int* ticket, cudaGraphConditionalHandle handle)
+{
+    int p = blockIdx.x;
+    IterState* st = states[p];
+    const double tol = tols[p];
+    const int max_iter = max_iters[p];
+    __shared__ double sd[256], su[256];
+    __shared__ bool last;
+    if (!st->done) {
+        const double* part = partials[p];
+        double d = 0, u = 0;
+        for (int q = threadIdx.x; q < nblk[p]; q += blockDim.x) {
+            d += part[2 * q];
+            u += part[2 * q + 1];
         }
+        sd[threadIdx.x] = d;
+        su[threadIdx.x] = u;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double td = 0, tu = 0;
-            for (int q = 0; q < kGridThreads / 32; ++q) {
-                td += sd[q];
-                tu += su[q];
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+                sd[threadIdx.x] += sd[threadIdx.x + w];
+                su[threadIdx.x] += su[threadIdx.x + w];
             }
-            a.partial[2 * blockIdx.x] = td;
-            a.partial[2 * blockIdx.x + 1] = tu;
+            __syncthreads();
         }
+        if (threadIdx.x == 0) {
+            double num = sd[0], den = su[0];
+            double rel = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+            int iter = st->iter + 1;
+            int conv = tol > 0.0 && rel <= tol;
+            st->iter = iter;
+            st->rel = rel;
+            st->converged = conv;
+            st->done = (conv || iter >= max_iter) ? 1 : 0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        last = t == (unsigned int)(n_prob - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        int active = 0;
+        for (int q = 0; q < n_prob; ++q) active |= !((volatile IterState*)states[q])->done;
+        *ticket = 0u;
+        cudaGraphSetConditional(handle, active ? 1 : 0);
     }
 }
 
@@ -973,6 +1119,236 @@ adr_status launch_mask_copy(Problem* p, const double* in, double* out)
 adr_status launch_state_reset(Problem* p)
 {
     k_reset<<<1, 1, 0, p->stream>>>(p->state);
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+
+// ------------------------------------------------------------ batch tables
+
+struct BatchDev {
+    int n = 0;
+    CurveArgs* ctab = nullptr;   // [2n]
+    GridArgs* gtab = nullptr;    // [2n]
+    BatchItem* items[kItemSets] = {nullptr, nullptr, nullptr};
+    int n_items[kItemSets] = {0, 0, 0};
+    int grid_items[kItemSets] = {0, 0, 0};  // persistent grid size per set
+    int* blk_prob = nullptr;
+    int* blk_local = nullptr;
+    int* nblk = nullptr;
+    int n_blk = 0;
+    IterState** states = nullptr;
+    double** partials = nullptr;
+    double* tol = nullptr;
+    int* max_iter = nullptr;
+    unsigned int* ticket = nullptr;
+    bool ref = false;
+    // work items per family and set, with their persistent grid sizes
+    BatchItem* it[2][kItemSets] = {};
+    int nit[2][kItemSets] = {};
+    int git[2][kItemSets] = {};
+    std::vector<void*> owned;
+};
+
+template <typename T>
+static adr_status bdev_alloc(BatchDev* b, T** ptr, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        return ADR_ENOMEM;
+    }
+    b->owned.push_back(q);
+    *ptr = static_cast<T*>(q);
+    return ADR_OK;
+}
+
+void batch_dev_destroy(BatchDev* b)
+{
+    if (!b) return;
+    for (void* q : b->owned) cudaFree(q);
+    delete b;
+}
+
+static adr_status batch_dev_items(BatchDev* b, Problem* const* ps, int fam, BatchItem** items_out,
+                                  int* counts, int* grids);
+
+// Build the device tables of a batch.  dts[i]: pseudo step of problem i.
+adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const double* tols,
+                            const int* max_iters, BatchDev** out)
+{
+    BatchDev* b = new BatchDev;
+    b->n = n;
+    b->ref = ps[0]->opts.prec == ADR_FP32_REFINE;
+    auto fail = [&](adr_status s) {
+        batch_dev_destroy(b);
+        return s;
+    };
+    std::vector<CurveArgs> ct(2 * n);
+    std::vector<GridArgs> gt(2 * n);
+    std::vector<int> bp, bl, nb(n);
+    std::vector<IterState*> sts(n);
+    std::vector<double*> parts(n);
+    for (int i = 0; i < n; ++i) {
+        Problem* p = ps[i];
+        for (int fam = 0; fam < 2; ++fam) {
+            CurveArgs a = curve_args(p, fam);
+            a.u_even = fam == 0 ? p->ubuf[0] : p->ubuf[2];
+            a.u_odd = fam == 0 ? p->ubuf[1] : p->ubuf[2];
+            a.state = p->state;
+            a.dt = dts[i];
+            a.td = p->opts.theta * dts[i];
+            a.paper = 0;
+            for (int k = 0; k < kItemSets; ++k) {
+                a.lanecs[k] = p->fam[fam].iset[k].lanec;
+                a.lanec32s[k] = p->fam[fam].iset[k].lanec32;
+            }
+            ct[2 * i + fam] = a;
+            GridArgs g{};
+            g.nx = p->grid.nx;
+            g.ny = p->grid.ny;
+            g.ntype = p->ntype;
+            g.mg = p->fam[fam].mg;
+            g.mc = p->fam[fam].mc;
+            g.v = p->fam[fam].v;
+            g.state = p->state;
+            g.partial = p->partial;
+            if (fam == 0) {
+                g.out_even = g.out_odd = p->ubuf[2];
+                g.parity_shift = 0;
+            } else {
+                g.out_even = p->ubuf[0];
+                g.out_odd = p->ubuf[1];
+                g.prev_even = p->ubuf[0];
+                g.prev_odd = p->ubuf[1];
+                g.parity_shift = 1;
+            }
+            gt[2 * i + fam] = g;
+        }
+        // work items of both families share the item lists (the B and G
+        // curves of a problem differ, so items are per family): the batch
+        // keeps one list per family and set
+        nb[i] = grid_map_blocks(p);
+        for (int q = 0; q < nb[i]; ++q) {
+            bp.push_back(i);
+            bl.push_back(q);
+        }
+        sts[i] = p->state;
+        parts[i] = p->partial;
+    }
+    b->n_blk = (int)bp.size();
+    adr_status s;
+    if ((s = bdev_alloc(b, &b->ctab, 2 * n)) || (s = bdev_alloc(b, &b->gtab, 2 * n)) ||
+        (s = bdev_alloc(b, &b->blk_prob, b->n_blk)) || (s = bdev_alloc(b, &b->blk_local, b->n_blk)) ||
+        (s = bdev_alloc(b, &b->nblk, n)) || (s = bdev_alloc(b, &b->states, n)) ||
+        (s = bdev_alloc(b, &b->partials, n)) || (s = bdev_alloc(b, &b->tol, n)) ||
+        (s = bdev_alloc(b, &b->max_iter, n)) || (s = bdev_alloc(b, &b->ticket, 1)))
+        return fail(s);
+    cudaError_t e;
+    if ((e = cudaMemcpy(b->ctab, ct.data(), sizeof(CurveArgs) * ct.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->gtab, gt.data(), sizeof(GridArgs) * gt.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->blk_prob, bp.data(), sizeof(int) * bp.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->blk_local, bl.data(), sizeof(int) * bl.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->nblk, nb.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->states, sts.data(), sizeof(IterState*) * n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->partials, parts.data(), sizeof(double*) * n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->tol, tols, sizeof(double) * n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->max_iter, max_iters, sizeof(int) * n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(b->ticket, 0, sizeof(unsigned int))))
+        return fail(cuda_fail(e, "batch tables"));
+    for (int fam = 0; fam < 2; ++fam)
+        if ((s = batch_dev_items(b, ps, fam, b->it[fam], b->nit[fam], b->git[fam]))) return fail(s);
+    *out = b;
+    return ADR_OK;
+}
+
+// Items of one family over all problems (one list per set), longest first.
+static adr_status batch_dev_items(BatchDev* b, Problem* const* ps, int fam, BatchItem** items_out,
+                           int* counts, int* grids)
+{
+    std::vector<BatchItem> its[kItemSets];
+    for (int i = 0; i < b->n; ++i) {
+        Family& F = ps[i]->fam[fam];
+        for (int k = 0; k < kItemSets; ++k) {
+            const ItemSet& I = F.iset[k];
+            if (!I.count) continue;
+            int maxc = I.BS / 32;
+            std::vector<int> T(I.count), cv((size_t)I.count * maxc);
+            cudaError_t e;
+            if ((e = cudaMemcpy(T.data(), I.T, sizeof(int) * I.count, cudaMemcpyDeviceToHost)) ||
+                (e = cudaMemcpy(cv.data(), I.curve, sizeof(int) * cv.size(), cudaMemcpyDeviceToHost)))
+                return cuda_fail(e, "batch items");
+            for (int q = 0; q < I.count; ++q) {
+                BatchItem bi;
+                bi.prob = i;
+                bi.T = T[q];
+                bi.local = q;
+                for (int r = 0; r < 8; ++r) bi.curves[r] = r < maxc ? cv[(size_t)q * maxc + r] : -1;
+                its[k].push_back(bi);
+            }
+        }
+    }
+    for (int k = 0; k < kItemSets; ++k) {
+        std::stable_sort(its[k].begin(), its[k].end(),
+                         [](const BatchItem& x, const BatchItem& y) { return x.T > y.T; });
+        counts[k] = (int)its[k].size();
+        items_out[k] = nullptr;
+        grids[k] = 0;
+        if (!counts[k]) continue;
+        TRY_S(bdev_alloc(b, &items_out[k], its[k].size()));
+        ADR_CUDA_TRY(cudaMemcpy(items_out[k], its[k].data(), sizeof(BatchItem) * its[k].size(),
+                                cudaMemcpyHostToDevice));
+        int BS = 256 << k, per_sm = 0, dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e;
+        if (BS == 256)
+            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<256, 0, true>, 256, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<256, 0, false>, 256, 0);
+        else if (BS == 512)
+            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<512, 0, true>, 512, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<512, 0, false>, 512, 0);
+        else
+            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<1024, 0, true>, 1024, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<1024, 0, false>, 1024, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+        int g = (per_sm > 0 ? per_sm : 1) * nsm;
+        grids[k] = counts[k] < g ? counts[k] : g;
+    }
+    return ADR_OK;
+}
+
+// one split step of every active problem (captured in the batch graph)
+adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHandle cond)
+{
+    BatchItem* const* itB = b->it[0];
+    BatchItem* const* itG = b->it[1];
+    const int *nB = b->nit[0], *gB = b->git[0], *nG = b->nit[1], *gG = b->git[1];
+#define ADR_BATCH_SOLVE(FAM_, IT, N, G)                                                            \
+    for (int k = kItemSets - 1; k >= 0; --k) {                                                     \
+        if (!N[k]) continue;                                                                       \
+        int BS = 256 << k;                                                                         \
+        if (BS == 256) {                                                                           \
+            if (b->ref) k_curve_solve_batch<256, FAM_, true><<<G[k], 256, 0, st>>>(b->ctab, IT[k], N[k], k); \
+            else k_curve_solve_batch<256, FAM_, false><<<G[k], 256, 0, st>>>(b->ctab, IT[k], N[k], k);     \
+        } else if (BS == 512) {                                                                    \
+            if (b->ref) k_curve_solve_batch<512, FAM_, true><<<G[k], 512, 0, st>>>(b->ctab, IT[k], N[k], k); \
+            else k_curve_solve_batch<512, FAM_, false><<<G[k], 512, 0, st>>>(b->ctab, IT[k], N[k], k);     \
+        } else {                                                                                   \
+            if (b->ref) k_curve_solve_batch<1024, FAM_, true><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], N[k], k); \
+            else k_curve_solve_batch<1024, FAM_, false><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], N[k], k);     \
+        }                                                                                          \
+    }
+    ADR_BATCH_SOLVE(0, itB, nB, gB)
+    k_grid_map_batch<false><<<b->n_blk, kGridThreads, 0, st>>>(b->gtab, 0, b->blk_prob, b->blk_local,
+                                                               b->nblk);
+    ADR_BATCH_SOLVE(1, itG, nG, gG)
+    k_grid_map_batch<true><<<b->n_blk, kGridThreads, 0, st>>>(b->gtab, 1, b->blk_prob, b->blk_local,
+                                                              b->nblk);
+#undef ADR_BATCH_SOLVE
+    k_check_batch<<<b->n, 256, 0, st>>>(b->states, (const double* const*)b->partials, b->nblk, b->n,
+                                        b->tol, b->max_iter, b->ticket, cond);
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }
