@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--other-prec", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--workload", default="sheared", choices=["sheared", "batch"])
+    ap.add_argument("--count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -384,10 +386,63 @@ def e2e(args, prob, dev, prec):
                         "adr_solve_stationary, D2H of u"}
 
 
+def run_batch(args):
+    """Many problems of uneven size and shape (N ~ U{128..1024}, square /
+    disc / L masks, constant flow of random direction): all solved to tol as
+    one batch, against the same problems solved one after another."""
+    import torch
+
+    from paper_2411_11041_gb300 import ADR_FP32_REFINE, ADR_FP64, Batch, Solver
+    from paper_2411_11041_gb300 import workloads as W
+    dev = torch.device("cuda:0")
+    prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
+    probs = W.batch(count=args.count)
+    t0 = time.perf_counter()
+    solvers = [Solver(p, device=dev, tol=args.tol, max_iter=200000, prec=prec) for p in probs]
+    setup_s = time.perf_counter() - t0
+    batch = Batch(solvers)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        batch.solve()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dofs = 0.0
+    for _ in range(args.steps):
+        outs, stats, st = batch.solve()
+        dofs += sum(x["line_dofs"] for x in stats)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_batch = e0.elapsed_time(e1) / args.steps
+    iters = [x["iters"] for x in stats]
+    # plain: one problem at a time through its own graph
+    for s in solvers[:4]:
+        s.solve_stationary()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for s in solvers:
+        s.solve_stationary()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_plain = e0.elapsed_time(e1)
+    line = {"metric": METRIC, "value": dofs / args.steps / (ms_batch / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == ADR_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batch{args.count}", "nodes": int(sum(p.nx * p.ny for p in probs)),
+                       "tol": args.tol, "iters_min_median_max": [min(iters), int(np.median(iters)), max(iters)],
+                       "step": "all problems solved to tol as one batch"},
+            "plain_sequential_ms": ms_plain, "batched_speedup": ms_plain / ms_batch,
+            "setup_s": setup_s}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

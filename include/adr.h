@@ -78,8 +78,10 @@ typedef struct {
     double tol;
     int max_iter;
     int init;        /* adr_init */
-    int reserved0;   /* must be 0 */
-    int reserved1;   /* must be 0 */
+    int rows_per_thread;    /* launch shape of the curve solve: 2, 4 or 8 rows per thread
+                               (0 = 8); a curve of m unknowns gets blocks of the smallest
+                               power-of-two T >= 32 with T * rows_per_thread >= m */
+    int map_blocks_per_sm;  /* blocks per SM of the curve -> grid map: 1..8 (0 = 8) */
 } adr_opts;
 
 /* Result statistics (host struct filled by the solve calls). */
@@ -94,7 +96,7 @@ typedef struct {
 typedef struct adr_problem adr_problem; /* opaque handle */
 
 /* Fill opts with the defaults: FP64, theta 0.5, dt auto, tol 1e-10,
- * max_iter 100000, zero initial state. */
+ * max_iter 100000, zero initial state, default launch shapes. */
 void adr_default_opts(adr_opts* opts);
 
 /*
@@ -192,6 +194,18 @@ adr_status adr_paper_u0(adr_problem* prob, double* u0);
  * ADR_EINVAL, ADR_ECUDA.
  */
 adr_status adr_time_kernels(adr_problem* prob, int reps, double* ms_out);
+
+/*
+ * adr_autotune -- choose the launch shapes of a handle by measurement (no
+ * counterpart in the paper; the result does not change the solution).  Each
+ * candidate (rows_per_thread in {2, 4, 8}, map_blocks_per_sm in {2, 4, 8}) is
+ * applied and one split step's kernels are timed reps times with CUDA events
+ * on the handle's stream; the fastest is kept.  Outputs (host, nullable): the
+ * chosen rows_per_thread and map_blocks_per_sm and its ms per split step.
+ * Errors: ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA.
+ */
+adr_status adr_autotune(adr_problem* prob, int reps, int* rows_per_thread,
+                        int* map_blocks_per_sm, double* ms_per_step);
 
 /*
  * Batches (many independent problems of uneven size and shape): every split

@@ -34,7 +34,7 @@ class adr_grid(C.Structure):
 class adr_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("theta", C.c_double), ("dt", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("init", C.c_int),
-                ("reserved0", C.c_int), ("reserved1", C.c_int)]
+                ("rows_per_thread", C.c_int), ("map_blocks_per_sm", C.c_int)]
 
 
 class adr_stats(C.Structure):
@@ -81,6 +81,7 @@ def lib():
         L.adr_split_step.argtypes = [vp, C.c_double, vp, vp, vp]
         L.adr_paper_u0.argtypes = [vp, vp]
         L.adr_time_kernels.argtypes = [vp, C.c_int, dp]
+        L.adr_autotune.argtypes = [vp, C.c_int, ip, ip, dp]
         L.adr_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.POINTER(vp)]
         L.adr_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(adr_stats)]
         L.adr_batch_destroy.argtypes = [vp]
@@ -94,7 +95,42 @@ EXPORTED = ["adr_default_opts", "adr_create", "adr_solve_stationary", "adr_step_
             "adr_destroy", "adr_last_error", "adr_num_lines", "adr_num_line_nodes",
             "adr_get_lines", "adr_get_crossings", "adr_split_step", "adr_paper_u0",
             "adr_time_kernels", "adr_batch_create", "adr_batch_solve", "adr_batch_destroy",
-            "adr_solve_batch"]
+            "adr_solve_batch", "adr_autotune"]
+
+
+def tune_key(prob, prec):
+    """Cache key of a problem's launch shapes: grid, domain, field kind, precision."""
+    b1, b2 = np.asarray(prob.beta1), np.asarray(prob.beta2)
+    const = bool(np.all(b1 == b1.flat[0]) and np.all(b2 == b2.flat[0]))
+    mask = np.asarray(prob.mask)
+    return f"{prob.nx}x{prob.ny}:{int(mask.sum())}:{'const' if const else 'curved'}:p{int(prec)}"
+
+
+def _tune_path():
+    return os.environ.get("ADR_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "adr_gb300", "tune.json"))
+
+
+def _tune_cache():
+    import json
+    try:
+        with open(_tune_path()) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save_tune_cache(c):
+    import json
+    path = _tune_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(c, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
 
 
 def _torch():
@@ -214,12 +250,17 @@ class Solver:
     the device once; the handle owns everything it derives from them.
     """
 
-    def __init__(self, prob, device="cuda:0", stream=None, **opts):
+    def __init__(self, prob, device="cuda:0", stream=None, autotune=False, **opts):
         torch = _torch()
         self.torch = torch
         self.device = torch.device(device)
         self.stream = stream
         self.nx, self.ny = int(prob.nx), int(prob.ny)
+        key = tune_key(prob, opts.get("prec", ADR_FP64)) if autotune else None
+        cached = _tune_cache().get(key) if key else None
+        if cached:
+            opts.setdefault("rows_per_thread", cached["rows_per_thread"])
+            opts.setdefault("map_blocks_per_sm", cached["map_blocks_per_sm"])
         self.opts = default_opts(**opts)
         def dev(a, dt):
             if isinstance(a, torch.Tensor):
@@ -230,6 +271,20 @@ class Solver:
         grid = adr_grid(self.nx, self.ny, prob.x0, prob.y0, prob.x1, prob.y1)
         with torch.cuda.device(self.device):
             self.h = adr_create(grid, mask, prob.mu, prob.sigma, b1, b2, f, self.opts, stream)
+        self.tuned = None
+        if key and not cached:
+            self.tuned = self.autotune()
+            c = _tune_cache()
+            c[key] = {"rows_per_thread": self.tuned[0], "map_blocks_per_sm": self.tuned[1],
+                      "ms_per_step": self.tuned[2]}
+            _save_tune_cache(c)
+
+    def autotune(self, reps=10):
+        """Measure the launch shapes and keep the fastest (adr_autotune)."""
+        r, m, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+        _check(lib().adr_autotune(self.h, int(reps), C.byref(r), C.byref(m), C.byref(ms)),
+               "adr_autotune")
+        return r.value, m.value, ms.value
 
     def close(self):
         if getattr(self, "h", None):

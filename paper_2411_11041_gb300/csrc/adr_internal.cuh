@@ -100,6 +100,8 @@ struct Problem {
     int N = 0;             // nx*ny
     int n_interior = 0;
     int n_sm = 0;
+    int rows_per_thread = 8;    // launch shape of the curve solve (<= 8)
+    int map_blocks_per_sm = 8;  // launch shape of the curve -> grid map
     bool const_beta = false;
     double bmax = 0;
     Family fam[2];
@@ -131,6 +133,18 @@ adr_status cuda_fail(cudaError_t e, const char* what);
         if (_e != cudaSuccess) return ::adr::cuda_fail(_e, #call); \
     } while (0)
 
+// free a buffer owned by the problem (NULL is a no-op)
+inline void dev_free(Problem* p, void* ptr)
+{
+    if (!ptr) return;
+    for (size_t i = 0; i < p->owned.size(); ++i)
+        if (p->owned[i] == ptr) {
+            cudaFree(ptr);
+            p->owned.erase(p->owned.begin() + i);
+            return;
+        }
+}
+
 template <typename T>
 adr_status dev_alloc(Problem* p, T** ptr, size_t count)
 {
@@ -151,6 +165,7 @@ adr_status build_geometry(Problem* p, const uint8_t* mask);
 
 // sweeps (sweep.cu)
 adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off);
+void release_groups(Problem* p, int fam);
 adr_status launch_map_coef(Problem* p, int fam);
 int grid_map_blocks(const Problem* p);
 adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper);

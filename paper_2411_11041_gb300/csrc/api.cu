@@ -46,6 +46,7 @@ struct adr_problem {
     int g_max_iter = -1;
     const double* g_fextra = nullptr;
     double line_unknowns[2] = {0, 0};
+    std::vector<int> offs[2];  // host copies of the curve offsets
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -200,6 +201,12 @@ adr_status check_opts(const adr_opts* o)
         set_error("unsupported opts.init");
         return ADR_EINVAL;
     }
+    if ((o->rows_per_thread != 0 && o->rows_per_thread != 2 && o->rows_per_thread != 4 &&
+         o->rows_per_thread != 8) ||
+        o->map_blocks_per_sm < 0 || o->map_blocks_per_sm > 8) {
+        set_error("opts.rows_per_thread must be 0, 2, 4 or 8 and map_blocks_per_sm 0..8");
+        return ADR_EINVAL;
+    }
     return ADR_OK;
 }
 
@@ -257,6 +264,8 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
     p->mu = mu;
     p->sigma = sigma;
     p->stream = static_cast<cudaStream_t>(stream);
+    if (p->opts.rows_per_thread > 0) p->rows_per_thread = p->opts.rows_per_thread;
+    if (p->opts.map_blocks_per_sm > 0) p->map_blocks_per_sm = p->opts.map_blocks_per_sm;
     p->N = grid->nx * grid->ny;
     {
         int dev = 0;
@@ -280,12 +289,18 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
     if ((s = build_geometry(p, mask))) return fail(s);
     for (int k = 0; k < 3; ++k)
         if ((s = dev_alloc(p, &p->ubuf[k], N))) return fail(s);
-    p->n_partial_blocks = grid_map_blocks(p);
+    {
+        int keep = p->map_blocks_per_sm;  // partial sums sized for the largest map grid
+        p->map_blocks_per_sm = 8;
+        p->n_partial_blocks = grid_map_blocks(p);
+        p->map_blocks_per_sm = keep;
+    }
     if ((s = dev_alloc(p, &p->partial, 2 * (size_t)p->n_partial_blocks)) ||
         (s = dev_alloc(p, &p->state, 1)) || (s = dev_alloc(p, &p->fextra, N)))
         return fail(s);
     for (int fam = 0; fam < 2; ++fam) {
-        std::vector<int> off(p->fam[fam].n_lines + 1);
+        std::vector<int>& off = h->offs[fam];
+        off.resize(p->fam[fam].n_lines + 1);
         if ((e = cudaMemcpy(off.data(), p->fam[fam].off, off.size() * sizeof(int),
                             cudaMemcpyDeviceToHost)))
             return fail(cuda_fail(e, "cudaMemcpy"));
@@ -445,6 +460,49 @@ adr_status adr_get_crossings(const adr_problem* h, int fam, int* seg, double* t,
     if (seg) ADR_CUDA_TRY(cudaMemcpy(seg, F.cg, sizeof(int) * n, cudaMemcpyDeviceToHost));
     if (t) ADR_CUDA_TRY(cudaMemcpy(t, F.ct, sizeof(double) * n, cudaMemcpyDeviceToHost));
     if (pos) ADR_CUDA_TRY(cudaMemcpy(pos, F.cpos, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return ADR_OK;
+}
+
+adr_status adr_autotune(adr_problem* h, int reps, int* rows_out, int* blocks_out, double* ms_out)
+{
+    g_err.clear();
+    if (!h || reps < 1) {
+        set_error("bad arguments to adr_autotune");
+        return ADR_EINVAL;
+    }
+    Problem* p = &h->p;
+    const int rows[3] = {2, 4, 8}, blocks[3] = {2, 4, 8};
+    double best = 1e300;
+    int bR = p->rows_per_thread, bM = p->map_blocks_per_sm;
+    double ms[4];
+    for (int R : rows) {
+        p->rows_per_thread = R;
+        drop_graph(h);
+        for (int fam = 0; fam < 2; ++fam) {
+            release_groups(p, fam);
+            TRY(setup_groups(p, fam, h->offs[fam]));
+        }
+        for (int M : blocks) {
+            p->map_blocks_per_sm = M;
+            TRY(adr_time_kernels(h, reps, ms));
+            double t = ms[0] + ms[1] + ms[2] + ms[3];
+            if (t < best) {
+                best = t;
+                bR = R;
+                bM = M;
+            }
+        }
+    }
+    p->rows_per_thread = bR;
+    p->map_blocks_per_sm = bM;
+    drop_graph(h);
+    for (int fam = 0; fam < 2; ++fam) {
+        release_groups(p, fam);
+        TRY(setup_groups(p, fam, h->offs[fam]));
+    }
+    if (rows_out) *rows_out = bR;
+    if (blocks_out) *blocks_out = bM;
+    if (ms_out) *ms_out = best;
     return ADR_OK;
 }
 

@@ -898,12 +898,13 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
     for (int l : order) {
         int m = off[l + 1] - off[l] - 2;
         int T = 32, lg = 5;
-        while (T < 1024 && (long long)T * kCmax < m) {
+        const int R = (p->rows_per_thread >= 1 && p->rows_per_thread <= kCmax) ? p->rows_per_thread : kCmax;
+        while (T < 1024 && (long long)T * R < m) {
             T *= 2;
             lg++;
         }
         if ((long long)T * kCmax < m) {
-            set_error("a curve has more than 16384 unknowns");
+            set_error("a curve has more than 8192 unknowns");
             return ADR_EINVAL;
         }
         byT[lg].push_back(l);
@@ -965,6 +966,31 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
     ADR_CUDA_TRY(cudaGetLastError());
     ADR_CUDA_TRY(cudaStreamSynchronize(st));
     return ADR_OK;
+}
+
+void release_groups(Problem* p, int fam)
+{
+    Family& F = p->fam[fam];
+    void* bufs[] = {F.soff, F.gcell, F.glx, F.gly, F.fac, F.fac32, F.Fl, F.srow};
+    for (void* q : bufs) dev_free(p, q);
+    F.soff = nullptr;
+    F.gcell = nullptr;
+    F.glx = nullptr;
+    F.gly = nullptr;
+    F.fac = nullptr;
+    F.fac32 = nullptr;
+    F.Fl = nullptr;
+    F.srow = nullptr;
+    for (int k = 0; k < kItemSets; ++k) {
+        ItemSet& I = F.iset[k];
+        dev_free(p, I.T);
+        dev_free(p, I.curve);
+        dev_free(p, I.lanec);
+        dev_free(p, I.lanec32);
+        I = ItemSet();
+    }
+    F.prep_valid = false;
+    F.load_plain = false;
 }
 
 adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper)
@@ -1085,7 +1111,8 @@ adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out
 int grid_map_blocks(const Problem* p)
 {
     long long need = (p->N + kGridThreads - 1) / kGridThreads;
-    long long cap = 8LL * (p->n_sm > 0 ? p->n_sm : 152);
+    int per_sm = (p->map_blocks_per_sm >= 1 && p->map_blocks_per_sm <= 8) ? p->map_blocks_per_sm : 8;
+    long long cap = (long long)per_sm * (p->n_sm > 0 ? p->n_sm : 152);
     return (int)(need < cap ? need : cap);
 }
 

@@ -61,3 +61,22 @@ def test_batch_reports_problems_that_hit_max_iter(torch_cuda):
     assert stats[1]["iters"] == 5 and stats[0]["iters"] > 5 and stats[2]["iters"] > 5
     ref = O.Oracle(probs[1]).solve_stationary(tol=1e-12, max_iter=5)[0]
     assert np.abs(outs[1].cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_autotune_keeps_the_solution(torch_cuda, tmp_path, monkeypatch):
+    from paper_2411_11041_gb300 import Solver, _tune_cache
+    monkeypatch.setenv("ADR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    p = W.sheared(n=129)
+    s0 = Solver(p, tol=1e-9)
+    u0, _, st0, _ = s0.solve_stationary()
+    s1 = Solver(p, tol=1e-9, autotune=True)
+    r, m, ms = s1.tuned
+    assert r in (2, 4, 8) and m in (2, 4, 8) and ms > 0
+    u1, _, st1, _ = s1.solve_stationary()
+    assert st1["iters"] == st0["iters"]
+    assert (u1 - u0).abs().max().item() <= 1e-12 * u0.abs().max().item()
+    assert len(_tune_cache()) == 1
+    s2 = Solver(p, tol=1e-9, autotune=True)  # from the cache
+    assert s2.tuned is None and s2.opts.rows_per_thread == r
+    u2, _, _, _ = s2.solve_stationary()
+    assert (u2 - u1).abs().max().item() <= 1e-12 * u0.abs().max().item()
