@@ -398,7 +398,8 @@ def run_batch(args):
     prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
     probs = W.batch(count=args.count)
     t0 = time.perf_counter()
-    solvers = [Solver(p, device=dev, tol=args.tol, max_iter=200000, prec=prec) for p in probs]
+    solvers = [Solver(p, device=dev, tol=args.tol, max_iter=200000, prec=prec, interp_weights=1)
+               for p in probs]
     setup_s = time.perf_counter() - t0
     batch = Batch(solvers)
     stream = torch.cuda.current_stream(dev)

@@ -42,7 +42,8 @@ typedef enum {
     ADR_EINVAL = 1,   /* invalid argument (sizes, mu/sigma <= 0, |beta| = 0, empty mask ...) */
     ADR_ENOMEM = 2,   /* device or host allocation failed */
     ADR_ECUDA = 3,    /* a CUDA call failed (message in adr_last_error) */
-    ADR_ENOCONV = 4,  /* max_iter reached before tol; outputs hold the last iterate */
+    ADR_ENOCONV = 4,  /* max_iter reached before tol, or the iteration diverged (a norm
+                         stopped being finite); outputs hold the last iterate */
     ADR_EGEOM = 5,    /* curve tracing failed (closed integral curve or |beta| = 0 on a curve) */
     ADR_ETIMEOUT = 6  /* reserved: a bounded device wait gave up */
 } adr_status;
@@ -82,6 +83,10 @@ typedef struct {
                                (0 = 8); a curve of m unknowns gets blocks of the smallest
                                power-of-two T >= 32 with T * rows_per_thread >= m */
     int map_blocks_per_sm;  /* blocks per SM of the curve -> grid map: 1..8 (0 = 8) */
+    int interp_weights;     /* curve -> grid: 0 = average of the row and column values (§6);
+                               1 = weights by the opposite direction's crossing gap, for
+                               flow nearly parallel to a grid axis */
+    int reserved;           /* must be 0 */
 } adr_opts;
 
 /* Result statistics (host struct filled by the solve calls). */

@@ -62,6 +62,7 @@ struct orc_problem {
     unsigned char* ntype; /* [ny*nx] node classes */
     int const_beta;
     double bmax;
+    int interp_weights; /* 0: plain average of the row and column values; 1: inverse-gap weights */
     family fam[2];
 };
 
@@ -800,6 +801,7 @@ void orc_destroy(orc_problem* p)
 }
 
 int orc_const_beta(const orc_problem* p) { return p->const_beta; }
+void orc_set_interp_weights(orc_problem* p, int mode) { p->interp_weights = mode ? 1 : 0; }
 
 void orc_node_types(const orc_problem* p, unsigned char* out)
 {
@@ -854,7 +856,11 @@ static double cross_value(const crossing* c, const double* v)
 
 /* line values -> grid (§6): linear interpolation between the nearest crossing
  * on each side along the node's row and along its column, then the average of
- * the two.  Non-interior nodes get 0. */
+ * the two (the paper's rule).  Optional reading for flow nearly parallel to a
+ * grid axis, where the crossings on one grid direction are sparse: weight the
+ * row value by the column gap and the column value by the row gap,
+ * (g_c row + g_r col) / (g_r + g_c), g = distance between the two crossings
+ * (a zero gap takes that direction's value alone).  Non-interior nodes get 0. */
 void orc_map_to_grid(const orc_problem* p, int fam, const double* vals, double* grid)
 {
     const family* F = &p->fam[fam];
@@ -880,7 +886,9 @@ void orc_map_to_grid(const orc_problem* p, int fam, const double* vals, double* 
                 double w = (r - c[2].pos) / (c[3].pos - c[2].pos);
                 col = (1.0 - w) * vD + w * vU;
             }
-            grid[node] = 0.5 * (row + col);
+            double gr = c[1].pos - c[0].pos, gc = c[3].pos - c[2].pos;
+            if (p->interp_weights && gr + gc > 0.0) grid[node] = (gc * row + gr * col) / (gr + gc);
+            else grid[node] = 0.5 * (row + col);
         }
 }
 
@@ -1142,6 +1150,8 @@ void orc_paper_u0(const orc_problem* p, double* u0)
     free(r);
 }
 
+/* relative update; a norm that is not finite (a diverging iteration) gives
+ * rel = infinity, which ends the iteration without convergence */
 static void relative_update(const orc_problem* p, const double* u, const double* un,
                             double* rel)
 {
@@ -1152,7 +1162,8 @@ static void relative_update(const orc_problem* p, const double* u, const double*
         num += dlt * dlt;
         den += un[k] * un[k];
     }
-    *rel = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+    if (!isfinite(num) || !isfinite(den)) *rel = INFINITY;
+    else *rel = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
 }
 
 /* Stationary problem (BVP1) as the large-time limit of Parabolic1 (§2),
@@ -1186,10 +1197,11 @@ int orc_solve_stationary(const orc_problem* p, double theta, double dt, double t
             status = ORC_OK;
             break;
         }
+        if (!isfinite(rel)) break; /* diverged */
         if (j + 1 < max_iter) memcpy(u, un, N * sizeof(double));
     }
     int done = (j < max_iter) ? j + 1 : max_iter;
-    if (tol <= 0.0) status = ORC_OK; /* a fixed number of steps was asked for */
+    if (tol <= 0.0 && isfinite(rel)) status = ORC_OK; /* a fixed number of steps was asked for */
     if (max_iter <= 0) memcpy(un, u, N * sizeof(double)), memcpy(uh, u, N * sizeof(double));
     for (size_t k = 0; k < N; ++k)
         u_out[k] = (theta == 0.5) ? 0.5 * (u[k] + uh[k]) : un[k];

@@ -32,6 +32,9 @@ int orc_create(int nx, int ny, double x0, double y0, double x1, double y1,
                orc_problem** out);
 void orc_destroy(orc_problem* p);
 
+/* curve -> grid weighting: 0 = plain average (default), 1 = inverse gaps */
+void orc_set_interp_weights(orc_problem* p, int mode);
+
 /* geometry queries */
 int orc_const_beta(const orc_problem* p);
 void orc_node_types(const orc_problem* p, unsigned char* out /* [ny*nx] */);

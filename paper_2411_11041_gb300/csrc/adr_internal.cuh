@@ -178,6 +178,7 @@ struct BatchDev;
 adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const double* tols,
                             const int* max_iters, BatchDev** out);
 adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHandle cond);
+adr_status batch_dev_reset(BatchDev* b, cudaStream_t st);
 void batch_dev_destroy(BatchDev* b);
 adr_status launch_state_reset(Problem* p);
 

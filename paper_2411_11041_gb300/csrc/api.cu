@@ -47,6 +47,7 @@ struct adr_problem {
     const double* g_fextra = nullptr;
     double line_unknowns[2] = {0, 0};
     std::vector<int> offs[2];  // host copies of the curve offsets
+    bool diverged = false;     // the last iteration stopped on a non-finite norm
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -151,6 +152,10 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     *converged = st.converged != 0;
+    if (st.iter > 0 && !std::isfinite(st.rel)) {
+        *converged = false;
+        h->diverged = true;
+    }
     if (stats) {
         stats->iters += st.iter;
         stats->rel_update = st.rel;
@@ -191,6 +196,10 @@ adr_status check_opts(const adr_opts* o)
     }
     if (!(o->theta > 0.0 && o->theta <= 1.0)) {
         set_error("opts.theta must lie in (0, 1]");
+        return ADR_EINVAL;
+    }
+    if (o->interp_weights != 0 && o->interp_weights != 1) {
+        set_error("opts.interp_weights must be 0 or 1");
         return ADR_EINVAL;
     }
     if (o->max_iter < 0 || !std::isfinite(o->dt) || std::isnan(o->tol)) {
@@ -346,6 +355,11 @@ adr_status adr_solve_stationary(adr_problem* h, const double* u_init, double* u_
     bool conv = false;
     TRY(run_iteration(h, o.theta, dt, p->sigma, nullptr, 0.0, o.tol, o.max_iter,
                       o.theta == 0.5, u_out, u_iter_out, stats, &conv));
+    if (h->diverged) {
+        h->diverged = false;
+        set_error("the iteration diverged (a norm stopped being finite)");
+        return ADR_ENOCONV;
+    }
     if (!conv && o.tol > 0.0) {
         set_error("max_iter reached before tol");
         return ADR_ENOCONV;
@@ -707,6 +721,7 @@ adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* co
             TRY(launch_state_reset(&h->p));
         }
         TRY(prepare_batch(b));
+        TRY(batch_dev_reset(b->dev, b->stream));
         ADR_CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
         ADR_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
         for (int i = 0; i < n; ++i)
@@ -723,7 +738,7 @@ adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* co
     bool all = true;
     for (int i = 0; i < n; ++i) {
         adr_problem* h = b->hs[i];
-        if (!st[i].converged && h->p.opts.tol > 0.0) all = false;
+        if ((!st[i].converged && h->p.opts.tol > 0.0) || !std::isfinite(st[i].rel)) all = false;
         if (stats) {
             stats[i].iters = st[i].iter;
             stats[i].rel_update = st[i].rel;

@@ -587,16 +587,31 @@ struct BatchItem {
     int curves[8];
 };
 
+// Active work lists of a batch: double-buffered index lists (buffer *sel is
+// current) rebuilt by k_batch_compact when a problem converges.
+struct ActiveLists {
+    int* items[2][2][3];  // [buffer][family][set] indices into the item arrays
+    int* blocks[2];       // [buffer] indices into the map block table
+    int* count;           // [buffer][2 fam * 3 sets + 1]
+    const int* const* blocks_dev;  // device copy of blocks[2] (for the map kernel)
+    int* sel;             // current buffer
+    int* changed;         // a problem finished in this step
+};
+constexpr int kCountPerBuf = 7;
+
 template <int BS, int FAM, bool REF>
 __global__ void __launch_bounds__(BS) k_curve_solve_batch(const CurveArgs* __restrict__ table,
                                                           const BatchItem* __restrict__ items,
-                                                          int n_items, int set)
+                                                          ActiveLists act, int set)
 {
     __shared__ double sR[2][BS];
     __shared__ float sRf[2][BS];
     __shared__ double sX[BS];
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const BatchItem& I = items[it];
+    const int cur = *act.sel;
+    const int* list = act.items[cur][FAM][set];
+    const int n_act = act.count[cur * kCountPerBuf + FAM * 3 + set];
+    for (int ii = blockIdx.x; ii < n_act; ii += gridDim.x) {
+        const BatchItem& I = items[list[ii]];
         const CurveArgs& a = table[2 * I.prob + FAM];
         if (a.state->done) continue;  // uniform: one problem per item
         if (REF)
@@ -627,20 +642,30 @@ struct GridArgs {
 // combined weights of the curve -> grid map (setup): the row value
 // (1-w) vL + w vR and the column value, each crossing v = (1-t) v[g] + t v[g+1],
 // averaged, written as 8 products with the curve values
+// (weights mode 1: the row value weighted by the column gap and the column
+// value by the row gap instead of 1/2 each)
 __global__ void k_map_coef(long long N, const uint8_t* ntype, const int* cg, const double* ct,
-                           const double* cw, int* mg, double* mc)
+                           const double* cw, const double* cpos, int weights, int* mg, double* mc)
 {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k >= N) return;
+    double ar = 0.5, ac = 0.5;
+    if (weights) {
+        double gr = cpos[4 * k + 1] - cpos[4 * k], gc = cpos[4 * k + 3] - cpos[4 * k + 2];
+        if (gr + gc > 0.0) {
+            ar = gc / (gr + gc);
+            ac = gr / (gr + gc);
+        }
+    }
     for (int q = 0; q < 4; ++q) {
         int g = cg[4 * k + q];
         double t = ct[4 * k + q];
         double w = cw[2 * k + (q >> 1)];
-        double side = (q & 1) ? w : 1.0 - w;  // left/down: 1-w, right/up: w
+        double side = ((q & 1) ? w : 1.0 - w) * (q < 2 ? ar : ac);
         bool ok = ntype[k] == kInterior && g >= 0;
         mg[4 * k + q] = ok ? g : 0;
-        mc[8 * k + 2 * q] = ok ? 0.5 * side * (1.0 - t) : 0.0;
-        mc[8 * k + 2 * q + 1] = ok ? 0.5 * side * t : 0.0;
+        mc[8 * k + 2 * q] = ok ? side * (1.0 - t) : 0.0;
+        mc[8 * k + 2 * q + 1] = ok ? side * t : 0.0;
     }
 }
 
@@ -719,22 +744,94 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_map(GridArgs a)
 template <bool NORMS>
 __global__ void __launch_bounds__(kGridThreads) k_grid_map_batch(const GridArgs* __restrict__ table,
                                                                 int fam, const int* blk_prob,
-                                                                const int* blk_local, const int* nblk)
+                                                                const int* blk_local, const int* nblk,
+                                                                const int* const* act_blocks,
+                                                                const int* act_count, const int* sel)
 {
-    int p = blk_prob[blockIdx.x], lb = blk_local[blockIdx.x];
-    const GridArgs& a = table[2 * p + fam];
-    if (a.state->done) return;
-    double dd = 0.0, uu = 0.0;
-    grid_map_body<NORMS>(a, (long long)lb * blockDim.x + threadIdx.x,
-                         (long long)nblk[p] * blockDim.x, dd, uu);
-    if (NORMS) block_sum2(dd, uu, a.partial + 2 * lb);
+    const int cur = *sel;
+    const int* list = act_blocks[cur];
+    const int n_act = act_count[cur * 7 + 6];
+    for (int ii = blockIdx.x; ii < n_act; ii += gridDim.x) {
+        int bk = list[ii];
+        int p = blk_prob[bk], lb = blk_local[bk];
+        const GridArgs& a = table[2 * p + fam];
+        if (a.state->done) continue;  // uniform per block
+        double dd = 0.0, uu = 0.0;
+        grid_map_body<NORMS>(a, (long long)lb * blockDim.x + threadIdx.x,
+                             (long long)nblk[p] * blockDim.x, dd, uu);
+        if (NORMS) block_sum2(dd, uu, a.partial + 2 * lb);
+        __syncthreads();  // block_sum2's shared arrays are reused
+    }
+}
+
+// rebuild the active lists into the other buffer when a problem finished
+__global__ void k_batch_compact(ActiveLists act, const BatchItem* const* items, const int* n_items,
+                                const int* blk_prob, int n_blk, IterState* const* states)
+{
+    if (!*act.changed) return;
+    const int cur = *act.sel, nxt = cur ^ 1;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (int fam = 0; fam < 2; ++fam)
+        for (int k = 0; k < 3; ++k) {
+            const int* list = act.items[cur][fam][k];
+            int n = act.count[cur * kCountPerBuf + fam * 3 + k];
+            for (long long i = t; i < n; i += stride) {
+                int idx = list[i];
+                if (!states[items[fam * 3 + k][idx].prob]->done) {
+                    int pos = atomicAdd(&act.count[nxt * kCountPerBuf + fam * 3 + k], 1);
+                    act.items[nxt][fam][k][pos] = idx;
+                }
+            }
+        }
+    const int* bl = act.blocks[cur];
+    int nb = act.count[cur * kCountPerBuf + 6];
+    for (long long i = t; i < nb; i += stride) {
+        int bk = bl[i];
+        if (!states[blk_prob[bk]]->done) {
+            int pos = atomicAdd(&act.count[nxt * kCountPerBuf + 6], 1);
+            act.blocks[nxt][pos] = bk;
+        }
+    }
+}
+
+// make the rebuilt lists current and clear the other buffer's counters
+__global__ void k_batch_flip(ActiveLists act)
+{
+    if (!*act.changed) return;
+    int nxt = *act.sel ^ 1;
+    for (int q = 0; q < kCountPerBuf; ++q) act.count[(nxt ^ 1) * kCountPerBuf + q] = 0;
+    *act.sel = nxt;
+    *act.changed = 0;
+}
+
+// all problems active: identity lists in buffer 0
+__global__ void k_batch_reset(ActiveLists act, const int* n_items, int n_blk)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (int fam = 0; fam < 2; ++fam)
+        for (int k = 0; k < 3; ++k)
+            for (long long i = t; i < n_items[fam * 3 + k]; i += stride) act.items[0][fam][k][i] = (int)i;
+    for (long long i = t; i < n_blk; i += stride) act.blocks[0][i] = (int)i;
+    if (t == 0) {
+        for (int fam = 0; fam < 2; ++fam)
+            for (int k = 0; k < 3; ++k) {
+                act.count[fam * 3 + k] = n_items[fam * 3 + k];
+                act.count[kCountPerBuf + fam * 3 + k] = 0;
+            }
+        act.count[6] = n_blk;
+        act.count[kCountPerBuf + 6] = 0;
+        *act.sel = 0;
+        *act.changed = 0;
+    }
 }
 
 // batched convergence test: block p reduces problem p's partial sums; the last
 // block to finish clears the graph condition when every problem is done
 __global__ void k_check_batch(IterState* const* states, const double* const* partials,
                               const int* nblk, int n_prob, const double* tols, const int* max_iters,
-                              unsigned int* ticket, cudaGraphConditionalHandle handle)
+                              unsigned int* ticket, cudaGraphConditionalHandle handle, int* changed)
 {
     int p = blockIdx.x;
     IterState* st = states[p];
@@ -762,12 +859,14 @@ __global__ void k_check_batch(IterState* const* states, const double* const* par
         if (threadIdx.x == 0) {
             double num = sd[0], den = su[0];
             double rel = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+            if (!isfinite(num) || !isfinite(den)) rel = INFINITY;  // diverged
             int iter = st->iter + 1;
             int conv = tol > 0.0 && rel <= tol;
             st->iter = iter;
             st->rel = rel;
             st->converged = conv;
-            st->done = (conv || iter >= max_iter) ? 1 : 0;
+            st->done = (conv || iter >= max_iter || !isfinite(rel)) ? 1 : 0;
+            if (st->done) *changed = 1;
         }
     }
     if (threadIdx.x == 0) {
@@ -811,12 +910,13 @@ __global__ void k_check(IterState* st, const double* partial, int nblocks, doubl
     if (threadIdx.x == 0) {
         double num = sd[0], den = su[0];
         double rel = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+        if (!isfinite(num) || !isfinite(den)) rel = INFINITY;  // diverged
         int iter = st->iter + 1;
         int conv = tol > 0.0 && rel <= tol;
         st->iter = iter;
         st->rel = rel;
         st->converged = conv;
-        st->done = (conv || iter >= max_iter) ? 1 : 0;
+        st->done = (conv || iter >= max_iter || !isfinite(rel)) ? 1 : 0;
         if (use_cond) cudaGraphSetConditional(handle, st->done ? 0 : 1);
     }
 }
@@ -1075,8 +1175,8 @@ adr_status launch_map_coef(Problem* p, int fam)
 {
     Family& F = p->fam[fam];
     long long N = p->N;
-    k_map_coef<<<(int)((N + 255) / 256), 256, 0, p->stream>>>(N, p->ntype, F.cg, F.ct, F.cw, F.mg,
-                                                            F.mc);
+    k_map_coef<<<(int)((N + 255) / 256), 256, 0, p->stream>>>(N, p->ntype, F.cg, F.ct, F.cw, F.cpos,
+                                                            p->opts.interp_weights, F.mg, F.mc);
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }
@@ -1170,6 +1270,11 @@ struct BatchDev {
     int* max_iter = nullptr;
     unsigned int* ticket = nullptr;
     bool ref = false;
+    // active lists (see ActiveLists)
+    ActiveLists act{};
+    const BatchItem** d_items = nullptr;  // [6] item arrays per family and set
+    int* d_n_items = nullptr;             // [6]
+    int map_grid = 0;
     // work items per family and set, with their persistent grid sizes
     BatchItem* it[2][kItemSets] = {};
     int nit[2][kItemSets] = {};
@@ -1286,7 +1391,46 @@ adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const 
         return fail(cuda_fail(e, "batch tables"));
     for (int fam = 0; fam < 2; ++fam)
         if ((s = batch_dev_items(b, ps, fam, b->it[fam], b->nit[fam], b->git[fam]))) return fail(s);
+    // active lists
+    std::vector<const BatchItem*> ip(6);
+    std::vector<int> ni(6);
+    for (int fam = 0; fam < 2; ++fam)
+        for (int k = 0; k < 3; ++k) {
+            ip[fam * 3 + k] = b->it[fam][k];
+            ni[fam * 3 + k] = b->nit[fam][k];
+            for (int buf = 0; buf < 2; ++buf)
+                if ((s = bdev_alloc(b, &b->act.items[buf][fam][k], ni[fam * 3 + k] + 1))) return fail(s);
+        }
+    for (int buf = 0; buf < 2; ++buf)
+        if ((s = bdev_alloc(b, &b->act.blocks[buf], b->n_blk + 1))) return fail(s);
+    {
+        int** bd = nullptr;
+        if ((s = bdev_alloc(b, &bd, 2))) return fail(s);
+        if ((e = cudaMemcpy(bd, b->act.blocks, sizeof(int*) * 2, cudaMemcpyHostToDevice)))
+            return fail(cuda_fail(e, "batch lists"));
+        b->act.blocks_dev = bd;
+    }
+    if ((s = bdev_alloc(b, &b->act.count, 2 * kCountPerBuf)) || (s = bdev_alloc(b, &b->act.sel, 1)) ||
+        (s = bdev_alloc(b, &b->act.changed, 1)) || (s = bdev_alloc(b, &b->d_items, 6)) ||
+        (s = bdev_alloc(b, &b->d_n_items, 6)))
+        return fail(s);
+    if ((e = cudaMemcpy(b->d_items, ip.data(), sizeof(BatchItem*) * 6, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->d_n_items, ni.data(), sizeof(int) * 6, cudaMemcpyHostToDevice)))
+        return fail(cuda_fail(e, "batch lists"));
+    {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        b->map_grid = std::min(b->n_blk, 8 * nsm);
+    }
     *out = b;
+    return ADR_OK;
+}
+
+adr_status batch_dev_reset(BatchDev* b, cudaStream_t st)
+{
+    k_batch_reset<<<256, 256, 0, st>>>(b->act, b->d_n_items, b->n_blk);
+    ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }
 
@@ -1357,25 +1501,32 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
         if (!N[k]) continue;                                                                       \
         int BS = 256 << k;                                                                         \
         if (BS == 256) {                                                                           \
-            if (b->ref) k_curve_solve_batch<256, FAM_, true><<<G[k], 256, 0, st>>>(b->ctab, IT[k], N[k], k); \
-            else k_curve_solve_batch<256, FAM_, false><<<G[k], 256, 0, st>>>(b->ctab, IT[k], N[k], k);     \
+            if (b->ref) k_curve_solve_batch<256, FAM_, true><<<G[k], 256, 0, st>>>(b->ctab, IT[k], b->act, k); \
+            else k_curve_solve_batch<256, FAM_, false><<<G[k], 256, 0, st>>>(b->ctab, IT[k], b->act, k);     \
         } else if (BS == 512) {                                                                    \
-            if (b->ref) k_curve_solve_batch<512, FAM_, true><<<G[k], 512, 0, st>>>(b->ctab, IT[k], N[k], k); \
-            else k_curve_solve_batch<512, FAM_, false><<<G[k], 512, 0, st>>>(b->ctab, IT[k], N[k], k);     \
+            if (b->ref) k_curve_solve_batch<512, FAM_, true><<<G[k], 512, 0, st>>>(b->ctab, IT[k], b->act, k); \
+            else k_curve_solve_batch<512, FAM_, false><<<G[k], 512, 0, st>>>(b->ctab, IT[k], b->act, k);     \
         } else {                                                                                   \
-            if (b->ref) k_curve_solve_batch<1024, FAM_, true><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], N[k], k); \
-            else k_curve_solve_batch<1024, FAM_, false><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], N[k], k);     \
+            if (b->ref) k_curve_solve_batch<1024, FAM_, true><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], b->act, k); \
+            else k_curve_solve_batch<1024, FAM_, false><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], b->act, k);     \
         }                                                                                          \
     }
+    const int* const* ab = (const int* const*)b->act.blocks;
     ADR_BATCH_SOLVE(0, itB, nB, gB)
-    k_grid_map_batch<false><<<b->n_blk, kGridThreads, 0, st>>>(b->gtab, 0, b->blk_prob, b->blk_local,
-                                                               b->nblk);
+    k_grid_map_batch<false><<<b->map_grid, kGridThreads, 0, st>>>(b->gtab, 0, b->blk_prob, b->blk_local,
+                                                                 b->nblk, b->act.blocks_dev, b->act.count,
+                                                                 b->act.sel);
     ADR_BATCH_SOLVE(1, itG, nG, gG)
-    k_grid_map_batch<true><<<b->n_blk, kGridThreads, 0, st>>>(b->gtab, 1, b->blk_prob, b->blk_local,
-                                                              b->nblk);
+    k_grid_map_batch<true><<<b->map_grid, kGridThreads, 0, st>>>(b->gtab, 1, b->blk_prob, b->blk_local,
+                                                                b->nblk, b->act.blocks_dev, b->act.count,
+                                                                b->act.sel);
 #undef ADR_BATCH_SOLVE
+    (void)ab;
     k_check_batch<<<b->n, 256, 0, st>>>(b->states, (const double* const*)b->partials, b->nblk, b->n,
-                                        b->tol, b->max_iter, b->ticket, cond);
+                                        b->tol, b->max_iter, b->ticket, cond, b->act.changed);
+    k_batch_compact<<<b->map_grid, 256, 0, st>>>(b->act, b->d_items, b->d_n_items, b->blk_prob,
+                                                 b->n_blk, b->states);
+    k_batch_flip<<<1, 1, 0, st>>>(b->act);
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }

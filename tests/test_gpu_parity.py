@@ -218,3 +218,33 @@ def test_refine_paper_u0_and_parabolic(torch_cuda):
     s.step_parabolic(u, 1e-3, 3, 1)
     ref, _, _ = o.step_parabolic(p.u0, 1e-3, 3, 1, tol=1e-9, max_iter=5000)
     assert relerr(u, ref) <= TOL_REF
+
+
+# ------------------------------------------------ inverse-gap weights, divergence
+
+@pytest.mark.parametrize("name", ["manufactured33", "L_mask", "disc_mask", "sheared65", "steep"])
+def test_weighted_map_mode_matches_oracle(torch_cuda, name):
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    torch = torch_cuda
+    p = PROBLEMS[name]()
+    o = O.Oracle(p, interp_weights=1)
+    s = Solver(p, interp_weights=1, tol=1e-9, max_iter=20000)
+    u = np.random.default_rng(2).normal(size=(p.ny, p.nx)) * o.interior()
+    uh, un = s.split_step(torch.tensor(u, device="cuda:0"), 0.05)
+    ouh, oun = o.split_step(0.5, 0.05, u)
+    assert relerr(uh, ouh) <= TOL64 and relerr(un, oun) <= TOL64
+    ug, _, stats, st = s.solve_stationary()
+    ref, _, it, _, ost = o.solve_stationary(tol=1e-9, max_iter=20000)
+    assert st == ADR_OK and ost == O.OK and stats["iters"] == it
+    assert relerr(ug, ref) <= TOL64
+
+
+def test_diverging_iteration_is_reported(torch_cuda):
+    from paper_2411_11041_gb300 import ADR_ENOCONV, Solver, lib
+    p = W.manufactured(n=17)
+    s = Solver(p, theta=0.1, dt=5.0, tol=1e-8, max_iter=100000)
+    u, _, stats, st = s.solve_stationary()
+    _, _, it, _, ost = O.Oracle(p).solve_stationary(theta=0.1, dt=5.0, tol=1e-8, max_iter=100000)
+    assert st == ADR_ENOCONV and ost == O.ENOCONV
+    assert b"diverged" in lib().adr_last_error()
+    assert abs(stats["iters"] - it) <= 2 and stats["iters"] < 2000

@@ -444,3 +444,51 @@ def test_one_split_step_equals_dense_directional_step(theta):
     u2, _, _ = o.step_parabolic(u, dt, 2, 0, theta=theta)
     _, ref2 = o.split_step(theta, dt, oun)
     np.testing.assert_allclose(u2, ref2, atol=1e-14 * np.abs(ref2).max())
+
+
+# ------------------------------------------- inverse-gap weighting, divergence
+
+@pytest.mark.parametrize("mask", ["square", "L"])
+def test_weighted_map_is_identity_for_aligned_lines(mask):
+    n = 21
+    o = O.Oracle(_prob(n, beta=(0.0, -1.0), mask=mask), interp_weights=1)
+    g = np.random.default_rng(1).normal(size=(n, n)) * o.interior()
+    for fam in (0, 1):
+        assert np.array_equal(o.map_to_grid(fam, o.gather(fam, g)), g)
+
+
+@pytest.mark.parametrize("beta", [(1.0, 0.5), (1.0, 0.03), (-0.2, 1.0)])
+def test_weighted_map_reproduces_linear_functions(beta):
+    n = 25
+    o = O.Oracle(_prob(n, beta=beta), interp_weights=1)
+    xi, eta = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float))
+    for fam in (0, 1):
+        L = o.lines(fam)
+        g = o.map_to_grid(fam, 0.4 + 0.7 * L["xi"] - 1.3 * L["eta"])
+        seg, _, _ = o.crossings(fam)
+        ok = o.interior() & np.all(seg >= 0, axis=2)
+        np.testing.assert_allclose(g[ok], (0.4 + 0.7 * xi - 1.3 * eta)[ok], atol=1e-12)
+
+
+def test_weighted_map_prefers_the_denser_direction():
+    """With flow at 1.5 degrees the row crossings of the B curves are far apart;
+    the weighted value of a smooth function is far closer to it than the
+    plain average."""
+    n = 65
+    X, Y = W.node_coords(n, n)
+    g = np.sin(np.pi * X) * np.sin(2 * np.pi * Y)
+    errs = []
+    for w in (0, 1):
+        o = O.Oracle(_prob(n, beta=(1.0, np.tan(np.radians(1.5)))), interp_weights=w)
+        errs.append(np.abs(o.map_to_grid(0, o.gather(0, g * o.interior())) - g * o.interior()).max())
+    assert errs[1] < 0.2 * errs[0], errs
+
+
+def test_diverging_iteration_stops_without_convergence():
+    """theta = 0.1 with a large step amplifies stiff modes by about -(1-theta)/theta
+    per step: the iteration must end as not converged once a norm overflows,
+    long before max_iter, instead of reading 0/inf as convergence."""
+    p = W.manufactured(n=17)
+    o = O.Oracle(p)
+    u, uit, it, rel, st = o.solve_stationary(theta=0.1, dt=5.0, tol=1e-8, max_iter=100000)
+    assert st == O.ENOCONV and not np.isfinite(rel) and it < 2000
