@@ -14,6 +14,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "adr_oracle.c")
+SRCS = [SRC, os.path.join(HERE, "cnn_oracle.c")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 OK, EINVAL, ENOMEM, ENOCONV, EGEOM = 0, 1, 2, 4, 5
@@ -22,10 +23,10 @@ OUTSIDE, DIRICHLET, INTERIOR = 0, 1, 2
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
-            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "adr_oracle.h"))):
+    deps = SRCS + [os.path.join(HERE, "adr_oracle.h")]
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(map(os.path.getmtime, deps)):
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
-                               "-shared", "-o", LIB, SRC, "-lm"])
+                               "-shared", "-o", LIB, *SRCS, "-lm"])
     return LIB
 
 
@@ -74,6 +75,19 @@ def lib():
         L.orc_step_parabolic.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.c_double,
                                          C.c_double, C.c_double, C.c_int, dp,
                                          C.POINTER(C.c_int)]
+        L.cnn_num_params.restype = C.c_long
+        L.cnn_set_size.argtypes = [C.c_int, C.c_int]
+        L.cnn_set_size.restype = None
+        L.cnn_param_offset.argtypes = [C.c_int, C.c_int]
+        L.cnn_param_offset.restype = C.c_long
+        L.cnn_channels.argtypes = [C.c_int]
+        L.cnn_dilation.argtypes = [C.c_int]
+        L.cnn_features.argtypes = [C.c_int, dp, dp, dp, up, C.c_double, C.c_double, dp]
+        L.cnn_target.argtypes = [C.c_int, dp, C.c_double, dp]
+        L.cnn_forward.argtypes = [dp, dp, vp, dp]
+        L.cnn_loss_grad.argtypes = [dp, C.c_int, dp, dp, vp]
+        L.cnn_loss_grad.restype = C.c_double
+        L.cnn_upsample.argtypes = [C.c_int, dp, C.c_double, up, dp]
         for fn in ("orc_q1_dense", "orc_p1_dense"):
             getattr(L, fn).argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                        C.c_double, up, C.c_double, C.c_double, dp, dp, dp, dp]
@@ -246,3 +260,74 @@ def q1_dense(prob, **kw):
 
 def p1_dense(prob, **kw):
     return _dense(lib().orc_p1_dense, prob, **kw)
+
+
+# ------------------------------------------------------------ warm-start net
+
+class CNN:
+    """FP64 reference of the warm-start network (cnn_oracle.c)."""
+    H = W = 64
+    LAYERS = 8
+
+    @staticmethod
+    def num_params():
+        return lib().cnn_num_params()
+
+    @staticmethod
+    def channels():
+        return [lib().cnn_channels(l) for l in range(CNN.LAYERS + 1)]
+
+    @staticmethod
+    def dilations():
+        return [lib().cnn_dilation(l) for l in range(CNN.LAYERS)]
+
+    @staticmethod
+    def offset(l, bias=False):
+        return lib().cnn_param_offset(l, int(bias))
+
+    @staticmethod
+    def features(prob):
+        x = np.zeros((64, 64, 8))
+        lib().cnn_features(prob.nx, _c(prob.f), _c(prob.beta1), _c(prob.beta2),
+                           _c(prob.mask, np.uint8), prob.mu, prob.sigma, x)
+        return x
+
+    @staticmethod
+    def target(u, sigma):
+        t = np.zeros((64, 64))
+        lib().cnn_target(u.shape[0], _c(u), sigma, t)
+        return t
+
+    @staticmethod
+    def forward(params, x):
+        out = np.zeros((64, 64))
+        lib().cnn_forward(_c(params), _c(x), None, out)
+        return out
+
+    @staticmethod
+    def set_size(h, w):
+        lib().cnn_set_size(int(h), int(w))
+
+    @staticmethod
+    def loss_grad(params, xs, ts, want_grad=True):
+        g = np.zeros(CNN.num_params()) if want_grad else None
+        loss = lib().cnn_loss_grad(_c(params), len(xs), _c(xs), _c(ts), _ptr(g))
+        return loss, g
+
+    @staticmethod
+    def upsample(y, sigma, interior, n=256):
+        u = np.zeros((n, n))
+        lib().cnn_upsample(n, _c(y), sigma, _c(interior, np.uint8), u)
+        return u
+
+    @staticmethod
+    def init_params(seed=0):
+        """He-normal weights, zero biases (the last layer scaled down)."""
+        rng = np.random.default_rng(seed)
+        p = np.zeros(CNN.num_params())
+        ch = CNN.channels()
+        for l in range(CNN.LAYERS):
+            n = 9 * ch[l] * ch[l + 1]
+            std = np.sqrt(2.0 / (9 * ch[l])) * (0.1 if l == CNN.LAYERS - 1 else 1.0)
+            p[CNN.offset(l):CNN.offset(l) + n] = rng.normal(0, std, n)
+        return p
