@@ -226,15 +226,16 @@ adr_status adr_autotune(adr_problem* prob, int reps, int* rows_per_thread,
  * batch's cudaStream_t (or NULL).  Errors: ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA.
  * adr_batch_solve: u_init (nullable host array of n device grids, read for
  * handles with init == ADR_INIT_USER), u_out (host array of n device grids
- * [ny][nx] of the respective handles), stats (nullable host array of n;
- * ms = device time of the whole batch).  Returns ADR_ENOCONV if a problem hit
+ * [ny][nx] of the respective handles), u_iter_out (nullable host array of n
+ * nullable device grids <- u_{j+1}, the iterate, as in adr_solve_stationary),
+ * stats (nullable host array of n; ms = device time of the whole batch).  Returns ADR_ENOCONV if a problem hit
  * max_iter (all outputs written).
  * adr_solve_batch: create, solve from the handles' initial states, destroy.
  */
 typedef struct adr_batch adr_batch;
 adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_batch** out);
 adr_status adr_batch_solve(adr_batch* batch, const double* const* u_init, double* const* u_out,
-                           adr_stats* stats);
+                           double* const* u_iter_out, adr_stats* stats);
 void adr_batch_destroy(adr_batch* batch);
 adr_status adr_solve_batch(adr_problem* const* probs, int n, double* const* u_out,
                            adr_stats* stats);
@@ -274,6 +275,71 @@ adr_status adr_cross_substep_noalloc(int nx, int ny, double mu, double theta, do
                                      const double* h, const double* xi, const double* eta,
                                      const int* seg, const double* t, const double* pos,
                                      double* u_out, void* stream);
+
+/*
+ * Learned warm start (no counterpart in the paper; the paper's iteration stays
+ * the solver and the judge of convergence, the network only supplies u_0).
+ *
+ * A convolutional network maps a problem on a 256 x 256 node grid to a
+ * prediction of sigma * u at every node; adr_cnn_initial_state turns it into an
+ * initial state for ADR_INIT_USER.  The grid is read as 64 x 64 cells of 4 x 4
+ * nodes, cell (r, c) holding nodes (4 r + a, 4 c + b), a, b in 0..3.
+ * Features (NHWC, [batch][64][64][24], BF16): channel 4 a + b = f at node
+ * (4 r + a, 4 c + b); 16, 17: cell means of beta1, beta2; 18: (log10 mu + 2.5)/1.5;
+ * 19: sigma - 1; 20: cell mean of the mask; 21..23: 0.
+ * Network: eight 3 x 3 convolutions with zero padding, dilations
+ * 1 2 4 8 16 32 1 1, channels 24 64 64 128 128 128 64 64 16, bias, ReLU after
+ * all but the last (539 k parameters).  Output ([batch][64][64][16], FP32):
+ * channel 4 a + b predicts sigma * u at node (4 r + a, 4 c + b), u the
+ * iterate the stationary solve converges to.  Parameters are one FP32 vector
+ * packed as W_0, b_0, W_1, b_1, ... with W_l[(tap * Cin + ci) * Cout + co],
+ * tap = 3 ky + kx.  Convolutions (forward, data and weight gradients) run on
+ * the BF16 tensor cores with FP32 accumulation; Adam keeps FP32 master
+ * parameters.  Loss: 1/2 of the mean squared error over all outputs of a batch.
+ */
+typedef struct adr_cnn adr_cnn; /* opaque network handle */
+
+/* Number of parameters (host call, no GPU needed). */
+long adr_cnn_num_params(void);
+
+/* adr_cnn_create: params (host float[adr_cnn_num_params()], copied) are the
+ * initial parameters; max_batch bounds the batch of every later call; stream is
+ * the handle's cudaStream_t (or NULL).  Errors: ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA. */
+adr_status adr_cnn_create(int max_batch, const float* params, void* stream, adr_cnn** out);
+void adr_cnn_destroy(adr_cnn* cnn);
+/* Host copies of the FP32 parameters; set also clears the Adam moments. */
+adr_status adr_cnn_set_params(adr_cnn* cnn, const float* params);
+adr_status adr_cnn_get_params(adr_cnn* cnn, float* params);
+
+/* adr_cnn_features: batch problems on n x n nodes, n = 256 (device arrays,
+ * problem b at offset b n n): f, beta1, beta2 double, mask uint8; mu, sigma
+ * device double[batch].  x: device BF16 (uint16 storage) [batch][64][64][24].
+ * Launch only.  Errors: ADR_EINVAL (n != 256, NULL pointer). */
+adr_status adr_cnn_features(int batch, int n, const double* f, const double* beta1,
+                            const double* beta2, const uint8_t* mask, const double* mu,
+                            const double* sigma, uint16_t* x, void* stream);
+/* adr_cnn_targets: t (device float [batch][64][64][16]) <- sigma_b u_b in the
+ * output layout; u device double [batch][n][n], n = 256.  Launch only. */
+adr_status adr_cnn_targets(int batch, int n, const double* u, const double* sigma, float* t,
+                           void* stream);
+/* adr_cnn_forward: y (device float [batch][64][64][16]) <- the network's output.
+ * Launch only, on the handle's stream.  Errors: ADR_EINVAL, ADR_ECUDA. */
+adr_status adr_cnn_forward(adr_cnn* cnn, int batch, const uint16_t* x, float* y);
+/* adr_cnn_loss_grad: forward and backward without an update.  grad (nullable
+ * device float[num_params]) <- d loss / d params; loss (nullable host) <- the
+ * loss (the call then waits for the stream). */
+adr_status adr_cnn_loss_grad(adr_cnn* cnn, int batch, const uint16_t* x, const float* t,
+                             float* grad, double* loss);
+/* adr_cnn_train_step: forward, backward and one Adam step (beta1 0.9, beta2
+ * 0.999, eps 1e-8, learning rate lr > 0).  loss: nullable host, the loss before
+ * the update (the call then waits for the stream). */
+adr_status adr_cnn_train_step(adr_cnn* cnn, int batch, const uint16_t* x, const float* t,
+                              float lr, double* loss);
+/* adr_cnn_initial_state: u_out (device double [256][256]) <- one prediction y
+ * (device float [64][64][16]) in grid layout, divided by the handle's sigma, 0
+ * at non-interior nodes.  Pass it as u_init with ADR_INIT_USER.  Launch only,
+ * on the problem's stream.  Errors: ADR_EINVAL (grid not 256 x 256). */
+adr_status adr_cnn_initial_state(adr_problem* prob, const float* y, double* u_out);
 
 #ifdef __cplusplus
 }

@@ -5,15 +5,16 @@
  * checked against; only the tests and the smoke check load it.
  *
  * The network maps a problem on a 256 x 256 node grid to an initial state.
- * Features at 64 x 64 (one cell per 4 x 4 block of nodes), NHWC, 8 channels:
- *   0: mean of f over the block          1: mean of beta1
- *   2: mean of beta2                      3: (log10(mu) + 2.5) / 1.5
- *   4: sigma - 1                          5: mean of the mask
- *   6, 7: 0
- * Eight 3 x 3 convolutions, zero padding, dilations 1 2 4 8 4 2 1 1,
- * channels 8 64 64 128 128 128 64 64 8, bias, ReLU after all but the last.
- * Output channel 0 predicts sigma * (block mean of the solution); the loss is
- * 1/2 of the mean squared error over channel 0 of all cells of the batch.
+ * The grid is read as 64 x 64 cells of 4 x 4 nodes; cell (r, c) holds the
+ * nodes (4 r + a, 4 c + b), a, b = 0..3.  Features, NHWC, 24 channels:
+ *   4 a + b: f at node (4 r + a, 4 c + b)      16, 17: cell means of beta1, beta2
+ *   18: (log10(mu) + 2.5) / 1.5                 19: sigma - 1
+ *   20: cell mean of the mask                   21..23: 0
+ * Eight 3 x 3 convolutions, zero padding, dilations 1 2 4 8 16 32 1 1,
+ * channels 24 64 64 128 128 128 64 64 16, bias, ReLU after all but the last.
+ * Output channel 4 a + b predicts sigma * u at node (4 r + a, 4 c + b), u the
+ * converged iterate of the stationary solve; the loss is 1/2 of the mean
+ * squared error over all outputs of the batch.
  * Weights of layer l: W[(tap * Cin + ci) * Cout + co], tap = 3 ky + kx.
  */
 #include <math.h>
@@ -21,6 +22,8 @@
 #include <string.h>
 
 #define CNN_LAYERS 8
+#define SUB 4     /* nodes per cell side */
+#define NOUT 16   /* outputs per cell */
 /* spatial size of the network grid: 64 x 64 for the model; the tests may
  * shrink it (the layers are size-agnostic) */
 static int CNN_H = 64, CNN_W = 64;
@@ -30,8 +33,8 @@ void cnn_set_size(int h, int w)
     CNN_W = w;
 }
 
-static const int CH[CNN_LAYERS + 1] = {8, 64, 64, 128, 128, 128, 64, 64, 8};
-static const int DIL[CNN_LAYERS] = {1, 2, 4, 8, 4, 2, 1, 1};
+static const int CH[CNN_LAYERS + 1] = {24, 64, 64, 128, 128, 128, 64, 64, NOUT};
+static const int DIL[CNN_LAYERS] = {1, 2, 4, 8, 16, 32, 1, 1};
 
 int cnn_layers(void) { return CNN_LAYERS; }
 int cnn_channels(int l) { return CH[l]; }
@@ -46,46 +49,38 @@ long cnn_param_offset(int l, int bias)
 }
 long cnn_num_params(void) { return cnn_param_offset(CNN_LAYERS, 0); }
 
-/* features of one problem on an n x n node grid, n = 256 (4 x 4 blocks) */
+/* features of one problem on the (4 CNN_H) x (4 CNN_W) node grid */
 void cnn_features(int n, const double* f, const double* b1, const double* b2,
                   const unsigned char* mask, double mu, double sigma, double* x)
 {
-    int blk = n / CNN_W;
     for (int r = 0; r < CNN_H; ++r)
         for (int c = 0; c < CNN_W; ++c) {
-            double sf = 0, s1 = 0, s2 = 0, sm = 0;
-            for (int a = 0; a < blk; ++a)
-                for (int b = 0; b < blk; ++b) {
-                    size_t k = (size_t)(r * blk + a) * n + (c * blk + b);
-                    sf += f[k];
+            double* o = x + ((size_t)r * CNN_W + c) * CH[0];
+            double s1 = 0, s2 = 0, sm = 0;
+            for (int a = 0; a < SUB; ++a)
+                for (int b = 0; b < SUB; ++b) {
+                    size_t k = (size_t)(r * SUB + a) * n + (c * SUB + b);
+                    o[a * SUB + b] = f[k];
                     s1 += b1[k];
                     s2 += b2[k];
                     sm += mask[k];
                 }
-            double inv = 1.0 / (blk * blk);
-            double* o = x + ((size_t)r * CNN_W + c) * 8;
-            o[0] = sf * inv;
-            o[1] = s1 * inv;
-            o[2] = s2 * inv;
-            o[3] = (log10(mu) + 2.5) / 1.5;
-            o[4] = sigma - 1.0;
-            o[5] = sm * inv;
-            o[6] = 0.0;
-            o[7] = 0.0;
+            o[16] = s1 / (SUB * SUB);
+            o[17] = s2 / (SUB * SUB);
+            o[18] = (log10(mu) + 2.5) / 1.5;
+            o[19] = sigma - 1.0;
+            o[20] = sm / (SUB * SUB);
+            o[21] = o[22] = o[23] = 0.0;
         }
 }
 
-/* target: sigma times the block means of the solution */
+/* target: sigma times the nodal values, in the output layout */
 void cnn_target(int n, const double* u, double sigma, double* t)
 {
-    int blk = n / CNN_W;
-    for (int r = 0; r < CNN_H; ++r)
-        for (int c = 0; c < CNN_W; ++c) {
-            double s = 0;
-            for (int a = 0; a < blk; ++a)
-                for (int b = 0; b < blk; ++b) s += u[(size_t)(r * blk + a) * n + (c * blk + b)];
-            t[(size_t)r * CNN_W + c] = sigma * s / (blk * blk);
-        }
+    for (int r = 0; r < CNN_H * SUB; ++r)
+        for (int c = 0; c < CNN_W * SUB; ++c)
+            t[((size_t)(r / SUB) * CNN_W + c / SUB) * NOUT + (r % SUB) * SUB + (c % SUB)] =
+                sigma * u[(size_t)r * n + c];
 }
 
 /* one convolution layer (pre-activation output) */
@@ -109,8 +104,8 @@ static void conv(const double* x, int cin, const double* W, const double* bias, 
 }
 
 /* forward pass of one sample; acts (nullable) receives the post-activation
- * output of every layer, layer l at acts + cnn_act_offset(l); out: channel 0
- * of the last layer [64*64] */
+ * output of every layer, layer l at acts + cnn_act_offset(l); out (nullable):
+ * the last layer's output [H][W][16] */
 long cnn_act_offset(int l)
 {
     long off = 0;
@@ -132,15 +127,14 @@ void cnn_forward(const double* params, const double* x, double* acts, double* ou
                 if (y[k] < 0.0) y[k] = 0.0;
         in = y;
     }
-    if (out) {
-        const double* y = A + cnn_act_offset(CNN_LAYERS - 1);
-        for (long k = 0; k < (long)CNN_H * CNN_W; ++k) out[k] = y[k * CH[CNN_LAYERS]];
-    }
+    if (out) memcpy(out, A + cnn_act_offset(CNN_LAYERS - 1),
+                    sizeof(double) * CNN_H * CNN_W * CH[CNN_LAYERS]);
     if (!acts) free(A);
 }
 
-/* loss and gradient over a batch: xs[b] features, ts[b] targets.  grad
- * (nullable, cnn_num_params) receives d loss / d params.  Returns the loss. */
+/* loss and gradient over a batch: xs[b] features [H][W][24], ts[b] targets
+ * [H][W][16].  grad (nullable, cnn_num_params) receives d loss / d params.
+ * Returns the loss. */
 double cnn_loss_grad(const double* params, int batch, const double* xs, const double* ts,
                      double* grad)
 {
@@ -148,19 +142,18 @@ double cnn_loss_grad(const double* params, int batch, const double* xs, const do
     double* acts = malloc(sizeof(double) * total);
     double* dy = malloc(sizeof(double) * HW * 128);
     double* dx = malloc(sizeof(double) * HW * 128);
-    double loss = 0.0, scale = 1.0 / (double)(batch * HW);
+    const int cl = CH[CNN_LAYERS];
+    double loss = 0.0, scale = 1.0 / ((double)batch * HW * cl);
     if (grad) memset(grad, 0, sizeof(double) * cnn_num_params());
     for (int b = 0; b < batch; ++b) {
-        const double* x = xs + (size_t)b * HW * 8;
-        const double* t = ts + (size_t)b * HW;
+        const double* x = xs + (size_t)b * HW * CH[0];
+        const double* t = ts + (size_t)b * HW * cl;
         cnn_forward(params, x, acts, NULL);
         const double* yl = acts + cnn_act_offset(CNN_LAYERS - 1);
-        int cl = CH[CNN_LAYERS];
-        memset(dy, 0, sizeof(double) * HW * cl);
-        for (long k = 0; k < HW; ++k) {
-            double e = yl[k * cl] - t[k];
+        for (long k = 0; k < HW * cl; ++k) {
+            double e = yl[k] - t[k];
             loss += 0.5 * e * e * scale;
-            dy[k * cl] = e * scale;
+            dy[k] = e * scale;
         }
         if (!grad) continue;
         for (int l = CNN_LAYERS - 1; l >= 0; --l) {
@@ -202,24 +195,13 @@ double cnn_loss_grad(const double* params, int batch, const double* xs, const do
     return loss;
 }
 
-/* bilinear upsampling of the 64 x 64 cell values (centres at node 4k + 1.5)
- * to the n x n nodes, divided by sigma and zero outside the interior mask */
-void cnn_upsample(int n, const double* y, double sigma, const unsigned char* interior, double* u)
+/* initial state from one output [H][W][16]: u = y / sigma at the interior
+ * nodes, 0 elsewhere */
+void cnn_unpack(int n, const double* y, double sigma, const unsigned char* interior, double* u)
 {
-    int blk = n / CNN_W;
-    for (int r = 0; r < n; ++r)
-        for (int c = 0; c < n; ++c) {
-            double fy = (r - (blk - 1) * 0.5) / blk, fx = (c - (blk - 1) * 0.5) / blk;
-            if (fy < 0) fy = 0;
-            if (fx < 0) fx = 0;
-            if (fy > CNN_H - 1) fy = CNN_H - 1;
-            if (fx > CNN_W - 1) fx = CNN_W - 1;
-            int y0 = (int)fy, x0 = (int)fx;
-            if (y0 > CNN_H - 2) y0 = CNN_H - 2;
-            if (x0 > CNN_W - 2) x0 = CNN_W - 2;
-            double ly = fy - y0, lx = fx - x0;
-            double v = (1 - ly) * ((1 - lx) * y[y0 * CNN_W + x0] + lx * y[y0 * CNN_W + x0 + 1]) +
-                       ly * ((1 - lx) * y[(y0 + 1) * CNN_W + x0] + lx * y[(y0 + 1) * CNN_W + x0 + 1]);
+    for (int r = 0; r < CNN_H * SUB; ++r)
+        for (int c = 0; c < CNN_W * SUB; ++c) {
+            double v = y[((size_t)(r / SUB) * CNN_W + c / SUB) * NOUT + (r % SUB) * SUB + (c % SUB)];
             u[(size_t)r * n + c] = interior[(size_t)r * n + c] ? v / sigma : 0.0;
         }
 }

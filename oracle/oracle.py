@@ -87,7 +87,7 @@ def lib():
         L.cnn_forward.argtypes = [dp, dp, vp, dp]
         L.cnn_loss_grad.argtypes = [dp, C.c_int, dp, dp, vp]
         L.cnn_loss_grad.restype = C.c_double
-        L.cnn_upsample.argtypes = [C.c_int, dp, C.c_double, up, dp]
+        L.cnn_unpack.argtypes = [C.c_int, dp, C.c_double, up, dp]
         for fn in ("orc_q1_dense", "orc_p1_dense"):
             getattr(L, fn).argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                        C.c_double, up, C.c_double, C.c_double, dp, dp, dp, dp]
@@ -287,25 +287,28 @@ class CNN:
 
     @staticmethod
     def features(prob):
-        x = np.zeros((64, 64, 8))
+        """[H][W][24] features of a problem on a (4 H) x (4 W) grid."""
+        x = np.zeros((CNN.H, CNN.W, 24))
         lib().cnn_features(prob.nx, _c(prob.f), _c(prob.beta1), _c(prob.beta2),
                            _c(prob.mask, np.uint8), prob.mu, prob.sigma, x)
         return x
 
     @staticmethod
     def target(u, sigma):
-        t = np.zeros((64, 64))
+        """[H][W][16]: sigma * u in the output layout."""
+        t = np.zeros((CNN.H, CNN.W, 16))
         lib().cnn_target(u.shape[0], _c(u), sigma, t)
         return t
 
     @staticmethod
     def forward(params, x):
-        out = np.zeros((64, 64))
+        out = np.zeros((CNN.H, CNN.W, 16))
         lib().cnn_forward(_c(params), _c(x), None, out)
         return out
 
     @staticmethod
     def set_size(h, w):
+        CNN.H, CNN.W = int(h), int(w)
         lib().cnn_set_size(int(h), int(w))
 
     @staticmethod
@@ -315,9 +318,11 @@ class CNN:
         return loss, g
 
     @staticmethod
-    def upsample(y, sigma, interior, n=256):
-        u = np.zeros((n, n))
-        lib().cnn_upsample(n, _c(y), sigma, _c(interior, np.uint8), u)
+    def unpack(y, sigma, interior):
+        """Initial state on the (4 H) x (4 W) grid from one output [H][W][16]."""
+        n = 4 * CNN.W
+        u = np.zeros((4 * CNN.H, n))
+        lib().cnn_unpack(n, _c(y), sigma, _c(interior, np.uint8), u)
         return u
 
     @staticmethod

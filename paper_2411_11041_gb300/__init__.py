@@ -84,10 +84,25 @@ def lib():
         L.adr_time_kernels.argtypes = [vp, C.c_int, dp]
         L.adr_autotune.argtypes = [vp, C.c_int, ip, ip, dp]
         L.adr_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.POINTER(vp)]
-        L.adr_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(adr_stats)]
+        L.adr_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                      C.POINTER(adr_stats)]
         L.adr_batch_destroy.argtypes = [vp]
         L.adr_batch_destroy.restype = None
         L.adr_solve_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(adr_stats)]
+        fp = C.POINTER(C.c_float)
+        L.adr_cnn_num_params.argtypes = []
+        L.adr_cnn_num_params.restype = C.c_long
+        L.adr_cnn_create.argtypes = [C.c_int, fp, vp, C.POINTER(vp)]
+        L.adr_cnn_destroy.argtypes = [vp]
+        L.adr_cnn_destroy.restype = None
+        L.adr_cnn_set_params.argtypes = [vp, fp]
+        L.adr_cnn_get_params.argtypes = [vp, fp]
+        L.adr_cnn_features.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.adr_cnn_targets.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp]
+        L.adr_cnn_forward.argtypes = [vp, C.c_int, vp, vp]
+        L.adr_cnn_loss_grad.argtypes = [vp, C.c_int, vp, vp, vp, dp]
+        L.adr_cnn_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, dp]
+        L.adr_cnn_initial_state.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
 
@@ -96,7 +111,10 @@ EXPORTED = ["adr_default_opts", "adr_create", "adr_solve_stationary", "adr_step_
             "adr_destroy", "adr_last_error", "adr_num_lines", "adr_num_line_nodes",
             "adr_get_lines", "adr_get_crossings", "adr_split_step", "adr_paper_u0",
             "adr_time_kernels", "adr_batch_create", "adr_batch_solve", "adr_batch_destroy",
-            "adr_solve_batch", "adr_autotune"]
+            "adr_solve_batch", "adr_autotune",
+            "adr_cnn_num_params", "adr_cnn_create", "adr_cnn_destroy", "adr_cnn_set_params",
+            "adr_cnn_get_params", "adr_cnn_features", "adr_cnn_targets", "adr_cnn_forward",
+            "adr_cnn_loss_grad", "adr_cnn_train_step", "adr_cnn_initial_state"]
 
 
 def tune_key(prob, prec):
@@ -216,11 +234,11 @@ def adr_batch_create(handles, stream=None):
     return b
 
 
-def adr_batch_solve(b, u_init, u_out):
+def adr_batch_solve(b, u_init, u_out, u_iter_out=None):
     n = len(u_out)
     stats = (adr_stats * n)()
     st = lib().adr_batch_solve(b, None if u_init is None else _ptr_array(u_init), _ptr_array(u_out),
-                               stats)
+                               None if u_iter_out is None else _ptr_array(u_iter_out), stats)
     _check(st, "adr_batch_solve", allow=(ADR_ENOCONV,))
     return st, [x.as_dict() for x in stats]
 
@@ -363,15 +381,162 @@ class Batch:
         self.solvers = list(solvers)
         self.b = adr_batch_create([s.h for s in self.solvers], stream)
 
-    def solve(self, u_init=None):
+    def solve(self, u_init=None, want_iter=False):
+        """Returns (u_out grids, stats, status), and the iterates u_{j+1}
+        after them when want_iter."""
         outs = [s._grid() for s in self.solvers]
-        st, stats = adr_batch_solve(self.b, u_init, outs)
+        its = [s._grid() for s in self.solvers] if want_iter else None
+        st, stats = adr_batch_solve(self.b, u_init, outs, its)
+        if want_iter:
+            return outs, stats, st, its
         return outs, stats, st
 
     def close(self):
         if getattr(self, "b", None):
             adr_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------- warm-start network
+
+def adr_cnn_num_params():
+    return int(lib().adr_cnn_num_params())
+
+
+def adr_cnn_create(max_batch, params, stream=None):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = C.c_void_p()
+    _check(lib().adr_cnn_create(int(max_batch), p.ctypes.data_as(C.POINTER(C.c_float)),
+                                _stream_ptr(stream), C.byref(h)), "adr_cnn_create")
+    return h
+
+
+def adr_cnn_destroy(h):
+    lib().adr_cnn_destroy(h)
+
+
+def adr_cnn_set_params(h, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().adr_cnn_set_params(h, p.ctypes.data_as(C.POINTER(C.c_float))),
+           "adr_cnn_set_params")
+
+
+def adr_cnn_get_params(h):
+    p = np.zeros(adr_cnn_num_params(), np.float32)
+    _check(lib().adr_cnn_get_params(h, p.ctypes.data_as(C.POINTER(C.c_float))),
+           "adr_cnn_get_params")
+    return p
+
+
+def adr_cnn_features(batch, n, f, beta1, beta2, mask, mu, sigma, x, stream=None):
+    _check(lib().adr_cnn_features(int(batch), int(n), _ptr(f), _ptr(beta1), _ptr(beta2),
+                                  _ptr(mask), _ptr(mu), _ptr(sigma), _ptr(x),
+                                  _stream_ptr(stream)), "adr_cnn_features")
+
+
+def adr_cnn_targets(batch, n, u, sigma, t, stream=None):
+    _check(lib().adr_cnn_targets(int(batch), int(n), _ptr(u), _ptr(sigma), _ptr(t),
+                                 _stream_ptr(stream)), "adr_cnn_targets")
+
+
+def adr_cnn_forward(h, batch, x, y):
+    _check(lib().adr_cnn_forward(h, int(batch), _ptr(x), _ptr(y)), "adr_cnn_forward")
+
+
+def adr_cnn_loss_grad(h, batch, x, t, grad=None):
+    loss = C.c_double(0)
+    _check(lib().adr_cnn_loss_grad(h, int(batch), _ptr(x), _ptr(t), _ptr(grad), C.byref(loss)),
+           "adr_cnn_loss_grad")
+    return loss.value
+
+
+def adr_cnn_train_step(h, batch, x, t, lr, want_loss=True):
+    loss = C.c_double(0)
+    _check(lib().adr_cnn_train_step(h, int(batch), _ptr(x), _ptr(t), C.c_float(lr),
+                                    C.byref(loss) if want_loss else None), "adr_cnn_train_step")
+    return loss.value if want_loss else None
+
+
+def adr_cnn_initial_state(prob_handle, y, u_out):
+    _check(lib().adr_cnn_initial_state(prob_handle, _ptr(y), _ptr(u_out)),
+           "adr_cnn_initial_state")
+
+
+class Network:
+    """The warm-start network on a CUDA device (adr_cnn_* calls).
+
+    Inputs are CUDA tensors: features ``x`` bfloat16 [B, 64, 64, 24], targets
+    and outputs float32 [B, 64, 64, 16]; parameters are a float32 host vector.
+    """
+
+    HW = 64
+
+    def __init__(self, max_batch, params=None, device="cuda:0", stream=None, seed=None):
+        from . import workloads
+        torch = _torch()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.max_batch = int(max_batch)
+        if params is None:
+            params = workloads.cnn_init_params() if seed is None else \
+                workloads.cnn_init_params(seed)
+        with torch.cuda.device(self.device):
+            self.h = adr_cnn_create(self.max_batch, params, stream)
+        self.grad = torch.zeros(adr_cnn_num_params(), dtype=torch.float32, device=self.device)
+
+    @property
+    def params(self):
+        return adr_cnn_get_params(self.h)
+
+    @params.setter
+    def params(self, p):
+        adr_cnn_set_params(self.h, p)
+
+    def features(self, f, beta1, beta2, mask, mu, sigma):
+        """Stacked device problems [B, 256, 256] (float64, mask uint8), mu and
+        sigma float64 [B] -> bfloat16 features [B, 64, 64, 24]."""
+        B, n = f.shape[0], f.shape[-1]
+        x = self.torch.empty((B, self.HW, self.HW, 24), dtype=self.torch.bfloat16,
+                             device=self.device)
+        adr_cnn_features(B, n, f, beta1, beta2, mask, mu, sigma, x)
+        return x
+
+    def targets(self, u, sigma):
+        B, n = u.shape[0], u.shape[-1]
+        t = self.torch.empty((B, self.HW, self.HW, 16), dtype=self.torch.float32,
+                             device=self.device)
+        adr_cnn_targets(B, n, u, sigma, t)
+        return t
+
+    def forward(self, x):
+        y = self.torch.empty((x.shape[0], self.HW, self.HW, 16), dtype=self.torch.float32,
+                             device=self.device)
+        adr_cnn_forward(self.h, x.shape[0], x, y)
+        return y
+
+    def loss_grad(self, x, t):
+        loss = adr_cnn_loss_grad(self.h, x.shape[0], x, t, self.grad)
+        return loss, self.grad
+
+    def train_step(self, x, t, lr, want_loss=True):
+        return adr_cnn_train_step(self.h, x.shape[0], x, t, lr, want_loss)
+
+    def initial_state(self, solver, y):
+        """Solver grid initial state from one prediction y [64, 64, 16]."""
+        u = solver._grid()
+        adr_cnn_initial_state(solver.h, y, u)
+        return u
+
+    def close(self):
+        if getattr(self, "h", None):
+            adr_cnn_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

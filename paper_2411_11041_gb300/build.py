@@ -23,6 +23,7 @@ UNITS = {
     "sweep.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
+    "cnn.cu": [],
 }
 
 

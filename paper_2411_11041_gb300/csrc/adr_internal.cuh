@@ -181,5 +181,7 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
 adr_status batch_dev_reset(BatchDev* b, cudaStream_t st);
 void batch_dev_destroy(BatchDev* b);
 adr_status launch_state_reset(Problem* p);
+// warm-start network (cnn.cu): prediction [64][64][16] -> initial state on the grid
+adr_status launch_cnn_unpack(Problem* p, const float* y, double* u);
 
 }  // namespace adr

@@ -235,6 +235,19 @@ void adr_default_opts(adr_opts* o)
     o->init = ADR_INIT_ZERO;
 }
 
+adr_status adr_cnn_initial_state(adr_problem* h, const float* y, double* u_out)
+{
+    if (!h || !y || !u_out) {
+        set_error("adr_cnn_initial_state: NULL argument");
+        return ADR_EINVAL;
+    }
+    if (h->p.grid.nx != 256 || h->p.grid.ny != 256) {
+        set_error("adr_cnn_initial_state: the network predicts 256 x 256 grids");
+        return ADR_EINVAL;
+    }
+    return launch_cnn_unpack(&h->p, y, u_out);
+}
+
 const char* adr_last_error(void) { return g_err.c_str(); }
 
 adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, double sigma,
@@ -699,7 +712,7 @@ adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_
 }
 
 adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* const* u_out,
-                           adr_stats* stats)
+                           double* const* u_iter_out, adr_stats* stats)
 {
     g_err.clear();
     if (!b || !u_out) {
@@ -725,7 +738,8 @@ adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* co
         ADR_CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
         ADR_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
         for (int i = 0; i < n; ++i)
-            TRY(launch_finish(&b->hs[i]->p, u_out[i], nullptr, b->hs[i]->p.opts.theta == 0.5));
+            TRY(launch_finish(&b->hs[i]->p, u_out[i], u_iter_out ? u_iter_out[i] : nullptr,
+                              b->hs[i]->p.opts.theta == 0.5));
         ADR_CUDA_TRY(cudaEventRecord(b->ev1, b->stream));
         for (int i = 0; i < n; ++i)
             ADR_CUDA_TRY(cudaMemcpyAsync(&st[i], b->hs[i]->p.state, sizeof(IterState),
@@ -760,7 +774,7 @@ adr_status adr_solve_batch(adr_problem* const* probs, int n, double* const* u_ou
     void* stream = (n > 0 && probs && probs[0]) ? (void*)probs[0]->p.stream : nullptr;
     adr_status s = adr_batch_create(probs, n, stream, &b);
     if (s) return s;
-    s = adr_batch_solve(b, nullptr, u_out, stats);
+    s = adr_batch_solve(b, nullptr, u_out, nullptr, stats);
     std::string keep = g_err;
     adr_batch_destroy(b);
     g_err = keep;

@@ -1,0 +1,788 @@
+// Warm-start network on the GPU: BF16 tensor-core convolutions with FP32
+// accumulation (forward, data gradient, weight gradient), loss, Adam, and the
+// feature / target / unpacking kernels.  See include/adr.h (adr_cnn_*).
+//
+// Network (the same definition as the FP64 reference): a 256 x 256 node grid
+// is read as 64 x 64 cells of 4 x 4 nodes; features NHWC, 24 channels (f at
+// the 16 nodes of the cell, block means of beta1, beta2, mu and sigma codes,
+// block mean of the mask, 3 zeros); eight 3 x 3 convolutions with zero
+// padding, channels 24 64 64 128 128 128 64 64 16, bias, ReLU after all but
+// the last; output channel 4 a + b = sigma * u at node (4 r + a, 4 c + b).
+// Parameters packed as W_0, b_0, W_1, b_1, ...; W_l[(tap * Cin + ci) * Cout + co].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "adr_internal.cuh"
+
+namespace {
+
+constexpr int kLayers = 8;
+constexpr int kCh[kLayers + 1] = {24, 64, 64, 128, 128, 128, 64, 64, 16};
+constexpr int kDil[kLayers] = {1, 2, 4, 8, 16, 32, 1, 1};
+constexpr int kHW = 64;   // cells per side
+constexpr int kSub = 4;   // nodes per cell side
+constexpr int kN = kHW * kSub;
+constexpr int kCin = 24, kCout = kSub * kSub;
+
+long param_offset(int l, bool bias)
+{
+    long off = 0;
+    for (int k = 0; k < l; ++k) off += 9L * kCh[k] * kCh[k + 1] + kCh[k + 1];
+    return bias ? off + 9L * kCh[l] * kCh[l + 1] : off;
+}
+
+typedef __nv_bfloat16 bf16;
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool ok)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(ok ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned (&r)[2], const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ------------------------------------------------------ convolution kernels
+
+struct ConvArgs {
+    int B, H, W, Cin, Cout, dil;
+    const bf16* x;      // [B][H][W][Cin]
+    const bf16* w;      // [9 Cin][Cout]
+    const float* bias;  // [Cout] or null
+    bf16* y;            // [B][H][W][Cout] or null
+    float* y32;         // [B][H][W][Cout] FP32 output or null
+    int relu;
+};
+
+// implicit GEMM: M = pixels, N = Cout, K = 9 Cin (tap-major); a block computes
+// 128 pixels x BN channels with 8 warps; double-buffered cp.async tiles.
+template <int BN>
+__global__ void __launch_bounds__(256) k_conv_fwd(ConvArgs a)
+{
+    constexpr int BM = 128, BK = 32, AS = BK + 8, BSTR = BN + 8;
+    constexpr int WN = BN >= 64 ? 2 : 1, WM = 8 / WN, TM = BM / WM, TN = BN / WN;
+    constexpr int MI = TM / 16, NI = TN / 8;
+    __shared__ __align__(16) bf16 As[2][BM][AS];
+    __shared__ __align__(16) bf16 Bs[2][BK][BSTR];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = warp / WN, wn = warp % WN;
+    const long long m0 = (long long)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int HW = a.H * a.W;
+    const long long M = (long long)a.B * HW;
+    const int K = 9 * a.Cin;
+    float acc[MI][NI][4];
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < NI; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+
+    auto load = [&](int st, int k0) {
+        for (int v = tid; v < BM * (BK / 8); v += 256) {
+            int row = v / (BK / 8), kg = v % (BK / 8);
+            long long p = m0 + row;
+            int k = k0 + kg * 8;
+            const bf16* src = a.x;
+            bool ok = false;
+            if (p < M && k < K) {
+                int tap = k / a.Cin, ci = k - tap * a.Cin;
+                int b = (int)(p / HW), rem = (int)(p - (long long)b * HW);
+                int r = rem / a.W, c = rem - r * a.W;
+                int rr = r + (tap / 3 - 1) * a.dil, cc = c + (tap % 3 - 1) * a.dil;
+                if (rr >= 0 && rr < a.H && cc >= 0 && cc < a.W) {
+                    src = a.x + (((long long)b * a.H + rr) * a.W + cc) * a.Cin + ci;
+                    ok = true;
+                }
+            }
+            cp_async16(&As[st][row][kg * 8], src, ok);
+        }
+        for (int v = tid; v < BK * (BN / 8); v += 256) {
+            int row = v / (BN / 8), ng = v % (BN / 8);
+            int k = k0 + row, n = n0 + ng * 8;
+            bool ok = k < K && n < a.Cout;
+            cp_async16(&Bs[st][row][ng * 8], ok ? a.w + (long long)k * a.Cout + n : a.w, ok);
+        }
+        cp_async_commit();
+    };
+    const int nk = (K + BK - 1) / BK;
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        const int st = kt & 1;
+        if (kt + 1 < nk) {
+            load(st ^ 1, (kt + 1) * BK);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            unsigned af[MI][4], bfr[NI][2];
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+                ldsm_x4(af[i], &As[st][wm * TM + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+#pragma unroll
+            for (int j = 0; j < NI; ++j) ldsm_x2_t(bfr[j], &Bs[st][kk + (lane & 15)][wn * TN + j * 8]);
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+#pragma unroll
+                for (int j = 0; j < NI; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < NI; ++j) {
+            int n = n0 + wn * TN + j * 8 + 2 * t;
+            if (n >= a.Cout) continue;
+            float b0 = a.bias ? a.bias[n] : 0.f, b1 = a.bias ? a.bias[n + 1] : 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                long long p = m0 + wm * TM + i * 16 + g + h * 8;
+                if (p >= M) continue;
+                float v0 = acc[i][j][2 * h] + b0, v1 = acc[i][j][2 * h + 1] + b1;
+                if (a.relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                if (a.y)
+                    *reinterpret_cast<__nv_bfloat162*>(a.y + p * a.Cout + n) = __floats2bfloat162_rn(v0, v1);
+                if (a.y32) {
+                    a.y32[p * a.Cout + n] = v0;
+                    a.y32[p * a.Cout + n + 1] = v1;
+                }
+            }
+        }
+}
+
+struct WgradArgs {
+    int B, H, W, Cin, Cout, dil;
+    const bf16* x;   // layer input [B][H][W][Cin]
+    const bf16* dy;  // gradient at the pre-activation [B][H][W][Cout]
+    float* part;     // [splits][9 Cin][Cout]
+    long long pchunk;
+};
+
+// dW[k][co] = sum_p X_patch[p][k] dY[p][co]: M = 9 Cin, N = Cout, reduction
+// over pixels (split over blockIdx.z; partial sums reduced afterwards)
+template <int BN>
+__global__ void __launch_bounds__(128) k_conv_wgrad(WgradArgs a)
+{
+    constexpr int BM = 64, BP = 32, AS = BM + 8, BSTR = BN + 8;
+    constexpr int WN = BN >= 64 ? 2 : 1, WM = 4 / WN, TM = BM / WM, TN = BN / WN;
+    constexpr int MI = TM / 16, NI = TN / 8;
+    __shared__ __align__(16) bf16 As[2][BP][AS];
+    __shared__ __align__(16) bf16 Bs[2][BP][BSTR];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = warp / WN, wn = warp % WN;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int HW = a.H * a.W;
+    const long long M = (long long)a.B * HW;
+    const int K = 9 * a.Cin;
+    const long long pbeg = (long long)blockIdx.z * a.pchunk;
+    const long long pend = pbeg + a.pchunk < M ? pbeg + a.pchunk : M;
+    float acc[MI][NI][4];
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < NI; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+    auto load = [&](int st, long long p0) {
+        for (int v = tid; v < BP * (BM / 8); v += 128) {
+            int row = v / (BM / 8), kg = v % (BM / 8);
+            long long p = p0 + row;
+            int k = m0 + kg * 8;
+            const bf16* src = a.x;
+            bool ok = false;
+            if (p < pend && k < K) {
+                int tap = k / a.Cin, ci = k - tap * a.Cin;
+                int b = (int)(p / HW), rem = (int)(p - (long long)b * HW);
+                int r = rem / a.W, c = rem - r * a.W;
+                int rr = r + (tap / 3 - 1) * a.dil, cc = c + (tap % 3 - 1) * a.dil;
+                if (rr >= 0 && rr < a.H && cc >= 0 && cc < a.W) {
+                    src = a.x + (((long long)b * a.H + rr) * a.W + cc) * a.Cin + ci;
+                    ok = true;
+                }
+            }
+            cp_async16(&As[st][row][kg * 8], src, ok);
+        }
+        for (int v = tid; v < BP * (BN / 8); v += 128) {
+            int row = v / (BN / 8), ng = v % (BN / 8);
+            long long p = p0 + row;
+            int n = n0 + ng * 8;
+            bool ok = p < pend && n < a.Cout;
+            cp_async16(&Bs[st][row][ng * 8], ok ? a.dy + p * a.Cout + n : a.dy, ok);
+        }
+        cp_async_commit();
+    };
+    const long long np = pend > pbeg ? (pend - pbeg + BP - 1) / BP : 0;
+    if (np > 0) load(0, pbeg);
+    for (long long pt = 0; pt < np; ++pt) {
+        const int st = (int)(pt & 1);
+        if (pt + 1 < np) {
+            load(st ^ 1, pbeg + (pt + 1) * BP);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BP; kk += 16) {
+            unsigned af[MI][4], bfr[NI][2];
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+                ldsm_x4_t(af[i], &As[st][kk + (lane & 7) + ((lane >> 4) << 3)]
+                                    [wm * TM + i * 16 + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+            for (int j = 0; j < NI; ++j) ldsm_x2_t(bfr[j], &Bs[st][kk + (lane & 15)][wn * TN + j * 8]);
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+#pragma unroll
+                for (int j = 0; j < NI; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+    float* part = a.part + (size_t)blockIdx.z * K * a.Cout;
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < NI; ++j) {
+            int n = n0 + wn * TN + j * 8 + 2 * t;
+            if (n >= a.Cout) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int k = m0 + wm * TM + i * 16 + g + h * 8;
+                if (k >= K) continue;
+                part[(size_t)k * a.Cout + n] = acc[i][j][2 * h];
+                part[(size_t)k * a.Cout + n + 1] = acc[i][j][2 * h + 1];
+            }
+        }
+}
+
+// grad[i] = sum over splits of part[s][i]  (fixed order: deterministic)
+__global__ void k_sum_splits(const float* part, int splits, long long n, float* grad)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int q = 0; q < splits; ++q) s += part[(size_t)q * n + i];
+    grad[i] = s;
+}
+
+// bias gradient: per channel sum over pixels (one block per channel)
+__global__ void k_bias_grad(const bf16* dy, long long M, int C, float* grad)
+{
+    int c = blockIdx.x;
+    float s = 0.f;
+    for (long long p = threadIdx.x; p < M; p += blockDim.x) s += __bfloat162float(dy[p * C + c]);
+    __shared__ float sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) grad[c] = sh[0];
+}
+
+// dYpre = dY where the layer's ReLU output is positive, else 0
+__global__ void k_relu_bwd(const bf16* dy, const bf16* y, long long n, bf16* out)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = __bfloat162float(y[i]) > 0.f ? dy[i] : __float2bfloat16(0.f);
+}
+
+// loss = 1/2 mean over all n outputs (y - t)^2, dY = (y - t) / n;
+// per-block partial sums of the loss (FP64)
+__global__ void k_loss(const float* y32, const float* t, long long n, bf16* dy, double* part)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double e2 = 0.0;
+    if (i < n) {
+        float e = y32[i] - t[i];
+        e2 = 0.5 * (double)e * (double)e;
+        dy[i] = __float2bfloat16(e / (float)n);
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = e2;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_loss(const double* part, int n, long long count, double* loss)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *loss = s / (double)count;
+}
+
+struct LayerTab {
+    long woff[kLayers], boff[kLayers];
+    int cin[kLayers], cout[kLayers];
+};
+
+// Adam on the FP32 parameters; refreshes the BF16 weights and the flipped,
+// transposed BF16 weights of the data gradient
+__global__ void k_adam(float* prm, float* m, float* v, const float* grad, long long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2, LayerTab T, bf16* wb,
+                       bf16* wt)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float g = grad[i];
+    float mi = b1 * m[i] + (1.f - b1) * g, vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    float p = prm[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    prm[i] = p;
+    for (int l = 0; l < kLayers; ++l) {
+        if (i >= T.woff[l] && i < T.boff[l]) {
+            long long q = i - T.woff[l];
+            int cin = T.cin[l], cout = T.cout[l];
+            int co = (int)(q % cout);
+            long long k = q / cout;
+            int tap = (int)(k / cin), ci = (int)(k % cin);
+            wb[i] = __float2bfloat16(p);
+            wt[T.woff[l] + ((long long)(8 - tap) * cout + co) * cin + ci] = __float2bfloat16(p);
+        }
+    }
+}
+
+// the same refresh without an update (after loading parameters)
+__global__ void k_refresh(const float* prm, long long n, LayerTab T, bf16* wb, bf16* wt)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float p = prm[i];
+    for (int l = 0; l < kLayers; ++l) {
+        if (i >= T.woff[l] && i < T.boff[l]) {
+            long long q = i - T.woff[l];
+            int cin = T.cin[l], cout = T.cout[l];
+            int co = (int)(q % cout);
+            long long k = q / cout;
+            int tap = (int)(k / cin), ci = (int)(k % cin);
+            wb[i] = __float2bfloat16(p);
+            wt[T.woff[l] + ((long long)(8 - tap) * cout + co) * cin + ci] = __float2bfloat16(p);
+        }
+    }
+}
+
+// features of a batch of 256 x 256 problems, one thread per cell
+__global__ void k_features(int batch, const double* f, const double* b1, const double* b2,
+                           const uint8_t* mask, const double* mu, const double* sigma, bf16* x)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)batch * kHW * kHW) return;
+    int b = (int)(q / (kHW * kHW)), rem = (int)(q % (kHW * kHW)), r = rem / kHW, c = rem % kHW;
+    double s1 = 0, s2 = 0, sm = 0;
+    size_t base = (size_t)b * kN * kN;
+    bf16* o = x + q * kCin;
+    for (int i = 0; i < kSub; ++i)
+        for (int j = 0; j < kSub; ++j) {
+            size_t k = base + (size_t)(r * kSub + i) * kN + (c * kSub + j);
+            o[i * kSub + j] = __float2bfloat16((float)f[k]);
+            s1 += b1[k];
+            s2 += b2[k];
+            sm += mask[k];
+        }
+    const double inv = 1.0 / (kSub * kSub);
+    o[16] = __float2bfloat16((float)(s1 * inv));
+    o[17] = __float2bfloat16((float)(s2 * inv));
+    o[18] = __float2bfloat16((float)((log10(mu[b]) + 2.5) / 1.5));
+    o[19] = __float2bfloat16((float)(sigma[b] - 1.0));
+    o[20] = __float2bfloat16((float)(sm * inv));
+    o[21] = o[22] = o[23] = __float2bfloat16(0.f);
+}
+
+// t[b][cell][4 a + b'] = sigma_b u_b at node (4 r + a, 4 c + b'), one thread per node
+__global__ void k_targets(int batch, const double* u, const double* sigma, float* t)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)batch * kN * kN) return;
+    int b = (int)(q / (kN * kN)), rem = (int)(q % (kN * kN)), r = rem / kN, c = rem % kN;
+    size_t cell = ((size_t)b * kHW + r / kSub) * kHW + c / kSub;
+    t[cell * kCout + (r % kSub) * kSub + (c % kSub)] = (float)(sigma[b] * u[q]);
+}
+
+// u at node (r, c) = y[cell][sub] / sigma on interior nodes, 0 elsewhere
+__global__ void k_unpack(const float* y, double sigma, const uint8_t* ntype, double* u)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)kN * kN) return;
+    int r = (int)(q / kN), c = (int)(q % kN);
+    float v = y[((size_t)(r / kSub) * kHW + c / kSub) * kCout + (r % kSub) * kSub + (c % kSub)];
+    u[q] = ntype[q] == adr::kInterior ? (double)v / sigma : 0.0;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+
+struct adr_cnn {
+    int max_batch = 0, hw = kHW;
+    cudaStream_t stream = nullptr;
+    long P = 0;
+    LayerTab T{};
+    float *prm = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    bf16 *wb = nullptr, *wt = nullptr;
+    bf16* act[kLayers] = {};  // post-activation outputs of layers 0..6 (bf16)
+    float* y32 = nullptr;     // last layer output (fp32) [M][8]
+    bf16 *dA = nullptr, *dB = nullptr, *dpre = nullptr;
+    float* part = nullptr;
+    long long part_size = 0;
+    double* lpart = nullptr;
+    double* loss = nullptr;
+    long step = 0;
+    std::vector<void*> owned;
+};
+
+namespace {
+
+template <typename T>
+adr_status cnn_alloc(adr_cnn* c, T** p, size_t n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        adr::set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        return ADR_ENOMEM;
+    }
+    c->owned.push_back(q);
+    *p = static_cast<T*>(q);
+    return ADR_OK;
+}
+
+void launch_conv(cudaStream_t st, const ConvArgs& a)
+{
+    long long M = (long long)a.B * a.H * a.W;
+    dim3 grid((unsigned)((M + 127) / 128), 1);
+    if (a.Cout >= 64) {
+        grid.y = (a.Cout + 63) / 64;
+        k_conv_fwd<64><<<grid, 256, 0, st>>>(a);
+    } else if (a.Cout % 16 == 0) {
+        grid.y = a.Cout / 16;
+        k_conv_fwd<16><<<grid, 256, 0, st>>>(a);
+    } else {
+        grid.y = (a.Cout + 7) / 8;
+        k_conv_fwd<8><<<grid, 256, 0, st>>>(a);
+    }
+}
+
+// forward of a batch: act[0..6] bf16, y32 of the last layer
+adr_status cnn_forward(adr_cnn* c, int batch, const bf16* x)
+{
+    const bf16* in = x;
+    for (int l = 0; l < kLayers; ++l) {
+        ConvArgs a{};
+        a.B = batch;
+        a.H = a.W = c->hw;
+        a.Cin = kCh[l];
+        a.Cout = kCh[l + 1];
+        a.dil = kDil[l];
+        a.x = in;
+        a.w = c->wb + c->T.woff[l];
+        a.bias = c->prm + c->T.boff[l];
+        a.relu = l < kLayers - 1;
+        if (l < kLayers - 1) a.y = c->act[l];
+        else a.y32 = c->y32;
+        launch_conv(c->stream, a);
+        in = c->act[l];
+    }
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+adr_status cnn_backward(adr_cnn* c, int batch, const bf16* x, const float* t)
+{
+    cudaStream_t st = c->stream;
+    const long long M = (long long)batch * c->hw * c->hw;
+    const long long nout = M * kCout;
+    int nb = (int)((nout + 255) / 256);
+    bf16* dy = c->dA;
+    k_loss<<<nb, 256, 0, st>>>(c->y32, t, nout, dy, c->lpart);
+    k_sum_loss<<<1, 1, 0, st>>>(c->lpart, nb, nout, c->loss);
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const int cin = kCh[l], cout = kCh[l + 1];
+        const bf16* dyp = dy;
+        if (l < kLayers - 1) {
+            k_relu_bwd<<<(int)((M * cout + 255) / 256), 256, 0, st>>>(dy, c->act[l], M * cout, c->dpre);
+            dyp = c->dpre;
+        }
+        const bf16* xin = l == 0 ? x : c->act[l - 1];
+        // weight gradient, split over pixels
+        WgradArgs w{};
+        w.B = batch;
+        w.H = w.W = c->hw;
+        w.Cin = cin;
+        w.Cout = cout;
+        w.dil = kDil[l];
+        w.x = xin;
+        w.dy = dyp;
+        w.part = c->part;
+        long long K = 9LL * cin;
+        int splits = (int)std::min<long long>(64, (M + 1023) / 1024);
+        if (splits < 1) splits = 1;
+        while ((long long)splits * K * cout > c->part_size) splits--;
+        w.pchunk = ((M + splits - 1) / splits + 31) / 32 * 32;
+        splits = (int)((M + w.pchunk - 1) / w.pchunk);
+        dim3 grid((unsigned)((K + 63) / 64), 1, (unsigned)splits);
+        if (cout >= 64) {
+            grid.y = (cout + 63) / 64;
+            k_conv_wgrad<64><<<grid, 128, 0, st>>>(w);
+        } else if (cout % 16 == 0) {
+            grid.y = cout / 16;
+            k_conv_wgrad<16><<<grid, 128, 0, st>>>(w);
+        } else {
+            grid.y = (cout + 7) / 8;
+            k_conv_wgrad<8><<<grid, 128, 0, st>>>(w);
+        }
+        long long nw = K * cout;
+        k_sum_splits<<<(int)((nw + 255) / 256), 256, 0, st>>>(c->part, splits, nw, c->grad + c->T.woff[l]);
+        k_bias_grad<<<cout, 256, 0, st>>>(dyp, M, cout, c->grad + c->T.boff[l]);
+        if (l > 0) {
+            // data gradient: correlation with the flipped, transposed weights
+            ConvArgs a{};
+            a.B = batch;
+            a.H = a.W = c->hw;
+            a.Cin = cout;
+            a.Cout = cin;
+            a.dil = kDil[l];
+            a.x = dyp;
+            a.w = c->wt + c->T.woff[l];
+            a.y = dy == c->dA ? c->dB : c->dA;
+            launch_conv(st, a);
+            dy = a.y;
+        }
+    }
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long adr_cnn_num_params(void) { return param_offset(kLayers, false); }
+
+void adr_cnn_destroy(adr_cnn* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (void* q : c->owned) cudaFree(q);
+    delete c;
+}
+
+adr_status adr_cnn_set_params(adr_cnn* c, const float* host)
+{
+    if (!c || !host) {
+        adr::set_error("NULL argument");
+        return ADR_EINVAL;
+    }
+    ADR_CUDA_TRY(cudaMemcpyAsync(c->prm, host, sizeof(float) * c->P, cudaMemcpyHostToDevice, c->stream));
+    ADR_CUDA_TRY(cudaMemsetAsync(c->m, 0, sizeof(float) * c->P, c->stream));
+    ADR_CUDA_TRY(cudaMemsetAsync(c->v, 0, sizeof(float) * c->P, c->stream));
+    c->step = 0;
+    k_refresh<<<(int)((c->P + 255) / 256), 256, 0, c->stream>>>(c->prm, c->P, c->T, c->wb, c->wt);
+    ADR_CUDA_TRY(cudaGetLastError());
+    ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return ADR_OK;
+}
+
+adr_status adr_cnn_get_params(adr_cnn* c, float* host)
+{
+    if (!c || !host) {
+        adr::set_error("NULL argument");
+        return ADR_EINVAL;
+    }
+    ADR_CUDA_TRY(cudaMemcpyAsync(host, c->prm, sizeof(float) * c->P, cudaMemcpyDeviceToHost, c->stream));
+    ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return ADR_OK;
+}
+
+adr_status adr_cnn_create(int max_batch, const float* params, void* stream, adr_cnn** out)
+{
+    if (!out || max_batch < 1 || !params) {
+        adr::set_error("adr_cnn_create needs max_batch >= 1, initial parameters and an output");
+        return ADR_EINVAL;
+    }
+    *out = nullptr;
+    adr_cnn* c = new (std::nothrow) adr_cnn;
+    if (!c) return ADR_ENOMEM;
+    c->max_batch = max_batch;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->P = param_offset(kLayers, false);
+    for (int l = 0; l < kLayers; ++l) {
+        c->T.woff[l] = param_offset(l, false);
+        c->T.boff[l] = param_offset(l, true);
+        c->T.cin[l] = kCh[l];
+        c->T.cout[l] = kCh[l + 1];
+    }
+    const long long M = (long long)max_batch * c->hw * c->hw;
+    adr_status s = ADR_OK;
+    auto fail = [&](adr_status st) {
+        adr_cnn_destroy(c);
+        return st;
+    };
+    if ((s = cnn_alloc(c, &c->prm, c->P)) || (s = cnn_alloc(c, &c->m, c->P)) ||
+        (s = cnn_alloc(c, &c->v, c->P)) || (s = cnn_alloc(c, &c->grad, c->P)) ||
+        (s = cnn_alloc(c, &c->wb, c->P)) || (s = cnn_alloc(c, &c->wt, c->P)) ||
+        (s = cnn_alloc(c, &c->y32, M * kCout)) || (s = cnn_alloc(c, &c->dA, M * 128)) ||
+        (s = cnn_alloc(c, &c->dB, M * 128)) || (s = cnn_alloc(c, &c->dpre, M * 128)) ||
+        (s = cnn_alloc(c, &c->lpart, (M * kCout + 255) / 256 + 1)) || (s = cnn_alloc(c, &c->loss, 1)))
+        return fail(s);
+    for (int l = 0; l < kLayers - 1; ++l)
+        if ((s = cnn_alloc(c, &c->act[l], M * kCh[l + 1]))) return fail(s);
+    c->part_size = 64LL * 9 * 128 * 128;
+    if ((s = cnn_alloc(c, &c->part, c->part_size))) return fail(s);
+    if ((s = adr_cnn_set_params(c, params))) return fail(s);
+    *out = c;
+    return ADR_OK;
+}
+
+adr_status adr_cnn_features(int batch, int n, const double* f, const double* b1, const double* b2,
+                            const uint8_t* mask, const double* mu, const double* sigma, uint16_t* x,
+                            void* stream)
+{
+    if (batch < 1 || n != kN || !f || !b1 || !b2 || !mask || !mu || !sigma || !x) {
+        adr::set_error("adr_cnn_features: bad arguments (the network reads 256 x 256 grids)");
+        return ADR_EINVAL;
+    }
+    long long q = (long long)batch * kHW * kHW;
+    k_features<<<(int)((q + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        batch, f, b1, b2, mask, mu, sigma, reinterpret_cast<bf16*>(x));
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+adr_status adr_cnn_targets(int batch, int n, const double* u, const double* sigma, float* t,
+                           void* stream)
+{
+    if (batch < 1 || n != kN || !u || !sigma || !t) {
+        adr::set_error("adr_cnn_targets: bad arguments (the network reads 256 x 256 grids)");
+        return ADR_EINVAL;
+    }
+    long long q = (long long)batch * kN * kN;
+    k_targets<<<(int)((q + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, u, sigma,
+                                                                                    t);
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+adr_status adr_cnn_forward(adr_cnn* c, int batch, const uint16_t* x, float* y)
+{
+    if (!c || batch < 1 || batch > c->max_batch || !x || !y) {
+        adr::set_error("adr_cnn_forward: bad arguments");
+        return ADR_EINVAL;
+    }
+    TRY_S(cnn_forward(c, batch, reinterpret_cast<const bf16*>(x)));
+    const long long M = (long long)batch * c->hw * c->hw;
+    ADR_CUDA_TRY(cudaMemcpyAsync(y, c->y32, sizeof(float) * M * kCout, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    return ADR_OK;
+}
+
+adr_status adr_cnn_loss_grad(adr_cnn* c, int batch, const uint16_t* x, const float* t, float* grad,
+                             double* loss)
+{
+    if (!c || batch < 1 || batch > c->max_batch || !x || !t) {
+        adr::set_error("adr_cnn_loss_grad: bad arguments");
+        return ADR_EINVAL;
+    }
+    const bf16* xb = reinterpret_cast<const bf16*>(x);
+    TRY_S(cnn_forward(c, batch, xb));
+    TRY_S(cnn_backward(c, batch, xb, t));
+    if (grad)
+        ADR_CUDA_TRY(cudaMemcpyAsync(grad, c->grad, sizeof(float) * c->P, cudaMemcpyDeviceToDevice,
+                                     c->stream));
+    if (loss) {
+        ADR_CUDA_TRY(cudaMemcpyAsync(loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return ADR_OK;
+}
+
+adr_status adr_cnn_train_step(adr_cnn* c, int batch, const uint16_t* x, const float* t, float lr,
+                              double* loss)
+{
+    if (!c || batch < 1 || batch > c->max_batch || !x || !t || !(lr > 0.f)) {
+        adr::set_error("adr_cnn_train_step: bad arguments");
+        return ADR_EINVAL;
+    }
+    const bf16* xb = reinterpret_cast<const bf16*>(x);
+    TRY_S(cnn_forward(c, batch, xb));
+    TRY_S(cnn_backward(c, batch, xb, t));
+    c->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
+    k_adam<<<(int)((c->P + 255) / 256), 256, 0, c->stream>>>(c->prm, c->m, c->v, c->grad, c->P, lr, b1,
+                                                             b2, 1e-8f, c1, c2, c->T, c->wb, c->wt);
+    ADR_CUDA_TRY(cudaGetLastError());
+    if (loss) {
+        ADR_CUDA_TRY(cudaMemcpyAsync(loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return ADR_OK;
+}
+
+}  // extern "C"
+
+namespace adr {
+// unpack one prediction [64][64][16] to the handle's 256 x 256 grid
+adr_status launch_cnn_unpack(Problem* p, const float* y, double* u)
+{
+    long long N = p->N;
+    k_unpack<<<(int)((N + 255) / 256), 256, 0, p->stream>>>(y, p->sigma, p->ntype, u);
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+}  // namespace adr

@@ -1,0 +1,155 @@
+"""Learned warm start: data generation with the method's own solver, training
+of the network on the GPU, and initial states for new problems.
+
+The network (adr_cnn_* calls, ``Network``) maps a problem on a 256 x 256 grid
+to a prediction of sigma times its converged iterate at every node;
+``adr_cnn_initial_state`` turns that into u_0 for ADR_INIT_USER.  The solve itself is unchanged: it iterates from u_0 to the same
+tolerance, so the answer meets the same test whatever the network predicts.
+
+Every array lives on the GPU; the host only draws the seeded problems and
+moves their nodal fields to the device once.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+from . import ADR_OK, Batch, Network, Solver
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def stack(probs, device="cuda:0"):
+    """Nodal fields of equally sized problems as device tensors [B, n, n]."""
+    torch = _torch()
+    dev = torch.device(device)
+    f = torch.as_tensor(np.stack([p.f for p in probs]), device=dev)
+    b1 = torch.as_tensor(np.stack([p.beta1 for p in probs]), device=dev)
+    b2 = torch.as_tensor(np.stack([p.beta2 for p in probs]), device=dev)
+    m = torch.as_tensor(np.stack([p.mask for p in probs]).astype(np.uint8), device=dev)
+    mu = torch.as_tensor([p.mu for p in probs], dtype=torch.float64, device=dev)
+    sg = torch.as_tensor([p.sigma for p in probs], dtype=torch.float64, device=dev)
+    return f, b1, b2, m, mu, sg
+
+
+def solver_opts(tol=1e-8, prec=0):
+    """Options of every solve of the warm-start workload (curve -> grid weights
+    by crossing gaps: the flow directions are random, some near a grid axis)."""
+    return dict(tol=tol, max_iter=200000, prec=prec, interp_weights=1)
+
+
+@dataclasses.dataclass
+class Dataset:
+    x: object  # bf16 [N, 64, 64, 24]
+    t: object  # fp32 [N, 64, 64, 16]
+    iters: np.ndarray  # iterations of each generating solve (zero initial state)
+
+
+def generate(net: Network, probs, chunk=128, tol=1e-8, prec=0, device="cuda:0"):
+    """Solve every problem with the batched solver from u_0 = 0 and keep the
+    network's features and targets: sigma times the iterate u_{j+1} the solve
+    converged to (its fixed point; for theta = 1/2 the reported solution is the
+    midpoint of the last step, which differs from it by the splitting error)."""
+    torch = _torch()
+    xs, ts, its = [], [], []
+    for k in range(0, len(probs), chunk):
+        part = probs[k:k + chunk]
+        solvers = [Solver(p, device=device, **solver_opts(tol, prec)) for p in part]
+        b = Batch(solvers)
+        outs, stats, st, its_u = b.solve(want_iter=True)
+        if st != ADR_OK:
+            raise RuntimeError("a generating solve did not converge")
+        f, b1, b2, m, mu, sg = stack(part, device)
+        xs.append(net.features(f, b1, b2, m, mu, sg))
+        ts.append(net.targets(torch.stack(its_u), sg))
+        its += [s["iters"] for s in stats]
+        b.close()
+        for s in solvers:
+            s.close()
+        del outs, its_u, f, b1, b2, m
+    return Dataset(torch.cat(xs), torch.cat(ts), np.asarray(its))
+
+
+def train(net: Network, data: Dataset, steps, batch=32, lr=1e-3, lr_final=1e-4, seed=0,
+          log_every=0):
+    """Adam on random minibatches; the learning rate decays geometrically
+    from lr to lr_final.  Returns the losses of the logged steps."""
+    torch = _torch()
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n = data.x.shape[0]
+    batch = min(batch, n, net.max_batch)
+    losses = []
+    for s in range(steps):
+        idx = torch.randint(0, n, (batch,), generator=g).to(data.x.device)
+        x = data.x.index_select(0, idx).contiguous()
+        t = data.t.index_select(0, idx).contiguous()
+        rate = lr * (lr_final / lr) ** (s / max(steps - 1, 1))
+        want = bool(log_every) and (s % log_every == 0 or s == steps - 1)
+        loss = net.train_step(x, t, rate, want_loss=want)
+        if want:
+            losses.append((s, loss))
+    return losses
+
+
+def initial_states(net: Network, solvers, x):
+    """u_0 of every solver from the features x (one network batch)."""
+    y = net.forward(x)
+    return [net.initial_state(s, y[i]) for i, s in enumerate(solvers)]
+
+
+def evaluate(net: Network, probs, tol=1e-8, prec=0, device="cuda:0", chunk=128, sequential=False):
+    """Held-out comparison on the same GPU: batched solves from u_0 = 0 and
+    from the network's u_0 (network time included), and optionally the plain
+    method (one problem after another, u_0 = 0).  Wall times in seconds of
+    the solve phase (handles and graphs are built before the clock starts)."""
+    torch = _torch()
+    res = {"zero_iters": [], "learned_iters": [], "zero_s": 0.0, "learned_s": 0.0,
+           "plain_s": 0.0, "net_s": 0.0}
+    for k in range(0, len(probs), chunk):
+        part = probs[k:k + chunk]
+        solvers = [Solver(p, device=device, **solver_opts(tol, prec)) for p in part]
+        f, b1, b2, m, mu, sg = stack(part, device)
+        learned = [Solver(p, device=device, init=1, **solver_opts(tol, prec)) for p in part]
+        bz, bl = Batch(solvers), Batch(learned)
+        bz.solve()  # warm-up: graph build
+        bl.solve([s._grid() for s in learned])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, sz, stz = bz.solve()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        x = net.features(f, b1, b2, m, mu, sg)
+        u0 = initial_states(net, learned, x)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        _, sl, stl = bl.solve(u0)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        if stz != ADR_OK or stl != ADR_OK:
+            raise RuntimeError("a held-out solve did not converge")
+        res["zero_s"] += t1 - t0
+        res["learned_s"] += t3 - t1
+        res["net_s"] += t2 - t1
+        res["zero_iters"] += [s["iters"] for s in sz]
+        res["learned_iters"] += [s["iters"] for s in sl]
+        if sequential:
+            for s in solvers:  # warm-up of each handle's graph
+                s.solve_stationary()
+            torch.cuda.synchronize()
+            t4 = time.perf_counter()
+            for s in solvers:
+                s.solve_stationary()
+            torch.cuda.synchronize()
+            res["plain_s"] += time.perf_counter() - t4
+        bz.close()
+        bl.close()
+        for s in solvers + learned:
+            s.close()
+    res["zero_iters"] = np.asarray(res["zero_iters"])
+    res["learned_iters"] = np.asarray(res["learned_iters"])
+    return res

@@ -169,3 +169,22 @@ def random_field(rng: np.random.Generator, nx: int, ny: int, smooth=True):
         a, px, py = rng.normal(), rng.uniform(0, 2 * math.pi), rng.uniform(0, 2 * math.pi)
         g += a * np.sin(kx * math.pi * X + px) * np.sin(ky * math.pi * Y + py)
     return g
+
+
+# warm-start network: layer widths (input features ... output channels)
+CNN_CHANNELS = (24, 64, 64, 128, 128, 128, 64, 64, 16)
+
+
+def cnn_init_params(seed=SEED_BASE + 6, last_scale=0.1):
+    """Initial parameters of the warm-start network, packed W_0, b_0, W_1, ...:
+    He-normal weights (std sqrt(2 / (9 Cin))), zero biases, the last layer's
+    weights scaled by ``last_scale``.  FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ch = CNN_CHANNELS
+    parts = []
+    for l in range(len(ch) - 1):
+        n = 9 * ch[l] * ch[l + 1]
+        std = math.sqrt(2.0 / (9 * ch[l])) * (last_scale if l == len(ch) - 2 else 1.0)
+        parts.append(rng.normal(0.0, std, n))
+        parts.append(np.zeros(ch[l + 1]))
+    return np.concatenate(parts).astype(np.float32)

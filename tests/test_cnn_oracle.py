@@ -1,5 +1,6 @@
 """Pins of the warm-start network's CPU reference: central finite differences
-of the loss, a brute-force convolution, the feature map and the upsampling."""
+of the loss, a brute-force convolution, the feature map, the targets and the
+unpacking to the grid."""
 import numpy as np
 import pytest
 
@@ -11,8 +12,8 @@ CNN = O.CNN
 
 def _batch(n=2, seed=0, hw=64):
     rng = np.random.default_rng(seed)
-    xs = rng.normal(size=(n, hw, hw, 8)) * 0.5
-    ts = rng.normal(size=(n, hw, hw))
+    xs = rng.normal(size=(n, hw, hw, 24)) * 0.5
+    ts = rng.normal(size=(n, hw, hw, 16))
     return xs, ts
 
 
@@ -25,7 +26,7 @@ def small_grid():
 
 def test_parameter_count_is_about_half_a_million():
     ch = CNN.channels()
-    assert ch[0] == 8 and ch[-1] == 8 and CNN.dilations() == [1, 2, 4, 8, 4, 2, 1, 1]
+    assert ch[0] == 24 and ch[-1] == 16 and CNN.dilations() == [1, 2, 4, 8, 16, 32, 1, 1]
     n = CNN.num_params()
     assert n == sum(9 * a * b + b for a, b in zip(ch[:-1], ch[1:]))
     assert 450_000 < n < 600_000
@@ -71,36 +72,67 @@ def test_first_layer_equals_brute_force_convolution():
     x = xs[0]
     p = np.zeros(CNN.num_params())
     rng = np.random.default_rng(4)
-    Wl = rng.normal(size=(3, 3, 8, 64))
-    bl = rng.normal(size=64)
+    ch = CNN.channels()
+    Wl = rng.normal(size=(3, 3, ch[0], ch[1]))
+    bl = rng.normal(size=ch[1])
     p[CNN.offset(0):CNN.offset(0, True)] = Wl.reshape(-1)
     p[CNN.offset(0, True):CNN.offset(1)] = bl
-    # identity-like rest: route channel 0 of layer 0 to the output through
-    # positive weights so that the output equals relu(layer0)[..., 0]
-    ch = CNN.channels()
+    # identity-like rest: route channel 0 of layer 0 to output channel 0
+    # through unit centre taps, so that the output equals relu(layer0)[..., 0]
     for l in range(1, CNN.LAYERS):
         w = np.zeros((3, 3, ch[l], ch[l + 1]))
         w[1, 1, 0, 0] = 1.0
         p[CNN.offset(l):CNN.offset(l, True)] = w.reshape(-1)
     out = CNN.forward(p, x)
     xp = np.pad(x, ((1, 1), (1, 1), (0, 0)))
-    ref = np.zeros((64, 64, 64))
+    ref = np.zeros((64, 64, ch[1]))
     for ky in range(3):
         for kx in range(3):
             ref += np.einsum("rci,io->rco", xp[ky:ky + 64, kx:kx + 64], Wl[ky, kx])
     ref += bl
-    np.testing.assert_allclose(out, np.maximum(ref[..., 0], 0.0), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(out[..., 0], np.maximum(ref[..., 0], 0.0), rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(out[..., 1:], 0.0)
 
 
-def test_features_target_and_upsampling():
-    p = W.random_problem(np.random.default_rng(2), 256, mask="square")
+def test_dilated_layer_reads_the_taps_it_should():
+    """A single unit weight at tap (ky, kx) of the dilation-32 layer shifts
+    the map by (ky - 1, kx - 1) * 32 cells (zero where the tap leaves the grid)."""
+    ch = CNN.channels()
+    assert CNN.dilations()[5] == 32
+    rng = np.random.default_rng(5)
+    x = np.abs(rng.normal(size=(64, 64, ch[0])))
+    for ky, kx in ((0, 2), (2, 1)):
+        p = np.zeros(CNN.num_params())
+        for l in range(CNN.LAYERS):
+            w = np.zeros((3, 3, ch[l], ch[l + 1]))
+            if l == 5:
+                w[ky, kx, 0, 0] = 1.0
+            else:
+                w[1, 1, 0, 0] = 1.0
+            p[CNN.offset(l):CNN.offset(l, True)] = w.reshape(-1)
+        out = CNN.forward(p, x)[..., 0]
+        dy, dx = (ky - 1) * 32, (kx - 1) * 32
+        ref = np.zeros((64, 64))
+        for r in range(64):
+            for c in range(64):
+                if 0 <= r + dy < 64 and 0 <= c + dx < 64:
+                    ref[r, c] = x[r + dy, c + dx, 0]
+        np.testing.assert_allclose(out, ref, rtol=0, atol=0)
+
+
+def test_features_target_and_unpacking():
+    p = W.random_problem(np.random.default_rng(2), 256, mask="disc")
     x = CNN.features(p)
-    assert np.allclose(x[..., 0], p.f.reshape(64, 4, 64, 4).mean(axis=(1, 3)))
-    assert np.allclose(x[..., 3], (np.log10(p.mu) + 2.5) / 1.5) and np.allclose(x[..., 6:], 0)
-    u = np.outer(np.linspace(0, 1, 256), np.linspace(0, 2, 256))
+    blocks = lambda a: a.reshape(64, 4, 64, 4).transpose(0, 2, 1, 3)  # [r][c][a][b]
+    np.testing.assert_array_equal(x[..., :16], blocks(p.f).reshape(64, 64, 16))
+    np.testing.assert_allclose(x[..., 16], blocks(p.beta1).mean(axis=(2, 3)), rtol=1e-14)
+    np.testing.assert_allclose(x[..., 17], blocks(p.beta2).mean(axis=(2, 3)), rtol=1e-14)
+    assert np.allclose(x[..., 18], (np.log10(p.mu) + 2.5) / 1.5) and np.allclose(x[..., 19], p.sigma - 1)
+    np.testing.assert_allclose(x[..., 20], blocks(p.mask.astype(float)).mean(axis=(2, 3)))
+    assert np.all(x[..., 21:] == 0)
+    u = np.random.default_rng(3).normal(size=(256, 256))
     t = CNN.target(u, 2.0)
-    assert np.allclose(t, 2.0 * u.reshape(64, 4, 64, 4).mean(axis=(1, 3)))
-    inter = np.ones((256, 256), np.uint8)
-    up = CNN.upsample(t, 2.0, inter)
-    # bilinear through the cell centres reproduces the bilinear field inside
-    assert np.abs(up[4:-4, 4:-4] - u[4:-4, 4:-4]).max() < 1e-12
+    np.testing.assert_array_equal(t, 2.0 * blocks(u).reshape(64, 64, 16))
+    inter = (np.random.default_rng(4).random((256, 256)) < 0.7).astype(np.uint8)
+    back = CNN.unpack(t, 2.0, inter)
+    np.testing.assert_array_equal(back, np.where(inter == 1, u, 0.0))
