@@ -64,8 +64,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--other-prec", action=argparse.BooleanOptionalAction, default=True)
-    ap.add_argument("--workload", default="sheared", choices=["sheared", "batch"])
+    ap.add_argument("--workload", default="sheared", choices=["sheared", "batch", "learned"])
     ap.add_argument("--count", type=int, default=256)
+    # learned warm start: training set, held-out set, Adam steps, minibatch
+    ap.add_argument("--train", type=int, default=2048)
+    ap.add_argument("--hold", type=int, default=128)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--batch-size", type=int, default=32)
     return ap.parse_args()
 
 
@@ -438,12 +443,151 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+# FP32-accumulated BF16 work of the warm-start network per sample (one 64 x 64
+# map): 2 * 4096 pixels * 9 taps * sum of Cin * Cout over the eight layers
+CNN_FLOPS_FWD = 2 * 4096 * 9 * (24 * 64 + 64 * 64 + 64 * 128 + 2 * 128 * 128 + 128 * 64
+                                 + 64 * 64 + 64 * 16)
+
+
+def bf16_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1900.0, 1700.0, "fallback"
+
+
+def run_learned(args):
+    """Learned warm start on 256 x 256 squares: the network is trained on the
+    GPU on solutions the batched solver generates, then held-out problems are
+    solved to tol from its initial states (network time included), batched.
+    Compared with the same batch from u = 0 and with the plain method (one
+    problem after another from u = 0)."""
+    import torch
+
+    from paper_2411_11041_gb300 import ADR_OK, Batch, Network, Solver
+    from paper_2411_11041_gb300 import warmstart as WS
+    from paper_2411_11041_gb300 import workloads as W
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    train = W.learned(args.train, n=256)
+    hold = W.learned(args.hold, n=256, seed=W.SEED_BASE + 5)
+    draw_s = time.perf_counter() - t0
+    net = Network(max(args.batch_size, args.hold))
+    t0 = time.perf_counter()
+    data = WS.generate(net, train, tol=args.tol)
+    torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = WS.train(net, data, args.train_steps, batch=args.batch_size, log_every=500)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    train_ms = e0.elapsed_time(e1)
+    step_ms = train_ms / args.train_steps
+    hd = WS.generate(net, hold, tol=args.tol)
+    zero_loss = 0.5 * float((hd.t.double() ** 2).mean())
+    held_loss = net.loss_grad(hd.x[:args.batch_size].contiguous(),
+                              hd.t[:args.batch_size].contiguous())[0]
+    # forward of the whole held-out set: the tensor-core kernels alone
+    x = hd.x.contiguous()
+    for _ in range(3):
+        net.forward(x)
+    e0.record(stream)
+    for _ in range(10):
+        net.forward(x)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = e0.elapsed_time(e1) / 10
+    # the timed region: features + network + unpack + batched solve
+    opts = WS.solver_opts(args.tol)
+    learned = [Solver(p, device=dev, init=1, **opts) for p in hold]
+    zero = [Solver(p, device=dev, **opts) for p in hold]
+    fields = WS.stack(hold, dev)
+    bl, bz = Batch(learned), Batch(zero)
+
+    def learned_step():
+        xs = net.features(*fields)
+        u0 = WS.initial_states(net, learned, xs)
+        return bl.solve(u0)
+
+    for _ in range(args.warmup):
+        learned_step()
+        bz.solve()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(0)
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, sl, stl = learned_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms_learned = e0.elapsed_time(e1) / args.steps
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, sz, stz = bz.solve()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_zero = e0.elapsed_time(e1) / args.steps
+    for s in zero:
+        s.solve_stationary()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for s in zero:
+        s.solve_stationary()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_plain = e0.elapsed_time(e1)
+    if stl != ADR_OK or stz != ADR_OK:
+        raise RuntimeError("a held-out solve did not converge")
+    itl = np.array([s["iters"] for s in sl])
+    itz = np.array([s["iters"] for s in sz])
+    peak, peak_sus, kind = bf16_peak()
+    fwd_tf = CNN_FLOPS_FWD * len(hold) / (fwd_ms * 1e-3) / 1e12
+    train_tf = 3 * CNN_FLOPS_FWD * args.batch_size / (step_ms * 1e-3) / 1e12
+    # kernels per timed step: features, 8 convolutions, one unpack per problem,
+    # then per batch iteration 2 curve solves, 2 maps, check, compact, flip
+    launches = 1 + 8 + len(hold) + 7 * int(itl.max())
+    line = {
+        "metric": "held-out 256^2 problems solved to 1e-8 per second (learned warm start, batched)",
+        "value": len(hold) / (ms_learned / 1e3), "unit": "problems/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve, bf16 net",
+        "data": "synthetic",
+        "config": {"workload": f"learned256x{args.hold}", "train_problems": args.train,
+                   "train_steps": args.train_steps, "minibatch": args.batch_size, "tol": args.tol,
+                   "step": "features + network + initial states + batched solve of the held-out set"},
+        "iters_mean": {"zero_init": float(itz.mean()), "learned_init": float(itl.mean()),
+                       "ratio": float(itl.sum() / itz.sum()),
+                       "share_of_problems_improved": float((itl < itz).mean())},
+        "ms": {"learned_batched": ms_learned, "zero_batched": ms_zero,
+               "plain_sequential": ms_plain},
+        "speedup": {"learned_batched_vs_plain": ms_plain / ms_learned,
+                    "learned_vs_zero_batched": ms_zero / ms_learned},
+        "training": {"draw_s": draw_s, "generate_s": gen_s, "train_s": train_ms / 1e3,
+                     "step_ms": step_ms, "train_tflops": train_tf,
+                     "held_out_loss": held_loss, "zero_prediction_loss": zero_loss,
+                     "loss_log": losses[-3:]},
+        "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
+                     "frac": fwd_tf / peak, "traffic": None, "peak_kind": kind + " bf16 burst",
+                     "kernel": "network forward (8 BF16 convolutions)", "kernel_ms": fwd_ms,
+                     "units_per_launch": len(hold)},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -479,13 +479,33 @@ __global__ void k_seeds(GridView g, const int* cand, long long ncand, uint8_t* v
     nseeds[fam] = ns;
 }
 
-// trace one curve: number of full RK4 steps M, length L and exit point
+// Accepted RK4 points of the traced curves, kept so that the node placement
+// reads them instead of integrating again.  Points of one curve sit in chunks
+// of kPoolChunk taken from a shared pool; a curve whose points do not fit
+// (pool exhausted, more than kPoolMaxChunks chunks) is re-traced instead,
+// which gives the same points.
+constexpr int kPoolChunk = 512;
+constexpr int kPoolMaxChunks = 512;
+struct PointPool {
+    double2* pts;        // [n_chunks * kPoolChunk]
+    int* tab;            // [seed slot * kPoolMaxChunks + c]: pool chunk of the curve's chunk c
+    int* stored;         // [seed slot]: 1 when every accepted point of the curve is in the pool
+    unsigned int* next;  // chunks handed out
+    unsigned int n_chunks;
+};
+
+// trace one curve: number of full RK4 steps M, length L and exit point; the
+// accepted points P_1 .. P_M go to the pool when it has room
 __device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mout, double* L,
-                         double* Xe, double* Ye)
+                         double* Xe, double* Ye, const PointPool& pool, int slot)
 {
     double ds = g.hs / kTraceStepsPerH;
     double cap_len = 10.0 * 2.0 * (g.W + g.H);
     long long npts = 0;
+    bool keep = pool.n_chunks > 0;
+    int* tab = pool.tab + (size_t)slot * kPoolMaxChunks;
+    int chunk = -1;
+    if (keep) pool.stored[slot] = 0;
     for (;;) {
         npts++;
         double Xn, Yn;
@@ -493,6 +513,19 @@ __device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mo
         if (interior_point(g, snap(Xn / g.hx), snap(Yn / g.hy))) {
             X = Xn;
             Y = Yn;
+            if (keep) {  // P_q, q = npts, at pool index q - 1 of the curve
+                long long i = npts - 1;
+                int c = (int)(i / kPoolChunk), o = (int)(i % kPoolChunk);
+                if (o == 0) {
+                    unsigned int got = c < kPoolMaxChunks ? atomicAdd(pool.next, 1u) : pool.n_chunks;
+                    if (got >= pool.n_chunks) keep = false;
+                    else {
+                        chunk = (int)got;
+                        tab[c] = chunk;
+                    }
+                }
+                if (keep) pool.pts[(size_t)chunk * kPoolChunk + o] = make_double2(X, Y);
+            }
             if (npts * ds > cap_len) return -1;
             continue;
         }
@@ -509,6 +542,7 @@ __device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mo
         *L = (npts - 1) * ds + lo * ds;
         *Xe = XE;
         *Ye = YE;
+        if (keep) pool.stored[slot] = 1;
         return 0;
     }
 }
@@ -532,13 +566,13 @@ __device__ __forceinline__ bool seed_of(const int* nseeds, int cap, int t, int* 
 
 __global__ void k_trace_count(GridView g, int cap, const double* sx, const double* sy,
                               const int* nseeds, int* M, double* L, double* XE, double* YE,
-                              long long* cn, int* status)
+                              long long* cn, int* status, PointPool pool)
 {
     int fam, s;
     if (!seed_of(nseeds, cap, blockIdx.x * blockDim.x + threadIdx.x, &fam, &s)) return;
     int m = 0;
     double len = 0, xe = 0, ye = 0;
-    if (trace_len(g, fam, sx[s], sy[s], &m, &len, &xe, &ye)) {
+    if (trace_len(g, fam, sx[s], sy[s], &m, &len, &xe, &ye, pool, s)) {
         atomicOr(status, kErrGeom);
         m = 0;
         len = 0.0;
@@ -560,12 +594,18 @@ struct FillOut {
     double* es;
 };
 
+// place n+1 nodes uniformly in arc length on the polyline P_0 .. P_M, exit
+// point: node j at s_j = j L / n lies on the RK4 step q = floor(s_j / ds)
+// (linear between its end points).  One warp per curve; a curve whose points
+// are not in the pool is re-traced by lane 0.
 __global__ void k_trace_fill(GridView g, int cap, const double* sx, const double* sy,
                              const int* nseeds, const int* M, const double* L, const double* XE,
-                             const double* YE, const long long* noff, FillOut o0, FillOut o1)
+                             const double* YE, const long long* noff, FillOut o0, FillOut o1,
+                             PointPool pool)
 {
     int fam, s;
-    if (!seed_of(nseeds, cap, blockIdx.x * blockDim.x + threadIdx.x, &fam, &s)) return;
+    const int lane = threadIdx.x & 31;
+    if (!seed_of(nseeds, cap, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, &fam, &s)) return;
     const FillOut& o = fam == 0 ? o0 : o1;
     int* off = o.off;
     double* h = o.h;
@@ -577,21 +617,63 @@ __global__ void k_trace_fill(GridView g, int cap, const double* sx, const double
     int m = M[s];
     int n = elements_for(g, len);
     int base = (int)noff[s];
-    off[li] = base;
-    h[li] = len / n;
+    const double xe = XE[s], ye = YE[s];
+    if (lane == 0) {
+        off[li] = base;
+        h[li] = len / n;
+    }
+    if (pool.n_chunks > 0 && pool.stored[s]) {
+        const int* tab = pool.tab + (size_t)s * kPoolMaxChunks;
+        for (int j = lane; j <= n; j += 32) {
+            double X, Y;
+            if (j == n) {
+                X = xe;
+                Y = ye;
+            } else {
+                double sj = j * (len / n);
+                int q = (int)floor(sj / ds);
+                if (q > m) q = m;
+                double Xa, Ya, Xb, Yb;
+                if (q == 0) {
+                    Xa = sx[s];
+                    Ya = sy[s];
+                } else {
+                    double2 a = pool.pts[(size_t)tab[(q - 1) / kPoolChunk] * kPoolChunk + (q - 1) % kPoolChunk];
+                    Xa = a.x;
+                    Ya = a.y;
+                }
+                if (q < m) {
+                    double2 b = pool.pts[(size_t)tab[q / kPoolChunk] * kPoolChunk + q % kPoolChunk];
+                    Xb = b.x;
+                    Yb = b.y;
+                } else {
+                    Xb = xe;
+                    Yb = ye;
+                }
+                double s0 = q * ds, s1 = (q < m) ? (q + 1) * ds : len;
+                double fr = (s1 > s0) ? (sj - s0) / (s1 - s0) : 0.0;
+                X = Xa + fr * (Xb - Xa);
+                Y = Ya + fr * (Yb - Ya);
+            }
+            xs[base + j] = snap(X / g.hx);
+            es[base + j] = snap(Y / g.hy);
+        }
+        return;
+    }
+    if (lane != 0) return;
     // (Xa, Ya) = P_q, (Xb, Yb) = P_{q+1}; P_0 is the seed, P_{m+1} the exit point
     int q = 0;
     double Xa = sx[s], Ya = sy[s], Xb, Yb;
     if (m > 0) rk4(g, fam, Xa, Ya, ds, &Xb, &Yb);
     else {
-        Xb = XE[s];
-        Yb = YE[s];
+        Xb = xe;
+        Yb = ye;
     }
     for (int j = 0; j <= n; ++j) {
         double X, Y;
         if (j == n) {
-            X = XE[s];
-            Y = YE[s];
+            X = xe;
+            Y = ye;
         } else {
             double sj = j * (len / n);
             int qj = (int)floor(sj / ds);
@@ -602,8 +684,8 @@ __global__ void k_trace_fill(GridView g, int cap, const double* sx, const double
                 Ya = Yb;
                 if (q < m) rk4(g, fam, Xa, Ya, ds, &Xb, &Yb);
                 else {
-                    Xb = XE[s];
-                    Yb = YE[s];
+                    Xb = xe;
+                    Yb = ye;
                 }
             }
             double s0 = q * ds, s1 = (q < m) ? (q + 1) * ds : len;
@@ -1055,8 +1137,33 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
     TRY(alloc_tmp(tg.v, &cn, n2));
     TRY(alloc_tmp(tg.v, &on, n2 + 2));
     int tot = ns[0] + ns[1];
-    k_trace_count<<<blocks_for(tot, 64), 64, 0, st>>>(g, cap, sx, sy, cnt + 1, M, L, XE, YE, cn,
-                                                      status_d);
+    // point pool: about kTraceStepsPerH^2 accepted points per hs^2 of the
+    // domain in each family, with room to spare and one partial chunk per
+    // curve; without room (or memory) the node placement re-traces
+    PointPool pool{};
+    {
+        double area = (double)(nx - 1) * (ny - 1) * p->gv.hx * p->gv.hy;
+        double est = 2.5 * kTraceStepsPerH * area / (p->gv.hs * p->gv.hs) + (double)tot * kPoolChunk;
+        double chunks = ceil(est / kPoolChunk);
+        const double max_chunks = (double)(3ull << 30) / (sizeof(double2) * kPoolChunk);
+        if (chunks > max_chunks) chunks = max_chunks;
+        pool.n_chunks = (unsigned int)chunks;
+        void* q = nullptr;
+        if (cudaMalloc(&q, (size_t)pool.n_chunks * kPoolChunk * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();  // no pool: every curve is re-traced
+            pool.n_chunks = 0;
+        } else {
+            tg.v.push_back(q);
+            pool.pts = static_cast<double2*>(q);
+            TRY(alloc_tmp(tg.v, &pool.tab, n2 * kPoolMaxChunks));
+            TRY(alloc_tmp(tg.v, &pool.stored, n2));
+            TRY(alloc_tmp(tg.v, &pool.next, 1));
+            ADR_CUDA_TRY(cudaMemsetAsync(pool.next, 0, sizeof(unsigned int), st));
+        }
+    }
+    // one warp per SM and FP64 pipe: the per-curve traces are serial chains
+    k_trace_count<<<blocks_for(tot, 32), 32, 0, st>>>(g, cap, sx, sy, cnt + 1, M, L, XE, YE, cn,
+                                                      status_d, pool);
     k_scan<<<1, 1024, 0, st>>>(cn, on, ns[0]);
     k_scan<<<1, 1024, 0, st>>>(cn + cap, on + cap, ns[1]);
     long long tn[2] = {0, 0};
@@ -1079,8 +1186,8 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
         TRY(dev_alloc(p, &F.eta, F.n_nodes));
         fo[fam] = {F.off, F.h, F.xi, F.eta};
     }
-    k_trace_fill<<<blocks_for(tot, 64), 64, 0, st>>>(g, cap, sx, sy, cnt + 1, M, L, XE, YE, on,
-                                                     fo[0], fo[1]);
+    k_trace_fill<<<blocks_for(32LL * tot, 128), 128, 0, st>>>(g, cap, sx, sy, cnt + 1, M, L, XE, YE,
+                                                               on, fo[0], fo[1], pool);
     for (int fam = 0; fam < 2; ++fam) {
         int nn = p->fam[fam].n_nodes;
         ADR_CUDA_TRY(cudaMemcpyAsync(p->fam[fam].off + p->fam[fam].n_lines, &nn, sizeof(int),

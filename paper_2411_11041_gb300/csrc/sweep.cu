@@ -1511,7 +1511,6 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
             else k_curve_solve_batch<1024, FAM_, false><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], b->act, k);     \
         }                                                                                          \
     }
-    const int* const* ab = (const int* const*)b->act.blocks;
     ADR_BATCH_SOLVE(0, itB, nB, gB)
     k_grid_map_batch<false><<<b->map_grid, kGridThreads, 0, st>>>(b->gtab, 0, b->blk_prob, b->blk_local,
                                                                  b->nblk, b->act.blocks_dev, b->act.count,
@@ -1521,7 +1520,6 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
                                                                 b->nblk, b->act.blocks_dev, b->act.count,
                                                                 b->act.sel);
 #undef ADR_BATCH_SOLVE
-    (void)ab;
     k_check_batch<<<b->n, 256, 0, st>>>(b->states, (const double* const*)b->partials, b->nblk, b->n,
                                         b->tol, b->max_iter, b->ticket, cond, b->act.changed);
     k_batch_compact<<<b->map_grid, 256, 0, st>>>(b->act, b->d_items, b->d_n_items, b->blk_prob,
