@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--n", "--grid-n", dest="n", type=int, default=2048)
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -181,6 +181,14 @@ def sum_over_ranks(ws, value, device):
     return float(t.item())
 
 
+def job_rate(ws, ms, units, device):
+    """Whole-job throughput of weak-scaled replicas: the units all ranks
+    processed over the slowest rank's time.  Returns (ms_max, units_all, rate/s)."""
+    ms_max = max_over_ranks(ws, ms, device)
+    units_all = sum_over_ranks(ws, units, device)
+    return ms_max, units_all, units_all / (ms_max / 1e3)
+
+
 # ------------------------------------------------------------- oracle legs
 
 def oracle_sample(n, budget_s=12.0, min_steps=1):
@@ -277,9 +285,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ws, ms, dev)
-    dofs_all = sum_over_ranks(ws, dofs, dev)
-    value = dofs_all / (ms_max / 1e3)
+    ms_max, dofs_all, value = job_rate(ws, ms, dofs, dev)
     # per-kernel device time in the solve's launch configuration (CUDA events)
     kms = solver.time_kernels(reps=20)
     units = [unknowns[0], prob.nx * prob.ny, unknowns[1], prob.nx * prob.ny]

@@ -44,7 +44,9 @@ typedef enum {
     ADR_ECUDA = 3,    /* a CUDA call failed (message in adr_last_error) */
     ADR_ENOCONV = 4,  /* max_iter reached before tol, or the iteration diverged (a norm
                          stopped being finite); outputs hold the last iterate */
-    ADR_EGEOM = 5,    /* curve tracing failed (closed integral curve or |beta| = 0 on a curve) */
+    ADR_EGEOM = 5,    /* the curve families do not cover the domain (§3, §6): tracing failed
+                         (closed integral curve, |beta| = 0 on a curve), a family has no
+                         inflow boundary, or an interior node meets no curve of a family */
     ADR_ETIMEOUT = 6  /* reserved: a bounded device wait gave up */
 } adr_status;
 

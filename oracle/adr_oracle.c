@@ -600,7 +600,12 @@ static int build_crossings(orc_problem* p, int fam)
     seg_slot* rows = calloc((size_t)ny * (nx - 1), sizeof(seg_slot));
     seg_slot* cols = calloc((size_t)nx * (ny - 1), sizeof(seg_slot));
     F->cross = calloc((size_t)4 * nx * ny, sizeof(crossing));
-    if (!rows || !cols || !F->cross) return -1;
+    int uncovered = 0;
+    if (!rows || !cols || !F->cross) {
+        free(rows);
+        free(cols);
+        return -1;
+    }
     for (int l = 0; l < F->n_lines; ++l)
         for (int g = F->off[l]; g + 1 < F->off[l + 1]; ++g) {
             double xa = F->xi[g], xb = F->xi[g + 1], ea = F->eta[g], eb = F->eta[g + 1];
@@ -680,10 +685,14 @@ static int build_crossings(orc_problem* p, int fam)
                 if (col[e].mn.valid) { c[3] = col[e].mn; break; }
                 if (p->ntype[(size_t)(e + 1) * nx + i] != ORC_INTERIOR) { c[3] = bnd; c[3].pos = e + 1; break; }
             }
+            /* no curve of the family on either grid line through the node
+               before the boundary: the family does not cover the node (the
+               curves of each family must cover the domain, §3 and §6) */
+            if (c[0].g == -1 && c[1].g == -1 && c[2].g == -1 && c[3].g == -1) uncovered = 1;
         }
     free(rows);
     free(cols);
-    return 0;
+    return uncovered;
 }
 
 /* ------------------------------------------------------------- create */
@@ -770,9 +779,14 @@ int orc_create(int nx, int ny, double x0, double y0, double x1, double y1,
             orc_destroy(p);
             return st > 0 ? st : ORC_ENOMEM;
         }
-        if (build_crossings(p, fam)) {
+        if (p->fam[fam].n_lines == 0) { /* no inflow boundary: no curve of the family */
             orc_destroy(p);
-            return ORC_ENOMEM;
+            return ORC_EGEOM;
+        }
+        st = build_crossings(p, fam);
+        if (st) {
+            orc_destroy(p);
+            return st < 0 ? ORC_ENOMEM : ORC_EGEOM;
         }
     }
     *out = p;

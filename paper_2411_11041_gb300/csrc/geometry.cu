@@ -22,7 +22,7 @@ inline int blocks_for(long long n, int t = kThreads)
 }
 
 // status bits raised by setup kernels
-enum : int { kErrInvalid = 1, kErrGeom = 2, kErrCapacity = 4 };
+enum : int { kErrInvalid = 1, kErrGeom = 2, kErrCapacity = 4, kErrUncovered = 8 };
 
 __device__ __forceinline__ double snap(double v)
 {
@@ -836,7 +836,7 @@ __global__ void k_slots_init(Slots s, size_t n)
 // nearest crossing on each side of every interior node (a non-interior grid
 // node met first stands for the boundary, value 0)
 __global__ void k_node_desc(GridView g, Slots rows, Slots cols, int* cg, double* ct,
-                            double* cw, double* cpos)
+                            double* cw, double* cpos, int* status)
 {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int nx = g.nx, ny = g.ny;
@@ -915,6 +915,9 @@ __global__ void k_node_desc(GridView g, Slots rows, Slots cols, int* cg, double*
         ct[4 * k + q] = T[q];
         cpos[4 * k + q] = Pp[q];
     }
+    // no curve of the family on either grid line through the node before the
+    // boundary: the family does not cover the node (§3, §6)
+    if (G[0] == -1 && G[1] == -1 && G[2] == -1 && G[3] == -1) atomicOr(status, kErrUncovered);
     cw[2 * k] = (Pp[1] == Pp[0]) ? 0.0 : (i - Pp[0]) / (Pp[1] - Pp[0]);
     cw[2 * k + 1] = (Pp[3] == Pp[2]) ? 0.0 : (r - Pp[2]) / (Pp[3] - Pp[2]);
 }
@@ -973,7 +976,7 @@ struct TmpGuard {
         if (_s != ADR_OK) return _s;   \
     } while (0)
 
-adr_status finish_family(Problem* p, int fam, TmpGuard& tg)
+adr_status finish_family(Problem* p, int fam, TmpGuard& tg, int* status_d)
 {
     Family& F = p->fam[fam];
     cudaStream_t st = p->stream;
@@ -1030,7 +1033,7 @@ adr_status finish_family(Problem* p, int fam, TmpGuard& tg)
     k_cross<0><<<nb, kThreads, 0, st>>>(g, F.n_nodes, lon, F.xi, F.eta, R, C);
     k_cross<1><<<nb, kThreads, 0, st>>>(g, F.n_nodes, lon, F.xi, F.eta, R, C);
     k_cross<2><<<nb, kThreads, 0, st>>>(g, F.n_nodes, lon, F.xi, F.eta, R, C);
-    k_node_desc<<<blocks_for(N), kThreads, 0, st>>>(g, R, C, F.cg, F.ct, F.cw, F.cpos);
+    k_node_desc<<<blocks_for(N), kThreads, 0, st>>>(g, R, C, F.cg, F.ct, F.cw, F.cpos, status_d);
     TRY(dev_alloc(p, &F.mg, 4 * (size_t)N));
     TRY(dev_alloc(p, &F.mc, 8 * (size_t)N));
     TRY(launch_map_coef(p, fam));
@@ -1271,8 +1274,15 @@ adr_status build_geometry(Problem* p, const uint8_t* mask)
         return ADR_EGEOM;
     }
     for (int fam = 0; fam < 2; ++fam) {
-        s = finish_family(p, fam, tg);
+        s = finish_family(p, fam, tg, info + 1);
         if (s != ADR_OK) return s;
+    }
+    ADR_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, st));
+    ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hinfo[1] & kErrUncovered) {
+        set_error("a curve family leaves an interior node uncovered (stagnation point or "
+                  "closed integral curves of beta or gamma)");
+        return ADR_EGEOM;
     }
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;

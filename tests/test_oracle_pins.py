@@ -492,3 +492,20 @@ def test_diverging_iteration_stops_without_convergence():
     o = O.Oracle(p)
     u, uit, it, rel, st = o.solve_stationary(theta=0.1, dt=5.0, tol=1e-8, max_iter=100000)
     assert st == O.ENOCONV and not np.isfinite(rel) and it < 2000
+
+
+def test_flows_whose_curves_do_not_cover_the_domain_are_rejected():
+    """The method needs both curve families to cover Omega_h (§3, §6).  A
+    rotating flow leaves a disc around its centre that no inflow-seeded beta
+    curve reaches; a source-like flow beta = x - c has no inflow boundary for
+    its beta family at all.  Both are geometry errors, not silent zeros."""
+    n = 34  # no node at the centre, so |beta| > 0 at every node
+    X, Y = W.node_coords(n, n)
+    sq = W.make_mask("square", n, n)
+    one = np.ones((n, n))
+    rot = W.Problem(n, n, 0.01, 1.0, -(Y - 0.5), X - 0.5, one, sq)
+    src = W.Problem(n, n, 0.01, 1.0, X - 0.5, Y - 0.5, one, sq)
+    for prob in (rot, src):
+        with pytest.raises(O.OracleError) as e:
+            O.Oracle(prob)
+        assert e.value.status == O.EGEOM
