@@ -1,13 +1,17 @@
 // Directional sweep kernels (the hot path).
 //
-//  k_line_sweep  one warp per curve: bilinear gather of the grid state onto
-//                the curve nodes (§6.1), linear-FEM assembly of the substep
-//                system (§6 eqs. SemiDiscrSplit1Dbeta / SemiDiscrSplit1Dgamma),
-//                partitioned tridiagonal solve, curve values u + dt d out.
-//  k_grid_map    one thread per grid node: curve -> grid interpolation through
-//                the nearest crossings on the node's row and column (§6), with
-//                the relative-update norms fused in.
-//  k_check       one block: convergence test and the CUDA-graph loop condition.
+//  k_curve_prep   once per (theta dt, sigma): assembles the substep systems
+//                 (§6 eqs. SemiDiscrSplit1Dbeta / SemiDiscrSplit1Dgamma) and
+//                 factors their partitioned elimination.
+//  k_curve_solve  every substep: bilinear gather of the grid state onto the
+//                 curve nodes (§6.1), right-hand side F - S u, the factored
+//                 elimination, curve values u + dt d out; a block of BS threads
+//                 holds BS/T curves of T threads each.
+//  k_grid_map     one thread per grid node: curve -> grid interpolation through
+//                 the nearest crossings on the node's row and column (§6), with
+//                 the relative-update norms fused in.
+//  k_check        one block: convergence test and the CUDA-graph loop condition.
+//  *_batch        the same steps for many problems in one persistent launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
