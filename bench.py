@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--other-prec", action=argparse.BooleanOptionalAction, default=True)
-    ap.add_argument("--workload", default="sheared", choices=["sheared", "batch", "learned"])
+    ap.add_argument("--workload", default="sheared",
+                    choices=["sheared", "batch", "learned", "data2d"])
     ap.add_argument("--count", type=int, default=256)
     # learned warm start: training set, held-out set, Adam steps, minibatch
     ap.add_argument("--train", type=int, default=2048)
@@ -511,17 +512,17 @@ def run_learned(args):
     opts = WS.solver_opts(args.tol)
     learned = [Solver(p, device=dev, init=1, **opts) for p in hold]
     zero = [Solver(p, device=dev, **opts) for p in hold]
+    paper = [Solver(p, device=dev, init=2, **opts) for p in hold]  # eq. u0stationary
     fields = WS.stack(hold, dev)
-    bl, bz = Batch(learned), Batch(zero)
+    bl, bz, bp = Batch(learned), Batch(zero), Batch(paper)
 
     def learned_step():
-        xs = net.features(*fields)
-        u0 = WS.initial_states(net, learned, xs)
-        return bl.solve(u0)
+        return bl.solve(WS.initial_states(net, learned, fields))
 
     for _ in range(args.warmup):
         learned_step()
         bz.solve()
+        bp.solve()
     torch.cuda.synchronize(dev)
     clocks = Clocks(0)
     clocks.start()
@@ -538,6 +539,12 @@ def run_learned(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_zero = e0.elapsed_time(e1) / args.steps
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, sp, stp = bp.solve()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_paper = e0.elapsed_time(e1) / args.steps
     for s in zero:
         s.solve_stationary()
     torch.cuda.synchronize(dev)
@@ -547,16 +554,18 @@ def run_learned(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_plain = e0.elapsed_time(e1)
-    if stl != ADR_OK or stz != ADR_OK:
+    if stl != ADR_OK or stz != ADR_OK or stp != ADR_OK:
         raise RuntimeError("a held-out solve did not converge")
     itl = np.array([s["iters"] for s in sl])
     itz = np.array([s["iters"] for s in sz])
+    itp = np.array([s["iters"] for s in sp])
     peak, peak_sus, kind = bf16_peak()
     fwd_tf = CNN_FLOPS_FWD * len(hold) / (fwd_ms * 1e-3) / 1e12
     train_tf = 3 * CNN_FLOPS_FWD * args.batch_size / (step_ms * 1e-3) / 1e12
-    # kernels per timed step: features, 8 convolutions, one unpack per problem,
-    # then per batch iteration 2 curve solves, 2 maps, check, compact, flip
-    launches = 1 + 8 + len(hold) + 7 * int(itl.max())
+    # kernels per timed step: the paper's u0 (4 per problem), features, 8
+    # convolutions, one unpack per problem, then per batch iteration 2 curve
+    # solves, 2 maps, check, compact, flip
+    launches = 5 * len(hold) + 1 + 8 + 7 * int(itl.max())
     line = {
         "metric": "held-out 256^2 problems solved to 1e-8 per second (learned warm start, batched)",
         "value": len(hold) / (ms_learned / 1e3), "unit": "problems/s", "n_gpus": 1,
@@ -564,12 +573,15 @@ def run_learned(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve, bf16 net",
         "data": "synthetic",
         "config": {"workload": f"learned256x{args.hold}", "train_problems": args.train,
+                   "network_input": "problem data + the paper's initial state (eq. u0stationary)",
                    "train_steps": args.train_steps, "minibatch": args.batch_size, "tol": args.tol,
-                   "step": "features + network + initial states + batched solve of the held-out set"},
-        "iters_mean": {"zero_init": float(itz.mean()), "learned_init": float(itl.mean()),
+                   "step": "paper u0 + features + network + initial states + batched solve of the "
+                           "held-out set"},
+        "iters_mean": {"zero_init": float(itz.mean()), "paper_u0_init": float(itp.mean()),
+                       "learned_init": float(itl.mean()),
                        "ratio": float(itl.sum() / itz.sum()),
                        "share_of_problems_improved": float((itl < itz).mean())},
-        "ms": {"learned_batched": ms_learned, "zero_batched": ms_zero,
+        "ms": {"learned_batched": ms_learned, "zero_batched": ms_zero, "paper_u0_batched": ms_paper,
                "plain_sequential": ms_plain},
         "speedup": {"learned_batched_vs_plain": ms_plain / ms_learned,
                     "learned_vs_zero_batched": ms_zero / ms_learned},
@@ -586,6 +598,51 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_data2d(args):
+    """The paper's experiment (eq. Data2D) as the paper runs it: 50 Crank-Nicolson
+    steps of dt = 0.001 from the state of eq. u0stationary, on n x n nodes
+    (default 61).  Latency-bound (the grid fits in L2); timed per solve."""
+    import torch
+
+    from paper_2411_11041_gb300 import ADR_INIT_PAPER_U0, Solver
+    from paper_2411_11041_gb300 import workloads as W
+    n = args.n if args.n != 2048 else 61
+    prob = W.data2d(n)
+    dev = torch.device("cuda:0")
+    s = Solver(prob, device=dev, tol=0.0, max_iter=50, dt=1e-3, init=ADR_INIT_PAPER_U0)
+    unknowns = s.line_unknowns()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        s.solve_stationary()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dofs = 0.0
+    for _ in range(args.steps):
+        _, _, st, _ = s.solve_stationary()
+        dofs += st["line_dofs"]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": METRIC.replace("time-to-1e-8 relative update", "50 steps of eq. Data2D"),
+            "value": dofs / args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"data2d{n}", "nodes": n * n, "line_unknowns_per_step": unknowns,
+                       "step": "50 split steps, dt = 0.001, theta = 0.5, from u0stationary",
+                       "l2": "fits in L2: a latency case"}}
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        o = O.Oracle(prob)
+        t0 = time.perf_counter()
+        o.solve_stationary(theta=0.5, dt=1e-3, tol=0.0, max_iter=50, init=2)
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": dofs / args.steps / secs, "unit": UNIT, "cores": 1,
+                                "kind": "oracle", "sample": f"the same 50-step solve ({secs:.2f} s)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -594,6 +651,8 @@ def main():
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "data2d":
+        run_data2d(args)
     else:
         run_ours(args)
 

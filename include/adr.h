@@ -282,22 +282,26 @@ adr_status adr_cross_substep_noalloc(int nx, int ny, double mu, double theta, do
  * Learned warm start (no counterpart in the paper; the paper's iteration stays
  * the solver and the judge of convergence, the network only supplies u_0).
  *
- * A convolutional network maps a problem on a 256 x 256 node grid to a
- * prediction of sigma * u at every node; adr_cnn_initial_state turns it into an
+ * A convolutional network maps a problem on a 256 x 256 node grid, and a
+ * first initial state u0 of it (normally the state of eq. u0stationary, from
+ * adr_paper_u0), to the smooth part of the correction u - u0, u the iterate
+ * the stationary solve converges to; adr_cnn_initial_state turns it into an
  * initial state for ADR_INIT_USER.  The grid is read as 64 x 64 cells of 4 x 4
- * nodes, cell (r, c) holding nodes (4 r + a, 4 c + b), a, b in 0..3.
- * Features (NHWC, [batch][64][64][24], BF16): channel 4 a + b = f at node
- * (4 r + a, 4 c + b); 16, 17: cell means of beta1, beta2; 18: (log10 mu + 2.5)/1.5;
- * 19: sigma - 1; 20: cell mean of the mask; 21..23: 0.
+ * nodes, cell (r, c) holding nodes (4 r + a, 4 c + b), a, b in 0..3.  Every
+ * problem is scaled by s = max |u0| (1 when u0 is NULL or zero).
+ * Features (NHWC, [batch][64][64][40], BF16): channel 4 a + b = f at node
+ * (4 r + a, 4 c + b); 16 + 4 a + b = u0 / s there; 32, 33: cell means of
+ * beta1, beta2; 34: (log10 mu + 2.5)/1.5; 35: sigma - 1; 36: cell mean of the
+ * mask; 37..39: 0.
  * Network: eight 3 x 3 convolutions with zero padding, dilations
- * 1 2 4 8 16 32 1 1, channels 24 64 64 128 128 128 64 64 16, bias, ReLU after
- * all but the last (539 k parameters).  Output ([batch][64][64][16], FP32):
- * channel 4 a + b predicts sigma * u at node (4 r + a, 4 c + b), u the
- * iterate the stationary solve converges to.  Parameters are one FP32 vector
- * packed as W_0, b_0, W_1, b_1, ... with W_l[(tap * Cin + ci) * Cout + co],
- * tap = 3 ky + kx.  Convolutions (forward, data and weight gradients) run on
- * the BF16 tensor cores with FP32 accumulation; Adam keeps FP32 master
- * parameters.  Loss: 1/2 of the mean squared error over all outputs of a batch.
+ * 1 2 4 8 16 32 1 1, channels 40 64 64 128 128 128 64 64 8, bias, ReLU after
+ * all but the last (544 k parameters).  Output ([batch][64][64][8], FP32):
+ * channel 0 predicts the cell mean of (u - u0) / s; channels 1..7 are not used.
+ * Parameters are one FP32 vector packed as W_0, b_0, W_1, b_1, ... with
+ * W_l[(tap * Cin + ci) * Cout + co], tap = 3 ky + kx.  Convolutions (forward,
+ * data and weight gradients) run on the BF16 tensor cores with FP32
+ * accumulation; Adam keeps FP32 master parameters.  Loss: 1/2 of the mean
+ * squared error of channel 0 over all cells of a batch.
  */
 typedef struct adr_cnn adr_cnn; /* opaque network handle */
 
@@ -314,17 +318,20 @@ adr_status adr_cnn_set_params(adr_cnn* cnn, const float* params);
 adr_status adr_cnn_get_params(adr_cnn* cnn, float* params);
 
 /* adr_cnn_features: batch problems on n x n nodes, n = 256 (device arrays,
- * problem b at offset b n n): f, beta1, beta2 double, mask uint8; mu, sigma
- * device double[batch].  x: device BF16 (uint16 storage) [batch][64][64][24].
- * Launch only.  Errors: ADR_EINVAL (n != 256, NULL pointer). */
+ * problem b at offset b n n): f, beta1, beta2 double, mask uint8, u0 double
+ * (nullable: zeros); mu, sigma device double[batch].  x: device BF16 (uint16
+ * storage) [batch][64][64][40]; scale: device double[batch] <- s of each
+ * problem.  Launch only.  Errors: ADR_EINVAL (n != 256, NULL pointer). */
 adr_status adr_cnn_features(int batch, int n, const double* f, const double* beta1,
                             const double* beta2, const uint8_t* mask, const double* mu,
-                            const double* sigma, uint16_t* x, void* stream);
-/* adr_cnn_targets: t (device float [batch][64][64][16]) <- sigma_b u_b in the
- * output layout; u device double [batch][n][n], n = 256.  Launch only. */
-adr_status adr_cnn_targets(int batch, int n, const double* u, const double* sigma, float* t,
-                           void* stream);
-/* adr_cnn_forward: y (device float [batch][64][64][16]) <- the network's output.
+                            const double* sigma, const double* u0, uint16_t* x, double* scale,
+                            void* stream);
+/* adr_cnn_targets: t (device float [batch][64][64]) <- the cell means of
+ * (u_b - u0_b) / s_b; u, u0 (nullable: zeros) device double [batch][n][n],
+ * n = 256; scale: device double[batch] from adr_cnn_features.  Launch only. */
+adr_status adr_cnn_targets(int batch, int n, const double* u, const double* u0,
+                           const double* scale, float* t, void* stream);
+/* adr_cnn_forward: y (device float [batch][64][64][8]) <- the network's output.
  * Launch only, on the handle's stream.  Errors: ADR_EINVAL, ADR_ECUDA. */
 adr_status adr_cnn_forward(adr_cnn* cnn, int batch, const uint16_t* x, float* y);
 /* adr_cnn_loss_grad: forward and backward without an update.  grad (nullable
@@ -337,11 +344,15 @@ adr_status adr_cnn_loss_grad(adr_cnn* cnn, int batch, const uint16_t* x, const f
  * the update (the call then waits for the stream). */
 adr_status adr_cnn_train_step(adr_cnn* cnn, int batch, const uint16_t* x, const float* t,
                               float lr, double* loss);
-/* adr_cnn_initial_state: u_out (device double [256][256]) <- one prediction y
- * (device float [64][64][16]) in grid layout, divided by the handle's sigma, 0
- * at non-interior nodes.  Pass it as u_init with ADR_INIT_USER.  Launch only,
- * on the problem's stream.  Errors: ADR_EINVAL (grid not 256 x 256). */
-adr_status adr_cnn_initial_state(adr_problem* prob, const float* y, double* u_out);
+/* adr_cnn_initial_state: u_out (device double [256][256]) <- u0 + s * v at the
+ * interior nodes, 0 elsewhere, v the bilinear interpolation of channel 0 of one
+ * prediction y (device float [64][64][8]) with cell centres at node
+ * 4 k + 1.5 (clamped at the outer half cells); u0 device double [256][256]
+ * (nullable: zeros); scale: device pointer to s (nullable: 1).  Pass u_out as
+ * u_init with ADR_INIT_USER.  Launch only, on the problem's stream.
+ * Errors: ADR_EINVAL (grid not 256 x 256). */
+adr_status adr_cnn_initial_state(adr_problem* prob, const float* y, const double* u0,
+                                 const double* scale, double* u_out);
 
 #ifdef __cplusplus
 }

@@ -33,8 +33,8 @@
 #define SNAP_TOL 1e-9
 /* element count n = ceil(|L| / h_s - NODE_TOL) */
 #define NODE_TOL 1e-9
-/* RK4 step for curve tracing, as a fraction of the curve spacing h_s */
-#define TRACE_STEPS_PER_H 8
+/* RK4 steps per curve spacing h_s along traced curves (step h_s / 2) */
+#define TRACE_STEPS_PER_H 2
 #define BISECT_ITERS 60
 
 typedef struct {

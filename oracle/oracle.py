@@ -82,12 +82,15 @@ def lib():
         L.cnn_param_offset.restype = C.c_long
         L.cnn_channels.argtypes = [C.c_int]
         L.cnn_dilation.argtypes = [C.c_int]
-        L.cnn_features.argtypes = [C.c_int, dp, dp, dp, up, C.c_double, C.c_double, dp]
-        L.cnn_target.argtypes = [C.c_int, dp, C.c_double, dp]
+        L.cnn_scale.argtypes = [C.c_int, vp]
+        L.cnn_scale.restype = C.c_double
+        L.cnn_features.argtypes = [C.c_int, dp, dp, dp, up, C.c_double, C.c_double, vp,
+                                   C.c_double, dp]
+        L.cnn_target.argtypes = [C.c_int, dp, vp, C.c_double, dp]
         L.cnn_forward.argtypes = [dp, dp, vp, dp]
         L.cnn_loss_grad.argtypes = [dp, C.c_int, dp, dp, vp]
         L.cnn_loss_grad.restype = C.c_double
-        L.cnn_unpack.argtypes = [C.c_int, dp, C.c_double, up, dp]
+        L.cnn_upsample.argtypes = [C.c_int, dp, vp, C.c_double, up, dp]
         for fn in ("orc_q1_dense", "orc_p1_dense"):
             getattr(L, fn).argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                        C.c_double, up, C.c_double, C.c_double, dp, dp, dp, dp]
@@ -97,6 +100,10 @@ def lib():
 
 def _c(a, dtype=np.float64):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _opt(a):
+    return None if a is None else _c(a)
 
 
 def _ptr(a):
@@ -286,23 +293,34 @@ class CNN:
         return lib().cnn_param_offset(l, int(bias))
 
     @staticmethod
-    def features(prob):
-        """[H][W][24] features of a problem on a (4 H) x (4 W) grid."""
-        x = np.zeros((CNN.H, CNN.W, 24))
+    def scale(u0):
+        """max |u0| over the grid (1 for None or zero)."""
+        u0c = _opt(u0)
+        return lib().cnn_scale(0 if u0c is None else u0c.shape[0], _ptr(u0c))
+
+    @staticmethod
+    def features(prob, u0=None):
+        """[H][W][40] features of a problem on a (4 H) x (4 W) grid, with its
+        first initial state u0 (None: zeros)."""
+        x = np.zeros((CNN.H, CNN.W, 40))
+        u0c = _opt(u0)
         lib().cnn_features(prob.nx, _c(prob.f), _c(prob.beta1), _c(prob.beta2),
-                           _c(prob.mask, np.uint8), prob.mu, prob.sigma, x)
+                           _c(prob.mask, np.uint8), prob.mu, prob.sigma, _ptr(u0c),
+                           CNN.scale(u0), x)
         return x
 
     @staticmethod
-    def target(u, sigma):
-        """[H][W][16]: sigma * u in the output layout."""
-        t = np.zeros((CNN.H, CNN.W, 16))
-        lib().cnn_target(u.shape[0], _c(u), sigma, t)
+    def target(u, u0=None):
+        """[H][W]: the cell means of (u - u0) / max |u0|."""
+        t = np.zeros((CNN.H, CNN.W))
+        u0c = _opt(u0)
+        lib().cnn_target(u.shape[0], _c(u), _ptr(u0c), CNN.scale(u0), t)
         return t
 
     @staticmethod
     def forward(params, x):
-        out = np.zeros((CNN.H, CNN.W, 16))
+        """The last layer's output [H][W][8]."""
+        out = np.zeros((CNN.H, CNN.W, 8))
         lib().cnn_forward(_c(params), _c(x), None, out)
         return out
 
@@ -318,11 +336,13 @@ class CNN:
         return loss, g
 
     @staticmethod
-    def unpack(y, sigma, interior):
-        """Initial state on the (4 H) x (4 W) grid from one output [H][W][16]."""
+    def upsample(y, interior, u0=None):
+        """Initial state u0 + max|u0| * bilinear(y[..., 0]) on the (4 H) x (4 W)
+        grid from one output [H][W][8]."""
         n = 4 * CNN.W
         u = np.zeros((4 * CNN.H, n))
-        lib().cnn_unpack(n, _c(y), sigma, _c(interior, np.uint8), u)
+        u0c = _opt(u0)
+        lib().cnn_upsample(n, _c(y), _ptr(u0c), CNN.scale(u0), _c(interior, np.uint8), u)
         return u
 
     @staticmethod

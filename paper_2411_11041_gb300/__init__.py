@@ -97,12 +97,12 @@ def lib():
         L.adr_cnn_destroy.restype = None
         L.adr_cnn_set_params.argtypes = [vp, fp]
         L.adr_cnn_get_params.argtypes = [vp, fp]
-        L.adr_cnn_features.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
-        L.adr_cnn_targets.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp]
+        L.adr_cnn_features.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.adr_cnn_targets.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
         L.adr_cnn_forward.argtypes = [vp, C.c_int, vp, vp]
         L.adr_cnn_loss_grad.argtypes = [vp, C.c_int, vp, vp, vp, dp]
         L.adr_cnn_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, dp]
-        L.adr_cnn_initial_state.argtypes = [vp, vp, vp]
+        L.adr_cnn_initial_state.argtypes = [vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -409,8 +409,15 @@ def adr_cnn_num_params():
     return int(lib().adr_cnn_num_params())
 
 
+def _cnn_params(params):
+    p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+    if p.size != adr_cnn_num_params():
+        raise ValueError(f"the network has {adr_cnn_num_params()} parameters, got {p.size}")
+    return p
+
+
 def adr_cnn_create(max_batch, params, stream=None):
-    p = np.ascontiguousarray(params, dtype=np.float32)
+    p = _cnn_params(params)
     h = C.c_void_p()
     _check(lib().adr_cnn_create(int(max_batch), p.ctypes.data_as(C.POINTER(C.c_float)),
                                 _stream_ptr(stream), C.byref(h)), "adr_cnn_create")
@@ -422,7 +429,7 @@ def adr_cnn_destroy(h):
 
 
 def adr_cnn_set_params(h, params):
-    p = np.ascontiguousarray(params, dtype=np.float32)
+    p = _cnn_params(params)
     _check(lib().adr_cnn_set_params(h, p.ctypes.data_as(C.POINTER(C.c_float))),
            "adr_cnn_set_params")
 
@@ -434,14 +441,14 @@ def adr_cnn_get_params(h):
     return p
 
 
-def adr_cnn_features(batch, n, f, beta1, beta2, mask, mu, sigma, x, stream=None):
+def adr_cnn_features(batch, n, f, beta1, beta2, mask, mu, sigma, u0, x, scale, stream=None):
     _check(lib().adr_cnn_features(int(batch), int(n), _ptr(f), _ptr(beta1), _ptr(beta2),
-                                  _ptr(mask), _ptr(mu), _ptr(sigma), _ptr(x),
-                                  _stream_ptr(stream)), "adr_cnn_features")
+                                  _ptr(mask), _ptr(mu), _ptr(sigma), _ptr(u0), _ptr(x),
+                                  _ptr(scale), _stream_ptr(stream)), "adr_cnn_features")
 
 
-def adr_cnn_targets(batch, n, u, sigma, t, stream=None):
-    _check(lib().adr_cnn_targets(int(batch), int(n), _ptr(u), _ptr(sigma), _ptr(t),
+def adr_cnn_targets(batch, n, u, u0, scale, t, stream=None):
+    _check(lib().adr_cnn_targets(int(batch), int(n), _ptr(u), _ptr(u0), _ptr(scale), _ptr(t),
                                  _stream_ptr(stream)), "adr_cnn_targets")
 
 
@@ -463,16 +470,20 @@ def adr_cnn_train_step(h, batch, x, t, lr, want_loss=True):
     return loss.value if want_loss else None
 
 
-def adr_cnn_initial_state(prob_handle, y, u_out):
-    _check(lib().adr_cnn_initial_state(prob_handle, _ptr(y), _ptr(u_out)),
+def adr_cnn_initial_state(prob_handle, y, u0, scale, u_out):
+    _check(lib().adr_cnn_initial_state(prob_handle, _ptr(y), _ptr(u0), _ptr(scale), _ptr(u_out)),
            "adr_cnn_initial_state")
 
 
 class Network:
     """The warm-start network on a CUDA device (adr_cnn_* calls).
 
-    Inputs are CUDA tensors: features ``x`` bfloat16 [B, 64, 64, 24], targets
-    and outputs float32 [B, 64, 64, 16]; parameters are a float32 host vector.
+    Inputs are CUDA tensors: features ``x`` bfloat16 [B, 64, 64, 40], targets
+    float32 [B, 64, 64], outputs float32 [B, 64, 64, 8] (channel 0 is the
+    prediction); parameters are a float32 host vector.  ``u0`` arguments are
+    the first initial states the network corrects (normally
+    ``Solver.paper_u0()``), stacked [B, 256, 256] float64, or None; ``scale``
+    is the per-problem scale features() returns (max |u0|).
     """
 
     HW = 64
@@ -498,24 +509,24 @@ class Network:
     def params(self, p):
         adr_cnn_set_params(self.h, p)
 
-    def features(self, f, beta1, beta2, mask, mu, sigma):
+    def features(self, f, beta1, beta2, mask, mu, sigma, u0=None):
         """Stacked device problems [B, 256, 256] (float64, mask uint8), mu and
-        sigma float64 [B] -> bfloat16 features [B, 64, 64, 24]."""
+        sigma float64 [B] -> (bfloat16 features [B, 64, 64, 40], scale [B])."""
         B, n = f.shape[0], f.shape[-1]
-        x = self.torch.empty((B, self.HW, self.HW, 24), dtype=self.torch.bfloat16,
+        x = self.torch.empty((B, self.HW, self.HW, 40), dtype=self.torch.bfloat16,
                              device=self.device)
-        adr_cnn_features(B, n, f, beta1, beta2, mask, mu, sigma, x)
-        return x
+        scale = self.torch.empty(B, dtype=self.torch.float64, device=self.device)
+        adr_cnn_features(B, n, f, beta1, beta2, mask, mu, sigma, u0, x, scale)
+        return x, scale
 
-    def targets(self, u, sigma):
+    def targets(self, u, scale, u0=None):
         B, n = u.shape[0], u.shape[-1]
-        t = self.torch.empty((B, self.HW, self.HW, 16), dtype=self.torch.float32,
-                             device=self.device)
-        adr_cnn_targets(B, n, u, sigma, t)
+        t = self.torch.empty((B, self.HW, self.HW), dtype=self.torch.float32, device=self.device)
+        adr_cnn_targets(B, n, u, u0, scale, t)
         return t
 
     def forward(self, x):
-        y = self.torch.empty((x.shape[0], self.HW, self.HW, 16), dtype=self.torch.float32,
+        y = self.torch.empty((x.shape[0], self.HW, self.HW, 8), dtype=self.torch.float32,
                              device=self.device)
         adr_cnn_forward(self.h, x.shape[0], x, y)
         return y
@@ -527,10 +538,11 @@ class Network:
     def train_step(self, x, t, lr, want_loss=True):
         return adr_cnn_train_step(self.h, x.shape[0], x, t, lr, want_loss)
 
-    def initial_state(self, solver, y):
-        """Solver grid initial state from one prediction y [64, 64, 16]."""
+    def initial_state(self, solver, y, u0=None, scale=None):
+        """Solver grid initial state u0 + s * bilinear(y[..., 0]) from one
+        prediction y [64, 64, 8]; scale: device tensor holding s (or None: 1)."""
         u = solver._grid()
-        adr_cnn_initial_state(solver.h, y, u)
+        adr_cnn_initial_state(solver.h, y, u0, scale, u)
         return u
 
     def close(self):

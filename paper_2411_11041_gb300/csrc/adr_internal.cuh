@@ -14,7 +14,7 @@ namespace adr {
 // Geometry readings of §6 (the paper leaves them open):
 constexpr double kSnapTol = 1e-9;   // index coordinates this close to an integer are snapped
 constexpr double kNodeTol = 1e-9;   // elements per curve: ceil(|L| / h_s - kNodeTol)
-constexpr int kTraceStepsPerH = 8;  // RK4 step h_s / 8 along traced curves
+constexpr int kTraceStepsPerH = 2;  // RK4 step h_s / 2 along traced curves
 constexpr int kBisectIters = 60;    // exit point of a traced curve
 
 enum NodeType : uint8_t { kOutside = 0, kDirichlet = 1, kInterior = 2 };
@@ -181,7 +181,8 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
 adr_status batch_dev_reset(BatchDev* b, cudaStream_t st);
 void batch_dev_destroy(BatchDev* b);
 adr_status launch_state_reset(Problem* p);
-// warm-start network (cnn.cu): prediction [64][64][16] -> initial state on the grid
-adr_status launch_cnn_unpack(Problem* p, const float* y, double* u);
+// warm-start network (cnn.cu): prediction [64][64][8] -> initial state on the grid
+adr_status launch_cnn_upsample(Problem* p, const float* y, const double* u0, const double* scale,
+                               double* u);
 
 }  // namespace adr

@@ -235,7 +235,8 @@ void adr_default_opts(adr_opts* o)
     o->init = ADR_INIT_ZERO;
 }
 
-adr_status adr_cnn_initial_state(adr_problem* h, const float* y, double* u_out)
+adr_status adr_cnn_initial_state(adr_problem* h, const float* y, const double* u0,
+                                 const double* scale, double* u_out)
 {
     if (!h || !y || !u_out) {
         set_error("adr_cnn_initial_state: NULL argument");
@@ -245,7 +246,7 @@ adr_status adr_cnn_initial_state(adr_problem* h, const float* y, double* u_out)
         set_error("adr_cnn_initial_state: the network predicts 256 x 256 grids");
         return ADR_EINVAL;
     }
-    return launch_cnn_unpack(&h->p, y, u_out);
+    return launch_cnn_upsample(&h->p, y, u0, scale, u_out);
 }
 
 const char* adr_last_error(void) { return g_err.c_str(); }

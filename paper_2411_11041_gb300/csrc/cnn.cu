@@ -3,11 +3,13 @@
 // feature / target / unpacking kernels.  See include/adr.h (adr_cnn_*).
 //
 // Network (the same definition as the FP64 reference): a 256 x 256 node grid
-// is read as 64 x 64 cells of 4 x 4 nodes; features NHWC, 24 channels (f at
-// the 16 nodes of the cell, block means of beta1, beta2, mu and sigma codes,
-// block mean of the mask, 3 zeros); eight 3 x 3 convolutions with zero
-// padding, channels 24 64 64 128 128 128 64 64 16, bias, ReLU after all but
-// the last; output channel 4 a + b = sigma * u at node (4 r + a, 4 c + b).
+// is read as 64 x 64 cells of 4 x 4 nodes, every problem scaled by
+// s = max |u0| of its first initial state u0; features NHWC, 40 channels (f
+// and u0 / s at the 16 nodes of the cell; cell means of beta1, beta2, mu and
+// sigma codes, cell mean of the mask, 3 zeros); eight 3 x 3 convolutions with
+// zero padding, channels 40 64 64 128 128 128 64 64 8, bias, ReLU after all
+// but the last; output channel 0 = the cell mean of (u - u0) / s, channels
+// 1..7 unused; initial state u0 + s * (bilinear interpolation of channel 0).
 // Parameters packed as W_0, b_0, W_1, b_1, ...; W_l[(tap * Cin + ci) * Cout + co].
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -22,12 +24,12 @@
 namespace {
 
 constexpr int kLayers = 8;
-constexpr int kCh[kLayers + 1] = {24, 64, 64, 128, 128, 128, 64, 64, 16};
+constexpr int kCh[kLayers + 1] = {40, 64, 64, 128, 128, 128, 64, 64, 8};
 constexpr int kDil[kLayers] = {1, 2, 4, 8, 16, 32, 1, 1};
 constexpr int kHW = 64;   // cells per side
 constexpr int kSub = 4;   // nodes per cell side
 constexpr int kN = kHW * kSub;
-constexpr int kCin = 24, kCout = kSub * kSub;
+constexpr int kCin = 40, kCout = 8;
 
 long param_offset(int l, bool bias)
 {
@@ -337,16 +339,17 @@ __global__ void k_relu_bwd(const bf16* dy, const bf16* y, long long n, bf16* out
     out[i] = __bfloat162float(y[i]) > 0.f ? dy[i] : __float2bfloat16(0.f);
 }
 
-// loss = 1/2 mean over all n outputs (y - t)^2, dY = (y - t) / n;
-// per-block partial sums of the loss (FP64)
-__global__ void k_loss(const float* y32, const float* t, long long n, bf16* dy, double* part)
+// loss = 1/2 mean over the M cells of (y[p][0] - t[p])^2, dY[p][0] = (y - t) / M,
+// other channels 0; per-block partial sums of the loss (FP64)
+__global__ void k_loss(const float* y32, int C, const float* t, long long M, bf16* dy, double* part)
 {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double e2 = 0.0;
-    if (i < n) {
-        float e = y32[i] - t[i];
+    if (p < M) {
+        float e = y32[p * C] - t[p];
         e2 = 0.5 * (double)e * (double)e;
-        dy[i] = __float2bfloat16(e / (float)n);
+        dy[p * C] = __float2bfloat16(e / (float)M);
+        for (int c = 1; c < C; ++c) dy[p * C + c] = __float2bfloat16(0.f);
     }
     __shared__ double sh[256];
     sh[threadIdx.x] = e2;
@@ -416,9 +419,34 @@ __global__ void k_refresh(const float* prm, long long n, LayerTab T, bf16* wb, b
     }
 }
 
-// features of a batch of 256 x 256 problems, one thread per cell
+// scale of every problem: max |u0| over its grid (1 when u0 is NULL or zero);
+// one block per problem, max of non-negative doubles through their bit patterns
+__global__ void k_scale(const double* u0, double* scale)
+{
+    const int b = blockIdx.x;
+    unsigned long long m = 0ull;
+    if (u0)
+        for (long long k = threadIdx.x; k < (long long)kN * kN; k += blockDim.x) {
+            unsigned long long v = (unsigned long long)__double_as_longlong(fabs(u0[(size_t)b * kN * kN + k]));
+            m = v > m ? v : m;
+        }
+    __shared__ unsigned long long sh[256];
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w && sh[threadIdx.x + w] > sh[threadIdx.x]) sh[threadIdx.x] = sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double v = __longlong_as_double((long long)sh[0]);
+        scale[b] = v > 0.0 ? v : 1.0;
+    }
+}
+
+// features of a batch of 256 x 256 problems, one thread per cell (u0 nullable)
 __global__ void k_features(int batch, const double* f, const double* b1, const double* b2,
-                           const uint8_t* mask, const double* mu, const double* sigma, bf16* x)
+                           const uint8_t* mask, const double* mu, const double* sigma,
+                           const double* u0, const double* scale, bf16* x)
 {
     long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= (long long)batch * kHW * kHW) return;
@@ -430,37 +458,60 @@ __global__ void k_features(int batch, const double* f, const double* b1, const d
         for (int j = 0; j < kSub; ++j) {
             size_t k = base + (size_t)(r * kSub + i) * kN + (c * kSub + j);
             o[i * kSub + j] = __float2bfloat16((float)f[k]);
+            o[16 + i * kSub + j] = __float2bfloat16(u0 ? (float)(u0[k] / scale[b]) : 0.f);
             s1 += b1[k];
             s2 += b2[k];
             sm += mask[k];
         }
     const double inv = 1.0 / (kSub * kSub);
-    o[16] = __float2bfloat16((float)(s1 * inv));
-    o[17] = __float2bfloat16((float)(s2 * inv));
-    o[18] = __float2bfloat16((float)((log10(mu[b]) + 2.5) / 1.5));
-    o[19] = __float2bfloat16((float)(sigma[b] - 1.0));
-    o[20] = __float2bfloat16((float)(sm * inv));
-    o[21] = o[22] = o[23] = __float2bfloat16(0.f);
+    o[32] = __float2bfloat16((float)(s1 * inv));
+    o[33] = __float2bfloat16((float)(s2 * inv));
+    o[34] = __float2bfloat16((float)((log10(mu[b]) + 2.5) / 1.5));
+    o[35] = __float2bfloat16((float)(sigma[b] - 1.0));
+    o[36] = __float2bfloat16((float)(sm * inv));
+    o[37] = o[38] = o[39] = __float2bfloat16(0.f);
 }
 
-// t[b][cell][4 a + b'] = sigma_b u_b at node (4 r + a, 4 c + b'), one thread per node
-__global__ void k_targets(int batch, const double* u, const double* sigma, float* t)
+// t[b][cell] = cell mean of (u - u0) / s_b, one thread per cell (u0 nullable)
+__global__ void k_targets(int batch, const double* u, const double* u0, const double* scale,
+                          float* t)
 {
     long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (q >= (long long)batch * kN * kN) return;
-    int b = (int)(q / (kN * kN)), rem = (int)(q % (kN * kN)), r = rem / kN, c = rem % kN;
-    size_t cell = ((size_t)b * kHW + r / kSub) * kHW + c / kSub;
-    t[cell * kCout + (r % kSub) * kSub + (c % kSub)] = (float)(sigma[b] * u[q]);
+    if (q >= (long long)batch * kHW * kHW) return;
+    int b = (int)(q / (kHW * kHW)), rem = (int)(q % (kHW * kHW)), r = rem / kHW, c = rem % kHW;
+    size_t base = (size_t)b * kN * kN;
+    double sum = 0.0;
+    for (int i = 0; i < kSub; ++i)
+        for (int j = 0; j < kSub; ++j) {
+            size_t k = base + (size_t)(r * kSub + i) * kN + (c * kSub + j);
+            sum += u[k] - (u0 ? u0[k] : 0.0);
+        }
+    t[q] = (float)(sum / (kSub * kSub) / scale[b]);
 }
 
-// u at node (r, c) = y[cell][sub] / sigma on interior nodes, 0 elsewhere
-__global__ void k_unpack(const float* y, double sigma, const uint8_t* ntype, double* u)
+// u = u0 + s * bilinear(y[..][0]) on the interior nodes, 0 elsewhere; cell
+// centres at node 4 k + 1.5, clamped at the outer half cells (u0 nullable)
+__global__ void k_upsample(const float* y, const double* u0, const double* scale,
+                           const uint8_t* ntype, double* u)
 {
     long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= (long long)kN * kN) return;
     int r = (int)(q / kN), c = (int)(q % kN);
-    float v = y[((size_t)(r / kSub) * kHW + c / kSub) * kCout + (r % kSub) * kSub + (c % kSub)];
-    u[q] = ntype[q] == adr::kInterior ? (double)v / sigma : 0.0;
+    if (ntype[q] != adr::kInterior) {
+        u[q] = 0.0;
+        return;
+    }
+    double fy = (r - (kSub - 1) * 0.5) / kSub, fx = (c - (kSub - 1) * 0.5) / kSub;
+    fy = fy < 0 ? 0 : (fy > kHW - 1 ? kHW - 1 : fy);
+    fx = fx < 0 ? 0 : (fx > kHW - 1 ? kHW - 1 : fx);
+    int y0 = (int)fy, x0 = (int)fx;
+    if (y0 > kHW - 2) y0 = kHW - 2;
+    if (x0 > kHW - 2) x0 = kHW - 2;
+    double ly = fy - y0, lx = fx - x0;
+    auto Y = [&](int rr, int cc) { return (double)y[((size_t)rr * kHW + cc) * kCout]; };
+    double v = (1 - ly) * ((1 - lx) * Y(y0, x0) + lx * Y(y0, x0 + 1)) +
+               ly * ((1 - lx) * Y(y0 + 1, x0) + lx * Y(y0 + 1, x0 + 1));
+    u[q] = (u0 ? u0[q] : 0.0) + (scale ? *scale : 1.0) * v;
 }
 
 }  // namespace
@@ -545,11 +596,10 @@ adr_status cnn_backward(adr_cnn* c, int batch, const bf16* x, const float* t)
 {
     cudaStream_t st = c->stream;
     const long long M = (long long)batch * c->hw * c->hw;
-    const long long nout = M * kCout;
-    int nb = (int)((nout + 255) / 256);
+    int nb = (int)((M + 255) / 256);
     bf16* dy = c->dA;
-    k_loss<<<nb, 256, 0, st>>>(c->y32, t, nout, dy, c->lpart);
-    k_sum_loss<<<1, 1, 0, st>>>(c->lpart, nb, nout, c->loss);
+    k_loss<<<nb, 256, 0, st>>>(c->y32, kCout, t, M, dy, c->lpart);
+    k_sum_loss<<<1, 1, 0, st>>>(c->lpart, nb, M, c->loss);
     for (int l = kLayers - 1; l >= 0; --l) {
         const int cin = kCh[l], cout = kCh[l + 1];
         const bf16* dyp = dy;
@@ -678,7 +728,7 @@ adr_status adr_cnn_create(int max_batch, const float* params, void* stream, adr_
         (s = cnn_alloc(c, &c->wb, c->P)) || (s = cnn_alloc(c, &c->wt, c->P)) ||
         (s = cnn_alloc(c, &c->y32, M * kCout)) || (s = cnn_alloc(c, &c->dA, M * 128)) ||
         (s = cnn_alloc(c, &c->dB, M * 128)) || (s = cnn_alloc(c, &c->dpre, M * 128)) ||
-        (s = cnn_alloc(c, &c->lpart, (M * kCout + 255) / 256 + 1)) || (s = cnn_alloc(c, &c->loss, 1)))
+        (s = cnn_alloc(c, &c->lpart, (M + 255) / 256 + 1)) || (s = cnn_alloc(c, &c->loss, 1)))
         return fail(s);
     for (int l = 0; l < kLayers - 1; ++l)
         if ((s = cnn_alloc(c, &c->act[l], M * kCh[l + 1]))) return fail(s);
@@ -690,30 +740,32 @@ adr_status adr_cnn_create(int max_batch, const float* params, void* stream, adr_
 }
 
 adr_status adr_cnn_features(int batch, int n, const double* f, const double* b1, const double* b2,
-                            const uint8_t* mask, const double* mu, const double* sigma, uint16_t* x,
-                            void* stream)
+                            const uint8_t* mask, const double* mu, const double* sigma,
+                            const double* u0, uint16_t* x, double* scale, void* stream)
 {
-    if (batch < 1 || n != kN || !f || !b1 || !b2 || !mask || !mu || !sigma || !x) {
+    if (batch < 1 || n != kN || !f || !b1 || !b2 || !mask || !mu || !sigma || !x || !scale) {
         adr::set_error("adr_cnn_features: bad arguments (the network reads 256 x 256 grids)");
         return ADR_EINVAL;
     }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_scale<<<batch, 256, 0, st>>>(u0, scale);
     long long q = (long long)batch * kHW * kHW;
-    k_features<<<(int)((q + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        batch, f, b1, b2, mask, mu, sigma, reinterpret_cast<bf16*>(x));
+    k_features<<<(int)((q + 255) / 256), 256, 0, st>>>(batch, f, b1, b2, mask, mu, sigma, u0, scale,
+                                                       reinterpret_cast<bf16*>(x));
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }
 
-adr_status adr_cnn_targets(int batch, int n, const double* u, const double* sigma, float* t,
-                           void* stream)
+adr_status adr_cnn_targets(int batch, int n, const double* u, const double* u0,
+                           const double* scale, float* t, void* stream)
 {
-    if (batch < 1 || n != kN || !u || !sigma || !t) {
+    if (batch < 1 || n != kN || !u || !scale || !t) {
         adr::set_error("adr_cnn_targets: bad arguments (the network reads 256 x 256 grids)");
         return ADR_EINVAL;
     }
-    long long q = (long long)batch * kN * kN;
-    k_targets<<<(int)((q + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, u, sigma,
-                                                                                    t);
+    long long q = (long long)batch * kHW * kHW;
+    k_targets<<<(int)((q + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, u, u0,
+                                                                                    scale, t);
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }
@@ -777,11 +829,12 @@ adr_status adr_cnn_train_step(adr_cnn* c, int batch, const uint16_t* x, const fl
 }  // extern "C"
 
 namespace adr {
-// unpack one prediction [64][64][16] to the handle's 256 x 256 grid
-adr_status launch_cnn_unpack(Problem* p, const float* y, double* u)
+// one prediction [64][64][8] around u0 to the handle's 256 x 256 grid
+adr_status launch_cnn_upsample(Problem* p, const float* y, const double* u0, const double* scale,
+                               double* u)
 {
     long long N = p->N;
-    k_unpack<<<(int)((N + 255) / 256), 256, 0, p->stream>>>(y, p->sigma, p->ntype, u);
+    k_upsample<<<(int)((N + 255) / 256), 256, 0, p->stream>>>(y, u0, scale, p->ntype, u);
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }

@@ -2,8 +2,13 @@
 of the network on the GPU, and initial states for new problems.
 
 The network (adr_cnn_* calls, ``Network``) maps a problem on a 256 x 256 grid
-to a prediction of sigma times its converged iterate at every node;
-``adr_cnn_initial_state`` turns that into u_0 for ADR_INIT_USER.  The solve itself is unchanged: it iterates from u_0 to the same
+and the paper's initial state u0 of it (eq. u0stationary, one steady sweep
+along the beta curves) to the cell means (4 x 4 nodes) of the correction
+u - u0, scaled by max |u0|, u the converged iterate; ``adr_cnn_initial_state``
+adds their bilinear interpolation to u0, giving u_0 for ADR_INIT_USER.  A
+network that predicts zero starts from the paper's u0.  Only the smooth part
+of the correction is predicted: smooth error modes are the slow ones of the
+split iteration, and the grid-scale rest of u - u0 costs few iterations.  The solve itself is unchanged: it iterates from u_0 to the same
 tolerance, so the answer meets the same test whatever the network predicts.
 
 Every array lives on the GPU; the host only draws the seeded problems and
@@ -45,16 +50,23 @@ def solver_opts(tol=1e-8, prec=0):
 
 @dataclasses.dataclass
 class Dataset:
-    x: object  # bf16 [N, 64, 64, 24]
-    t: object  # fp32 [N, 64, 64, 16]
+    x: object  # bf16 [N, 64, 64, 40]
+    t: object  # fp32 [N, 64, 64]
     iters: np.ndarray  # iterations of each generating solve (zero initial state)
+
+
+def paper_states(solvers):
+    """The paper's initial state (eq. u0stationary) of every solver, stacked."""
+    torch = _torch()
+    return torch.stack([s.paper_u0() for s in solvers])
 
 
 def generate(net: Network, probs, chunk=128, tol=1e-8, prec=0, device="cuda:0"):
     """Solve every problem with the batched solver from u_0 = 0 and keep the
-    network's features and targets: sigma times the iterate u_{j+1} the solve
-    converged to (its fixed point; for theta = 1/2 the reported solution is the
-    midpoint of the last step, which differs from it by the splitting error)."""
+    network's features (with the paper's u0) and targets: the cell means of
+    u_{j+1} - u0 over max |u0|, u_{j+1} the iterate the solve converged to (its
+    fixed point; for theta = 1/2 the reported solution is the midpoint of the
+    last step, which differs from it by the splitting error)."""
     torch = _torch()
     xs, ts, its = [], [], []
     for k in range(0, len(probs), chunk):
@@ -65,13 +77,15 @@ def generate(net: Network, probs, chunk=128, tol=1e-8, prec=0, device="cuda:0"):
         if st != ADR_OK:
             raise RuntimeError("a generating solve did not converge")
         f, b1, b2, m, mu, sg = stack(part, device)
-        xs.append(net.features(f, b1, b2, m, mu, sg))
-        ts.append(net.targets(torch.stack(its_u), sg))
+        u0 = paper_states(solvers)
+        x, scale = net.features(f, b1, b2, m, mu, sg, u0)
+        xs.append(x)
+        ts.append(net.targets(torch.stack(its_u), scale, u0))
         its += [s["iters"] for s in stats]
         b.close()
         for s in solvers:
             s.close()
-        del outs, its_u, f, b1, b2, m
+        del outs, its_u, f, b1, b2, m, u0
     return Dataset(torch.cat(xs), torch.cat(ts), np.asarray(its))
 
 
@@ -96,10 +110,13 @@ def train(net: Network, data: Dataset, steps, batch=32, lr=1e-3, lr_final=1e-4, 
     return losses
 
 
-def initial_states(net: Network, solvers, x):
-    """u_0 of every solver from the features x (one network batch)."""
+def initial_states(net: Network, solvers, fields):
+    """u_0 of every solver: the paper's state, the features, one network
+    batch, and the corrected states.  fields = stack(problems)."""
+    u0 = paper_states(solvers)
+    x, scale = net.features(*fields, u0)
     y = net.forward(x)
-    return [net.initial_state(s, y[i]) for i, s in enumerate(solvers)]
+    return [net.initial_state(s, y[i], u0[i], scale[i:i + 1]) for i, s in enumerate(solvers)]
 
 
 def evaluate(net: Network, probs, tol=1e-8, prec=0, device="cuda:0", chunk=128, sequential=False):
@@ -123,8 +140,7 @@ def evaluate(net: Network, probs, tol=1e-8, prec=0, device="cuda:0", chunk=128, 
         _, sz, stz = bz.solve()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        x = net.features(f, b1, b2, m, mu, sg)
-        u0 = initial_states(net, learned, x)
+        u0 = initial_states(net, learned, (f, b1, b2, m, mu, sg))
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         _, sl, stl = bl.solve(u0)

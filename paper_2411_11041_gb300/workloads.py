@@ -172,7 +172,7 @@ def random_field(rng: np.random.Generator, nx: int, ny: int, smooth=True):
 
 
 # warm-start network: layer widths (input features ... output channels)
-CNN_CHANNELS = (24, 64, 64, 128, 128, 128, 64, 64, 16)
+CNN_CHANNELS = (40, 64, 64, 128, 128, 128, 64, 64, 8)
 
 
 def cnn_init_params(seed=SEED_BASE + 6, last_scale=0.1):
@@ -188,3 +188,11 @@ def cnn_init_params(seed=SEED_BASE + 6, last_scale=0.1):
         parts.append(rng.normal(0.0, std, n))
         parts.append(np.zeros(ch[l + 1]))
     return np.concatenate(parts).astype(np.float32)
+
+
+def data2d(n=61):
+    """The paper's numerical experiment (eq. Data2D): unit square, mu = 1,
+    beta = (-5(y+1), 5(x+1)), sigma = 1, f = 5, on n x n nodes."""
+    X, Y = node_coords(n, n)
+    return Problem(n, n, 1.0, 1.0, -5.0 * (Y + 1.0), 5.0 * (X + 1.0), np.full((n, n), 5.0),
+                   make_mask("square", n, n), name=f"data2d{n}")

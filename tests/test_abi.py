@@ -62,3 +62,17 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(libadr):
     st = P.lib().adr_create(ctypes.byref(g), dummy, 1.0, 1.0, dummy, dummy, dummy, ctypes.byref(o),
                             None, ctypes.byref(h))
     assert st == P.ADR_EINVAL and b"theta" in P.lib().adr_last_error()
+
+
+def test_network_parameter_layout_without_gpu(libadr):
+    """The seeded initial parameters have the library's parameter count, and
+    the binding refuses a vector of another length before any copy."""
+    import numpy as np
+
+    import paper_2411_11041_gb300 as P
+    from paper_2411_11041_gb300 import workloads as W
+    ch = W.CNN_CHANNELS
+    assert P.adr_cnn_num_params() == sum(9 * a * b + b for a, b in zip(ch[:-1], ch[1:]))
+    assert W.cnn_init_params().size == P.adr_cnn_num_params()
+    with pytest.raises(ValueError):
+        P.adr_cnn_create(1, np.zeros(10, np.float32))

@@ -12,8 +12,8 @@ CNN = O.CNN
 
 def _batch(n=2, seed=0, hw=64):
     rng = np.random.default_rng(seed)
-    xs = rng.normal(size=(n, hw, hw, 24)) * 0.5
-    ts = rng.normal(size=(n, hw, hw, 16))
+    xs = rng.normal(size=(n, hw, hw, 40)) * 0.5
+    ts = rng.normal(size=(n, hw, hw))
     return xs, ts
 
 
@@ -26,7 +26,7 @@ def small_grid():
 
 def test_parameter_count_is_about_half_a_million():
     ch = CNN.channels()
-    assert ch[0] == 24 and ch[-1] == 16 and CNN.dilations() == [1, 2, 4, 8, 16, 32, 1, 1]
+    assert ch[0] == 40 and ch[-1] == 8 and CNN.dilations() == [1, 2, 4, 8, 16, 32, 1, 1]
     n = CNN.num_params()
     assert n == sum(9 * a * b + b for a, b in zip(ch[:-1], ch[1:]))
     assert 450_000 < n < 600_000
@@ -120,19 +120,35 @@ def test_dilated_layer_reads_the_taps_it_should():
         np.testing.assert_allclose(out, ref, rtol=0, atol=0)
 
 
-def test_features_target_and_unpacking():
+def test_features_target_and_upsampling():
     p = W.random_problem(np.random.default_rng(2), 256, mask="disc")
-    x = CNN.features(p)
+    u0 = np.random.default_rng(5).normal(size=(256, 256))
+    s0 = np.abs(u0).max()
+    assert CNN.scale(u0) == s0 and CNN.scale(None) == 1.0 and CNN.scale(0 * u0) == 1.0
+    x = CNN.features(p, u0)
     blocks = lambda a: a.reshape(64, 4, 64, 4).transpose(0, 2, 1, 3)  # [r][c][a][b]
     np.testing.assert_array_equal(x[..., :16], blocks(p.f).reshape(64, 64, 16))
-    np.testing.assert_allclose(x[..., 16], blocks(p.beta1).mean(axis=(2, 3)), rtol=1e-14)
-    np.testing.assert_allclose(x[..., 17], blocks(p.beta2).mean(axis=(2, 3)), rtol=1e-14)
-    assert np.allclose(x[..., 18], (np.log10(p.mu) + 2.5) / 1.5) and np.allclose(x[..., 19], p.sigma - 1)
-    np.testing.assert_allclose(x[..., 20], blocks(p.mask.astype(float)).mean(axis=(2, 3)))
-    assert np.all(x[..., 21:] == 0)
+    np.testing.assert_array_equal(x[..., 16:32], blocks(u0 / s0).reshape(64, 64, 16))
+    np.testing.assert_allclose(x[..., 32], blocks(p.beta1).mean(axis=(2, 3)), rtol=1e-14)
+    np.testing.assert_allclose(x[..., 33], blocks(p.beta2).mean(axis=(2, 3)), rtol=1e-14)
+    assert np.allclose(x[..., 34], (np.log10(p.mu) + 2.5) / 1.5) and np.allclose(x[..., 35], p.sigma - 1)
+    np.testing.assert_allclose(x[..., 36], blocks(p.mask.astype(float)).mean(axis=(2, 3)))
+    assert np.all(x[..., 37:] == 0)
+    assert np.all(CNN.features(p)[..., 16:32] == 0)  # no first state: zeros
+    # target: cell means of (u - u0) / s
     u = np.random.default_rng(3).normal(size=(256, 256))
-    t = CNN.target(u, 2.0)
-    np.testing.assert_array_equal(t, 2.0 * blocks(u).reshape(64, 64, 16))
+    np.testing.assert_allclose(CNN.target(u, u0), blocks(u - u0).mean(axis=(2, 3)) / s0,
+                               rtol=1e-12, atol=1e-14)
+    # a bilinear correction d: its cell means are its values at the cell
+    # centres, and the bilinear interpolation through them gives d back
+    # inside (the outer half cells are clamped)
+    X, Y = W.node_coords(256, 256)
+    d = 0.3 + 2.0 * X - 1.5 * Y + 0.7 * X * Y
+    t = CNN.target(u0 + d, u0)
+    y = np.zeros((64, 64, 8))
+    y[..., 0] = t
+    y[..., 1:] = 123.0  # channels 1..7 are not read
     inter = (np.random.default_rng(4).random((256, 256)) < 0.7).astype(np.uint8)
-    back = CNN.unpack(t, 2.0, inter)
-    np.testing.assert_array_equal(back, np.where(inter == 1, u, 0.0))
+    back = CNN.upsample(y, inter, u0)
+    ref = np.where(inter == 1, u0 + d, 0.0)
+    assert np.abs(back - ref)[2:-2, 2:-2].max() < 1e-12

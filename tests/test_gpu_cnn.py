@@ -46,8 +46,8 @@ def _stack(probs, torch):
 
 def _rand_inputs(batch, seed, torch):
     rng = np.random.default_rng(seed)
-    x = (rng.normal(size=(batch, 64, 64, 24)) * 0.5).astype(np.float32)
-    t = rng.normal(size=(batch, 64, 64, 16)).astype(np.float32) * 0.3
+    x = (rng.normal(size=(batch, 64, 64, 40)) * 0.5).astype(np.float32)
+    t = rng.normal(size=(batch, 64, 64)).astype(np.float32) * 0.3
     xd = torch.as_tensor(x).to("cuda:0").to(torch.bfloat16)
     td = torch.as_tensor(t).to("cuda:0")
     return xd, td, xd.float().double().cpu().numpy(), t.astype(np.float64)
@@ -63,13 +63,20 @@ def test_features_and_targets_match_reference(torch_cuda):
     probs = W.learned(3, n=256, seed=99)
     net = Network(4)
     f, b1, b2, m, mu, sg = _stack(probs, torch)
-    x = net.features(f, b1, b2, m, mu, sg).float().cpu().numpy()
+    u0 = torch.as_tensor(np.stack([np.cos(2 * p.f) * p.beta2 for p in probs]), device="cuda:0")
+    xg, scale = net.features(f, b1, b2, m, mu, sg, u0)
+    x = xg.float().cpu().numpy()
+    x_none = net.features(f, b1, b2, m, mu, sg)[0].float().cpu().numpy()
     u = torch.as_tensor(np.stack([np.sin(3 * p.f) + p.beta1 for p in probs]), device="cuda:0")
-    t = net.targets(u, sg).cpu().numpy()
+    t = net.targets(u, scale, u0).cpu().numpy()
     for b, p in enumerate(probs):
-        ref = CNN.features(p)
+        u0b = u0[b].cpu().numpy()
+        assert scale[b].item() == CNN.scale(u0b)
+        ref = CNN.features(p, u0b)
         assert np.all(np.abs(x[b] - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-30)
-        tr = CNN.target(u[b].cpu().numpy(), p.sigma)
+        ref0 = CNN.features(p)
+        assert np.all(np.abs(x_none[b] - ref0) <= 2.0 ** -8 * np.abs(ref0) + 1e-30)
+        tr = CNN.target(u[b].cpu().numpy(), u0b)
         assert np.abs(t[b] - tr).max() <= 1e-6 * np.abs(tr).max()
 
 
@@ -77,9 +84,9 @@ def test_features_reject_grids_that_are_not_multiples_of_64(torch_cuda):
     torch = torch_cuda
     from paper_2411_11041_gb300 import AdrError, adr_cnn_features
     z = torch.zeros((1, 96, 96), dtype=torch.float64, device="cuda:0")
-    x = torch.zeros((1, 64, 64, 8), dtype=torch.bfloat16, device="cuda:0")
+    x = torch.zeros((1, 64, 64, 40), dtype=torch.bfloat16, device="cuda:0")
     with pytest.raises(AdrError, match="EINVAL"):
-        adr_cnn_features(1, 96, z, z, z, z.to(torch.uint8), z[0, 0], z[0, 0], x)
+        adr_cnn_features(1, 96, z, z, z, z.to(torch.uint8), z[0, 0], z[0, 0], None, x, z[0, 0])
 
 
 def test_forward_matches_reference(torch_cuda):
@@ -137,7 +144,7 @@ def _bf16_model_grad(p, x, t, torch):
         h = F.conv2d(h, Ws[l], bs[l], padding=dil[l], dilation=dil[l])
         if l < CNN.LAYERS - 1:
             h = R.apply(torch.relu(h))
-    loss = 0.5 * ((h - torch.as_tensor(t).permute(0, 3, 1, 2)) ** 2).mean()
+    loss = 0.5 * ((h[:, 0] - torch.as_tensor(t)) ** 2).mean()
     loss.backward()
     g = []
     for l in range(CNN.LAYERS):
@@ -204,7 +211,7 @@ def test_training_reduces_the_loss(torch_cuda):
     from paper_2411_11041_gb300 import Network
     net = Network(8, W.cnn_init_params(8))
     x, _, _, _ = _rand_inputs(8, 4, torch)
-    t = (0.5 * x[..., :16].float()).contiguous()  # a target the network can represent
+    t = (0.5 * x[..., 16].float()).contiguous()  # a target the network can represent
     l0 = net.train_step(x, t, 1e-3)
     for _ in range(200):
         l1 = net.train_step(x, t, 1e-3)
@@ -213,18 +220,25 @@ def test_training_reduces_the_loss(torch_cuda):
     assert l1 < 0.75 * l0, (l0, l1)
 
 
-def test_initial_state_unpacks_like_the_reference(torch_cuda):
+def test_initial_state_upsamples_like_the_reference(torch_cuda):
     torch = torch_cuda
     from paper_2411_11041_gb300 import Network, Solver
     prob = W.learned(1, n=256, seed=98)[0]
     prob.mask = W.make_mask("disc", 256, 256)
     s = Solver(prob)
     rng = np.random.default_rng(9)
-    y = rng.normal(size=(64, 64, 16)).astype(np.float32)
+    y = rng.normal(size=(64, 64, 8)).astype(np.float32)
+    u0 = rng.normal(size=(256, 256))
     net = Network(1)
-    u = net.initial_state(s, torch.as_tensor(y, device="cuda:0")).cpu().numpy()
-    ref = CNN.unpack(y.astype(np.float64), prob.sigma, O.Oracle(prob).interior())
-    np.testing.assert_array_equal(u, ref)
+    yd = torch.as_tensor(y, device="cuda:0")
+    inter = O.Oracle(prob).interior()
+    sc = torch.tensor([CNN.scale(u0)], dtype=torch.float64, device="cuda:0")
+    u = net.initial_state(s, yd, torch.as_tensor(u0, device="cuda:0"), sc).cpu().numpy()
+    ref = CNN.upsample(y.astype(np.float64), inter, u0)
+    assert np.abs(u - ref).max() <= 1e-13 * np.abs(ref).max()
+    u = net.initial_state(s, yd).cpu().numpy()
+    ref = CNN.upsample(y.astype(np.float64), inter)
+    assert np.abs(u - ref).max() <= 1e-13 * np.abs(ref).max()
     s.close()
 
 
@@ -233,7 +247,7 @@ def test_initial_state_rejects_other_grids(torch_cuda):
     from paper_2411_11041_gb300 import AdrError, Network, Solver
     s = Solver(W.manufactured(n=64))
     net = Network(1)
-    y = torch.zeros((64, 64, 16), dtype=torch.float32, device="cuda:0")
+    y = torch.zeros((64, 64, 8), dtype=torch.float32, device="cuda:0")
     with pytest.raises(AdrError, match="EINVAL"):
         net.initial_state(s, y)
     s.close()

@@ -41,12 +41,6 @@ def _const(n, beta, mask="square", mu=0.1, sigma=1.0, nx=None, seed=0):
     return W.Problem(nx, n, mu, sigma, np.full((n, nx), beta[0]), np.full((n, nx), beta[1]), f, m)
 
 
-def _data2d(n):
-    X, Y = W.node_coords(n, n)
-    return W.Problem(n, n, 1.0, 1.0, -5.0 * (Y + 1.0), 5.0 * (X + 1.0), np.full((n, n), 5.0),
-                     W.make_mask("square", n, n), name="data2d")
-
-
 PROBLEMS = {
     "manufactured33": lambda: W.manufactured(n=33),
     "aligned17": lambda: W.manufactured(n=17, beta=(1.0, 0.0)),
@@ -56,7 +50,7 @@ PROBLEMS = {
     "steep": lambda: _const(64, (0.02, 1.0), mu=1e-4),
     "long_lines": lambda: _const(300, (1.0, 0.37), mu=1e-2),
     "sheared65": lambda: W.sheared(n=65),
-    "data2d": lambda: _data2d(33),
+    "data2d": lambda: W.data2d(33),
     "tiny3": lambda: _const(3, (1.0, 0.5)),
 }
 
@@ -248,3 +242,16 @@ def test_diverging_iteration_is_reported(torch_cuda):
     assert st == ADR_ENOCONV and ost == O.ENOCONV
     assert b"diverged" in lib().adr_last_error()
     assert abs(stats["iters"] - it) <= 2 and stats["iters"] < 2000
+
+
+def test_data2d_paper_procedure_matches_oracle(torch_cuda):
+    """eq. Data2D as the paper runs it: 50 steps of dt = 0.001 from the state
+    of eq. u0stationary (61 x 61 nodes)."""
+    from paper_2411_11041_gb300 import ADR_INIT_PAPER_U0, ADR_OK, Solver
+    p = W.data2d(61)
+    s = Solver(p, tol=0.0, max_iter=50, dt=1e-3, init=ADR_INIT_PAPER_U0)
+    u, uit, stats, st = s.solve_stationary(want_iter=True)
+    ref, refit, it, _, ost = O.Oracle(p).solve_stationary(theta=0.5, dt=1e-3, tol=0.0, max_iter=50,
+                                                          init=2)
+    assert st == ADR_OK and ost == O.OK and stats["iters"] == it == 50
+    assert relerr(u, ref) <= TOL64 and relerr(uit, refit) <= TOL64

@@ -1,7 +1,8 @@
 """What the trained warm-start network gains: a network trained on the GPU on
 solutions the method generated must cut the iterations to the same tolerance
-on held-out problems, and the answers from its initial states must be the
-answers from u_0 = 0 (the iteration stays the judge of convergence)."""
+on held-out problems (against u_0 = 0; against the paper's own initial state
+it must not lose more than 5 %), and the answers from its initial states must
+be the answers from u_0 = 0 (the iteration stays the judge of convergence)."""
 import numpy as np
 import pytest
 
@@ -36,11 +37,19 @@ def test_trained_network_reduces_iterations_on_held_out_problems(torch_cuda):
     res = WS.evaluate(net, hold)
     z, l = res["zero_iters"], res["learned_iters"]
     assert l.sum() < 0.97 * z.sum(), (l.sum(), z.sum())
+    # against the paper's own initial state, which the network corrects: the
+    # split iteration's slow modes are the smooth ones, so the network's
+    # (smooth) residual error must be far below 1 % of u to gain much on it;
+    # the trained network matches it rather than beats it
+    ps = [Solver(p, init=2, **WS.solver_opts()) for p in hold]
+    _, sp, stp = Batch(ps).solve()
+    assert stp == ADR_OK
+    paper = sum(x["iters"] for x in sp)
+    assert l.sum() <= 1.05 * paper, (l.sum(), paper)
     # same answers: both runs stop at a relative update of 1e-8
     zs = [Solver(p, **WS.solver_opts()) for p in hold[:8]]
     ls = [Solver(p, init=1, **WS.solver_opts()) for p in hold[:8]]
-    f, b1, b2, m, mu, sg = WS.stack(hold[:8])
-    u0 = WS.initial_states(net, ls, net.features(f, b1, b2, m, mu, sg))
+    u0 = WS.initial_states(net, ls, WS.stack(hold[:8]))
     uz, _, stz = Batch(zs).solve()
     ul, _, stl = Batch(ls).solve(u0)
     assert stz == ADR_OK and stl == ADR_OK
