@@ -50,6 +50,11 @@ KERNELS = ["curve solve B", "curve->grid map B", "curve solve G", "curve->grid m
 #   maps: crossings 16 + t 32 + w 16 + v 8 + type 1 + out 8 (+ u_j 8 for the norms) B
 BYTES_PER_UNIT = [108.0, 81.0, 76.0, 89.0]
 FLOPS_PER_UNIT = [26.0, 16.0, 24.0, 20.0]
+# DRAM bytes per launch (read + write, summed over the block-size launches of a
+# curve solve) from one ncu capture of the 2048^2 sheared workload
+# (profiles/dram_traffic_sweep_sheared2048_fp64.md); valid while these kernels
+# are unchanged
+NCU_TRAFFIC_SHEARED2048 = [530.5e6, 402.7e6, 423.7e6, 443.4e6]
 
 
 def parse():
@@ -304,6 +309,10 @@ def run_ours(args):
                 "traffic": None, "peak_kind": hbm_kind}
     roof.update({"kernel": KERNELS[k], "kernel_ms": kms[k], "units_per_launch": units[k],
                  "all_kernels_ms": dict(zip(KERNELS, kms))})
+    if args.n == 2048:
+        roof["traffic"] = NCU_TRAFFIC_SHEARED2048[k]
+        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture"
+        roof["algorithmic_bytes"] = BYTES_PER_UNIT[k] * units[k]
     launches = int(sum(5 * it + 3 for it in iters))
     # the other precision mode on the same workload: time to tol and agreement
     other = {}
