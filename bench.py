@@ -44,17 +44,19 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # every array the kernel must touch once; flops count the kernel's FP64
 # arithmetic per unit (fma = 2, divide = 1).
 KERNELS = ["curve solve B", "curve->grid map B", "curve solve G", "curve->grid map G"]
-#   curve solve B: cell 4 + lambda 16 + F 8 + S row 24 + factors 32 + rp 8 + v 8 + u 8 B;
-#                  gather 9 + rhs 6 + elimination 3 + upward 2 + back 4 + update 2 flop
-#   curve solve G: the same without F and S rows (S = mu K is constant per curve)
-#   maps: crossings 16 + t 32 + w 16 + v 8 + type 1 + out 8 (+ u_j 8 for the norms) B
-BYTES_PER_UNIT = [108.0, 81.0, 76.0, 89.0]
-FLOPS_PER_UNIT = [26.0, 16.0, 24.0, 20.0]
+#   curve solve B: cell 4 + corner weights 32 + F 8 + S rows 24 + factors 32 + v 8 + u 8 B
+#                  (F and S carry the row factor ip); gather 7 (1 mul + 3 fma) + rhs 6
+#                  (3 fma) + elimination 2 + upward 2 + back 4 + update 2 flop
+#   curve solve G: cell 4 + corner weights 32 + row coefficient 8 + factors 32 + v 8 + u 8 B;
+#                  gather 7 + rhs 4 + elimination 2 + upward 2 + back 4 + update 2 flop
+#   maps: crossings 16 + coefficients 64 + type 1 + out 8 (+ u_j 8 for the norms) B, 8 fma
+BYTES_PER_UNIT = [116.0, 81.0, 92.0, 89.0]
+FLOPS_PER_UNIT = [23.0, 16.0, 21.0, 20.0]
 # DRAM bytes per launch (read + write, summed over the block-size launches of a
 # curve solve) from one ncu capture of the 2048^2 sheared workload
-# (profiles/dram_traffic_sweep_sheared2048_fp64.md); valid while these kernels
-# are unchanged
-NCU_TRAFFIC_SHEARED2048 = [530.5e6, 402.7e6, 423.7e6, 443.4e6]
+# (profiles/dram_traffic_sweep_sheared2048_fp64.md); None where the kernel has
+# changed since the capture
+NCU_TRAFFIC_SHEARED2048 = [None, 402.7e6, None, 443.4e6]
 
 
 def parse():
@@ -309,7 +311,7 @@ def run_ours(args):
                 "traffic": None, "peak_kind": hbm_kind}
     roof.update({"kernel": KERNELS[k], "kernel_ms": kms[k], "units_per_launch": units[k],
                  "all_kernels_ms": dict(zip(KERNELS, kms))})
-    if args.n == 2048:
+    if args.n == 2048 and NCU_TRAFFIC_SHEARED2048[k] is not None:
         roof["traffic"] = NCU_TRAFFIC_SHEARED2048[k]
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture"
         roof["algorithmic_bytes"] = BYTES_PER_UNIT[k] * units[k]

@@ -61,8 +61,8 @@ struct Family {
     int n_slots = 0;
     int* soff = nullptr;      // [n_lines+1]
     int* gcell = nullptr;     // [n_slots] bilinear cell r*nx + i of the row's node
-    double* glx = nullptr;    // [n_slots] bilinear weights lambda_x, lambda_y
-    double* gly = nullptr;
+    double* gw = nullptr;     // [4 n_slots] bilinear corner weights (1-lx)(1-ly), lx(1-ly),
+                              // (1-lx)ly, lx ly
     double* Fl = nullptr;     // [n_slots] load F = M f (B)
     double* srow = nullptr;   // [3*n_slots] S sub/diag/super (B)
     double* fac = nullptr;    // [4*n_slots] elimination factors cp, vp, ip, lp

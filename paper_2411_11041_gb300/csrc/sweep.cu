@@ -54,16 +54,17 @@ struct CurveArgs {
     const int* soff;       // curve -> first slot
     const double* h;
     int* gcell;            // per slot: bilinear cell r*nx + i of the row's node
-    double* glx;           // per slot: lambda_x, lambda_y of the row's node
-    double* gly;
+    double* gw;            // 4 planes per slot: the cell's corner weights of the row's node
     const double* bnorm;   // per node
     const double* fval;    // per node
     const double* xi;      // per node (setup of the gather descriptors)
     const double* eta;
     const double* fextra;  // load kernel only
     double fx_scale;
-    double* Fl;            // per slot: load F (B)
-    double* srow;          // 3 planes per slot: S sub/diag/super (B)
+    double* Fl;            // per slot: load F (B); times the row's pivot ip when scaled
+    double* srow;          // 3 planes per slot: S sub/diag/super (B), times ip when scaled;
+                           // G when scaled: one plane, (mu / h) ip
+    int scaled;            // FP64 mode: F and S rows carry the factor ip of their row
     double* fac;           // 4 planes per slot: cp, vp, ip, lp
     float* fac32;          // the same factors rounded to FP32 (reduced-precision mode)
     const double* lanecs[3];   // reduced-system constants of the item sets (batched launches)
@@ -119,6 +120,18 @@ __device__ __forceinline__ void item_chunk(const CurveArgs& a, const int* item_T
     item_chunk_of(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC, b);
 }
 
+// bilinear gather at a row's node from its cell and corner weights (slot sl)
+__device__ __forceinline__ double gather_w(const double* __restrict__ u, int nx, int cell,
+                                           const double* __restrict__ w, size_t NS, int sl)
+{
+    const double* r0 = u + cell;
+    double p11 = __ldg(r0), p12 = __ldg(r0 + 1), p21 = __ldg(r0 + nx), p22 = __ldg(r0 + nx + 1);
+    double v = __ldg(w + sl) * p11;
+    v = fma(__ldg(w + NS + sl), p12, v);
+    v = fma(__ldg(w + 2 * NS + sl), p21, v);
+    return fma(__ldg(w + 3 * NS + sl), p22, v);
+}
+
 __device__ __forceinline__ double gather_at(const double* __restrict__ u, int nx, int cell,
                                             double lx, double ly)
 {
@@ -143,9 +156,13 @@ __global__ void __launch_bounds__(BS) k_curve_gdesc(CurveArgs a, const int* item
         i = i > a.nx - 2 ? a.nx - 2 : (i < 0 ? 0 : i);
         r = r > a.ny - 2 ? a.ny - 2 : (r < 0 ? 0 : r);
         size_t sl = b.so + (size_t)j * b.T + b.lt;
+        const size_t NS = a.n_slots;
+        const double lx = x - i, ly = y - r;
         a.gcell[sl] = r * a.nx + i;
-        a.glx[sl] = x - i;
-        a.gly[sl] = y - r;
+        a.gw[sl] = (1.0 - lx) * (1.0 - ly);
+        a.gw[NS + sl] = lx * (1.0 - ly);
+        a.gw[2 * NS + sl] = (1.0 - lx) * ly;
+        a.gw[3 * NS + sl] = lx * ly;
     }
 }
 
@@ -173,7 +190,9 @@ __global__ void __launch_bounds__(BS) k_curve_load(CurveArgs a, const int* item_
     double f0 = fat(b.s), f1 = fat(b.s + 1);
     for (int j = 0; j < b.cnt; ++j) {
         double f2 = fat(b.s + j + 2);
-        a.Fl[b.so + (size_t)j * b.T + b.lt] = Mo * (f0 + 4.0 * f1 + f2);
+        const size_t sl = b.so + (size_t)j * b.T + b.lt;
+        double F = Mo * (f0 + 4.0 * f1 + f2);
+        a.Fl[sl] = a.scaled ? F * a.fac[2 * a.n_slots + sl] : F;  // row factor ip (k_curve_prep)
         f0 = f1;
         f1 = f2;
     }
@@ -243,6 +262,15 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
             a.fac[NS + sl] = vp;
             a.fac[2 * NS + sl] = ip;
             a.fac[3 * NS + sl] = lp;
+            if (a.scaled) {  // fold the row factor into the right-hand side's rows
+                if (FAM == 0) {
+                    a.srow[sl] = Ssub * ip;
+                    a.srow[NS + sl] = Sdia * ip;
+                    a.srow[2 * NS + sl] = Ssup * ip;
+                } else {
+                    a.srow[sl] = (a.mu / h) * ip;
+                }
+            }
             if (a.fac32) {
                 a.fac32[sl] = (float)cp;
                 a.fac32[NS + sl] = (float)vp;
@@ -317,16 +345,13 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
     const int base = b.base, n = b.n, s = b.s, cnt = b.cnt;
     const size_t NS = a.n_slots, so = b.so;
     const bool paper = a.paper != 0;
-    auto uslot = [&](int sl) -> double {
-        return gather_at(u, a.nx, __ldg(a.gcell + sl), __ldg(a.glx + sl), __ldg(a.gly + sl));
-    };
+    auto uslot = [&](int sl) -> double { return gather_w(u, a.nx, __ldg(a.gcell + sl), a.gw, NS, sl); };
     double rp[kCmax], ur[kCmax];
     double rpp = 0.0;
     const int so32 = (int)so;
     const double* __restrict__ cpP = a.fac;
     const double* __restrict__ vpP = a.fac + NS;
     if (cnt > 0) {
-        const double muh = a.mu / a.h[b.line];
         // node s (row s-1: the previous thread's last row) and node s+1 (own row 0)
         double u0 = (paper || s == 0) ? 0.0 : uslot(so32 + (b.c - 1) * T + (lt - 1));
         double u1 = paper ? 0.0 : uslot(so32 + lt);
@@ -339,13 +364,16 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
                 else if (j + 1 < cnt) u2 = uslot(sl + T);
                 else if (s + cnt < b.m) u2 = uslot(so32 + lt + 1);  // next thread's row 0
                 else u2 = 0.0;                                      // the curve's end node
+                // right-hand side times the row's factor ip (folded into F and S)
                 double r;
-                if (FAM == 0)
-                    r = __ldg(a.Fl + sl) - (__ldg(a.srow + sl) * u0 + __ldg(a.srow + NS + sl) * u1 +
-                                            __ldg(a.srow + 2 * NS + sl) * u2);
-                else
-                    r = muh * ((u0 + u2) - 2.0 * u1);
-                rpp = r * __ldg(a.fac + 2 * NS + sl) - __ldg(a.fac + 3 * NS + sl) * rpp;
+                if (FAM == 0) {
+                    r = fma(-__ldg(a.srow + sl), u0, __ldg(a.Fl + sl));
+                    r = fma(-__ldg(a.srow + NS + sl), u1, r);
+                    r = fma(-__ldg(a.srow + 2 * NS + sl), u2, r);
+                } else {
+                    r = __ldg(a.srow + sl) * fma(-2.0, u1, u0 + u2);
+                }
+                rpp = fma(-__ldg(a.fac + 3 * NS + sl), rpp, r);
                 rp[j] = rpp;
                 ur[j] = u1;
                 u0 = u1;
@@ -485,9 +513,7 @@ __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Tit
     const size_t NS = a.n_slots;
     const int so32 = (int)b.so;
     const bool paper = a.paper != 0;
-    auto uslot = [&](int sl) -> double {
-        return gather_at(u, a.nx, __ldg(a.gcell + sl), __ldg(a.glx + sl), __ldg(a.gly + sl));
-    };
+    auto uslot = [&](int sl) -> double { return gather_w(u, a.nx, __ldg(a.gcell + sl), a.gw, NS, sl); };
     double r64[kCmax], ur[kCmax];
     float r32[kCmax];
     double muh = 0.0, h = 1.0;
@@ -972,8 +998,7 @@ static CurveArgs curve_args(Problem* p, int fam)
     a.soff = F.soff;
     a.h = F.h;
     a.gcell = F.gcell;
-    a.glx = F.glx;
-    a.gly = F.gly;
+    a.gw = F.gw;
     a.bnorm = F.bnorm;
     a.fval = F.fval;
     a.xi = F.xi;
@@ -985,6 +1010,7 @@ static CurveArgs curve_args(Problem* p, int fam)
     a.v = F.v;
     a.n_slots = F.n_slots;
     a.mu = p->mu;
+    a.scaled = p->opts.prec == ADR_FP64;
     return a;
 }
 
@@ -1031,13 +1057,14 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
     TRY_S(dev_alloc(p, &F.soff, F.n_lines + 1));
     ADR_CUDA_TRY(cudaMemcpy(F.soff, soff.data(), sizeof(int) * soff.size(), cudaMemcpyHostToDevice));
     TRY_S(dev_alloc(p, &F.gcell, NS));
-    TRY_S(dev_alloc(p, &F.glx, NS));
-    TRY_S(dev_alloc(p, &F.gly, NS));
+    TRY_S(dev_alloc(p, &F.gw, 4 * NS));
     TRY_S(dev_alloc(p, &F.fac, 4 * NS));
     if (p->opts.prec == ADR_FP32_REFINE) TRY_S(dev_alloc(p, &F.fac32, 4 * NS));
     if (fam == 0) {
         TRY_S(dev_alloc(p, &F.Fl, NS));
         TRY_S(dev_alloc(p, &F.srow, 3 * NS));
+    } else if (p->opts.prec == ADR_FP64) {
+        TRY_S(dev_alloc(p, &F.srow, NS));
     }
     CurveArgs a = curve_args(p, fam);
     cudaStream_t st = p->stream;
@@ -1075,12 +1102,11 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
 void release_groups(Problem* p, int fam)
 {
     Family& F = p->fam[fam];
-    void* bufs[] = {F.soff, F.gcell, F.glx, F.gly, F.fac, F.fac32, F.Fl, F.srow};
+    void* bufs[] = {F.soff, F.gcell, F.gw, F.fac, F.fac32, F.Fl, F.srow};
     for (void* q : bufs) dev_free(p, q);
     F.soff = nullptr;
     F.gcell = nullptr;
-    F.glx = nullptr;
-    F.gly = nullptr;
+    F.gw = nullptr;
     F.fac = nullptr;
     F.fac32 = nullptr;
     F.Fl = nullptr;
@@ -1122,6 +1148,7 @@ adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper)
     F.prep_td = td;
     F.prep_sig = sig;
     F.prep_paper = paper;
+    if (fam == 0) F.load_plain = false;  // a scaled load carries the new factors
     return ADR_OK;
 }
 
