@@ -201,6 +201,186 @@ __global__ void __launch_bounds__(256) k_conv_fwd(ConvArgs a)
         }
 }
 
+// ------------------------------------------------ tensor-core convolution
+// The same implicit GEMM on the 5th-generation tensor cores: tcgen05.mma
+// (kind::f16, BF16 operands, FP32 accumulator in tensor memory), one CTA of
+// 128 threads per 128 output pixels and all N = Cout output channels.  A
+// (im2col rows) and B (weights, K-major) are staged by cp.async into shared
+// memory in the 128-byte-swizzled K-major layout, two stages deep; one thread
+// issues the MMAs of a stage and commits them to that stage's mbarrier, which
+// frees the stage for the copies two steps later.  The epilogue reads the
+// accumulator rows back with tcgen05.ld (thread t <-> row t), adds the bias,
+// applies the ReLU and stores BF16.  Every mbarrier wait is bounded; on a
+// timeout the kernel sets *err, skips the epilogue and frees its tensor memory.
+
+constexpr long long kWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (the leading offset is not used by this layout)
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M x N
+__device__ __forceinline__ uint32_t umma_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err)
+{
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, int* err)
+{
+    constexpr int BK = 64, A_BYTES = 128 * 128, B_BYTES = N * 128, STAGE = A_BYTES + B_BYTES;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int HW = a.H * a.W;
+    const long long M = (long long)a.B * HW, m0 = (long long)blockIdx.x * 128;
+    const int K = 9 * a.Cin;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = tmem_base;
+    // this thread stages the 16-byte K chunk c of the rows r = tid/8 + 16 i
+    const int c = tid & 7, r0 = tid >> 3;
+    int pb[8], py[8], px[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        long long m = m0 + r0 + 16 * i;
+        if (m < M) {
+            int b = (int)(m / HW), rem = (int)(m - (long long)b * HW);
+            pb[i] = b;
+            py[i] = rem / a.W;
+            px[i] = rem - py[i] * a.W;
+        } else {
+            pb[i] = -1;
+            py[i] = px[i] = 0;
+        }
+    }
+    const int nk = (K + BK - 1) / BK;
+    bool ok = true;
+    for (int kt = 0; kt < nk && ok; ++kt) {
+        const int st = kt & 1;
+        if (kt >= 2) ok = mbar_wait(smem_u32(&mbar[st]), ((kt - 2) >> 1) & 1, err);
+        if (!ok) break;
+        const uint32_t sa = sbase + st * STAGE, sb = sa + A_BYTES;
+        const int k = kt * BK + c * 8;
+        const bool kin = k < K;
+        const int tap = kin ? k / a.Cin : 0, ci = k - tap * a.Cin;
+        const int dy = (tap / 3 - 1) * a.dil, dx = (tap % 3 - 1) * a.dil;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = r0 + 16 * i;
+            const int yy = py[i] + dy, xx = px[i] + dx;
+            const bool in = kin && pb[i] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16* src = in ? a.x + (((long long)pb[i] * a.H + yy) * a.W + xx) * a.Cin + ci : a.x;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + sw128(r, c)), "l"(src),
+                         "r"(in ? 16 : 0));
+        }
+#pragma unroll
+        for (int i = 0; i < N / 16; ++i) {
+            const int r = r0 + 16 * i;  // output channel
+            const bf16* src = kin ? a.w + (long long)r * K + k : a.w;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sb + sw128(r, c)), "l"(src),
+                         "r"(kin ? 16 : 0));
+        }
+        asm volatile("cp.async.commit_group;\n");
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t idesc = umma_idesc(128, N);
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+                const uint64_t ad = umma_sdesc(sa + ks * 32), bd = umma_sdesc(sb + ks * 32);
+                const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&mbar[st])));
+        }
+        __syncthreads();
+    }
+    if (ok && nk >= 1) ok = mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1, err);
+    if (ok && nk >= 2) ok = mbar_wait(smem_u32(&mbar[(nk - 2) & 1]), ((nk - 2) >> 1) & 1, err);
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (ok) {
+        const long long m = m0 + tid;  // accumulator row = tensor-memory lane
+        const uint32_t lane = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tmem + lane + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (m < M) {
+                uint32_t packed[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
+                    if (a.bias) {
+                        f0 += a.bias[c0 + 2 * j];
+                        f1 += a.bias[c0 + 2 * j + 1];
+                    }
+                    if (a.relu) {
+                        f0 = fmaxf(f0, 0.f);
+                        f1 = fmaxf(f1, 0.f);
+                    }
+                    __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+                    packed[j] = *reinterpret_cast<uint32_t*>(&h);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(a.y + m * N + c0);
+                dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(N));
+}
+
 struct WgradArgs {
     int B, H, W, Cin, Cout, dil;
     const bf16* x;   // layer input [B][H][W][Cin]
@@ -373,11 +553,36 @@ struct LayerTab {
     int cin[kLayers], cout[kLayers];
 };
 
-// Adam on the FP32 parameters; refreshes the BF16 weights and the flipped,
-// transposed BF16 weights of the data gradient
+// BF16 copies of one FP32 parameter: the weights as stored (W[k][co], the
+// mma.sync forward), K-major for the tensor-core forward (Wk[co][k]), and the
+// flipped, transposed weights of the data gradient, [k'][ci] for mma.sync
+// and K-major [ci][k'] for the tensor cores (k' = (8 - tap) Cout + co)
+struct WeightCopies {
+    bf16 *wb, *wt, *wk, *wtk;
+};
+
+__device__ __forceinline__ void write_copies(long long i, float p, const LayerTab& T, const WeightCopies& w)
+{
+    for (int l = 0; l < kLayers; ++l) {
+        if (i >= T.woff[l] && i < T.boff[l]) {
+            long long q = i - T.woff[l];
+            int cin = T.cin[l], cout = T.cout[l];
+            int co = (int)(q % cout);
+            long long k = q / cout;
+            int tap = (int)(k / cin), ci = (int)(k % cin);
+            long long kp = (long long)(8 - tap) * cout + co;
+            const bf16 pb = __float2bfloat16(p);
+            w.wb[i] = pb;
+            w.wt[T.woff[l] + kp * cin + ci] = pb;
+            w.wk[T.woff[l] + (long long)co * 9 * cin + k] = pb;
+            w.wtk[T.woff[l] + (long long)ci * 9 * cout + kp] = pb;
+        }
+    }
+}
+
+// Adam on the FP32 parameters; refreshes the BF16 weight copies
 __global__ void k_adam(float* prm, float* m, float* v, const float* grad, long long n, float lr,
-                       float b1, float b2, float eps, float c1, float c2, LayerTab T, bf16* wb,
-                       bf16* wt)
+                       float b1, float b2, float eps, float c1, float c2, LayerTab T, WeightCopies w)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -387,36 +592,15 @@ __global__ void k_adam(float* prm, float* m, float* v, const float* grad, long l
     v[i] = vi;
     float p = prm[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     prm[i] = p;
-    for (int l = 0; l < kLayers; ++l) {
-        if (i >= T.woff[l] && i < T.boff[l]) {
-            long long q = i - T.woff[l];
-            int cin = T.cin[l], cout = T.cout[l];
-            int co = (int)(q % cout);
-            long long k = q / cout;
-            int tap = (int)(k / cin), ci = (int)(k % cin);
-            wb[i] = __float2bfloat16(p);
-            wt[T.woff[l] + ((long long)(8 - tap) * cout + co) * cin + ci] = __float2bfloat16(p);
-        }
-    }
+    write_copies(i, p, T, w);
 }
 
 // the same refresh without an update (after loading parameters)
-__global__ void k_refresh(const float* prm, long long n, LayerTab T, bf16* wb, bf16* wt)
+__global__ void k_refresh(const float* prm, long long n, LayerTab T, WeightCopies w)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float p = prm[i];
-    for (int l = 0; l < kLayers; ++l) {
-        if (i >= T.woff[l] && i < T.boff[l]) {
-            long long q = i - T.woff[l];
-            int cin = T.cin[l], cout = T.cout[l];
-            int co = (int)(q % cout);
-            long long k = q / cout;
-            int tap = (int)(k / cin), ci = (int)(k % cin);
-            wb[i] = __float2bfloat16(p);
-            wt[T.woff[l] + ((long long)(8 - tap) * cout + co) * cin + ci] = __float2bfloat16(p);
-        }
-    }
+    write_copies(i, prm[i], T, w);
 }
 
 // scale of every problem: max |u0| over its grid (1 when u0 is NULL or zero);
@@ -524,7 +708,8 @@ struct adr_cnn {
     long P = 0;
     LayerTab T{};
     float *prm = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
-    bf16 *wb = nullptr, *wt = nullptr;
+    bf16 *wb = nullptr, *wt = nullptr, *wk = nullptr, *wtk = nullptr;
+    int* err = nullptr;  // a bounded wait of a tensor-core kernel gave up
     bf16* act[kLayers] = {};  // post-activation outputs of layers 0..6 (bf16)
     float* y32 = nullptr;     // last layer output (fp32) [M][8]
     bf16 *dA = nullptr, *dB = nullptr, *dpre = nullptr;
@@ -552,9 +737,25 @@ adr_status cnn_alloc(adr_cnn* c, T** p, size_t n)
     return ADR_OK;
 }
 
-void launch_conv(cudaStream_t st, const ConvArgs& a)
+template <int N>
+constexpr int tc_smem_bytes()
+{
+    return 2 * (128 * 128 + N * 128) + 1024;
+}
+
+// tensor-core path for 64 or 128 output channels with a BF16 output (wk: the
+// K-major weights); mma.sync otherwise
+void launch_conv(cudaStream_t st, const ConvArgs& a, const bf16* wk = nullptr, int* err = nullptr)
 {
     long long M = (long long)a.B * a.H * a.W;
+    if (wk && err && a.y && !a.y32 && (a.Cout == 64 || a.Cout == 128)) {
+        ConvArgs t = a;
+        t.w = wk;
+        const unsigned blocks = (unsigned)((M + 127) / 128);
+        if (a.Cout == 64) k_conv_tc<64><<<blocks, 128, tc_smem_bytes<64>(), st>>>(t, err);
+        else k_conv_tc<128><<<blocks, 128, tc_smem_bytes<128>(), st>>>(t, err);
+        return;
+    }
     dim3 grid((unsigned)((M + 127) / 128), 1);
     if (a.Cout >= 64) {
         grid.y = (a.Cout + 63) / 64;
@@ -585,7 +786,7 @@ adr_status cnn_forward(adr_cnn* c, int batch, const bf16* x)
         a.relu = l < kLayers - 1;
         if (l < kLayers - 1) a.y = c->act[l];
         else a.y32 = c->y32;
-        launch_conv(c->stream, a);
+        launch_conv(c->stream, a, c->wk + c->T.woff[l], c->err);
         in = c->act[l];
     }
     ADR_CUDA_TRY(cudaGetLastError());
@@ -649,7 +850,7 @@ adr_status cnn_backward(adr_cnn* c, int batch, const bf16* x, const float* t)
             a.x = dyp;
             a.w = c->wt + c->T.woff[l];
             a.y = dy == c->dA ? c->dB : c->dA;
-            launch_conv(st, a);
+            launch_conv(st, a, c->wtk + c->T.woff[l], c->err);
             dy = a.y;
         }
     }
@@ -682,7 +883,8 @@ adr_status adr_cnn_set_params(adr_cnn* c, const float* host)
     ADR_CUDA_TRY(cudaMemsetAsync(c->m, 0, sizeof(float) * c->P, c->stream));
     ADR_CUDA_TRY(cudaMemsetAsync(c->v, 0, sizeof(float) * c->P, c->stream));
     c->step = 0;
-    k_refresh<<<(int)((c->P + 255) / 256), 256, 0, c->stream>>>(c->prm, c->P, c->T, c->wb, c->wt);
+    k_refresh<<<(int)((c->P + 255) / 256), 256, 0, c->stream>>>(c->prm, c->P, c->T,
+                                                                WeightCopies{c->wb, c->wt, c->wk, c->wtk});
     ADR_CUDA_TRY(cudaGetLastError());
     ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return ADR_OK;
@@ -726,6 +928,8 @@ adr_status adr_cnn_create(int max_batch, const float* params, void* stream, adr_
     if ((s = cnn_alloc(c, &c->prm, c->P)) || (s = cnn_alloc(c, &c->m, c->P)) ||
         (s = cnn_alloc(c, &c->v, c->P)) || (s = cnn_alloc(c, &c->grad, c->P)) ||
         (s = cnn_alloc(c, &c->wb, c->P)) || (s = cnn_alloc(c, &c->wt, c->P)) ||
+        (s = cnn_alloc(c, &c->wk, c->P)) || (s = cnn_alloc(c, &c->wtk, c->P)) ||
+        (s = cnn_alloc(c, &c->err, 1)) ||
         (s = cnn_alloc(c, &c->y32, M * kCout)) || (s = cnn_alloc(c, &c->dA, M * 128)) ||
         (s = cnn_alloc(c, &c->dB, M * 128)) || (s = cnn_alloc(c, &c->dpre, M * 128)) ||
         (s = cnn_alloc(c, &c->lpart, (M + 255) / 256 + 1)) || (s = cnn_alloc(c, &c->loss, 1)))
@@ -734,6 +938,12 @@ adr_status adr_cnn_create(int max_batch, const float* params, void* stream, adr_
         if ((s = cnn_alloc(c, &c->act[l], M * kCh[l + 1]))) return fail(s);
     c->part_size = 64LL * 9 * 128 * 128;
     if ((s = cnn_alloc(c, &c->part, c->part_size))) return fail(s);
+    ADR_CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    // the tensor-core kernels use more than 48 KB of shared memory (per device)
+    ADR_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc_smem_bytes<64>()));
+    ADR_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc_smem_bytes<128>()));
     if ((s = adr_cnn_set_params(c, params))) return fail(s);
     *out = c;
     return ADR_OK;
@@ -797,8 +1007,14 @@ adr_status adr_cnn_loss_grad(adr_cnn* c, int batch, const uint16_t* x, const flo
         ADR_CUDA_TRY(cudaMemcpyAsync(grad, c->grad, sizeof(float) * c->P, cudaMemcpyDeviceToDevice,
                                      c->stream));
     if (loss) {
+        int e = 0;
         ADR_CUDA_TRY(cudaMemcpyAsync(loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        ADR_CUDA_TRY(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (e) {
+            adr::set_error("a tensor-core kernel gave up waiting for its MMAs");
+            return ADR_ETIMEOUT;
+        }
     }
     return ADR_OK;
 }
@@ -816,12 +1032,19 @@ adr_status adr_cnn_train_step(adr_cnn* c, int batch, const uint16_t* x, const fl
     c->step++;
     const float b1 = 0.9f, b2 = 0.999f;
     float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
-    k_adam<<<(int)((c->P + 255) / 256), 256, 0, c->stream>>>(c->prm, c->m, c->v, c->grad, c->P, lr, b1,
-                                                             b2, 1e-8f, c1, c2, c->T, c->wb, c->wt);
+    k_adam<<<(int)((c->P + 255) / 256), 256, 0, c->stream>>>(
+        c->prm, c->m, c->v, c->grad, c->P, lr, b1, b2, 1e-8f, c1, c2, c->T,
+        WeightCopies{c->wb, c->wt, c->wk, c->wtk});
     ADR_CUDA_TRY(cudaGetLastError());
     if (loss) {
+        int e = 0;
         ADR_CUDA_TRY(cudaMemcpyAsync(loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        ADR_CUDA_TRY(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (e) {
+            adr::set_error("a tensor-core kernel gave up waiting for its MMAs");
+            return ADR_ETIMEOUT;
+        }
     }
     return ADR_OK;
 }
