@@ -270,6 +270,7 @@ def run_ours(args):
     prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
     prob = W.sheared(n=args.n)
     solver = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec)
+    tuned = solver.autotune(10)  # launch shapes by measurement (adr_autotune), before timing
     unknowns = solver.line_unknowns()
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -349,6 +350,8 @@ def run_ours(args):
                    "line_unknowns_per_step": unknowns, "iters_per_solve": iters,
                    "step": "one stationary solve to tol from u=0",
                    "l2": "working set > 129 MB L2 (curve data and maps ~1 GB)",
+                   "launch_shape": {"rows_per_thread": tuned[0], "map_blocks_per_sm": tuned[1],
+                                    "tuned_ms_per_split_step": tuned[2]},
                    "parallelism": f"replicas x{ws}"},
         "roofline": roof, "gpu_launches": launches, "clocks": clk,
     }

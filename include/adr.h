@@ -84,7 +84,7 @@ typedef struct {
     int rows_per_thread;    /* launch shape of the curve solve: 2, 4 or 8 rows per thread
                                (0 = 8); a curve of m unknowns gets blocks of the smallest
                                power-of-two T >= 32 with T * rows_per_thread >= m */
-    int map_blocks_per_sm;  /* blocks per SM of the curve -> grid map: 1..8 (0 = 8) */
+    int map_blocks_per_sm;  /* blocks per SM of the curve -> grid map: 1..8 (0 = 4) */
     int interp_weights;     /* curve -> grid: 0 = average of the row and column values (§6);
                                1 = weights by the opposite direction's crossing gap, for
                                flow nearly parallel to a grid axis */

@@ -101,7 +101,7 @@ struct Problem {
     int n_interior = 0;
     int n_sm = 0;
     int rows_per_thread = 8;    // launch shape of the curve solve (<= 8)
-    int map_blocks_per_sm = 8;  // launch shape of the curve -> grid map
+    int map_blocks_per_sm = 4;  // launch shape of the curve -> grid map
     bool const_beta = false;
     double bmax = 0;
     Family fam[2];

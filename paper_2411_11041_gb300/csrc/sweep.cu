@@ -1242,7 +1242,7 @@ adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out
 int grid_map_blocks(const Problem* p)
 {
     long long need = (p->N + kGridThreads - 1) / kGridThreads;
-    int per_sm = (p->map_blocks_per_sm >= 1 && p->map_blocks_per_sm <= 8) ? p->map_blocks_per_sm : 8;
+    int per_sm = (p->map_blocks_per_sm >= 1 && p->map_blocks_per_sm <= 8) ? p->map_blocks_per_sm : 4;
     long long cap = (long long)per_sm * (p->n_sm > 0 ? p->n_sm : 152);
     return (int)(need < cap ? need : cap);
 }
