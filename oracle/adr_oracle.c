@@ -63,6 +63,7 @@ struct orc_problem {
     int const_beta;
     double bmax;
     int interp_weights; /* 0: plain average of the row and column values; 1: inverse-gap weights */
+    int stabilize;      /* 0: Galerkin on the B lines (the paper); 1: SUPG on the B lines */
     family fam[2];
 };
 
@@ -816,6 +817,7 @@ void orc_destroy(orc_problem* p)
 
 int orc_const_beta(const orc_problem* p) { return p->const_beta; }
 void orc_set_interp_weights(orc_problem* p, int mode) { p->interp_weights = mode ? 1 : 0; }
+void orc_set_stabilization(orc_problem* p, int mode) { p->stabilize = mode ? 1 : 0; }
 
 void orc_node_types(const orc_problem* p, unsigned char* out)
 {
@@ -915,21 +917,41 @@ void orc_map_to_grid(const orc_problem* p, int fam, const double* vals, double* 
  * int |beta| u' w dl with |beta| linear on the element and integrated exactly;
  * F = M f (f linear on the element).  Row q of the outputs is line row q+1;
  * a[0] and c[n-2] are set to 0. */
-/* One row k (1 <= k <= n-1) of a line's operator S and load F.
+/* SUPG parameter of an element of length h with mean |beta| b (the
+ * stabilisation the paper's conclusions propose for the 1D problems along
+ * beta): tau = h / (2 b) (coth Pe - 1 / Pe), Pe = b h / (2 mu), the choice that
+ * makes the 1D solution of -mu u'' + b u' = f nodally exact; the small-Pe
+ * branch is the series Pe / 3 - Pe^3 / 45 of coth Pe - 1 / Pe. */
+static double supg_tau(double h, double b, double mu)
+{
+    if (!(b > 0.0)) return 0.0;
+    double pe = b * h / (2.0 * mu);
+    double xi = pe < 1e-3 ? pe / 3.0 - pe * pe * pe / 45.0 : 1.0 / tanh(pe) - 1.0 / pe;
+    return h / (2.0 * b) * xi;
+}
+
+/* One row k (1 <= k <= n-1) of a line's mass M, operator S and load F.
  * B lines (eq. SemiDiscrSplit1Dbeta1): S = mu K + C + sigma M,
  *   s_i(u, w) = int (mu u' w' + |beta| u' w + sigma u w) dl, F = M f.
  * G lines (eq. SemiDiscrSplit1Dgamma1): S = mu K, m_i(u, w) = int mu u' w' dl.
  * Linear elements of length h: M = h/6 [2 1; 1 2], K = 1/h [1 -1; -1 1];
  * C integrates |beta| u' w exactly with |beta| linear on the element
- * (reading: the paper does not say how the coefficient is integrated). */
+ * (reading: the paper does not say how the coefficient is integrated).
+ * With SUPG on the B lines the test function w + tau |beta| w' adds, per
+ * element (tau from the element's mean |beta|; |beta| and f linear, the
+ * integrals exact): tau int u_t |beta| w' to M, tau int (|beta|^2 u' w' +
+ * sigma u |beta| w') to S and tau int f |beta| w' to F. */
 static void line_row(const orc_problem* p, int fam, int line, int k, double sig,
-                     const double* fl, double* Ssub, double* Sdia, double* Ssup,
-                     double* Fk)
+                     const double* fl, double* Msub, double* Mdia, double* Msup,
+                     double* Ssub, double* Sdia, double* Ssup, double* Fk)
 {
     const family* F = &p->fam[fam];
     const double* bn = F->bnorm + F->off[line];
     double h = F->h[line], mu = p->mu;
     double Mo = h / 6.0, Md = 2.0 * h / 3.0, Ko = -1.0 / h, Kd = 2.0 / h;
+    *Msub = Mo;
+    *Mdia = Md;
+    *Msup = Mo;
     if (fam == 0) {
         double Csub = -(bn[k - 1] / 6.0 + bn[k] / 3.0);
         double Cdia = (bn[k - 1] - bn[k + 1]) / 6.0;
@@ -938,6 +960,27 @@ static void line_row(const orc_problem* p, int fam, int line, int k, double sig,
         *Sdia = mu * Kd + Cdia + sig * Md;
         *Ssup = mu * Ko + Csup + sig * Mo;
         *Fk = h / 6.0 * (fl[k - 1] + 4.0 * fl[k] + fl[k + 1]);
+        if (p->stabilize) {
+            double bm = bn[k - 1], b0 = bn[k], bp = bn[k + 1];
+            double fm = fl[k - 1], f0 = fl[k], fp = fl[k + 1];
+            double tl = supg_tau(h, 0.5 * (bm + b0), mu), tr = supg_tau(h, 0.5 * (b0 + bp), mu);
+            /* int phi_j |beta| phi_n' over the left (phi_n' = 1/h) and right
+               (phi_n' = -1/h) element */
+            double mb_sub = tl * (2.0 * bm + b0) / 6.0;
+            double mb_dia = tl * (bm + 2.0 * b0) / 6.0 - tr * (2.0 * b0 + bp) / 6.0;
+            double mb_sup = -tr * (b0 + 2.0 * bp) / 6.0;
+            /* int |beta|^2 phi_j' phi_n' */
+            double al = tl * (bm * bm + bm * b0 + b0 * b0) / (3.0 * h);
+            double ar = tr * (b0 * b0 + b0 * bp + bp * bp) / (3.0 * h);
+            *Msub += mb_sub;
+            *Mdia += mb_dia;
+            *Msup += mb_sup;
+            *Ssub += -al + sig * mb_sub;
+            *Sdia += al + ar + sig * mb_dia;
+            *Ssup += -ar + sig * mb_sup;
+            *Fk += tl * (2.0 * fm * bm + fm * b0 + f0 * bm + 2.0 * f0 * b0) / 6.0 -
+                   tr * (2.0 * f0 * b0 + f0 * bp + fp * b0 + 2.0 * fp * bp) / 6.0;
+        }
     } else {
         *Ssub = mu * Ko;
         *Sdia = mu * Kd;
@@ -957,13 +1000,12 @@ int orc_line_system(const orc_problem* p, int fam, int line, double theta, doubl
     const family* F = &p->fam[fam];
     int n = F->off[line + 1] - F->off[line] - 1;
     if (n < 2) return 0;
-    double h = F->h[line], Mo = h / 6.0, Md = 2.0 * h / 3.0;
     for (int k = 1; k < n; ++k) {
-        double Ssub, Sdia, Ssup, Fk;
-        line_row(p, fam, line, k, sig, fl, &Ssub, &Sdia, &Ssup, &Fk);
-        a[k - 1] = (k == 1) ? 0.0 : Mo + theta * dt * Ssub;
-        b[k - 1] = Md + theta * dt * Sdia;
-        c[k - 1] = (k == n - 1) ? 0.0 : Mo + theta * dt * Ssup;
+        double Msub, Mdia, Msup, Ssub, Sdia, Ssup, Fk;
+        line_row(p, fam, line, k, sig, fl, &Msub, &Mdia, &Msup, &Ssub, &Sdia, &Ssup, &Fk);
+        a[k - 1] = (k == 1) ? 0.0 : Msub + theta * dt * Ssub;
+        b[k - 1] = Mdia + theta * dt * Sdia;
+        c[k - 1] = (k == n - 1) ? 0.0 : Msup + theta * dt * Ssup;
         r[k - 1] = Fk - (Ssub * u[k - 1] + Sdia * u[k] + Ssup * u[k + 1]);
     }
     return n - 1;
@@ -1147,8 +1189,9 @@ void orc_paper_u0(const orc_problem* p, double* u0)
         int base = F->off[l], n = F->off[l + 1] - base - 1;
         if (n < 2) continue;
         for (int k = 1; k < n; ++k) {
-            double Ssub, Sdia, Ssup, Fk;
-            line_row(p, 0, l, k, p->sigma, F->fval + base, &Ssub, &Sdia, &Ssup, &Fk);
+            double Msub, Mdia, Msup, Ssub, Sdia, Ssup, Fk;
+            line_row(p, 0, l, k, p->sigma, F->fval + base, &Msub, &Mdia, &Msup, &Ssub, &Sdia, &Ssup,
+                     &Fk);
             a[k - 1] = (k == 1) ? 0.0 : Ssub;
             b[k - 1] = Sdia;
             c[k - 1] = (k == n - 1) ? 0.0 : Ssup;

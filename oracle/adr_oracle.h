@@ -34,6 +34,8 @@ void orc_destroy(orc_problem* p);
 
 /* curve -> grid weighting: 0 = plain average (default), 1 = inverse gaps */
 void orc_set_interp_weights(orc_problem* p, int mode);
+/* 1D problems on the B lines: 0 = Galerkin (the paper, default), 1 = SUPG */
+void orc_set_stabilization(orc_problem* p, int mode);
 
 /* geometry queries */
 int orc_const_beta(const orc_problem* p);

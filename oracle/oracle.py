@@ -48,6 +48,8 @@ def lib():
         L.orc_const_beta.argtypes = [vp]
         L.orc_set_interp_weights.argtypes = [vp, C.c_int]
         L.orc_set_interp_weights.restype = None
+        L.orc_set_stabilization.argtypes = [vp, C.c_int]
+        L.orc_set_stabilization.restype = None
         L.orc_node_types.argtypes = [vp, up]
         L.orc_num_lines.argtypes = [vp, C.c_int]
         L.orc_num_line_nodes.argtypes = [vp, C.c_int]
@@ -119,7 +121,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """One problem in the oracle.  Mirrors the library's handle."""
 
-    def __init__(self, prob, interp_weights=0):
+    def __init__(self, prob, interp_weights=0, stabilize=0):
         self.prob = prob
         self.nx, self.ny = prob.nx, prob.ny
         self.mask = _c(prob.mask, np.uint8)
@@ -133,6 +135,8 @@ class Oracle:
         self.h = h
         if interp_weights:
             lib().orc_set_interp_weights(h, 1)
+        if stabilize:
+            lib().orc_set_stabilization(h, 1)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -509,3 +509,70 @@ def test_flows_whose_curves_do_not_cover_the_domain_are_rejected():
         with pytest.raises(O.OracleError) as e:
             O.Oracle(prob)
         assert e.value.status == O.EGEOM
+
+
+def _exact_1d(x, L, mu, b, c):
+    """-mu u'' + b u' = c on [0, L], u(0) = u(L) = 0 (exponentials written to
+    stay finite for large b L / mu)."""
+    r = b / mu
+    return c / b * (x - L * (np.exp(r * (x - L)) - np.exp(-r * L)) / (1.0 - np.exp(-r * L)))
+
+
+@pytest.mark.parametrize("mu", [1e-3, 0.1])
+def test_supg_line_solve_is_nodally_exact(mu):
+    """With tau = h/(2b)(coth Pe - 1/Pe) the SUPG solution of -mu u'' + b u' = c
+    is exact at the nodes (textbook result for linear elements), for large and
+    small element Peclet numbers; Galerkin is not at large Pe."""
+    n, b, c = 33, 1.0, 1.0
+    p = W.Problem(n, n, mu, 1.0, np.full((n, n), b), np.zeros((n, n)), np.full((n, n), c),
+                  W.make_mask("square", n, n))
+    errs = {}
+    for stab in (1, 0):
+        o = O.Oracle(p, stabilize=stab)
+        L = o.lines(0)
+        line = len(L["off"]) // 2  # an interior grid row
+        a0, a1 = L["off"][line], L["off"][line + 1]
+        x = (L["xi"][a0:a1] - L["xi"][a0]) / (n - 1)
+        u = np.zeros(a1 - a0)
+        fl = np.full(a1 - a0, c)
+        dt = 1e9  # theta = 1: dt d = (M/dt + S)^-1 (F - S u) -> S^-1 F
+        a, bb, cc, r = o.line_system(0, line, 1.0, dt, u, fl, sigma=0.0)
+        d = O.thomas(a, bb, cc, r)
+        ex = _exact_1d(x[1:-1], x[-1], mu, b, c)
+        errs[stab] = np.abs(dt * d - ex).max() / np.abs(ex).max()
+    assert errs[1] < 1e-7, errs
+    if mu == 1e-3:  # Pe = 15.6: Galerkin is far from the nodal values
+        assert errs[0] > 1e-2, errs
+
+
+def test_supg_reduces_to_galerkin_as_pe_vanishes():
+    """tau ~ h^2 / (12 mu) as Pe -> 0: the stabilised line systems differ from
+    the Galerkin ones by O(Pe) relatively."""
+    n = 33
+    p = W.manufactured(n=n, mu=10.0, beta=(1.0, 0.5))  # Pe = |beta| h / (2 mu) ~ 2e-3
+    u = np.random.default_rng(0).normal(size=40)
+    out = []
+    for stab in (0, 1):
+        o = O.Oracle(p, stabilize=stab)
+        L = o.lines(0)
+        line = max(range(len(L["off"]) - 1), key=lambda l: L["off"][l + 1] - L["off"][l])
+        m = L["off"][line + 1] - L["off"][line]
+        out.append(np.concatenate(o.line_system(0, line, 0.5, 0.01, u[:m], np.ones(m))))
+    rel = np.abs(out[1] - out[0]).max() / np.abs(out[0]).max()
+    assert 0 < rel < 1e-2, rel
+
+
+def test_supg_keeps_a_steep_solution_within_its_bounds():
+    """Aligned flow with mu = 1e-4 on 33^2 nodes (Pe ~ 16): the Galerkin lines
+    oscillate (the converged midpoint leaves [0, f / sigma] visibly), SUPG
+    stays within the bounds of the maximum principle up to 1 %."""
+    n = 33
+    p = W.Problem(n, n, 1e-4, 1.0, np.ones((n, n)), np.zeros((n, n)), np.ones((n, n)),
+                  W.make_mask("square", n, n))
+    res = {}
+    for stab in (0, 1):
+        u, _, it, _, st = O.Oracle(p, stabilize=stab).solve_stationary(tol=1e-10, max_iter=20000)
+        assert st == O.OK
+        res[stab] = (u.min(), u.max())
+    assert res[0][1] > 1.05 or res[0][0] < -0.05, res  # Galerkin over/undershoots
+    assert res[1][0] > -0.01 and res[1][1] < 1.01, res
