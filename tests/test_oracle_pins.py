@@ -511,7 +511,7 @@ def test_flows_whose_curves_do_not_cover_the_domain_are_rejected():
         assert e.value.status == O.EGEOM
 
 
-def _exact_1d(x, L, mu, b, c):
+def _exact_advection_1d(x, L, mu, b, c):
     """-mu u'' + b u' = c on [0, L], u(0) = u(L) = 0 (exponentials written to
     stay finite for large b L / mu)."""
     r = b / mu
@@ -538,7 +538,7 @@ def test_supg_line_solve_is_nodally_exact(mu):
         dt = 1e9  # theta = 1: dt d = (M/dt + S)^-1 (F - S u) -> S^-1 F
         a, bb, cc, r = o.line_system(0, line, 1.0, dt, u, fl, sigma=0.0)
         d = O.thomas(a, bb, cc, r)
-        ex = _exact_1d(x[1:-1], x[-1], mu, b, c)
+        ex = _exact_advection_1d(x[1:-1], x[-1], mu, b, c)
         errs[stab] = np.abs(dt * d - ex).max() / np.abs(ex).max()
     assert errs[1] < 1e-7, errs
     if mu == 1e-3:  # Pe = 15.6: Galerkin is far from the nodal values
