@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stabilize", type=int, default=0, choices=[0, 1],
+                    help="1: SUPG on the B curves (FP64 only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--other-prec", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--workload", default="sheared",
@@ -269,7 +271,8 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
     prob = W.sheared(n=args.n)
-    solver = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec)
+    solver = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec,
+                    stabilize=args.stabilize)
     tuned = solver.autotune(10)  # launch shapes by measurement (adr_autotune), before timing
     unknowns = solver.line_unknowns()
     stream = torch.cuda.current_stream(dev)
@@ -347,6 +350,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": f"sheared{args.n}", "nodes": prob.nx * prob.ny,
                    "mu": prob.mu, "sigma": prob.sigma, "tol": args.tol, "prec": args.prec,
+                   "stabilize": args.stabilize,
                    "line_unknowns_per_step": unknowns, "iters_per_solve": iters,
                    "step": "one stationary solve to tol from u=0",
                    "l2": "working set > 129 MB L2 (curve data and maps ~1 GB)",

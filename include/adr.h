@@ -47,7 +47,7 @@ typedef enum {
     ADR_EGEOM = 5,    /* the curve families do not cover the domain (§3, §6): tracing failed
                          (closed integral curve, |beta| = 0 on a curve), a family has no
                          inflow boundary, or an interior node meets no curve of a family */
-    ADR_ETIMEOUT = 6  /* reserved: a bounded device wait gave up */
+    ADR_ETIMEOUT = 6  /* a bounded device wait gave up (tensor-core network kernels) */
 } adr_status;
 
 typedef enum {
@@ -59,7 +59,8 @@ typedef enum {
     ADR_INIT_ZERO = 0,     /* u_0 = 0 */
     ADR_INIT_USER = 1,     /* u_0 = caller array (non-interior nodes ignored) */
     ADR_INIT_PAPER_U0 = 2, /* s(u_0, v) = <l, v>  (§5, eq. u0stationary) */
-    ADR_INIT_LEARNED = 3   /* reserved for a learned initial state */
+    ADR_INIT_LEARNED = 3   /* not accepted: pass the network's state with ADR_INIT_USER
+                              (adr_cnn_initial_state) */
 } adr_init;
 
 /* Grid of nx x ny nodes on [x0,x1] x [y0,y1]; nx, ny >= 3. */
@@ -88,7 +89,11 @@ typedef struct {
     int interp_weights;     /* curve -> grid: 0 = average of the row and column values (§6);
                                1 = weights by the opposite direction's crossing gap, for
                                flow nearly parallel to a grid axis */
-    int reserved;           /* must be 0 */
+    int stabilize;          /* the 1D problems on the B curves: 0 = Galerkin (§6, the paper);
+                               1 = SUPG, the per-line stabilisation the paper's conclusions
+                               propose for singularly perturbed problems (test function
+                               w + tau |beta| w', tau = h/(2|beta|)(coth Pe - 1/Pe) per element);
+                               FP64 mode only */
 } adr_opts;
 
 /* Result statistics (host struct filled by the solve calls). */

@@ -202,6 +202,14 @@ adr_status check_opts(const adr_opts* o)
         set_error("opts.interp_weights must be 0 or 1");
         return ADR_EINVAL;
     }
+    if (o->stabilize != 0 && o->stabilize != 1) {
+        set_error("opts.stabilize must be 0 or 1");
+        return ADR_EINVAL;
+    }
+    if (o->stabilize && o->prec != ADR_FP64) {
+        set_error("opts.stabilize needs opts.prec == ADR_FP64");
+        return ADR_EINVAL;
+    }
     if (o->max_iter < 0 || !std::isfinite(o->dt) || std::isnan(o->tol)) {
         set_error("opts.max_iter must be >= 0 and dt, tol finite");
         return ADR_EINVAL;

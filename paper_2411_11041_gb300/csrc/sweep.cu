@@ -65,6 +65,7 @@ struct CurveArgs {
     double* srow;          // 3 planes per slot: S sub/diag/super (B), times ip when scaled;
                            // G when scaled: one plane, (mu / h) ip
     int scaled;            // FP64 mode: F and S rows carry the factor ip of their row
+    int supg;              // B curves: SUPG-stabilised element forms (mass, S and load)
     double* fac;           // 4 planes per slot: cp, vp, ip, lp
     float* fac32;          // the same factors rounded to FP32 (reduced-precision mode)
     const double* lanecs[3];   // reduced-system constants of the item sets (batched launches)
@@ -142,6 +143,17 @@ __device__ __forceinline__ double gather_at(const double* __restrict__ u, int nx
     return b + ly * (t - b);
 }
 
+// SUPG parameter of a B-curve element of length h with mean |beta| b:
+// tau = h / (2 b) (coth Pe - 1 / Pe), Pe = b h / (2 mu), the value that makes
+// the 1D solution of -mu u'' + b u' = f nodally exact (series below Pe = 1e-3)
+__device__ __forceinline__ double supg_tau(double h, double b, double mu)
+{
+    if (!(b > 0.0)) return 0.0;
+    const double pe = b * h / (2.0 * mu);
+    const double xi = pe < 1e-3 ? pe / 3.0 - pe * pe * pe / 45.0 : 1.0 / tanh(pe) - 1.0 / pe;
+    return h / (2.0 * b) * xi;
+}
+
 // gather descriptors of every row's node, in slot layout (setup)
 template <int BS>
 __global__ void __launch_bounds__(BS) k_curve_gdesc(CurveArgs a, const int* item_T,
@@ -192,6 +204,14 @@ __global__ void __launch_bounds__(BS) k_curve_load(CurveArgs a, const int* item_
         double f2 = fat(b.s + j + 2);
         const size_t sl = b.so + (size_t)j * b.T + b.lt;
         double F = Mo * (f0 + 4.0 * f1 + f2);
+        if (a.supg) {  // + tau int f |beta| phi' over the two elements of the row's node
+            const int g = b.base + b.s + j;
+            const double h = a.h[b.line];
+            const double bm = a.bnorm[g], b0 = a.bnorm[g + 1], bp = a.bnorm[g + 2];
+            const double tl = supg_tau(h, 0.5 * (bm + b0), a.mu), tr = supg_tau(h, 0.5 * (b0 + bp), a.mu);
+            F += tl * (2.0 * f0 * bm + f0 * b0 + f1 * bm + 2.0 * f1 * b0) / 6.0 -
+                 tr * (2.0 * f1 * b0 + f1 * bp + f2 * b0 + 2.0 * f2 * bp) / 6.0;
+        }
         a.Fl[sl] = a.scaled ? F * a.fac[2 * a.n_slots + sl] : F;  // row factor ip (k_curve_prep)
         f0 = f1;
         f1 = f2;
@@ -225,6 +245,7 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
             const int q = b.s + j;
             const size_t sl = b.so + (size_t)j * T + lt;
             double Ssub, Sdia, Ssup;
+            double Msub = Mo, Mdia = Md, Msup = Mo;
             if (FAM == 0) {
                 b2 = a.bnorm[base + q + 2];
                 double Csub = -(b0 * (1.0 / 6.0) + b1 * (1.0 / 3.0));
@@ -233,6 +254,21 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
                 Ssub = a.mu * Ko + Csub + a.sig * Mo;
                 Sdia = a.mu * Kd + Cdia + a.sig * Md;
                 Ssup = a.mu * Ko + Csup + a.sig * Mo;
+                if (a.supg) {  // SUPG terms of the two elements of node q + 1
+                    const double tl = supg_tau(h, 0.5 * (b0 + b1), a.mu);
+                    const double tr = supg_tau(h, 0.5 * (b1 + b2), a.mu);
+                    const double mbs = tl * (2.0 * b0 + b1) / 6.0;
+                    const double mbd = tl * (b0 + 2.0 * b1) / 6.0 - tr * (2.0 * b1 + b2) / 6.0;
+                    const double mbp = -tr * (b1 + 2.0 * b2) / 6.0;
+                    const double al = tl * (b0 * b0 + b0 * b1 + b1 * b1) / (3.0 * h);
+                    const double ar = tr * (b1 * b1 + b1 * b2 + b2 * b2) / (3.0 * h);
+                    Msub += mbs;
+                    Mdia += mbd;
+                    Msup += mbp;
+                    Ssub += -al + a.sig * mbs;
+                    Sdia += al + ar + a.sig * mbd;
+                    Ssup += -ar + a.sig * mbp;
+                }
                 a.srow[sl] = Ssub;
                 a.srow[NS + sl] = Sdia;
                 a.srow[2 * NS + sl] = Ssup;
@@ -243,9 +279,9 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
                 Sdia = a.mu * Kd;
                 Ssup = Ssub;
             }
-            double A = (q == 0) ? 0.0 : mw * Mo + td * Ssub;
-            double B = mw * Md + td * Sdia;
-            double C = (q == m - 1) ? 0.0 : mw * Mo + td * Ssup;
+            double A = (q == 0) ? 0.0 : mw * Msub + td * Ssub;
+            double B = mw * Mdia + td * Sdia;
+            double C = (q == m - 1) ? 0.0 : mw * Msup + td * Ssup;
             double ip, cp, vp, lp;
             if (j == 0) {
                 ip = 1.0 / B;
@@ -1011,6 +1047,7 @@ static CurveArgs curve_args(Problem* p, int fam)
     a.n_slots = F.n_slots;
     a.mu = p->mu;
     a.scaled = p->opts.prec == ADR_FP64;
+    a.supg = p->opts.stabilize;
     return a;
 }
 

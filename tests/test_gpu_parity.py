@@ -255,3 +255,29 @@ def test_data2d_paper_procedure_matches_oracle(torch_cuda):
                                                           init=2)
     assert st == ADR_OK and ost == O.OK and stats["iters"] == it == 50
     assert relerr(u, ref) <= TOL64 and relerr(uit, refit) <= TOL64
+
+
+@pytest.mark.parametrize("name", ["aligned17", "steep", "L_mask", "sheared65", "data2d"])
+def test_supg_mode_matches_oracle(torch_cuda, name):
+    """SUPG on the B curves (opts.stabilize): the split step, the converged
+    solve and the paper's initial state against the oracle's stabilised forms."""
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    torch = torch_cuda
+    p = PROBLEMS[name]()
+    o = O.Oracle(p, stabilize=1)
+    s = Solver(p, tol=1e-10, max_iter=20000, stabilize=1)
+    u = np.random.default_rng(12).normal(size=(p.ny, p.nx)) * o.interior()
+    uh, un = s.split_step(torch.tensor(u, device="cuda:0"), o.default_dt())
+    ouh, oun = o.split_step(0.5, o.default_dt(), u)
+    assert relerr(uh, ouh) <= TOL64 and relerr(un, oun) <= TOL64
+    out, _, stats, st = s.solve_stationary()
+    ref, _, it, _, ost = o.solve_stationary(tol=1e-10, max_iter=20000)
+    assert st == ADR_OK and ost == O.OK and stats["iters"] == it
+    assert relerr(out, ref) <= TOL64
+    assert relerr(s.paper_u0(), o.paper_u0()) <= TOL64
+
+
+def test_supg_needs_fp64(torch_cuda):
+    from paper_2411_11041_gb300 import AdrError, Solver
+    with pytest.raises(AdrError, match="EINVAL"):
+        Solver(W.manufactured(n=17), stabilize=1, prec=1)
