@@ -322,7 +322,7 @@ def run_ours(args):
     launches = int(sum(5 * it + 3 for it in iters))
     # the other precision mode on the same workload: time to tol and agreement
     other = {}
-    if args.other_prec:
+    if args.other_prec and not args.stabilize:  # FP32+refine has no SUPG forms
         oprec = ADR_FP32_REFINE if prec == ADR_FP64 else ADR_FP64
         s2 = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=oprec)
         s2.solve_stationary()
