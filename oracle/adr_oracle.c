@@ -124,11 +124,11 @@ double orc_bilinear(const orc_problem* p, const double* grid, double xi, double 
 
 /* §3: b = beta/|beta|, gamma = (beta2, -beta1), p = gamma/|gamma|.  Family 0
  * follows b, family 1 follows p.  beta at a point is the bilinear interpolant
- * of the nodal field.  Arguments are physical offsets from (x0, y0). */
-static int direction(const orc_problem* p, int fam, double X, double Y,
+ * of the nodal field.  The point is given in index coordinates (xi, eta); the
+ * returned direction is the physical unit vector. */
+static int direction(const orc_problem* p, int fam, double xi, double eta,
                      double* dx, double* dy)
 {
-    double xi = X / p->hx, eta = Y / p->hy;
     double b1 = bilin(p, p->beta1, xi, eta), b2 = bilin(p, p->beta2, xi, eta);
     double nb = sqrt(b1 * b1 + b2 * b2);
     if (!(nb > 0.0)) return -1;
@@ -142,19 +142,20 @@ static int direction(const orc_problem* p, int fam, double X, double Y,
     return 0;
 }
 
-/* one classical Runge-Kutta step of x' = dir(x) over arc length ds
+/* one classical Runge-Kutta step of x' = dir(x) over an arc length ds
  * (eqs. CauchyBeta / CauchyGamma with the field normalised, so that the
- * curve parameter is arc length). */
-static int rk4(const orc_problem* p, int fam, double X, double Y, double ds,
+ * curve parameter is arc length), carried out in index coordinates: the step
+ * is (sx, sy) = (ds / hx, ds / hy) along the two axes. */
+static int rk4(const orc_problem* p, int fam, double X, double Y, double sx, double sy,
                double* Xo, double* Yo)
 {
     double k1x, k1y, k2x, k2y, k3x, k3y, k4x, k4y;
     if (direction(p, fam, X, Y, &k1x, &k1y)) return -1;
-    if (direction(p, fam, X + 0.5 * ds * k1x, Y + 0.5 * ds * k1y, &k2x, &k2y)) return -1;
-    if (direction(p, fam, X + 0.5 * ds * k2x, Y + 0.5 * ds * k2y, &k3x, &k3y)) return -1;
-    if (direction(p, fam, X + ds * k3x, Y + ds * k3y, &k4x, &k4y)) return -1;
-    *Xo = X + ds / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
-    *Yo = Y + ds / 6.0 * (k1y + 2.0 * k2y + 2.0 * k3y + k4y);
+    if (direction(p, fam, X + 0.5 * sx * k1x, Y + 0.5 * sy * k1y, &k2x, &k2y)) return -1;
+    if (direction(p, fam, X + 0.5 * sx * k2x, Y + 0.5 * sy * k2y, &k3x, &k3y)) return -1;
+    if (direction(p, fam, X + sx * k3x, Y + sy * k3y, &k4x, &k4y)) return -1;
+    *Xo = X + sx / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
+    *Yo = Y + sy / 6.0 * (k1y + 2.0 * k2y + 2.0 * k3y + k4y);
     return 0;
 }
 
@@ -431,7 +432,7 @@ static int boundary_loops(const orc_problem* p, bedge** out, int* count)
     return 0;
 }
 
-/* trace one curve from a seed; stores the RK4 points (physical offsets) */
+/* trace one curve from a seed; stores the RK4 points (index coordinates) */
 typedef struct {
     double *X, *Y;
     int n, cap;
@@ -441,6 +442,7 @@ static int trace_curve(const orc_problem* p, int fam, double X0, double Y0,
                        trace_buf* tb, double* Lout)
 {
     double ds = p->hs / TRACE_STEPS_PER_H;
+    double sx = ds / p->hx, sy = ds / p->hy; /* the step in index units */
     double cap_len = 10.0 * 2.0 * ((p->x1 - p->x0) + (p->y1 - p->y0));
     tb->n = 0;
     double X = X0, Y = Y0;
@@ -457,8 +459,8 @@ static int trace_curve(const orc_problem* p, int fam, double X0, double Y0,
         tb->Y[tb->n] = Y;
         tb->n++;
         double Xn, Yn;
-        if (rk4(p, fam, X, Y, ds, &Xn, &Yn)) return ORC_EGEOM;
-        if (interior_point(p, snap(Xn / p->hx), snap(Yn / p->hy))) {
+        if (rk4(p, fam, X, Y, sx, sy, &Xn, &Yn)) return ORC_EGEOM;
+        if (interior_point(p, snap(Xn), snap(Yn))) {
             X = Xn;
             Y = Yn;
             if ((tb->n) * ds > cap_len) return ORC_EGEOM; /* closed curve */
@@ -467,12 +469,12 @@ static int trace_curve(const orc_problem* p, int fam, double X0, double Y0,
         double lo = 0.0, hi = 1.0;
         for (int it = 0; it < BISECT_ITERS; ++it) {
             double mid = 0.5 * (lo + hi);
-            if (rk4(p, fam, X, Y, mid * ds, &Xn, &Yn)) return ORC_EGEOM;
-            if (interior_point(p, snap(Xn / p->hx), snap(Yn / p->hy))) lo = mid;
+            if (rk4(p, fam, X, Y, mid * sx, mid * sy, &Xn, &Yn)) return ORC_EGEOM;
+            if (interior_point(p, snap(Xn), snap(Yn))) lo = mid;
             else hi = mid;
         }
         double Xe = X, Ye = Y;
-        if (lo > 0.0 && rk4(p, fam, X, Y, lo * ds, &Xe, &Ye)) return ORC_EGEOM;
+        if (lo > 0.0 && rk4(p, fam, X, Y, lo * sx, lo * sy, &Xe, &Ye)) return ORC_EGEOM;
         if (tb->n == tb->cap) {
             tb->cap *= 2;
             double* a = realloc(tb->X, sizeof(double) * tb->cap);
@@ -515,7 +517,7 @@ static int build_curved(orc_problem* p, int fam)
         if (!(w > 0.0)) continue;
         while ((k + 0.5) * p->hs < cum + w) {
             double phi = ((k + 0.5) * p->hs - cum) / w;
-            double X0 = (i + phi * DXI[d]) * p->hx, Y0 = (r + phi * DETA[d]) * p->hy;
+            double X0 = i + phi * DXI[d], Y0 = r + phi * DETA[d]; /* index coordinates */
             double L = 0.0;
             int st = trace_curve(p, fam, X0, Y0, &tb, &L);
             if (st) return st;
@@ -536,8 +538,8 @@ static int build_curved(orc_problem* p, int fam)
                     X = tb.X[q] + fr * (tb.X[q + 1] - tb.X[q]);
                     Y = tb.Y[q] + fr * (tb.Y[q + 1] - tb.Y[q]);
                 }
-                F->xi[base + j] = snap(X / p->hx);
-                F->eta[base + j] = snap(Y / p->hy);
+                F->xi[base + j] = snap(X);
+                F->eta[base + j] = snap(Y);
                 node_data(p, F, base + j);
             }
             F->off[F->n_lines] = base;

@@ -67,10 +67,10 @@ __device__ double bilin(const GridView& g, const double* a, double xi, double et
            ly * lx * p22;
 }
 
-// unit direction of family fam at physical offset (X, Y): b (B) or p (G), §3
-__device__ int direction(const GridView& g, int fam, double X, double Y, double* dx, double* dy)
+// physical unit direction of family fam at the index coordinates (xi, eta):
+// b (B) or p (G), §3
+__device__ int direction(const GridView& g, int fam, double xi, double eta, double* dx, double* dy)
 {
-    double xi = X / g.hx, eta = Y / g.hy;
     double b1 = bilin(g, g.beta1, xi, eta), b2 = bilin(g, g.beta2, xi, eta);
     double nb = sqrt(b1 * b1 + b2 * b2);
     if (!(nb > 0.0)) return -1;
@@ -84,17 +84,19 @@ __device__ int direction(const GridView& g, int fam, double X, double Y, double*
     return 0;
 }
 
-// classical RK4 step of x' = dir(x) over arc length ds (eqs. CauchyBeta/CauchyGamma)
-__device__ int rk4(const GridView& g, int fam, double X, double Y, double ds, double* Xo,
-                   double* Yo)
+// classical RK4 step of x' = dir(x) over an arc length ds (eqs.
+// CauchyBeta/CauchyGamma), in index coordinates: the step is (sx, sy) =
+// (ds / hx, ds / hy) along the two axes
+__device__ int rk4(const GridView& g, int fam, double X, double Y, double sx, double sy,
+                   double* Xo, double* Yo)
 {
     double k1x, k1y, k2x, k2y, k3x, k3y, k4x, k4y;
     if (direction(g, fam, X, Y, &k1x, &k1y)) return -1;
-    if (direction(g, fam, X + 0.5 * ds * k1x, Y + 0.5 * ds * k1y, &k2x, &k2y)) return -1;
-    if (direction(g, fam, X + 0.5 * ds * k2x, Y + 0.5 * ds * k2y, &k3x, &k3y)) return -1;
-    if (direction(g, fam, X + ds * k3x, Y + ds * k3y, &k4x, &k4y)) return -1;
-    *Xo = X + ds / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
-    *Yo = Y + ds / 6.0 * (k1y + 2.0 * k2y + 2.0 * k3y + k4y);
+    if (direction(g, fam, X + 0.5 * sx * k1x, Y + 0.5 * sy * k1y, &k2x, &k2y)) return -1;
+    if (direction(g, fam, X + 0.5 * sx * k2x, Y + 0.5 * sy * k2y, &k3x, &k3y)) return -1;
+    if (direction(g, fam, X + sx * k3x, Y + sy * k3y, &k4x, &k4y)) return -1;
+    *Xo = X + sx / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
+    *Yo = Y + sy / 6.0 * (k1y + 2.0 * k2y + 2.0 * k3y + k4y);
     return 0;
 }
 
@@ -451,8 +453,8 @@ __global__ void k_seeds(GridView g, const int* cand, long long ncand, uint8_t* v
                 while ((k + 0.5) * g.hs < cum + w) {
                     double phi = ((k + 0.5) * g.hs - cum) / w;
                     if (ns < cap) {
-                        sx[ns] = (i + phi * kDXI[d]) * g.hx;
-                        sy[ns] = (r + phi * kDETA[d]) * g.hy;
+                        sx[ns] = i + phi * kDXI[d];  // index coordinates
+                        sy[ns] = r + phi * kDETA[d];
                     }
                     ns++;
                     k++;
@@ -500,6 +502,7 @@ __device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mo
                          double* Xe, double* Ye, const PointPool& pool, int slot)
 {
     double ds = g.hs / kTraceStepsPerH;
+    const double sx = ds / g.hx, sy = ds / g.hy;  // the step in index units
     double cap_len = 10.0 * 2.0 * (g.W + g.H);
     long long npts = 0;
     bool keep = pool.n_chunks > 0;
@@ -509,8 +512,8 @@ __device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mo
     for (;;) {
         npts++;
         double Xn, Yn;
-        if (rk4(g, fam, X, Y, ds, &Xn, &Yn)) return -1;
-        if (interior_point(g, snap(Xn / g.hx), snap(Yn / g.hy))) {
+        if (rk4(g, fam, X, Y, sx, sy, &Xn, &Yn)) return -1;
+        if (interior_point(g, snap(Xn), snap(Yn))) {
             X = Xn;
             Y = Yn;
             if (keep) {  // P_q, q = npts, at pool index q - 1 of the curve
@@ -532,12 +535,12 @@ __device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mo
         double lo = 0.0, hi = 1.0;
         for (int it = 0; it < kBisectIters; ++it) {
             double mid = 0.5 * (lo + hi);
-            if (rk4(g, fam, X, Y, mid * ds, &Xn, &Yn)) return -1;
-            if (interior_point(g, snap(Xn / g.hx), snap(Yn / g.hy))) lo = mid;
+            if (rk4(g, fam, X, Y, mid * sx, mid * sy, &Xn, &Yn)) return -1;
+            if (interior_point(g, snap(Xn), snap(Yn))) lo = mid;
             else hi = mid;
         }
         double XE = X, YE = Y;
-        if (lo > 0.0 && rk4(g, fam, X, Y, lo * ds, &XE, &YE)) return -1;
+        if (lo > 0.0 && rk4(g, fam, X, Y, lo * sx, lo * sy, &XE, &YE)) return -1;
         *Mout = (int)(npts - 1);
         *L = (npts - 1) * ds + lo * ds;
         *Xe = XE;
@@ -655,8 +658,8 @@ __global__ void k_trace_fill(GridView g, int cap, const double* sx, const double
                 X = Xa + fr * (Xb - Xa);
                 Y = Ya + fr * (Yb - Ya);
             }
-            xs[base + j] = snap(X / g.hx);
-            es[base + j] = snap(Y / g.hy);
+            xs[base + j] = snap(X);
+            es[base + j] = snap(Y);
         }
         return;
     }
@@ -664,7 +667,8 @@ __global__ void k_trace_fill(GridView g, int cap, const double* sx, const double
     // (Xa, Ya) = P_q, (Xb, Yb) = P_{q+1}; P_0 is the seed, P_{m+1} the exit point
     int q = 0;
     double Xa = sx[s], Ya = sy[s], Xb, Yb;
-    if (m > 0) rk4(g, fam, Xa, Ya, ds, &Xb, &Yb);
+    const double stx = ds / g.hx, sty = ds / g.hy;  // the step in index units
+    if (m > 0) rk4(g, fam, Xa, Ya, stx, sty, &Xb, &Yb);
     else {
         Xb = xe;
         Yb = ye;
@@ -682,7 +686,7 @@ __global__ void k_trace_fill(GridView g, int cap, const double* sx, const double
                 q++;
                 Xa = Xb;
                 Ya = Yb;
-                if (q < m) rk4(g, fam, Xa, Ya, ds, &Xb, &Yb);
+                if (q < m) rk4(g, fam, Xa, Ya, stx, sty, &Xb, &Yb);
                 else {
                     Xb = xe;
                     Yb = ye;
@@ -693,8 +697,8 @@ __global__ void k_trace_fill(GridView g, int cap, const double* sx, const double
             X = Xa + fr * (Xb - Xa);
             Y = Ya + fr * (Yb - Ya);
         }
-        xs[base + j] = snap(X / g.hx);
-        es[base + j] = snap(Y / g.hy);
+        xs[base + j] = snap(X);
+        es[base + j] = snap(Y);
     }
 }
 
