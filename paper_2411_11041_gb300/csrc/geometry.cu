@@ -407,78 +407,172 @@ __global__ void k_row_cand_fill(GridView g, const long long* start, int* cand)
 
 // one thread per family (block f): walk the loops from the candidate starts
 // and place the seeds (X0, Y0 physical offsets) at sx/sy + f*cap
-__global__ void k_seeds(GridView g, const int* cand, long long ncand, uint8_t* vis_h_all,
-                        uint8_t* vis_v_all, long long total, double* sx_all, double* sy_all,
-                        int cap, int* nseeds, int* status)
+// Seeds on the inflow boundary (eq. cauchyStartSets).  The boundary of the
+// staircase domain is walked loop by loop, counter-clockwise, each loop from
+// its first +x edge in (row, column) order; an edge's weight is its inflow
+// measure max(0, -n . dir(mid)) |e|, and a seed goes where the running measure
+// reaches (k + 1/2) h_s.  The walk is split so that only the running sum is
+// serial: every boundary edge's successor is found in parallel (the walk's
+// turn rule is local), one thread follows the successors, the weights are
+// computed in parallel, one thread per family accumulates them in walk order
+// (the same sums and comparisons, so the seeds are bit-identical), and the
+// seeds are written in parallel.
+//
+// Boundary edges carry undirected ids: the horizontal edge (i, r)-(i+1, r) is
+// r (nx-1) + i, the vertical edge (i, r)-(i, r+1) is nh + r nx + i.
+
+__device__ __forceinline__ int edge_id(const GridView& g, int i, int r, int d)
 {
-    if (threadIdx.x != 0) return;
-    int fam = blockIdx.x;
-    int nx = g.nx, ny = g.ny;
-    uint8_t* vis_h = vis_h_all + (size_t)fam * ny * (nx - 1);
-    uint8_t* vis_v = vis_v_all + (size_t)fam * nx * (ny - 1);
-    double* sx = sx_all + (size_t)fam * cap;
-    double* sy = sy_all + (size_t)fam * cap;
-    double cum = 0.0;
-    long long k = 0;
-    int ns = 0;
+    const int nh = g.ny * (g.nx - 1);
+    switch (d) {
+    case 0: return r * (g.nx - 1) + i;
+    case 2: return r * (g.nx - 1) + i - 1;
+    case 1: return nh + r * g.nx + i;
+    default: return nh + (r - 1) * g.nx + i;
+    }
+}
+
+// per undirected edge: its walk start vertex and direction (packed
+// (r nx + i) * 4 + d, -1 when it is not a boundary edge) and its successor
+__global__ void k_bnd_succ(GridView g, int* info, int* succ)
+{
+    const long long nh = (long long)g.ny * (g.nx - 1), nv = (long long)g.nx * (g.ny - 1);
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= nh + nv) return;
+    int i, r, d;
+    if (e < nh) {
+        r = (int)(e / (g.nx - 1));
+        i = (int)(e % (g.nx - 1));
+        const int s = hedge_dir(g, i, r);
+        if (s == 0) {
+            info[e] = -1;
+            succ[e] = -1;
+            return;
+        }
+        d = s > 0 ? 0 : 2;
+        if (s < 0) i += 1;
+    } else {
+        const long long q = e - nh;
+        r = (int)(q / g.nx);
+        i = (int)(q % g.nx);
+        const int s = vedge_dir(g, i, r);
+        if (s == 0) {
+            info[e] = -1;
+            succ[e] = -1;
+            return;
+        }
+        d = s > 0 ? 1 : 3;
+        if (s < 0) r += 1;
+    }
+    info[e] = (r * g.nx + i) * 4 + d;
+    const int ib = i + kDXI[d], rb = r + kDETA[d];
+    const int pref[3] = {(d + 1) & 3, d, (d + 3) & 3};
+    int nxt = -1;
+    for (int q = 0; q < 3; ++q)
+        if (out_edge(g, ib, rb, pref[q])) {
+            nxt = edge_id(g, ib, rb, pref[q]);
+            break;
+        }
+    succ[e] = nxt;
+}
+
+// the walk: one thread follows the successors, loop after loop
+__global__ void k_bnd_walk(GridView g, const int* cand, long long ncand, const int* succ,
+                           uint8_t* visited, long long total, int* order, int* norder)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int pos = 0;
     for (long long c = 0; c < ncand; ++c) {
-        int e0 = cand[c];
-        int r0 = e0 / (nx - 1), i0 = e0 % (nx - 1);
-        if (vis_h[(size_t)r0 * (nx - 1) + i0]) continue;
-        int i = i0, r = r0, d = 0;
+        int e = cand[c];  // a +x edge: horizontal id
+        if (visited[e]) continue;
         long long steps = 0;
         for (;;) {
-            uint8_t* mark;
-            if (d == 0) mark = &vis_h[(size_t)r * (nx - 1) + i];
-            else if (d == 2) mark = &vis_h[(size_t)r * (nx - 1) + i - 1];
-            else if (d == 1) mark = &vis_v[(size_t)r * nx + i];
-            else mark = &vis_v[(size_t)(r - 1) * nx + i];
-            if (*mark) break;
-            *mark = 1;
-            // the edge from (i, r) in direction d
-            int ib = i + kDXI[d], rb = r + kDETA[d];
-            size_t A = (size_t)r * nx + i, B = (size_t)rb * nx + ib;
-            double m1 = 0.5 * (g.beta1[A] + g.beta1[B]), m2 = 0.5 * (g.beta2[A] + g.beta2[B]);
-            double nm = sqrt(m1 * m1 + m2 * m2);
-            if (!(nm > 0.0)) {
-                atomicOr(status, kErrGeom);
-                nseeds[fam] = 0;
-                return;
-            }
-            double vx = fam == 0 ? m1 / nm : m2 / nm, vy = fam == 0 ? m2 / nm : -m1 / nm;
-            double nxo = (double)kDETA[d], nyo = (double)(-kDXI[d]);
-            double len = (d & 1) ? g.hy : g.hx;
-            double w = -(nxo * vx + nyo * vy) * len;
-            if (w > 0.0) {
-                while ((k + 0.5) * g.hs < cum + w) {
-                    double phi = ((k + 0.5) * g.hs - cum) / w;
-                    if (ns < cap) {
-                        sx[ns] = i + phi * kDXI[d];  // index coordinates
-                        sy[ns] = r + phi * kDETA[d];
-                    }
-                    ns++;
-                    k++;
-                }
-                cum += w;
-            }
-            i = ib;
-            r = rb;
-            int nd = -1;
-            int pref[3] = {(d + 1) & 3, d, (d + 3) & 3};
-            for (int q = 0; q < 3; ++q)
-                if (out_edge(g, i, r, pref[q])) {
-                    nd = pref[q];
-                    break;
-                }
-            if (nd < 0 || ++steps > total + 4) break;
-            d = nd;
+            if (visited[e]) break;
+            visited[e] = 1;
+            if (pos < total) order[pos] = e;
+            pos++;
+            const int nxt = succ[e];
+            if (nxt < 0 || ++steps > total + 4) break;
+            e = nxt;
         }
     }
-    if (ns > cap) {
-        atomicOr(status, kErrCapacity);
-        ns = cap;
+    *norder = pos < total ? pos : (int)total;
+}
+
+// inflow weight of every walked edge, for both families ([fam][pos])
+__global__ void k_bnd_weight(GridView g, const int* order, const int* norder, const int* info,
+                             double* w, int cap_order, int* status)
+{
+    const int n = *norder;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n <= 0 || t >= 2LL * n) return;
+    const int fam = (int)(t / n), pos = (int)(t % n);
+    const int in = info[order[pos]];
+    const int d = in & 3, v = in >> 2, r = v / g.nx, i = v % g.nx;
+    const int ib = i + kDXI[d], rb = r + kDETA[d];
+    const size_t A = (size_t)r * g.nx + i, B = (size_t)rb * g.nx + ib;
+    const double m1 = 0.5 * (g.beta1[A] + g.beta1[B]), m2 = 0.5 * (g.beta2[A] + g.beta2[B]);
+    const double nm = sqrt(m1 * m1 + m2 * m2);
+    if (!(nm > 0.0)) {
+        atomicOr(status, kErrGeom);
+        w[(size_t)fam * cap_order + pos] = 0.0;
+        return;
     }
-    nseeds[fam] = ns;
+    const double vx = fam == 0 ? m1 / nm : m2 / nm, vy = fam == 0 ? m2 / nm : -m1 / nm;
+    const double nxo = (double)kDETA[d], nyo = (double)(-kDXI[d]);
+    const double len = (d & 1) ? g.hy : g.hx;
+    w[(size_t)fam * cap_order + pos] = -(nxo * vx + nyo * vy) * len;
+}
+
+// the running measure in walk order, one thread per family: the first seed
+// index of every edge (kf[n] = total) and the measure before it
+__global__ void k_bnd_scan(GridView g, const int* norder, const double* w, int cap_order,
+                           long long* kf, double* cb)
+{
+    const int fam = threadIdx.x;
+    if (fam > 1) return;
+    const int n = *norder;
+    const double* wf = w + (size_t)fam * cap_order;
+    long long* kff = kf + (size_t)fam * (cap_order + 1);
+    double* cbf = cb + (size_t)fam * cap_order;
+    double cum = 0.0;
+    long long k = 0;
+    for (int pos = 0; pos < n; ++pos) {
+        const double wv = wf[pos];
+        kff[pos] = k;
+        cbf[pos] = cum;
+        if (wv > 0.0) {
+            while ((k + 0.5) * g.hs < cum + wv) k++;
+            cum += wv;
+        }
+    }
+    kff[n] = k;
+}
+
+// the seeds (index coordinates) of every edge, in parallel ([fam][pos])
+__global__ void k_bnd_emit(GridView g, const int* order, const int* norder, const int* info,
+                           const double* w, const long long* kf, const double* cb, int cap_order,
+                           double* sx_all, double* sy_all, int cap, int* nseeds, int* status)
+{
+    const int n = *norder;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n <= 0 || t >= 2LL * n) return;
+    const int fam = (int)(t / n), pos = (int)(t % n);
+    const long long* kff = kf + (size_t)fam * (cap_order + 1);
+    const double wv = w[(size_t)fam * cap_order + pos], cum = cb[(size_t)fam * cap_order + pos];
+    const int in = info[order[pos]];
+    const int d = in & 3, v = in >> 2, r = v / g.nx, i = v % g.nx;
+    for (long long k = kff[pos]; k < kff[pos + 1]; ++k) {
+        if (k >= cap) break;
+        const double phi = ((k + 0.5) * g.hs - cum) / wv;
+        sx_all[(size_t)fam * cap + k] = i + phi * kDXI[d];
+        sy_all[(size_t)fam * cap + k] = r + phi * kDETA[d];
+    }
+    if (pos == 0) {
+        const long long ns = kff[n];
+        if (ns > cap) atomicOr(status, kErrCapacity);
+        nseeds[fam] = (int)(ns > cap ? cap : ns);
+    }
 }
 
 // Accepted RK4 points of the traced curves, kept so that the node placement
@@ -1116,16 +1210,31 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
     k_row_cand_fill<<<blocks_for(ny, 64), 64, 0, st>>>(g, rs, cand);
     double hmax = p->gv.hx > p->gv.hy ? p->gv.hx : p->gv.hy;
     int cap = (int)(nbe * ceil(hmax / p->gv.hs)) + 4;
-    size_t nh = (size_t)ny * (nx - 1), nv = (size_t)nx * (ny - 1);
-    uint8_t *vh, *vv;
-    TRY(alloc_tmp(tg.v, &vh, 2 * nh));
-    TRY(alloc_tmp(tg.v, &vv, 2 * nv));
-    ADR_CUDA_TRY(cudaMemsetAsync(vh, 0, 2 * nh, st));
-    ADR_CUDA_TRY(cudaMemsetAsync(vv, 0, 2 * nv, st));
+    const long long ne = (long long)ny * (nx - 1) + (long long)nx * (ny - 1);
+    int *info, *succ, *order, *norder;
+    uint8_t* visited;
+    TRY(alloc_tmp(tg.v, &info, ne));
+    TRY(alloc_tmp(tg.v, &succ, ne));
+    TRY(alloc_tmp(tg.v, &visited, ne));
+    TRY(alloc_tmp(tg.v, &order, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg.v, &norder, 1));
+    ADR_CUDA_TRY(cudaMemsetAsync(visited, 0, ne, st));
+    const int cap_order = nbe + 1;
+    double *w, *cb;
+    long long* kf;
+    TRY(alloc_tmp(tg.v, &w, 2 * (size_t)cap_order));
+    TRY(alloc_tmp(tg.v, &cb, 2 * (size_t)cap_order));
+    TRY(alloc_tmp(tg.v, &kf, 2 * ((size_t)cap_order + 1)));
     double *sx, *sy;
     TRY(alloc_tmp(tg.v, &sx, 2 * (size_t)cap));
     TRY(alloc_tmp(tg.v, &sy, 2 * (size_t)cap));
-    k_seeds<<<2, 32, 0, st>>>(g, cand, ncand, vh, vv, nbe, sx, sy, cap, cnt + 1, status_d);
+    k_bnd_succ<<<blocks_for(ne), kThreads, 0, st>>>(g, info, succ);
+    k_bnd_walk<<<1, 32, 0, st>>>(g, cand, ncand, succ, visited, nbe, order, norder);
+    k_bnd_weight<<<blocks_for(2LL * nbe), kThreads, 0, st>>>(g, order, norder, info, w, cap_order,
+                                                           status_d);
+    k_bnd_scan<<<1, 32, 0, st>>>(g, norder, w, cap_order, kf, cb);
+    k_bnd_emit<<<blocks_for(2LL * nbe), kThreads, 0, st>>>(g, order, norder, info, w, kf, cb, cap_order,
+                                                         sx, sy, cap, cnt + 1, status_d);
     int ns[2] = {0, 0};
     ADR_CUDA_TRY(cudaMemcpyAsync(ns, cnt + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     ADR_CUDA_TRY(cudaStreamSynchronize(st));
