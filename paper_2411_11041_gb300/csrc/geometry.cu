@@ -67,11 +67,38 @@ __device__ double bilin(const GridView& g, const double* a, double xi, double et
            ly * lx * p22;
 }
 
+// beta1 and beta2 bilinear at one point: bilin's cell, local coordinates,
+// weights and sums, with the cell and the four weights computed once for the
+// two fields (the same values, bit for bit, as two calls of bilin).  The
+// traces are chains of dependent FP64 operations, each of which costs tens of
+// cycles, so every operation taken off a stage shortens them.
+__device__ __forceinline__ void bilin_beta(const GridView& g, double xi, double eta, double* b1,
+                                           double* b2)
+{
+    int i = __double2int_rd(xi), r = __double2int_rd(eta);  // (int)floor, one conversion
+    if (i > g.nx - 2) i = g.nx - 2;
+    if (i < 0) i = 0;
+    if (r > g.ny - 2) r = g.ny - 2;
+    if (r < 0) r = 0;
+    const double lx = xi - i, ly = eta - r;
+    const double ax = 1.0 - lx, ay = 1.0 - ly;
+    const double w11 = ay * ax, w12 = ay * lx, w21 = ly * ax, w22 = ly * lx;
+    const size_t o = (size_t)r * g.nx + i;
+    const double* p = g.beta1 + o;
+    const double* q = g.beta2 + o;
+    const double p11 = p[0], p12 = p[1], p21 = p[g.nx], p22 = p[g.nx + 1];
+    const double q11 = q[0], q12 = q[1], q21 = q[g.nx], q22 = q[g.nx + 1];
+    *b1 = w11 * p11 + w12 * p12 + w21 * p21 + w22 * p22;
+    *b2 = w11 * q11 + w12 * q12 + w21 * q21 + w22 * q22;
+}
+
 // physical unit direction of family fam at the index coordinates (xi, eta):
 // b (B) or p (G), §3
-__device__ int direction(const GridView& g, int fam, double xi, double eta, double* dx, double* dy)
+__device__ __forceinline__ int direction(const GridView& g, int fam, double xi, double eta,
+                                         double* dx, double* dy)
 {
-    double b1 = bilin(g, g.beta1, xi, eta), b2 = bilin(g, g.beta2, xi, eta);
+    double b1, b2;
+    bilin_beta(g, xi, eta, &b1, &b2);
     double nb = sqrt(b1 * b1 + b2 * b2);
     if (!(nb > 0.0)) return -1;
     if (fam == 0) {
@@ -132,18 +159,36 @@ __global__ void k_ntype(GridView g, uint8_t* ntype, int* counts /* [0] interior,
     if (t != kOutside) atomicMin(&counts[2], (int)k);  // first node of Omega_h
 }
 
-// field checks over Omega_h: finite data, |beta| > 0, constant field, max |beta|
+// field checks over Omega_h: finite data, |beta| > 0, constant field, max |beta|;
+// each block reduces its nodes first and issues one atomic per result
 __global__ void k_fields(GridView g, int first, int* status, int* nonconst,
                          unsigned long long* bmax_bits)
 {
+    __shared__ unsigned long long smax[kThreads / 32];
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k >= (long long)g.nx * g.ny) return;
-    if (g.ntype[k] == kOutside) return;
-    double b1 = g.beta1[k], b2 = g.beta2[k];
-    double nb = sqrt(b1 * b1 + b2 * b2);
-    if (!(nb > 0.0) || !isfinite(nb) || !isfinite(g.f[k])) atomicOr(status, kErrInvalid);
-    if (b1 != g.beta1[first] || b2 != g.beta2[first]) atomicOr(nonconst, 1);
-    if (isfinite(nb)) atomicMax(bmax_bits, (unsigned long long)__double_as_longlong(nb));
+    int bad = 0, nc = 0;
+    unsigned long long bm = 0;  // bits of |beta| >= 0 order like the values
+    if (k < (long long)g.nx * g.ny && g.ntype[k] != kOutside) {
+        double b1 = g.beta1[k], b2 = g.beta2[k];
+        double nb = sqrt(b1 * b1 + b2 * b2);
+        bad = !(nb > 0.0) || !isfinite(nb) || !isfinite(g.f[k]);
+        nc = b1 != g.beta1[first] || b2 != g.beta2[first];
+        if (isfinite(nb)) bm = (unsigned long long)__double_as_longlong(nb);
+    }
+    bad = __syncthreads_or(bad);
+    nc = __syncthreads_or(nc);
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, bm, o);
+        bm = v > bm ? v : bm;
+    }
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = bm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) bm = smax[w] > bm ? smax[w] : bm;
+        if (bad) atomicOr(status, kErrInvalid);
+        if (nc) atomicOr(nonconst, 1);
+        if (bm) atomicMax(bmax_bits, bm);
+    }
 }
 
 // -------------------------------------------------- straight curve families
@@ -413,10 +458,11 @@ __global__ void k_row_cand_fill(GridView g, const long long* start, int* cand)
 // measure max(0, -n . dir(mid)) |e|, and a seed goes where the running measure
 // reaches (k + 1/2) h_s.  The walk is split so that only the running sum is
 // serial: every boundary edge's successor is found in parallel (the walk's
-// turn rule is local), one thread follows the successors, the weights are
-// computed in parallel, one thread per family accumulates them in walk order
-// (the same sums and comparisons, so the seeds are bit-identical), and the
-// seeds are written in parallel.
+// turn rule is local), the boundary edges get compact ids, one thread follows
+// the successors in shared memory, the weights are computed in parallel, one
+// warp per family accumulates them in walk order (the same sums, so the seeds
+// are bit-identical), every edge's first seed index follows from the sums in
+// parallel, and the seeds are written in parallel.
 //
 // Boundary edges carry undirected ids: the horizontal edge (i, r)-(i+1, r) is
 // r (nx-1) + i, the vertical edge (i, r)-(i, r+1) is nh + r nx + i.
@@ -476,27 +522,96 @@ __global__ void k_bnd_succ(GridView g, int* info, int* succ)
     succ[e] = nxt;
 }
 
-// the walk: one thread follows the successors, loop after loop
-__global__ void k_bnd_walk(GridView g, const int* cand, long long ncand, const int* succ,
-                           uint8_t* visited, long long total, int* order, int* norder)
+// compact ids of the boundary edges (in any order: only the walk and the
+// kernels after it use them, through cinfo); one atomic per warp
+__global__ void k_bnd_compact(long long ne, const int* info, int* cid, int* cinfo, int* cedge,
+                              int* nb, int cap)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int pos = 0;
-    for (long long c = 0; c < ncand; ++c) {
-        int e = cand[c];  // a +x edge: horizontal id
-        if (visited[e]) continue;
-        long long steps = 0;
-        for (;;) {
-            if (visited[e]) break;
-            visited[e] = 1;
-            if (pos < total) order[pos] = e;
-            pos++;
-            const int nxt = succ[e];
-            if (nxt < 0 || ++steps > total + 4) break;
-            e = nxt;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int in = e < ne ? info[e] : -1;
+    const unsigned m = __ballot_sync(0xffffffffu, in >= 0);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(nb, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (in >= 0) {
+        const int id = base + __popc(m & ((1u << lane) - 1u));
+        if (id < cap) {
+            cid[e] = id;
+            cinfo[id] = in;
+            cedge[id] = (int)e;
         }
     }
-    *norder = pos < total ? pos : (int)total;
+}
+
+// the successor of every boundary edge as a compact id (-1: none)
+__global__ void k_bnd_csucc(const int* nbp, const int* cedge, const int* succ, const int* cid,
+                            int* csucc, int cap)
+{
+    const int nb = *nbp;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb || t >= cap) return;
+    const int s = succ[cedge[t]];
+    const int c = s >= 0 ? cid[s] : -1;
+    csucc[t] = c >= 0 && c < nb && c < cap ? c : -1;
+}
+
+// The walk, over compact ids: loop after loop, each from the first unvisited
+// candidate in candidate order, following the successors until an edge comes
+// round again.  The successors and the visited flags sit in shared memory when
+// they fit (use_smem), else in global memory.  Warp 0 runs it: the lanes test
+// 32 candidates at a time, lane 0 follows the successors.
+__global__ void k_bnd_walk(const int* cand, long long ncand, const int* cid, const int* nbp,
+                           const int* csucc, uint8_t* cvis, int use_smem, int smem_cap,
+                           long long total, int* order, int* norder)
+{
+    extern __shared__ int walk_sm[];
+    const int nb = *nbp;
+    const int* S = csucc;
+    uint8_t* V = cvis;
+    if (use_smem && nb <= smem_cap) {
+        int* sS = walk_sm;
+        uint8_t* sV = reinterpret_cast<uint8_t*>(walk_sm + smem_cap);
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            sS[t] = csucc[t];
+            sV[t] = 0;
+        }
+        __syncthreads();
+        S = sS;
+        V = sV;
+    }
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int pos = 0;
+    for (long long c0 = 0; c0 < ncand; c0 += 32) {
+        const long long c = c0 + lane;
+        int e = c < ncand ? cid[cand[c]] : -1;
+        if (e >= nb) e = -1;
+        unsigned m = __ballot_sync(0xffffffffu, e >= 0 && !V[e]);
+        while (m) {
+            const int j = __ffs(m) - 1;
+            const int start = __shfl_sync(0xffffffffu, e, j);
+            if (lane == 0) {
+                int x = start;
+                long long steps = 0;
+                int sx = S[x], vx = V[x];  // the successor and the flag of x, fetched together
+                for (;;) {
+                    if (vx) break;
+                    V[x] = 1;
+                    if (pos < total) order[pos] = x;
+                    pos++;
+                    if (sx < 0 || ++steps > total + 4) break;
+                    x = sx;
+                    sx = S[x];
+                    vx = V[x];
+                }
+            }
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            __syncwarp();
+            m = __ballot_sync(0xffffffffu, lane > j && e >= 0 && !V[e]);
+        }
+    }
+    if (lane == 0) *norder = pos < total ? pos : (int)total;
 }
 
 // inflow weight of every walked edge, for both families ([fam][pos])
@@ -524,29 +639,65 @@ __global__ void k_bnd_weight(GridView g, const int* order, const int* norder, co
     w[(size_t)fam * cap_order + pos] = -(nxo * vx + nyo * vy) * len;
 }
 
-// the running measure in walk order, one thread per family: the first seed
-// index of every edge (kf[n] = total) and the measure before it
-__global__ void k_bnd_scan(GridView g, const int* norder, const double* w, int cap_order,
-                           long long* kf, double* cb)
+// the running inflow measure in walk order, one warp per family: cb[pos] is
+// the measure before edge pos and cb[n] the total, the sum taken edge by edge
+// in walk order.  The lanes fetch the next 32 weights while every lane runs
+// the same serial sum over the current 32; lane t keeps the value before
+// edge base + t for a coalesced store.
+__global__ void k_bnd_scan(const int* norder, const double* w, int cap_order, double* cb)
 {
-    const int fam = threadIdx.x;
+    const int fam = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (fam > 1) return;
     const int n = *norder;
     const double* wf = w + (size_t)fam * cap_order;
-    long long* kff = kf + (size_t)fam * (cap_order + 1);
-    double* cbf = cb + (size_t)fam * cap_order;
+    double* cbf = cb + (size_t)fam * (cap_order + 1);
     double cum = 0.0;
-    long long k = 0;
-    for (int pos = 0; pos < n; ++pos) {
-        const double wv = wf[pos];
-        kff[pos] = k;
-        cbf[pos] = cum;
-        if (wv > 0.0) {
-            while ((k + 0.5) * g.hs < cum + wv) k++;
-            cum += wv;
+    double wn = lane < n ? wf[lane] : 0.0;
+    for (int base = 0; base < n; base += 32) {
+        const double wl = wn;
+        wn = base + 32 + lane < n ? wf[base + 32 + lane] : 0.0;
+        double mine = 0.0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const double wv = __shfl_sync(0xffffffffu, wl, j);
+            if (lane == j) mine = cum;
+            if (wv > 0.0) cum += wv;  // past n the weights are 0
         }
+        if (base + lane < n) cbf[base + lane] = mine;
     }
-    kff[n] = k;
+    if (lane == 0) cbf[n] = cum;
+}
+
+// seed level of index k, (k + 1/2) h_s
+__device__ __forceinline__ double seed_level(const GridView& g, long long k)
+{
+    return (k + 0.5) * g.hs;
+}
+
+// The first seed index of every edge, kf[pos] (kf[n] = seeds in all): the
+// smallest k >= 0 whose level is not below cb[pos].  Raising k edge by edge
+// while the level is below cum + w gives the same k: the measure never
+// decreases and the level rises with k, so each edge's k is the smallest one
+// for the measure after it.
+__global__ void k_bnd_kidx(GridView g, const int* norder, const double* cb, int cap_order,
+                           long long* kf, int* status)
+{
+    const int n = *norder;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n < 0 || t >= 2LL * (n + 1)) return;
+    const int fam = (int)(t / (n + 1)), pos = (int)(t % (n + 1));
+    const double X = cb[(size_t)fam * (cap_order + 1) + pos];
+    long long k = 0;
+    if (!isfinite(X)) {
+        atomicOr(status, kErrGeom);
+    } else if (seed_level(g, 0) < X) {
+        const double e = ceil(X / g.hs - 0.5);
+        k = e > 0.0 ? (long long)e : 0;
+        for (int it = 0; it < 8 && k > 0 && seed_level(g, k - 1) >= X; ++it) k--;
+        for (int it = 0; it < 8 && seed_level(g, k) < X; ++it) k++;
+        if ((k > 0 && seed_level(g, k - 1) >= X) || seed_level(g, k) < X) atomicOr(status, kErrGeom);
+    }
+    kf[(size_t)fam * (cap_order + 1) + pos] = k;
 }
 
 // the seeds (index coordinates) of every edge, in parallel ([fam][pos])
@@ -559,7 +710,8 @@ __global__ void k_bnd_emit(GridView g, const int* order, const int* norder, cons
     if (n <= 0 || t >= 2LL * n) return;
     const int fam = (int)(t / n), pos = (int)(t % n);
     const long long* kff = kf + (size_t)fam * (cap_order + 1);
-    const double wv = w[(size_t)fam * cap_order + pos], cum = cb[(size_t)fam * cap_order + pos];
+    const double wv = w[(size_t)fam * cap_order + pos];
+    const double cum = cb[(size_t)fam * (cap_order + 1) + pos];
     const int in = info[order[pos]];
     const int d = in & 3, v = in >> 2, r = v / g.nx, i = v % g.nx;
     for (long long k = kff[pos]; k < kff[pos + 1]; ++k) {
@@ -1211,30 +1363,56 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
     double hmax = p->gv.hx > p->gv.hy ? p->gv.hx : p->gv.hy;
     int cap = (int)(nbe * ceil(hmax / p->gv.hs)) + 4;
     const long long ne = (long long)ny * (nx - 1) + (long long)nx * (ny - 1);
-    int *info, *succ, *order, *norder;
-    uint8_t* visited;
+    int *info, *succ, *cid, *order, *norder;
     TRY(alloc_tmp(tg.v, &info, ne));
     TRY(alloc_tmp(tg.v, &succ, ne));
-    TRY(alloc_tmp(tg.v, &visited, ne));
+    TRY(alloc_tmp(tg.v, &cid, ne));
     TRY(alloc_tmp(tg.v, &order, (size_t)nbe + 1));
     TRY(alloc_tmp(tg.v, &norder, 1));
-    ADR_CUDA_TRY(cudaMemsetAsync(visited, 0, ne, st));
+    ADR_CUDA_TRY(cudaMemsetAsync(cid, 0xff, ne * sizeof(int), st));
+    // compact boundary edges: info, global id, successor, visited flag
+    int *cinfo, *cedge, *csucc, *nbc;
+    uint8_t* cvis;
+    TRY(alloc_tmp(tg.v, &cinfo, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg.v, &cedge, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg.v, &csucc, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg.v, &cvis, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg.v, &nbc, 1));
+    ADR_CUDA_TRY(cudaMemsetAsync(cvis, 0, (size_t)nbe + 1, st));
+    ADR_CUDA_TRY(cudaMemsetAsync(nbc, 0, sizeof(int), st));
     const int cap_order = nbe + 1;
     double *w, *cb;
     long long* kf;
     TRY(alloc_tmp(tg.v, &w, 2 * (size_t)cap_order));
-    TRY(alloc_tmp(tg.v, &cb, 2 * (size_t)cap_order));
+    TRY(alloc_tmp(tg.v, &cb, 2 * ((size_t)cap_order + 1)));
     TRY(alloc_tmp(tg.v, &kf, 2 * ((size_t)cap_order + 1)));
     double *sx, *sy;
     TRY(alloc_tmp(tg.v, &sx, 2 * (size_t)cap));
     TRY(alloc_tmp(tg.v, &sy, 2 * (size_t)cap));
+    // the walk keeps successors and flags (5 bytes an edge) in shared memory
+    // when they fit in a block's opt-in limit
+    int dev = 0, smem_max = 0;
+    ADR_CUDA_TRY(cudaGetDevice(&dev));
+    ADR_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t walk_smem = (size_t)nbe * 5 + 16;
+    const int use_smem = nbe > 0 && walk_smem <= (size_t)smem_max;
+    if (use_smem)
+        ADR_CUDA_TRY(cudaFuncSetAttribute(k_bnd_walk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)walk_smem));
     k_bnd_succ<<<blocks_for(ne), kThreads, 0, st>>>(g, info, succ);
-    k_bnd_walk<<<1, 32, 0, st>>>(g, cand, ncand, succ, visited, nbe, order, norder);
-    k_bnd_weight<<<blocks_for(2LL * nbe), kThreads, 0, st>>>(g, order, norder, info, w, cap_order,
+    k_bnd_compact<<<blocks_for(ne), kThreads, 0, st>>>(ne, info, cid, cinfo, cedge, nbc,
+                                                             nbe + 1);
+    k_bnd_csucc<<<blocks_for((long long)nbe + 1), kThreads, 0, st>>>(nbc, cedge, succ, cid, csucc,
+                                                                      nbe + 1);
+    k_bnd_walk<<<1, 1024, use_smem ? walk_smem : 0, st>>>(cand, ncand, cid, nbc, csucc, cvis,
+                                                          use_smem, nbe, nbe, order, norder);
+    k_bnd_weight<<<blocks_for(2LL * nbe), kThreads, 0, st>>>(g, order, norder, cinfo, w, cap_order,
                                                            status_d);
-    k_bnd_scan<<<1, 32, 0, st>>>(g, norder, w, cap_order, kf, cb);
-    k_bnd_emit<<<blocks_for(2LL * nbe), kThreads, 0, st>>>(g, order, norder, info, w, kf, cb, cap_order,
-                                                         sx, sy, cap, cnt + 1, status_d);
+    k_bnd_scan<<<1, 64, 0, st>>>(norder, w, cap_order, cb);
+    k_bnd_kidx<<<blocks_for(2LL * (nbe + 2)), kThreads, 0, st>>>(g, norder, cb, cap_order, kf,
+                                                               status_d);
+    k_bnd_emit<<<blocks_for(2LL * nbe), kThreads, 0, st>>>(g, order, norder, cinfo, w, kf, cb,
+                                                         cap_order, sx, sy, cap, cnt + 1, status_d);
     int ns[2] = {0, 0};
     ADR_CUDA_TRY(cudaMemcpyAsync(ns, cnt + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     ADR_CUDA_TRY(cudaStreamSynchronize(st));
