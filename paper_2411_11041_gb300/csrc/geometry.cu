@@ -742,60 +742,6 @@ struct PointPool {
     unsigned int n_chunks;
 };
 
-// trace one curve: number of full RK4 steps M, length L and exit point; the
-// accepted points P_1 .. P_M go to the pool when it has room
-__device__ int trace_len(const GridView& g, int fam, double X, double Y, int* Mout, double* L,
-                         double* Xe, double* Ye, const PointPool& pool, int slot)
-{
-    double ds = g.hs / kTraceStepsPerH;
-    const double sx = ds / g.hx, sy = ds / g.hy;  // the step in index units
-    double cap_len = 10.0 * 2.0 * (g.W + g.H);
-    long long npts = 0;
-    bool keep = pool.n_chunks > 0;
-    int* tab = pool.tab + (size_t)slot * kPoolMaxChunks;
-    int chunk = -1;
-    if (keep) pool.stored[slot] = 0;
-    for (;;) {
-        npts++;
-        double Xn, Yn;
-        if (rk4(g, fam, X, Y, sx, sy, &Xn, &Yn)) return -1;
-        if (interior_point(g, snap(Xn), snap(Yn))) {
-            X = Xn;
-            Y = Yn;
-            if (keep) {  // P_q, q = npts, at pool index q - 1 of the curve
-                long long i = npts - 1;
-                int c = (int)(i / kPoolChunk), o = (int)(i % kPoolChunk);
-                if (o == 0) {
-                    unsigned int got = c < kPoolMaxChunks ? atomicAdd(pool.next, 1u) : pool.n_chunks;
-                    if (got >= pool.n_chunks) keep = false;
-                    else {
-                        chunk = (int)got;
-                        tab[c] = chunk;
-                    }
-                }
-                if (keep) pool.pts[(size_t)chunk * kPoolChunk + o] = make_double2(X, Y);
-            }
-            if (npts * ds > cap_len) return -1;
-            continue;
-        }
-        double lo = 0.0, hi = 1.0;
-        for (int it = 0; it < kBisectIters; ++it) {
-            double mid = 0.5 * (lo + hi);
-            if (rk4(g, fam, X, Y, mid * sx, mid * sy, &Xn, &Yn)) return -1;
-            if (interior_point(g, snap(Xn), snap(Yn))) lo = mid;
-            else hi = mid;
-        }
-        double XE = X, YE = Y;
-        if (lo > 0.0 && rk4(g, fam, X, Y, lo * sx, lo * sy, &XE, &YE)) return -1;
-        *Mout = (int)(npts - 1);
-        *L = (npts - 1) * ds + lo * ds;
-        *Xe = XE;
-        *Ye = YE;
-        if (keep) pool.stored[slot] = 1;
-        return 0;
-    }
-}
-
 // seed t of the combined launch: family 0 takes t < nseeds[0], family 1 the
 // rest; per-seed arrays of family f live at offset f*cap
 __device__ __forceinline__ bool seed_of(const int* nseeds, int cap, int t, int* fam, int* s)
@@ -813,20 +759,108 @@ __device__ __forceinline__ bool seed_of(const int* nseeds, int cap, int t, int* 
     return false;
 }
 
-__global__ void k_trace_count(GridView g, int cap, const double* sx, const double* sy,
+// Trace every curve: number of full RK4 steps M, length L and exit point; the
+// accepted points P_1 .. P_M go to the pool when it has room.  A curve takes
+// full RK4 steps while their end points lie inside Omega_h, then locates its
+// exit within the first step that leaves by kBisectIters bisections of that
+// step, then takes the partial step found.  Each lane runs this as a state
+// machine, and every pass of the warp's loop makes one RK4 step per lane
+// (a full step, a bisection trial or the final partial step): the same steps
+// with the same arguments as tracing each curve alone.  An FP64 warp
+// instruction costs the same whatever the number of active lanes, so a lane
+// that bisected on a branch of its own would add its 61 steps to the warp's
+// time, once for every curve of the warp.
+__global__ void k_trace_count(GridView g, int cap, const double* sx0, const double* sy0,
                               const int* nseeds, int* M, double* L, double* XE, double* YE,
                               long long* cn, int* status, PointPool pool)
 {
-    int fam, s;
-    if (!seed_of(nseeds, cap, blockIdx.x * blockDim.x + threadIdx.x, &fam, &s)) return;
+    int fam = 0, s = 0;
+    const bool have = seed_of(nseeds, cap, blockIdx.x * blockDim.x + threadIdx.x, &fam, &s);
+    const double ds = g.hs / kTraceStepsPerH;
+    const double sx = ds / g.hx, sy = ds / g.hy;  // the step in index units
+    const double cap_len = 10.0 * 2.0 * (g.W + g.H);
+    double X = have ? sx0[s] : 0.0, Y = have ? sy0[s] : 0.0;
+    double lo = 0.0, hi = 1.0, xe = 0.0, ye = 0.0;
+    long long npts = 0;
+    enum { kStep, kBisect, kFinal, kDone, kFailed };
+    int phase = have ? kStep : kDone, it = 0;
+    bool keep = have && pool.n_chunks > 0;
+    int* tab = pool.tab + (size_t)s * kPoolMaxChunks;
+    int chunk = -1;
+    if (keep) pool.stored[s] = 0;
+    while (__any_sync(0xffffffffu, phase < kDone)) {
+        if (phase >= kDone) continue;
+        const double mid = 0.5 * (lo + hi);
+        double tx = sx, ty = sy;
+        if (phase == kBisect) {
+            tx = mid * sx;
+            ty = mid * sy;
+        } else if (phase == kFinal) {
+            tx = lo * sx;
+            ty = lo * sy;
+        }
+        if (phase == kStep) npts++;
+        double Xn, Yn;
+        if (rk4(g, fam, X, Y, tx, ty, &Xn, &Yn)) {
+            phase = kFailed;
+            continue;
+        }
+        if (phase == kFinal) {
+            xe = Xn;
+            ye = Yn;
+            phase = kDone;
+            continue;
+        }
+        const bool inside = interior_point(g, snap(Xn), snap(Yn));
+        if (phase == kStep) {
+            if (inside) {
+                X = Xn;
+                Y = Yn;
+                if (keep) {  // P_q, q = npts, at pool index q - 1 of the curve
+                    long long i = npts - 1;
+                    int c = (int)(i / kPoolChunk), o = (int)(i % kPoolChunk);
+                    if (o == 0) {
+                        unsigned int got = c < kPoolMaxChunks ? atomicAdd(pool.next, 1u) : pool.n_chunks;
+                        if (got >= pool.n_chunks) keep = false;
+                        else {
+                            chunk = (int)got;
+                            tab[c] = chunk;
+                        }
+                    }
+                    if (keep) pool.pts[(size_t)chunk * kPoolChunk + o] = make_double2(X, Y);
+                }
+                if (npts * ds > cap_len) phase = kFailed;
+            } else {
+                phase = kBisect;
+                lo = 0.0;
+                hi = 1.0;
+                it = 0;
+            }
+        } else {  // kBisect
+            if (inside) lo = mid;
+            else hi = mid;
+            if (++it == kBisectIters) {
+                if (lo > 0.0) {
+                    phase = kFinal;
+                } else {
+                    xe = X;
+                    ye = Y;
+                    phase = kDone;
+                }
+            }
+        }
+    }
+    if (!have) return;
     int m = 0;
-    double len = 0, xe = 0, ye = 0;
-    if (trace_len(g, fam, sx[s], sy[s], &m, &len, &xe, &ye, pool, s)) {
+    double len = 0.0;
+    if (phase == kDone) {
+        m = (int)(npts - 1);
+        len = (npts - 1) * ds + lo * ds;
+        if (keep) pool.stored[s] = 1;
+    } else {
         atomicOr(status, kErrGeom);
-        m = 0;
-        len = 0.0;
-        xe = sx[s];
-        ye = sy[s];
+        xe = sx0[s];
+        ye = sy0[s];
     }
     M[s] = m;
     L[s] = len;

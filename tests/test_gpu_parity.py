@@ -41,6 +41,18 @@ def _const(n, beta, mask="square", mu=0.1, sigma=1.0, nx=None, seed=0):
     return W.Problem(nx, n, mu, sigma, np.full((n, nx), beta[0]), np.full((n, nx), beta[1]), f, m)
 
 
+def _perforated(n, every):
+    """Sheared flow on the square with a mask-0 node every `every` nodes: one
+    2 x 2-cell hole around each, so one boundary loop per hole.  The inflow
+    walk keeps its successor table in shared memory up to about 46 000
+    boundary edges and in global memory beyond."""
+    p = W.sheared(n=n)
+    m = p.mask.copy()
+    idx = np.arange(every // 2, n - 1, every)
+    m[np.ix_(idx, idx)] = 0
+    return W.Problem(n, n, p.mu, p.sigma, p.beta1, p.beta2, p.f, m, name=f"perforated{n}")
+
+
 PROBLEMS = {
     "manufactured33": lambda: W.manufactured(n=33),
     "aligned17": lambda: W.manufactured(n=17, beta=(1.0, 0.0)),
@@ -52,6 +64,8 @@ PROBLEMS = {
     "sheared65": lambda: W.sheared(n=65),
     "data2d": lambda: W.data2d(33),
     "tiny3": lambda: _const(3, (1.0, 0.5)),
+    "perforated129": lambda: _perforated(129, 8),  # 2 560 boundary edges, 257 loops
+    "perforated401": lambda: _perforated(401, 4),  # 81 600 boundary edges
 }
 
 
