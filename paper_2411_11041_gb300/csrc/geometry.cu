@@ -759,49 +759,122 @@ __device__ __forceinline__ bool seed_of(const int* nseeds, int cap, int t, int* 
     return false;
 }
 
+// Two warps trace each 32 curves: lane l of warp 0 and lane l of warp 1 work
+// on the same curve.  Warp 0 computes the x halves of every RK4 stage (beta1
+// at the stage point, the x component of the direction, the x coordinate),
+// warp 1 the y halves, and the two trade what the other half needs through
+// shared memory: the cell index and local coordinate, then the field value,
+// at every stage, and the new point with its interior-test halves at every
+// step.  An FP64 warp instruction holds its sub-partition's FP64 unit for
+// about 64 cycles, and the two warps run on different sub-partitions, so a
+// stage's chain is about a third shorter.  Every value comes from the same
+// operations as in rk4, direction and interior_point, so the points are the
+// same.  All lanes of both warps reach every barrier: a lane whose curve is
+// done computes on its last point and drops the result.
+struct Trade {
+    double a, b;
+    int i, j, k;
+};
+
+// publish this warp's values for the lane, read the other warp's; the buffer
+// alternates, so that one barrier per trade suffices
+__device__ __forceinline__ Trade trade(Trade (*buf)[2][32], int& nb, int w, int lane, Trade mine)
+{
+    buf[nb][w][lane] = mine;
+    __syncthreads();
+    Trade o = buf[nb][w ^ 1][lane];
+    nb ^= 1;
+    return o;
+}
+
+// this warp's direction component at the stage point whose own coordinate is
+// c (the other warp holds the other coordinate); bad is raised where |beta|
+// is not positive (direction's failure)
+__device__ __forceinline__ double half_direction(const GridView& g, int w, int fam, double c,
+                                                 Trade (*buf)[2][32], int& nb, int lane, bool& bad)
+{
+    const int lim = w == 0 ? g.nx - 2 : g.ny - 2;
+    int q = __double2int_rd(c);
+    if (q > lim) q = lim;
+    if (q < 0) q = 0;
+    const double l = c - q, a = 1.0 - l;
+    const Trade t = trade(buf, nb, w, lane, Trade{l, a, q, 0, 0});
+    const int i = w == 0 ? q : t.i, r = w == 0 ? t.i : q;
+    const double lx = w == 0 ? l : t.a, ax = w == 0 ? a : t.b;
+    const double ly = w == 0 ? t.a : l, ay = w == 0 ? t.b : a;
+    const double w11 = ay * ax, w12 = ay * lx, w21 = ly * ax, w22 = ly * lx;
+    const double* p = (w == 0 ? g.beta1 : g.beta2) + ((size_t)r * g.nx + i);
+    const double v = w11 * p[0] + w12 * p[1] + w21 * p[g.nx] + w22 * p[g.nx + 1];
+    const Trade u = trade(buf, nb, w, lane, Trade{v, 0.0, 0, 0, 0});
+    const double b1 = w == 0 ? v : u.a, b2 = w == 0 ? u.a : v;
+    const double nrm = sqrt(b1 * b1 + b2 * b2);
+    if (!(nrm > 0.0)) bad = true;
+    const double num = w == 0 ? (fam == 0 ? b1 : b2) : (fam == 0 ? b2 : -b1);
+    return num / nrm;
+}
+
+// this warp's coordinate after one classical RK4 step of step component st
+__device__ __forceinline__ double half_rk4(const GridView& g, int w, int fam, double c, double st,
+                                           Trade (*buf)[2][32], int& nb, int lane, bool& bad)
+{
+    const double k1 = half_direction(g, w, fam, c, buf, nb, lane, bad);
+    const double k2 = half_direction(g, w, fam, c + 0.5 * st * k1, buf, nb, lane, bad);
+    const double k3 = half_direction(g, w, fam, c + 0.5 * st * k2, buf, nb, lane, bad);
+    const double k4 = half_direction(g, w, fam, c + st * k3, buf, nb, lane, bad);
+    return c + st / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+}
+
 // Trace every curve: number of full RK4 steps M, length L and exit point; the
 // accepted points P_1 .. P_M go to the pool when it has room.  A curve takes
 // full RK4 steps while their end points lie inside Omega_h, then locates its
 // exit within the first step that leaves by kBisectIters bisections of that
 // step, then takes the partial step found.  Each lane runs this as a state
-// machine, and every pass of the warp's loop makes one RK4 step per lane
-// (a full step, a bisection trial or the final partial step): the same steps
-// with the same arguments as tracing each curve alone.  An FP64 warp
-// instruction costs the same whatever the number of active lanes, so a lane
-// that bisected on a branch of its own would add its 61 steps to the warp's
-// time, once for every curve of the warp.
-__global__ void k_trace_count(GridView g, int cap, const double* sx0, const double* sy0,
-                              const int* nseeds, int* M, double* L, double* XE, double* YE,
-                              long long* cn, int* status, PointPool pool)
+// machine, and every pass of the loop makes one RK4 step per lane (a full
+// step, a bisection trial or the final partial step): the same steps with the
+// same arguments as tracing each curve alone.  A lane that bisected on a
+// branch of its own would add its 61 steps to the warp's time, once for every
+// curve of the warp.
+__global__ void __launch_bounds__(64) k_trace_count(GridView g, int cap, const double* sx0,
+                                                    const double* sy0, const int* nseeds, int* M,
+                                                    double* L, double* XE, double* YE,
+                                                    long long* cn, int* status, PointPool pool)
 {
+    __shared__ Trade buf[2][2][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int fam = 0, s = 0;
-    const bool have = seed_of(nseeds, cap, blockIdx.x * blockDim.x + threadIdx.x, &fam, &s);
+    const bool have = seed_of(nseeds, cap, blockIdx.x * 32 + lane, &fam, &s);
     const double ds = g.hs / kTraceStepsPerH;
     const double sx = ds / g.hx, sy = ds / g.hy;  // the step in index units
+    const double stp = w == 0 ? sx : sy;          // this warp's component
+    const double lim = w == 0 ? (double)g.nx : (double)g.ny;
     const double cap_len = 10.0 * 2.0 * (g.W + g.H);
     double X = have ? sx0[s] : 0.0, Y = have ? sy0[s] : 0.0;
     double lo = 0.0, hi = 1.0, xe = 0.0, ye = 0.0;
     long long npts = 0;
     enum { kStep, kBisect, kFinal, kDone, kFailed };
-    int phase = have ? kStep : kDone, it = 0;
-    bool keep = have && pool.n_chunks > 0;
+    int phase = have ? kStep : kDone, it = 0, nb = 0;
+    bool keep = w == 0 && have && pool.n_chunks > 0;  // warp 0 writes the pool
     int* tab = pool.tab + (size_t)s * kPoolMaxChunks;
     int chunk = -1;
     if (keep) pool.stored[s] = 0;
     while (__any_sync(0xffffffffu, phase < kDone)) {
-        if (phase >= kDone) continue;
+        const bool act = phase < kDone;
         const double mid = 0.5 * (lo + hi);
-        double tx = sx, ty = sy;
-        if (phase == kBisect) {
-            tx = mid * sx;
-            ty = mid * sy;
-        } else if (phase == kFinal) {
-            tx = lo * sx;
-            ty = lo * sy;
-        }
-        if (phase == kStep) npts++;
-        double Xn, Yn;
-        if (rk4(g, fam, X, Y, tx, ty, &Xn, &Yn)) {
+        double st = stp;
+        if (phase == kBisect) st = mid * stp;
+        else if (phase == kFinal) st = lo * stp;
+        if (act && phase == kStep) npts++;
+        bool bad = false;
+        const double c = half_rk4(g, w, fam, w == 0 ? X : Y, st, buf, nb, lane, bad);
+        // this half of interior_point(snap(Xn), snap(Yn)), then the other's
+        const double cs = snap(c);
+        const bool ok = isfinite(cs) && !(cs < -1.0) && !(cs > lim);
+        const double fc = floor(cs);
+        const int q1 = ok ? (int)fc : 0, q0 = ok && cs == fc ? q1 - 1 : q1;
+        const Trade t = trade(buf, nb, w, lane, Trade{c, 0.0, q0, q1, ok ? 1 : 0});
+        if (!act) continue;
+        const double Xn = w == 0 ? c : t.a, Yn = w == 0 ? t.a : c;
+        if (bad) {
             phase = kFailed;
             continue;
         }
@@ -811,20 +884,30 @@ __global__ void k_trace_count(GridView g, int cap, const double* sx0, const doub
             phase = kDone;
             continue;
         }
-        const bool inside = interior_point(g, snap(Xn), snap(Yn));
+        bool inside = ok && t.k;
+        if (inside) {
+            const int i0 = w == 0 ? q0 : t.i, i1 = w == 0 ? q1 : t.j;
+            const int r0 = w == 0 ? t.i : q0, r1 = w == 0 ? t.j : q1;
+            for (int r = r0; r <= r1 && inside; ++r)
+                for (int i = i0; i <= i1; ++i)
+                    if (!cell_on(g, i, r)) {
+                        inside = false;
+                        break;
+                    }
+        }
         if (phase == kStep) {
             if (inside) {
                 X = Xn;
                 Y = Yn;
                 if (keep) {  // P_q, q = npts, at pool index q - 1 of the curve
                     long long i = npts - 1;
-                    int c = (int)(i / kPoolChunk), o = (int)(i % kPoolChunk);
+                    int c2 = (int)(i / kPoolChunk), o = (int)(i % kPoolChunk);
                     if (o == 0) {
-                        unsigned int got = c < kPoolMaxChunks ? atomicAdd(pool.next, 1u) : pool.n_chunks;
+                        unsigned int got = c2 < kPoolMaxChunks ? atomicAdd(pool.next, 1u) : pool.n_chunks;
                         if (got >= pool.n_chunks) keep = false;
                         else {
                             chunk = (int)got;
-                            tab[c] = chunk;
+                            tab[c2] = chunk;
                         }
                     }
                     if (keep) pool.pts[(size_t)chunk * kPoolChunk + o] = make_double2(X, Y);
@@ -850,7 +933,7 @@ __global__ void k_trace_count(GridView g, int cap, const double* sx0, const doub
             }
         }
     }
-    if (!have) return;
+    if (!have || w != 0) return;
     int m = 0;
     double len = 0.0;
     if (phase == kDone) {
@@ -1489,8 +1572,8 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
             ADR_CUDA_TRY(cudaMemsetAsync(pool.next, 0, sizeof(unsigned int), st));
         }
     }
-    // one warp per SM and FP64 pipe: the per-curve traces are serial chains
-    k_trace_count<<<blocks_for(tot, 32), 32, 0, st>>>(g, cap, sx, sy, cnt + 1, M, L, XE, YE, cn,
+    // 32 curves per block of two warps: the per-curve traces are serial chains
+    k_trace_count<<<blocks_for(tot, 32), 64, 0, st>>>(g, cap, sx, sy, cnt + 1, M, L, XE, YE, cn,
                                                       status_d, pool);
     k_scan<<<1, 1024, 0, st>>>(cn, on, ns[0]);
     k_scan<<<1, 1024, 0, st>>>(cn + cap, on + cap, ns[1]);
