@@ -367,9 +367,10 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
 
 // curve solve of one work item (block size T, curves[0 .. BS/T-1], reduced-
 // system constants Lc); the whole block calls it
-template <int BS, int FAM>
+template <int BS, int FAM, bool SU = false>
 __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, const int* curves,
-                                                 const double* Lc, double (*sR)[BS])
+                                                 const double* Lc, double (*sR)[BS],
+                                                 double* sU = nullptr)
 {
     constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
     const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
@@ -411,7 +412,8 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
                 }
                 rpp = fma(-__ldg(a.fac + 3 * NS + sl), rpp, r);
                 rp[j] = rpp;
-                ur[j] = u1;
+                if (SU) sU[j * BS + tid] = u1;
+                else ur[j] = u1;
                 u0 = u1;
                 u1 = u2;
             }
@@ -450,7 +452,7 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
         if (j < cnt) {
             const int sl = so32 + j * T + lt;
             if (j < cnt - 1) x = rp[j] - __ldg(cpP + sl) * x - __ldg(vpP + sl) * Gm;
-            v[base + s + j + 1] = (paper ? 0.0 : ur[j]) + w * x;
+            v[base + s + j + 1] = (paper ? 0.0 : (SU ? sU[j * BS + tid] : ur[j])) + w * x;
         }
     }
     if (b.active && n >= 2 && lt == 0) {
@@ -465,8 +467,10 @@ __global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item
 {
     if (a.state && a.state->done) return;
     __shared__ double sR[2][BS];
-    curve_solve_body<BS, FAM>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
-                              lanec + (size_t)blockIdx.x * Items<BS>::NF * BS, sR);
+    constexpr bool SU = BS <= 512;  // the gathered row values in shared memory
+    __shared__ double sU[SU ? kCmax * BS : 1];
+    curve_solve_body<BS, FAM, SU>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
+                                  lanec + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sU);
 }
 
 // ----------------------------------------------- FP32 solve + FP64 refinement
