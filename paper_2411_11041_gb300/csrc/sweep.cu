@@ -367,7 +367,11 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
 
 // curve solve of one work item (block size T, curves[0 .. BS/T-1], reduced-
 // system constants Lc); the whole block calls it
-template <int BS, int FAM, bool SU = false>
+// SU: the gathered row values live in shared memory (sU, kCmax * BS) instead
+// of registers; PF: the reduction's factors are loaded a level ahead.  Both
+// trade registers for latency; the persistent batch kernels, which hold more
+// state, run faster without them.
+template <int BS, int FAM, bool SU = false, bool PF = false>
 __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, const int* curves,
                                                  const double* Lc, double (*sR)[BS],
                                                  double* sU = nullptr)
@@ -424,24 +428,60 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
 #pragma unroll
     for (int j = kCmax - 2; j >= 0; --j)
         if (j <= cnt - 2) rho = rp[j] - __ldg(cpP + so32 + j * T + lt) * rho;
-    sR[0][tid] = rho;
-    __syncthreads();
-    double rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.0;
-    double R = cnt > 0 ? rpp - Lc[tid] * rhoN : 0.0;
+    double R, G;
     int buf = 1;
-#pragma unroll
-    for (int l = 0; l < LMAX; ++l) {
-        const int d = 1 << l;
-        sR[buf][tid] = R;
-        __syncthreads();
-        if (l < L) {
-            double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
-            double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
-            R = R - Lc[(1 + l) * BS + tid] * Rm - Lc[(1 + LMAX + l) * BS + tid] * Rp;
+    if (PF) {
+        // the reduction's factors are loaded a level ahead, so that each load
+        // is in flight while the block waits at the barrier before it is used
+        const double lc0 = Lc[tid];
+        double k1n = 0.0, k2n = 0.0;
+        if (L > 0) {
+            k1n = Lc[BS + tid];
+            k2n = Lc[(1 + LMAX) * BS + tid];
         }
-        buf ^= 1;
+        sR[0][tid] = rho;
+        __syncthreads();
+        double rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.0;
+        R = cnt > 0 ? rpp - lc0 * rhoN : 0.0;
+        double ib = 0.0;
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l) {
+            const int d = 1 << l;
+            const double k1 = k1n, k2 = k2n;
+            if (l + 1 < L) {
+                k1n = Lc[(2 + l) * BS + tid];
+                k2n = Lc[(2 + LMAX + l) * BS + tid];
+            }
+            if (l + 1 == LMAX) ib = Lc[(NF - 1) * BS + tid];
+            sR[buf][tid] = R;
+            __syncthreads();
+            if (l < L) {
+                double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
+                double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
+                R = R - k1 * Rm - k2 * Rp;
+            }
+            buf ^= 1;
+        }
+        G = R * ib;
+    } else {
+        sR[0][tid] = rho;
+        __syncthreads();
+        double rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.0;
+        R = cnt > 0 ? rpp - Lc[tid] * rhoN : 0.0;
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l) {
+            const int d = 1 << l;
+            sR[buf][tid] = R;
+            __syncthreads();
+            if (l < L) {
+                double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
+                double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
+                R = R - Lc[(1 + l) * BS + tid] * Rm - Lc[(1 + LMAX + l) * BS + tid] * Rp;
+            }
+            buf ^= 1;
+        }
+        G = R * Lc[(NF - 1) * BS + tid];
     }
-    double G = R * Lc[(NF - 1) * BS + tid];
     sR[buf][tid] = G;
     __syncthreads();
     double Gm = lt > 0 ? sR[buf][tid - 1] : 0.0;
@@ -469,8 +509,9 @@ __global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item
     __shared__ double sR[2][BS];
     constexpr bool SU = BS <= 512;  // the gathered row values in shared memory
     __shared__ double sU[SU ? kCmax * BS : 1];
-    curve_solve_body<BS, FAM, SU>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
-                                  lanec + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sU);
+    curve_solve_body<BS, FAM, SU, true>(a, item_T[blockIdx.x],
+                                        item_curve + blockIdx.x * Items<BS>::MAXC,
+                                        lanec + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sU);
 }
 
 // ----------------------------------------------- FP32 solve + FP64 refinement
