@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item
 // one FP32 pass of the partitioned elimination over the calling thread's rows;
 // every thread of the block must call it (it synchronises); returns in x the
 // thread's solution rows and in *gprev the previous thread's last unknown
-template <int BS>
+template <int BS, bool PF = false>
 __device__ __forceinline__ void elim32(const float (&rhs)[kCmax], float (&x)[kCmax], int cnt,
                                        int so32, int T, int lt, int L, const float* __restrict__ f32,
                                        size_t NS, const float* __restrict__ L32, float (*sR)[BS],
@@ -550,19 +550,49 @@ __device__ __forceinline__ void elim32(const float (&rhs)[kCmax], float (&x)[kCm
     float rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.f;
     float R = cnt > 0 ? rpp - L32[tid] * rhoN : 0.f;
     int buf = 1;
-#pragma unroll
-    for (int l = 0; l < LMAX; ++l) {
-        const int d = 1 << l;
-        sR[buf][tid] = R;
-        __syncthreads();
-        if (l < L) {
-            float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
-            float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
-            R = R - L32[(1 + l) * BS + tid] * Rm - L32[(1 + LMAX + l) * BS + tid] * Rp;
+    float G;
+    if (PF) {
+        // factors a level ahead, in flight during the barrier (as in the
+        // FP64 solve)
+        float k1n = 0.f, k2n = 0.f, ib = 0.f;
+        if (L > 0) {
+            k1n = L32[BS + tid];
+            k2n = L32[(1 + LMAX) * BS + tid];
         }
-        buf ^= 1;
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l) {
+            const int d = 1 << l;
+            const float k1 = k1n, k2 = k2n;
+            if (l + 1 < L) {
+                k1n = L32[(2 + l) * BS + tid];
+                k2n = L32[(2 + LMAX + l) * BS + tid];
+            }
+            if (l + 1 == LMAX) ib = L32[(NF - 1) * BS + tid];
+            sR[buf][tid] = R;
+            __syncthreads();
+            if (l < L) {
+                float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
+                float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
+                R = R - k1 * Rm - k2 * Rp;
+            }
+            buf ^= 1;
+        }
+        G = R * ib;
+    } else {
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l) {
+            const int d = 1 << l;
+            sR[buf][tid] = R;
+            __syncthreads();
+            if (l < L) {
+                float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
+                float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
+                R = R - L32[(1 + l) * BS + tid] * Rm - L32[(1 + LMAX + l) * BS + tid] * Rp;
+            }
+            buf ^= 1;
+        }
+        G = R * L32[(NF - 1) * BS + tid];
     }
-    float G = R * L32[(NF - 1) * BS + tid];
     sR[buf][tid] = G;
     __syncthreads();
     float Gm = lt > 0 ? sR[buf][tid - 1] : 0.f;
@@ -579,7 +609,7 @@ __device__ __forceinline__ void elim32(const float (&rhs)[kCmax], float (&x)[kCm
     }
 }
 
-template <int BS, int FAM>
+template <int BS, int FAM, bool PF = false>
 __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Titem,
                                                      const int* curves, const float* L32,
                                                      float (*sR)[BS], double* sX)
@@ -630,7 +660,7 @@ __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Tit
         }
     }
     float x0[kCmax], x1[kCmax], g0;
-    elim32<BS>(r32, x0, cnt, so32, T, lt, L, a.fac32, NS, L32, sR, &g0);
+    elim32<BS, PF>(r32, x0, cnt, so32, T, lt, L, a.fac32, NS, L32, sR, &g0);
     // neighbours of the chunk in x0: x_{s-1} = g0 (previous thread), x_e from the next thread
     sX[tid] = cnt > 0 ? (double)x0[0] : 0.0;
     __syncthreads();
@@ -664,7 +694,7 @@ __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Tit
             }
         }
     }
-    elim32<BS>(r32, x1, cnt, so32, T, lt, L, a.fac32, NS, L32, sR, &g0);
+    elim32<BS, PF>(r32, x1, cnt, so32, T, lt, L, a.fac32, NS, L32, sR, &g0);
     const double w = paper ? 1.0 : a.dt;
 #pragma unroll
     for (int j = 0; j < kCmax; ++j)
@@ -682,7 +712,7 @@ __global__ void __launch_bounds__(BS) k_curve_solve_ref(CurveArgs a, const int* 
     if (a.state && a.state->done) return;
     __shared__ float sR[2][BS];
     __shared__ double sX[BS];
-    curve_solve_ref_body<BS, FAM>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
+    curve_solve_ref_body<BS, FAM, true>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
                                   lanec32 + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sX);
 }
 
