@@ -133,13 +133,28 @@ adr_status cuda_fail(cudaError_t e, const char* what);
         if (_e != cudaSuccess) return ::adr::cuda_fail(_e, #call); \
     } while (0)
 
-// free a buffer owned by the problem (NULL is a no-op)
+// The library's stream-ordered memory pool on the current device (api.cu).
+// Problem buffers and setup temporaries come from it and go back to it; it
+// keeps up to kPoolKeepBytes of freed memory mapped, so that creating and
+// destroying problems does not map and unmap device memory every time.
+// NULL when no pool could be made (the device's default pool is used then).
+constexpr unsigned long long kPoolKeepBytes = 8ull << 30;
+cudaMemPool_t device_pool();
+
+// stream-ordered allocation of n bytes from the library's pool
+inline cudaError_t pool_alloc(void** q, size_t n, cudaStream_t st)
+{
+    cudaMemPool_t pool = device_pool();
+    return pool ? cudaMallocFromPoolAsync(q, n, pool, st) : cudaMallocAsync(q, n, st);
+}
+
+// free a buffer owned by the problem (NULL is a no-op), in stream order
 inline void dev_free(Problem* p, void* ptr)
 {
     if (!ptr) return;
     for (size_t i = 0; i < p->owned.size(); ++i)
         if (p->owned[i] == ptr) {
-            cudaFree(ptr);
+            cudaFreeAsync(ptr, p->stream);
             p->owned.erase(p->owned.begin() + i);
             return;
         }
@@ -149,10 +164,10 @@ template <typename T>
 adr_status dev_alloc(Problem* p, T** ptr, size_t count)
 {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    cudaError_t e = pool_alloc(&q, count * sizeof(T) + 16, p->stream);
     if (e != cudaSuccess) {
         *ptr = nullptr;
-        set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        set_error(std::string("device allocation failed: ") + cudaGetErrorString(e));
         return ADR_ENOMEM;
     }
     p->owned.push_back(q);

@@ -5,6 +5,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -16,6 +18,32 @@ namespace adr {
 static thread_local std::string g_err;
 
 void set_error(const std::string& msg) { g_err = msg; }
+
+cudaMemPool_t device_pool()
+{
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;
+    } else {
+        unsigned long long keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pools[dev] = pool;
+    return pool;
+}
 
 adr_status cuda_fail(cudaError_t e, const char* what)
 {
@@ -332,9 +360,10 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
     for (int fam = 0; fam < 2; ++fam) {
         std::vector<int>& off = h->offs[fam];
         off.resize(p->fam[fam].n_lines + 1);
-        if ((e = cudaMemcpy(off.data(), p->fam[fam].off, off.size() * sizeof(int),
-                            cudaMemcpyDeviceToHost)))
-            return fail(cuda_fail(e, "cudaMemcpy"));
+        if ((e = cudaMemcpyAsync(off.data(), p->fam[fam].off, off.size() * sizeof(int),
+                                 cudaMemcpyDeviceToHost, p->stream)) ||
+            (e = cudaStreamSynchronize(p->stream)))
+            return fail(cuda_fail(e, "cudaMemcpyAsync"));
         double u = 0;
         for (int l = 0; l < p->fam[fam].n_lines; ++l) u += std::max(0, off[l + 1] - off[l] - 2);
         h->line_unknowns[fam] = u;
@@ -351,10 +380,11 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
 void adr_destroy(adr_problem* h)
 {
     if (!h) return;
-    if (h->p.stream) cudaStreamSynchronize(h->p.stream);
-    else cudaDeviceSynchronize();
+    // a batch may still use the buffers on its own stream
+    cudaDeviceSynchronize();
     drop_graph(h);
-    for (void* q : h->p.owned) cudaFree(q);
+    for (void* q : h->p.owned) cudaFreeAsync(q, h->p.stream);
+    cudaStreamSynchronize(h->p.stream);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

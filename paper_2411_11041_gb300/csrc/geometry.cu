@@ -1315,27 +1315,30 @@ __global__ void k_reverse_hist(const int* hist, long long* rev, int maxlen)
     rev[k] = hist[maxlen - k];
 }
 
+// setup temporaries: stream-ordered from the library's pool, freed in stream
+// order when the guard goes out of scope
+struct TmpGuard {
+    std::vector<void*> v;
+    cudaStream_t st = nullptr;
+    ~TmpGuard()
+    {
+        for (void* q : v) cudaFreeAsync(q, st);
+    }
+};
+
 template <typename T>
-adr_status alloc_tmp(std::vector<void*>& tmp, T** p, size_t n)
+adr_status alloc_tmp(TmpGuard& tg, T** p, size_t n)
 {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 16);
+    cudaError_t e = pool_alloc(&q, n * sizeof(T) + 16, tg.st);
     if (e != cudaSuccess) {
-        set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        set_error(std::string("device allocation failed: ") + cudaGetErrorString(e));
         return ADR_ENOMEM;
     }
-    tmp.push_back(q);
+    tg.v.push_back(q);
     *p = static_cast<T*>(q);
     return ADR_OK;
 }
-
-struct TmpGuard {
-    std::vector<void*> v;
-    ~TmpGuard()
-    {
-        for (void* q : v) cudaFree(q);
-    }
-};
 
 #define TRY(x)                         \
     do {                               \
@@ -1361,8 +1364,8 @@ adr_status finish_family(Problem* p, int fam, TmpGuard& tg, int* status_d)
                                                           F.fval);
     int* lon;
     int* maxlen;
-    TRY(alloc_tmp(tg.v, &lon, F.n_nodes + 1));
-    TRY(alloc_tmp(tg.v, &maxlen, 1));
+    TRY(alloc_tmp(tg, &lon, F.n_nodes + 1));
+    TRY(alloc_tmp(tg, &maxlen, 1));
     ADR_CUDA_TRY(cudaMemsetAsync(maxlen, 0, sizeof(int), st));
     k_line_of_node<<<blocks_for(F.n_lines), kThreads, 0, st>>>(F.n_lines, F.off, lon, maxlen);
     ADR_CUDA_TRY(cudaMemcpyAsync(&F.max_nodes, maxlen, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1371,9 +1374,9 @@ adr_status finish_family(Problem* p, int fam, TmpGuard& tg, int* status_d)
     int ml = F.max_nodes;
     int* hist;
     long long *rev, *start;
-    TRY(alloc_tmp(tg.v, &hist, ml + 1));
-    TRY(alloc_tmp(tg.v, &rev, ml + 2));
-    TRY(alloc_tmp(tg.v, &start, ml + 2));
+    TRY(alloc_tmp(tg, &hist, ml + 1));
+    TRY(alloc_tmp(tg, &rev, ml + 2));
+    TRY(alloc_tmp(tg, &start, ml + 2));
     ADR_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (ml + 1), st));
     k_len_hist<<<blocks_for(F.n_lines), kThreads, 0, st>>>(F.n_lines, F.off, hist);
     k_reverse_hist<<<blocks_for(ml + 1), kThreads, 0, st>>>(hist, rev, ml);
@@ -1382,18 +1385,18 @@ adr_status finish_family(Problem* p, int fam, TmpGuard& tg, int* status_d)
     // crossing slots
     size_t nr = (size_t)p->grid.ny * (p->grid.nx - 1), nc = (size_t)p->grid.nx * (p->grid.ny - 1);
     Slots R, C;
-    TRY(alloc_tmp(tg.v, &R.minpos, nr));
-    TRY(alloc_tmp(tg.v, &R.maxpos, nr));
-    TRY(alloc_tmp(tg.v, &R.ming, nr));
-    TRY(alloc_tmp(tg.v, &R.maxg, nr));
-    TRY(alloc_tmp(tg.v, &R.mint, nr));
-    TRY(alloc_tmp(tg.v, &R.maxt, nr));
-    TRY(alloc_tmp(tg.v, &C.minpos, nc));
-    TRY(alloc_tmp(tg.v, &C.maxpos, nc));
-    TRY(alloc_tmp(tg.v, &C.ming, nc));
-    TRY(alloc_tmp(tg.v, &C.maxg, nc));
-    TRY(alloc_tmp(tg.v, &C.mint, nc));
-    TRY(alloc_tmp(tg.v, &C.maxt, nc));
+    TRY(alloc_tmp(tg, &R.minpos, nr));
+    TRY(alloc_tmp(tg, &R.maxpos, nr));
+    TRY(alloc_tmp(tg, &R.ming, nr));
+    TRY(alloc_tmp(tg, &R.maxg, nr));
+    TRY(alloc_tmp(tg, &R.mint, nr));
+    TRY(alloc_tmp(tg, &R.maxt, nr));
+    TRY(alloc_tmp(tg, &C.minpos, nc));
+    TRY(alloc_tmp(tg, &C.maxpos, nc));
+    TRY(alloc_tmp(tg, &C.ming, nc));
+    TRY(alloc_tmp(tg, &C.maxg, nc));
+    TRY(alloc_tmp(tg, &C.mint, nc));
+    TRY(alloc_tmp(tg, &C.maxt, nc));
     k_slots_init<<<blocks_for((long long)nr), kThreads, 0, st>>>(R, nr);
     k_slots_init<<<blocks_for((long long)nc), kThreads, 0, st>>>(C, nc);
     int nb = blocks_for(F.n_nodes);
@@ -1414,7 +1417,7 @@ adr_status build_straight(Problem* p, int fam, int first, TmpGuard& tg)
     Family& F = p->fam[fam];
     cudaStream_t st = p->stream;
     LineParams* P;
-    TRY(alloc_tmp(tg.v, &P, 1));
+    TRY(alloc_tmp(tg, &P, 1));
     k_line_params<<<1, 1, 0, st>>>(p->gv, fam, first, P);
     LineParams hp;
     ADR_CUDA_TRY(cudaMemcpyAsync(&hp, P, sizeof hp, cudaMemcpyDeviceToHost, st));
@@ -1425,10 +1428,10 @@ adr_status build_straight(Problem* p, int fam, int first, TmpGuard& tg)
         return ADR_EGEOM;
     }
     long long *cl, *cn, *ol, *on;
-    TRY(alloc_tmp(tg.v, &cl, nk));
-    TRY(alloc_tmp(tg.v, &cn, nk));
-    TRY(alloc_tmp(tg.v, &ol, nk + 1));
-    TRY(alloc_tmp(tg.v, &on, nk + 1));
+    TRY(alloc_tmp(tg, &cl, nk));
+    TRY(alloc_tmp(tg, &cn, nk));
+    TRY(alloc_tmp(tg, &ol, nk + 1));
+    TRY(alloc_tmp(tg, &on, nk + 1));
     k_straight_count<<<blocks_for(nk, 64), 64, 0, st>>>(p->gv, P, cl, cn);
     k_scan<<<1, 1024, 0, st>>>(cl, ol, nk);
     k_scan<<<1, 1024, 0, st>>>(cn, on, nk);
@@ -1460,13 +1463,13 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
     const GridView& g = p->gv;
     int nx = p->grid.nx, ny = p->grid.ny;
     int* cnt;  // [0] boundary edges, [1..2] seeds per family
-    TRY(alloc_tmp(tg.v, &cnt, 3));
+    TRY(alloc_tmp(tg, &cnt, 3));
     ADR_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(int), st));
     k_count_bedges<<<blocks_for((long long)nx * ny), kThreads, 0, st>>>(g, cnt);
     // loop-start candidates in (row, column) order
     long long *rc, *rs;
-    TRY(alloc_tmp(tg.v, &rc, ny));
-    TRY(alloc_tmp(tg.v, &rs, ny + 1));
+    TRY(alloc_tmp(tg, &rc, ny));
+    TRY(alloc_tmp(tg, &rs, ny + 1));
     k_row_cand_count<<<blocks_for(ny, 64), 64, 0, st>>>(g, rc);
     k_scan<<<1, 1024, 0, st>>>(rc, rs, ny);
     int nbe = 0;
@@ -1475,37 +1478,37 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
     ADR_CUDA_TRY(cudaMemcpyAsync(&ncand, rs + ny, sizeof ncand, cudaMemcpyDeviceToHost, st));
     ADR_CUDA_TRY(cudaStreamSynchronize(st));
     int* cand;
-    TRY(alloc_tmp(tg.v, &cand, ncand + 1));
+    TRY(alloc_tmp(tg, &cand, ncand + 1));
     k_row_cand_fill<<<blocks_for(ny, 64), 64, 0, st>>>(g, rs, cand);
     double hmax = p->gv.hx > p->gv.hy ? p->gv.hx : p->gv.hy;
     int cap = (int)(nbe * ceil(hmax / p->gv.hs)) + 4;
     const long long ne = (long long)ny * (nx - 1) + (long long)nx * (ny - 1);
     int *info, *succ, *cid, *order, *norder;
-    TRY(alloc_tmp(tg.v, &info, ne));
-    TRY(alloc_tmp(tg.v, &succ, ne));
-    TRY(alloc_tmp(tg.v, &cid, ne));
-    TRY(alloc_tmp(tg.v, &order, (size_t)nbe + 1));
-    TRY(alloc_tmp(tg.v, &norder, 1));
+    TRY(alloc_tmp(tg, &info, ne));
+    TRY(alloc_tmp(tg, &succ, ne));
+    TRY(alloc_tmp(tg, &cid, ne));
+    TRY(alloc_tmp(tg, &order, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg, &norder, 1));
     ADR_CUDA_TRY(cudaMemsetAsync(cid, 0xff, ne * sizeof(int), st));
     // compact boundary edges: info, global id, successor, visited flag
     int *cinfo, *cedge, *csucc, *nbc;
     uint8_t* cvis;
-    TRY(alloc_tmp(tg.v, &cinfo, (size_t)nbe + 1));
-    TRY(alloc_tmp(tg.v, &cedge, (size_t)nbe + 1));
-    TRY(alloc_tmp(tg.v, &csucc, (size_t)nbe + 1));
-    TRY(alloc_tmp(tg.v, &cvis, (size_t)nbe + 1));
-    TRY(alloc_tmp(tg.v, &nbc, 1));
+    TRY(alloc_tmp(tg, &cinfo, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg, &cedge, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg, &csucc, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg, &cvis, (size_t)nbe + 1));
+    TRY(alloc_tmp(tg, &nbc, 1));
     ADR_CUDA_TRY(cudaMemsetAsync(cvis, 0, (size_t)nbe + 1, st));
     ADR_CUDA_TRY(cudaMemsetAsync(nbc, 0, sizeof(int), st));
     const int cap_order = nbe + 1;
     double *w, *cb;
     long long* kf;
-    TRY(alloc_tmp(tg.v, &w, 2 * (size_t)cap_order));
-    TRY(alloc_tmp(tg.v, &cb, 2 * ((size_t)cap_order + 1)));
-    TRY(alloc_tmp(tg.v, &kf, 2 * ((size_t)cap_order + 1)));
+    TRY(alloc_tmp(tg, &w, 2 * (size_t)cap_order));
+    TRY(alloc_tmp(tg, &cb, 2 * ((size_t)cap_order + 1)));
+    TRY(alloc_tmp(tg, &kf, 2 * ((size_t)cap_order + 1)));
     double *sx, *sy;
-    TRY(alloc_tmp(tg.v, &sx, 2 * (size_t)cap));
-    TRY(alloc_tmp(tg.v, &sy, 2 * (size_t)cap));
+    TRY(alloc_tmp(tg, &sx, 2 * (size_t)cap));
+    TRY(alloc_tmp(tg, &sy, 2 * (size_t)cap));
     // the walk keeps successors and flags (5 bytes an edge) in shared memory
     // when they fit in a block's opt-in limit
     int dev = 0, smem_max = 0;
@@ -1541,12 +1544,12 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
     double *L, *XE, *YE;
     long long *cn, *on;
     size_t n2 = 2 * (size_t)cap;
-    TRY(alloc_tmp(tg.v, &M, n2));
-    TRY(alloc_tmp(tg.v, &L, n2));
-    TRY(alloc_tmp(tg.v, &XE, n2));
-    TRY(alloc_tmp(tg.v, &YE, n2));
-    TRY(alloc_tmp(tg.v, &cn, n2));
-    TRY(alloc_tmp(tg.v, &on, n2 + 2));
+    TRY(alloc_tmp(tg, &M, n2));
+    TRY(alloc_tmp(tg, &L, n2));
+    TRY(alloc_tmp(tg, &XE, n2));
+    TRY(alloc_tmp(tg, &YE, n2));
+    TRY(alloc_tmp(tg, &cn, n2));
+    TRY(alloc_tmp(tg, &on, n2 + 2));
     int tot = ns[0] + ns[1];
     // point pool: about kTraceStepsPerH^2 accepted points per hs^2 of the
     // domain in each family, with room to spare and one partial chunk per
@@ -1566,9 +1569,9 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
         } else {
             tg.v.push_back(q);
             pool.pts = static_cast<double2*>(q);
-            TRY(alloc_tmp(tg.v, &pool.tab, n2 * kPoolMaxChunks));
-            TRY(alloc_tmp(tg.v, &pool.stored, n2));
-            TRY(alloc_tmp(tg.v, &pool.next, 1));
+            TRY(alloc_tmp(tg, &pool.tab, n2 * kPoolMaxChunks));
+            TRY(alloc_tmp(tg, &pool.stored, n2));
+            TRY(alloc_tmp(tg, &pool.next, 1));
             ADR_CUDA_TRY(cudaMemsetAsync(pool.next, 0, sizeof(unsigned int), st));
         }
     }
@@ -1617,6 +1620,7 @@ adr_status build_geometry(Problem* p, const uint8_t* mask)
     int nx = p->grid.nx, ny = p->grid.ny;
     size_t N = (size_t)nx * ny, NC = (size_t)(nx - 1) * (ny - 1);
     TmpGuard tg;
+    tg.st = st;
     TRY(dev_alloc(p, &p->cell, NC));
     TRY(dev_alloc(p, &p->ntype, N));
     k_cells<<<blocks_for((long long)NC), kThreads, 0, st>>>(mask, nx, ny, p->cell);
@@ -1635,8 +1639,8 @@ adr_status build_geometry(Problem* p, const uint8_t* mask)
     g.f = p->f;
     int* info;  // [0] interior count, [1] status, [2] first node, [3] nonconst
     unsigned long long* bmax;
-    TRY(alloc_tmp(tg.v, &info, 4));
-    TRY(alloc_tmp(tg.v, &bmax, 1));
+    TRY(alloc_tmp(tg, &info, 4));
+    TRY(alloc_tmp(tg, &bmax, 1));
     int init[4] = {0, 0, 0x7fffffff, 0};
     ADR_CUDA_TRY(cudaMemcpyAsync(info, init, sizeof init, cudaMemcpyHostToDevice, st));
     ADR_CUDA_TRY(cudaMemsetAsync(bmax, 0, sizeof(unsigned long long), st));

@@ -1135,7 +1135,9 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
 {
     Family& F = p->fam[fam];
     std::vector<int> order(F.n_lines), Tof(F.n_lines);
-    ADR_CUDA_TRY(cudaMemcpy(order.data(), F.order, sizeof(int) * F.n_lines, cudaMemcpyDeviceToHost));
+    ADR_CUDA_TRY(cudaMemcpyAsync(order.data(), F.order, sizeof(int) * F.n_lines, cudaMemcpyDeviceToHost,
+                                 p->stream));
+    ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
     std::vector<int> byT[11];  // index log2(T)
     for (int l : order) {
         int m = off[l + 1] - off[l] - 2;
@@ -1167,7 +1169,9 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
     F.n_slots = (int)tot + 1;
     size_t NS = F.n_slots;
     TRY_S(dev_alloc(p, &F.soff, F.n_lines + 1));
-    ADR_CUDA_TRY(cudaMemcpy(F.soff, soff.data(), sizeof(int) * soff.size(), cudaMemcpyHostToDevice));
+    // buffers from the stream-ordered pool are written in the stream's order
+    ADR_CUDA_TRY(cudaMemcpyAsync(F.soff, soff.data(), sizeof(int) * soff.size(), cudaMemcpyHostToDevice,
+                                 p->stream));
     TRY_S(dev_alloc(p, &F.gcell, NS));
     TRY_S(dev_alloc(p, &F.gw, 4 * NS));
     TRY_S(dev_alloc(p, &F.fac, 4 * NS));
@@ -1200,8 +1204,10 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
         TRY_S(dev_alloc(p, &I.curve, (size_t)I.count * maxc));
         TRY_S(dev_alloc(p, &I.lanec, (size_t)I.count * nf * BS));
         if (p->opts.prec == ADR_FP32_REFINE) TRY_S(dev_alloc(p, &I.lanec32, (size_t)I.count * nf * BS));
-        ADR_CUDA_TRY(cudaMemcpy(I.T, iT.data(), sizeof(int) * iT.size(), cudaMemcpyHostToDevice));
-        ADR_CUDA_TRY(cudaMemcpy(I.curve, icv.data(), sizeof(int) * icv.size(), cudaMemcpyHostToDevice));
+        ADR_CUDA_TRY(cudaMemcpyAsync(I.T, iT.data(), sizeof(int) * iT.size(), cudaMemcpyHostToDevice,
+                                     p->stream));
+        ADR_CUDA_TRY(cudaMemcpyAsync(I.curve, icv.data(), sizeof(int) * icv.size(), cudaMemcpyHostToDevice,
+                                     p->stream));
         if (BS == 256) k_curve_gdesc<256><<<I.count, 256, 0, st>>>(a, I.T, I.curve);
         else if (BS == 512) k_curve_gdesc<512><<<I.count, 512, 0, st>>>(a, I.T, I.curve);
         else k_curve_gdesc<1024><<<I.count, 1024, 0, st>>>(a, I.T, I.curve);
