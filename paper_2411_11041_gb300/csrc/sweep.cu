@@ -741,7 +741,7 @@ struct ActiveLists {
 constexpr int kCountPerBuf = 7;
 
 template <int BS, int FAM, bool REF>
-__global__ void __launch_bounds__(BS) k_curve_solve_batch(const CurveArgs* __restrict__ table,
+__global__ void __launch_bounds__(BS, REF && BS == 256 ? 2 : 1) k_curve_solve_batch(const CurveArgs* __restrict__ table,
                                                           const BatchItem* __restrict__ items,
                                                           ActiveLists act, int set)
 {
