@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(BS, BS == 256 ? (REF ? 2 : 4) : 1) k_curve_sol
             curve_solve_ref_body<BS, FAM>(a, I.T, I.curves,
                                           a.lanec32s[set] + (size_t)I.local * Items<BS>::NF * BS, sRf, sX);
         else
-            curve_solve_body<BS, FAM, SU>(a, I.T, I.curves,
+            curve_solve_body<BS, FAM, SU, SU>(a, I.T, I.curves,
                                           a.lanecs[set] + (size_t)I.local * Items<BS>::NF * BS, sR, sU);
         __syncthreads();  // shared arrays are reused by the next item
     }
