@@ -368,9 +368,11 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
 // curve solve of one work item (block size T, curves[0 .. BS/T-1], reduced-
 // system constants Lc); the whole block calls it
 // SU: the gathered row values live in shared memory (sU, kCmax * BS) instead
-// of registers; PF: the reduction's factors are loaded a level ahead.  Both
-// trade registers for latency; the persistent batch kernels, which hold more
-// state, run faster without them.
+// of registers; PF: the reduction's factors are loaded a level ahead, so that
+// they are in flight during the barrier before each level.  The kernels that
+// use them are compiled for a register count that keeps enough blocks per SM
+// (measured: the single-problem kernels at BS <= 512 and the 256-thread
+// FP64 batch kernel).
 template <int BS, int FAM, bool SU = false, bool PF = false>
 __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, const int* curves,
                                                  const double* Lc, double (*sR)[BS],
