@@ -446,24 +446,26 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
         double rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.0;
         R = cnt > 0 ? rpp - lc0 * rhoN : 0.0;
         double ib = 0.0;
+        // L (levels of this item's curves) is the same for the whole block
 #pragma unroll
         for (int l = 0; l < LMAX; ++l) {
+            if (l >= L) break;
             const int d = 1 << l;
             const double k1 = k1n, k2 = k2n;
             if (l + 1 < L) {
                 k1n = Lc[(2 + l) * BS + tid];
                 k2n = Lc[(2 + LMAX + l) * BS + tid];
+            } else {
+                ib = Lc[(NF - 1) * BS + tid];
             }
-            if (l + 1 == LMAX) ib = Lc[(NF - 1) * BS + tid];
             sR[buf][tid] = R;
             __syncthreads();
-            if (l < L) {
-                double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
-                double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
-                R = R - k1 * Rm - k2 * Rp;
-            }
+            double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
+            double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
+            R = R - k1 * Rm - k2 * Rp;
             buf ^= 1;
         }
+        if (L == 0) ib = Lc[(NF - 1) * BS + tid];
         G = R * ib;
     } else {
         sR[0][tid] = rho;
@@ -472,14 +474,13 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
         R = cnt > 0 ? rpp - Lc[tid] * rhoN : 0.0;
 #pragma unroll
         for (int l = 0; l < LMAX; ++l) {
+            if (l >= L) break;  // uniform over the block
             const int d = 1 << l;
             sR[buf][tid] = R;
             __syncthreads();
-            if (l < L) {
-                double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
-                double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
-                R = R - Lc[(1 + l) * BS + tid] * Rm - Lc[(1 + LMAX + l) * BS + tid] * Rp;
-            }
+            double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
+            double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
+            R = R - Lc[(1 + l) * BS + tid] * Rm - Lc[(1 + LMAX + l) * BS + tid] * Rp;
             buf ^= 1;
         }
         G = R * Lc[(NF - 1) * BS + tid];
@@ -563,34 +564,34 @@ __device__ __forceinline__ void elim32(const float (&rhs)[kCmax], float (&x)[kCm
         }
 #pragma unroll
         for (int l = 0; l < LMAX; ++l) {
+            if (l >= L) break;  // uniform over the block
             const int d = 1 << l;
             const float k1 = k1n, k2 = k2n;
             if (l + 1 < L) {
                 k1n = L32[(2 + l) * BS + tid];
                 k2n = L32[(2 + LMAX + l) * BS + tid];
+            } else {
+                ib = L32[(NF - 1) * BS + tid];
             }
-            if (l + 1 == LMAX) ib = L32[(NF - 1) * BS + tid];
             sR[buf][tid] = R;
             __syncthreads();
-            if (l < L) {
-                float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
-                float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
-                R = R - k1 * Rm - k2 * Rp;
-            }
+            float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
+            float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
+            R = R - k1 * Rm - k2 * Rp;
             buf ^= 1;
         }
+        if (L == 0) ib = L32[(NF - 1) * BS + tid];
         G = R * ib;
     } else {
 #pragma unroll
         for (int l = 0; l < LMAX; ++l) {
+            if (l >= L) break;  // uniform over the block
             const int d = 1 << l;
             sR[buf][tid] = R;
             __syncthreads();
-            if (l < L) {
-                float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
-                float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
-                R = R - L32[(1 + l) * BS + tid] * Rm - L32[(1 + LMAX + l) * BS + tid] * Rp;
-            }
+            float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
+            float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
+            R = R - L32[(1 + l) * BS + tid] * Rm - L32[(1 + LMAX + l) * BS + tid] * Rp;
             buf ^= 1;
         }
         G = R * L32[(NF - 1) * BS + tid];
