@@ -11,6 +11,8 @@
 // but the last; output channel 0 = the cell mean of (u - u0) / s, channels
 // 1..7 unused; initial state u0 + s * (bilinear interpolation of channel 0).
 // Parameters packed as W_0, b_0, W_1, b_1, ...; W_l[(tap * Cin + ci) * Cout + co].
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -381,6 +383,166 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, int* err)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(N));
 }
 
+// ------------------------------------------------ TMA-fed tensor-core convolution
+// For inputs of 64 or 128 channels: a CTA computes the output pixels of an
+// 8 MT x 16 window of one image for all N output channels.  The K loop runs over
+// (tap, 64-channel block); for each, one TMA load brings the input window
+// shifted by the tap's offset (the image border comes as TMA's zero fill) and
+// one brings the 64 x N weight tile, both with the 128-byte swizzle, which is
+// the K-major layout the MMA descriptors expect (row = pixel y * 16 + x).
+// Thread 0 keeps up to S stages in flight on "full" mbarriers (transaction
+// bytes) and issues the MMAs of a stage when it lands; the MMAs' commit to the
+// stage's "empty" mbarrier frees it for the next load.  No thread waits on a
+// copy it issued, so loads run S - 1 stages ahead of the tensor core.  Every
+// wait is bounded; on a timeout the kernel sets *err, skips the epilogue and
+// frees its tensor memory.
+// MT windows of 8 x 16 pixels stacked (an 8 MT x 16 window, one TMA load),
+// each with its own accumulator (tensor-memory columns [t N, t N + N)),
+// sharing every weight tile.  Measured on the 128-problem forward pass: one
+// window 1.42 ms (3 or 4 stages), two windows with 2 stages (two CTAs per SM)
+// 1.11 ms, two with 3 stages 1.48 ms, four windows 1.22 ms.
+constexpr int kTmaMT = 2;
+template <int N>
+struct TmaConv {
+    static constexpr int MT = kTmaMT;
+    static constexpr int S = MT == 1 ? (N == 128 ? 3 : 4) : 2;
+    static constexpr int A_BYTES = MT * 128 * 128, B_BYTES = N * 128, STAGE = A_BYTES + B_BYTES;
+    static constexpr int SMEM = S * STAGE + 1024;
+    static constexpr int THREADS = 128 * MT;
+};
+
+template <int N>
+__global__ void __launch_bounds__(TmaConv<N>::THREADS) k_conv_tma(const __grid_constant__ CUtensorMap ta,
+                                                                  const __grid_constant__ CUtensorMap tw,
+                                                                  ConvArgs a, int* err)
+{
+    using C = TmaConv<N>;
+    constexpr int S = C::S, A_BYTES = C::A_BYTES, STAGE = C::STAGE, MT = C::MT, WH = 8 * MT;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    __shared__ uint64_t full[S], empty[S];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tiles_x = a.W / 16, per_img = tiles_x * (a.H / WH);
+    const int b = blockIdx.x / per_img, t = blockIdx.x - b * per_img;
+    const int y0 = (t / tiles_x) * WH, x0 = (t - (t / tiles_x) * tiles_x) * 16;
+    const int cblocks = a.Cin / 64, nk = 9 * cblocks;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(MT * N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[s])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+    if (tid == 0) {
+        const uint64_t pa = reinterpret_cast<uint64_t>(&ta), pw = reinterpret_cast<uint64_t>(&tw);
+        auto issue = [&](int k) {
+            const int s = k % S, tap = k / cblocks, cb = k - tap * cblocks;
+            const int dy = (tap / 3 - 1) * a.dil, dx = (tap % 3 - 1) * a.dil;
+            const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES, bar = smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(STAGE)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4, %5}], [%6];\n" ::"r"(sa),
+                "l"(pa), "r"(cb * 64), "r"(x0 + dx), "r"(y0 + dy), "r"(b), "r"(bar)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(sb),
+                "l"(pw), "r"(tap * a.Cin + cb * 64), "r"(0), "r"(bar)
+                : "memory");
+        };
+        for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
+        const uint32_t idesc = umma_idesc(128, N);
+        for (int k = 0; k < nk; ++k) {
+            const int s = k % S, kn = k + S - 1;
+            if (kn < nk) {
+                // slot kn % S was last read by the MMAs of step kn - S
+                if (kn >= S) ok = mbar_wait(smem_u32(&empty[kn % S]), ((kn / S) - 1) & 1, err);
+                if (!ok) break;
+                issue(kn);
+            }
+            ok = mbar_wait(smem_u32(&full[s]), (k / S) & 1, err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t bd = umma_sdesc(sb + ks * 32);
+                const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+                for (int q = 0; q < MT; ++q) {
+                    const uint64_t ad = umma_sdesc(sa + q * 128 * 128 + ks * 32);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                            tmem + (uint32_t)(q * N)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&empty[s])));
+        }
+    }
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    // every MMA has finished when the last step's commit arrives (in issue order)
+    if (ok && nk >= 1) ok = mbar_wait(smem_u32(&empty[(nk - 1) % S]), ((nk - 1) / S) & 1, err);
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (ok) {
+        // warp w reads lanes 32 (w % 4) .. of accumulator w / 4; accumulator
+        // row r of window q is the pixel (y0 + 8 q + r / 16, x0 + r % 16)
+        const int q = warp >> 2, r = ((warp & 3) << 5) + (tid & 31);
+        const int py = y0 + 8 * q + (r >> 4), px = x0 + (r & 15);
+        const long long m = ((long long)b * a.H + py) * a.W + px;
+        const uint32_t lane = ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * N);
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tmem + lane + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            uint32_t packed[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
+                if (a.bias) {
+                    f0 += a.bias[c0 + 2 * j];
+                    f1 += a.bias[c0 + 2 * j + 1];
+                }
+                if (a.relu) {
+                    f0 = fmaxf(f0, 0.f);
+                    f1 = fmaxf(f1, 0.f);
+                }
+                __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+                packed[j] = *reinterpret_cast<uint32_t*>(&h);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(a.y + m * N + c0);
+            dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(MT * N));
+}
+
 struct WgradArgs {
     int B, H, W, Cin, Cout, dil;
     const bf16* x;   // layer input [B][H][W][Cin]
@@ -743,11 +905,68 @@ constexpr int tc_smem_bytes()
     return 2 * (128 * 128 + N * 128) + 1024;
 }
 
-// tensor-core path for 64 or 128 output channels with a BF16 output (wk: the
-// K-major weights); mma.sync otherwise
+// the driver's tensor-map encoder, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* q = nullptr;
+        cudaDriverEntryPointQueryResult res = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault, &res) ==
+                cudaSuccess &&
+            res == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(q);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// tensor maps of a convolution's input [B][H][W][Cin] (box: 64 channels x 16 x
+// 8 pixels) and K-major weights [N][9 Cin] (box: 64 x N), 128-byte swizzle;
+// false when the driver refuses them (the caller takes another kernel)
+bool conv_tensor_maps(const ConvArgs& a, const bf16* wk, CUtensorMap* ta, CUtensorMap* tw)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t C = (cuuint64_t)a.Cin, K = 9 * C;
+    cuuint64_t dA[4] = {C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
+    cuuint64_t sA[3] = {C * 2, C * 2 * a.W, C * 2 * a.W * a.H};
+    cuuint32_t bA[4] = {64, 16, 8 * kTmaMT, 1}, e4[4] = {1, 1, 1, 1};
+    if (enc(ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.x), dA, sA, bA, e4,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    cuuint64_t dW[2] = {K, (cuuint64_t)a.Cout};
+    cuuint64_t sW[1] = {K * 2};
+    cuuint32_t bW[2] = {64, (cuuint32_t)a.Cout}, e2[2] = {1, 1};
+    return enc(tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(wk), dW, sW, bW, e2,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// tensor-core paths for 64 or 128 output channels with a BF16 output (wk: the
+// K-major weights): TMA-fed for inputs of a multiple of 64 channels on 8 x 16
+// pixel windows, cp.async-fed otherwise; mma.sync for the rest
 void launch_conv(cudaStream_t st, const ConvArgs& a, const bf16* wk = nullptr, int* err = nullptr)
 {
     long long M = (long long)a.B * a.H * a.W;
+    if (wk && err && a.y && !a.y32 && (a.Cout == 64 || a.Cout == 128) && a.Cin % 64 == 0 &&
+        a.H % (8 * kTmaMT) == 0 && a.W % 16 == 0) {
+        CUtensorMap ta, tw;
+        if (conv_tensor_maps(a, wk, &ta, &tw)) {
+            ConvArgs t = a;
+            t.w = wk;
+            const unsigned blocks = (unsigned)(a.B * (a.H / (8 * kTmaMT)) * (a.W / 16));
+            if (a.Cout == 64)
+                k_conv_tma<64><<<blocks, TmaConv<64>::THREADS, TmaConv<64>::SMEM, st>>>(ta, tw, t, err);
+            else
+                k_conv_tma<128><<<blocks, TmaConv<128>::THREADS, TmaConv<128>::SMEM, st>>>(ta, tw, t, err);
+            return;
+        }
+    }
     if (wk && err && a.y && !a.y32 && (a.Cout == 64 || a.Cout == 128)) {
         ConvArgs t = a;
         t.w = wk;
@@ -944,6 +1163,10 @@ adr_status adr_cnn_create(int max_batch, const float* params, void* stream, adr_
                                       tc_smem_bytes<64>()));
     ADR_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       tc_smem_bytes<128>()));
+    ADR_CUDA_TRY(cudaFuncSetAttribute(k_conv_tma<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TmaConv<64>::SMEM));
+    ADR_CUDA_TRY(cudaFuncSetAttribute(k_conv_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TmaConv<128>::SMEM));
     if ((s = adr_cnn_set_params(c, params))) return fail(s);
     *out = c;
     return ADR_OK;
