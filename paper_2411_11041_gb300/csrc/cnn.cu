@@ -390,17 +390,20 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, int* err)
 // shifted by the tap's offset (the image border comes as TMA's zero fill) and
 // one brings the 64 x N weight tile, both with the 128-byte swizzle, which is
 // the K-major layout the MMA descriptors expect (row = pixel y * 16 + x).
-// Thread 0 keeps up to S stages in flight on "full" mbarriers (transaction
-// bytes) and issues the MMAs of a stage when it lands; the MMAs' commit to the
-// stage's "empty" mbarrier frees it for the next load.  No thread waits on a
-// copy it issued, so loads run S - 1 stages ahead of the tensor core.  Every
-// wait is bounded; on a timeout the kernel sets *err, skips the epilogue and
-// frees its tensor memory.
+// Thread 0 (the producer) keeps up to S stages in flight on "full" mbarriers
+// (transaction bytes); thread 32 (the MMA issuer, another warp) issues a
+// stage's MMAs as soon as it lands, and their commit to the stage's "empty"
+// mbarrier frees it for the producer.  The MMAs of consecutive stages queue
+// back to back.  Every wait is bounded; on a timeout the kernel sets *err,
+// waits (bounded) for the loads it issued that no MMA consumed, skips the
+// epilogue and frees its tensor memory.
 // MT windows of 8 x 16 pixels stacked (an 8 MT x 16 window, one TMA load),
 // each with its own accumulator (tensor-memory columns [t N, t N + N)),
-// sharing every weight tile.  Measured on the 128-problem forward pass: one
-// window 1.42 ms (3 or 4 stages), two windows with 2 stages (two CTAs per SM)
-// 1.11 ms, two with 3 stages 1.48 ms, four windows 1.22 ms.
+// sharing every weight tile.  Measured on the 128-problem forward pass with
+// one thread loading and issuing: one window 1.42 ms (3 or 4 stages), two
+// windows with 2 stages (two CTAs per SM) 1.11 ms, two with 3 stages 1.48 ms,
+// four windows 1.22 ms; with the producer and the MMA issuer apart, two
+// windows 1.06 ms with 2 stages and 1.29 ms with 3 (one CTA per SM).
 constexpr int kTmaMT = 2;
 template <int N>
 struct TmaConv {
@@ -444,11 +447,16 @@ __global__ void __launch_bounds__(TmaConv<N>::THREADS) k_conv_tma(const __grid_c
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     const uint32_t tmem = tmem_base;
+    __shared__ int consumed;  // steps whose MMAs were issued (set by the issuer)
     bool ok = true;
+    int issued = 0;
     if (tid == 0) {
+        // producer: loads run up to S stages ahead of the MMAs
         const uint64_t pa = reinterpret_cast<uint64_t>(&ta), pw = reinterpret_cast<uint64_t>(&tw);
-        auto issue = [&](int k) {
+        for (int k = 0; k < nk; ++k) {
             const int s = k % S, tap = k / cblocks, cb = k - tap * cblocks;
+            // slot s was last read by the MMAs of step k - S
+            if (k >= S && !(ok = mbar_wait(smem_u32(&empty[s]), ((k / S) - 1) & 1, err))) break;
             const int dy = (tap / 3 - 1) * a.dil, dx = (tap % 3 - 1) * a.dil;
             const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES, bar = smem_u32(&full[s]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(STAGE)
@@ -463,19 +471,15 @@ __global__ void __launch_bounds__(TmaConv<N>::THREADS) k_conv_tma(const __grid_c
                 "[%4];\n" ::"r"(sb),
                 "l"(pw), "r"(tap * a.Cin + cb * 64), "r"(0), "r"(bar)
                 : "memory");
-        };
-        for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
+            issued = k + 1;
+        }
+    } else if (tid == 32) {
+        // MMA issuer: each stage's MMAs as soon as its bytes land
         const uint32_t idesc = umma_idesc(128, N);
-        for (int k = 0; k < nk; ++k) {
-            const int s = k % S, kn = k + S - 1;
-            if (kn < nk) {
-                // slot kn % S was last read by the MMAs of step kn - S
-                if (kn >= S) ok = mbar_wait(smem_u32(&empty[kn % S]), ((kn / S) - 1) & 1, err);
-                if (!ok) break;
-                issue(kn);
-            }
-            ok = mbar_wait(smem_u32(&full[s]), (k / S) & 1, err);
-            if (!ok) break;
+        int k = 0;
+        for (; k < nk; ++k) {
+            const int s = k % S;
+            if (!(ok = mbar_wait(smem_u32(&full[s]), (k / S) & 1, err))) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n");
             const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES;
 #pragma unroll
@@ -495,8 +499,15 @@ __global__ void __launch_bounds__(TmaConv<N>::THREADS) k_conv_tma(const __grid_c
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_u32(&empty[s])));
         }
+        consumed = k;
     }
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!all_ok && tid == 0) {
+        // a wait gave up: let the loads this CTA issued and no MMA consumed land
+        // before the shared memory is released (bounded like every wait)
+        for (int k = consumed; k < issued; ++k) mbar_wait(smem_u32(&full[k % S]), (k / S) & 1, err);
+    }
+    ok = all_ok;
     // every MMA has finished when the last step's commit arrives (in issue order)
     if (ok && nk >= 1) ok = mbar_wait(smem_u32(&empty[(nk - 1) % S]), ((nk - 1) / S) & 1, err);
     asm volatile("tcgen05.fence::after_thread_sync;\n");
