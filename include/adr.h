@@ -119,7 +119,9 @@ void adr_default_opts(adr_opts* opts);
  * families; any other field gives RK4-traced curves seeded on the inflow
  * boundary (eqs. cauchyStartSets, CauchyBeta, CauchyGamma).  opts: host
  * pointer (copied).  On success *out owns its device buffers until
- * adr_destroy.  Inputs may be freed after the call returns.
+ * adr_destroy.  They come from the library's stream-ordered memory pool on
+ * the current device, allocated in the order of `stream` (and setup's
+ * temporaries too).  Inputs may be freed after the call returns.
  * Errors: ADR_EINVAL (bad sizes/coefficients, |beta| = 0 or non-finite data on
  * Omega_h, empty mask), ADR_EGEOM, ADR_ENOMEM, ADR_ECUDA.
  */
@@ -157,7 +159,10 @@ adr_status adr_solve_stationary(adr_problem* prob, const double* u_init, double*
 adr_status adr_step_parabolic(adr_problem* prob, double dt, int nsteps, int mode,
                               double* u_inout, adr_stats* stats);
 
-/* Release a handle and its device buffers (NULL is a no-op). */
+/* Release a handle and its device buffers (NULL is a no-op).  The device is
+ * synchronised first (a batch may still use the buffers on its stream); the
+ * buffers go back to the library's pool, which keeps up to 8 GB of freed
+ * device memory mapped for later handles and returns the rest to the driver. */
 void adr_destroy(adr_problem* prob);
 
 /* Message of the last failing call on this thread ("" if none). */
