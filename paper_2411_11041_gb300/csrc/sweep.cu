@@ -612,10 +612,10 @@ __device__ __forceinline__ void elim32(const float (&rhs)[kCmax], float (&x)[kCm
     }
 }
 
-template <int BS, int FAM, bool PF = false>
+template <int BS, int FAM, bool PF = false, bool SU = false>
 __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Titem,
                                                      const int* curves, const float* L32,
-                                                     float (*sR)[BS], double* sX)
+                                                     float (*sR)[BS], double* sX, double* sU = nullptr)
 {
     const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
     double* __restrict__ v = a.v;
@@ -639,7 +639,7 @@ __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Tit
 #pragma unroll
         for (int j = 0; j < kCmax; ++j) {
             r64[j] = 0.0;
-            ur[j] = 0.0;
+            if (!SU) ur[j] = 0.0;
             r32[j] = 0.f;
             if (j < cnt) {
                 const int sl = so32 + j * T + lt;
@@ -656,7 +656,8 @@ __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Tit
                     r = muh * ((u0 + u2) - 2.0 * u1);
                 r64[j] = r;
                 r32[j] = (float)r;
-                ur[j] = u1;
+                if (SU) sU[j * BS + tid] = u1;
+                else ur[j] = u1;
                 u0 = u1;
                 u1 = u2;
             }
@@ -701,7 +702,9 @@ __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Tit
     const double w = paper ? 1.0 : a.dt;
 #pragma unroll
     for (int j = 0; j < kCmax; ++j)
-        if (j < cnt) v[base + s + j + 1] = (paper ? 0.0 : ur[j]) + w * ((double)x0[j] + (double)x1[j]);
+        if (j < cnt)
+            v[base + s + j + 1] =
+                (paper ? 0.0 : (SU ? sU[j * BS + tid] : ur[j])) + w * ((double)x0[j] + (double)x1[j]);
     if (b.active && n >= 2 && lt == 0) {
         v[base] = 0.0;
         v[base + n] = 0.0;
@@ -709,14 +712,17 @@ __device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Tit
 }
 
 template <int BS, int FAM>
-__global__ void __launch_bounds__(BS) k_curve_solve_ref(CurveArgs a, const int* item_T,
+__global__ void __launch_bounds__(BS, BS == 256 ? 3 : (BS == 512 ? 2 : 1)) k_curve_solve_ref(CurveArgs a, const int* item_T,
                                                         const int* item_curve, const float* lanec32)
 {
     if (a.state && a.state->done) return;
     __shared__ float sR[2][BS];
     __shared__ double sX[BS];
-    curve_solve_ref_body<BS, FAM, true>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
-                                  lanec32 + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sX);
+    constexpr bool SU = BS <= 512;  // the gathered row values in shared memory
+    __shared__ double sU[SU ? kCmax * BS : 1];
+    curve_solve_ref_body<BS, FAM, true, SU>(a, item_T[blockIdx.x],
+                                            item_curve + blockIdx.x * Items<BS>::MAXC,
+                                            lanec32 + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sX, sU);
 }
 
 // ------------------------------------------------------------ batched problems
