@@ -750,14 +750,14 @@ struct ActiveLists {
 constexpr int kCountPerBuf = 7;
 
 template <int BS, int FAM, bool REF>
-__global__ void __launch_bounds__(BS, BS == 256 ? (REF ? 2 : 4) : 1) k_curve_solve_batch(const CurveArgs* __restrict__ table,
+__global__ void __launch_bounds__(BS, BS == 256 ? (REF ? 3 : 4) : 1) k_curve_solve_batch(const CurveArgs* __restrict__ table,
                                                           const BatchItem* __restrict__ items,
                                                           ActiveLists act, int set)
 {
     __shared__ double sR[2][BS];
     __shared__ float sRf[2][BS];
     __shared__ double sX[BS];
-    constexpr bool SU = !REF && BS == 256;  // the gathered row values in shared memory
+    constexpr bool SU = BS == 256;  // the gathered row values in shared memory
     __shared__ double sU[SU ? kCmax * BS : 1];
     const int cur = *act.sel;
     const int* list = act.items[cur][FAM][set];
@@ -767,8 +767,9 @@ __global__ void __launch_bounds__(BS, BS == 256 ? (REF ? 2 : 4) : 1) k_curve_sol
         const CurveArgs& a = table[2 * I.prob + FAM];
         if (a.state->done) continue;  // uniform: one problem per item
         if (REF)
-            curve_solve_ref_body<BS, FAM>(a, I.T, I.curves,
-                                          a.lanec32s[set] + (size_t)I.local * Items<BS>::NF * BS, sRf, sX);
+            curve_solve_ref_body<BS, FAM, false, SU>(a, I.T, I.curves,
+                                                     a.lanec32s[set] + (size_t)I.local * Items<BS>::NF * BS,
+                                                     sRf, sX, sU);
         else
             curve_solve_body<BS, FAM, SU, SU>(a, I.T, I.curves,
                                           a.lanecs[set] + (size_t)I.local * Items<BS>::NF * BS, sR, sU);
