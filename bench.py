@@ -56,7 +56,7 @@ FLOPS_PER_UNIT = [23.0, 16.0, 21.0, 20.0]
 # curve solve) from one ncu capture of the 2048^2 sheared workload
 # (profiles/dram_traffic_sweep_sheared2048_fp64.md); None where the kernel has
 # changed since the capture
-NCU_TRAFFIC_SHEARED2048 = [565.9e6, 398.9e6, 498.3e6, 435.8e6]
+NCU_TRAFFIC_SHEARED2048 = [565.2e6, 399.0e6, 499.0e6, 435.3e6]
 
 
 def parse():
