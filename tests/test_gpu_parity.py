@@ -64,6 +64,11 @@ PROBLEMS = {
     "sheared65": lambda: W.sheared(n=65),
     "data2d": lambda: W.data2d(33),
     "tiny3": lambda: _const(3, (1.0, 0.5)),
+    # lines of 4 100 nodes (4 098 unknowns): the 1024-thread curve solve.
+    # mu is small so that dt mu / h^2 stays moderate at the test's largest dt
+    # (with mu = 0.1 and dt = 0.3 it is 5e5, and the partitioned and the serial
+    # eliminations then differ by 2e-12 from rounding alone)
+    "thin_long": lambda: _const(5, (1.0, 0.0), nx=4100, mu=1e-4),
     "perforated129": lambda: _perforated(129, 8),  # 2 560 boundary edges, 257 loops
     "perforated401": lambda: _perforated(401, 4),  # 81 600 boundary edges
 }
@@ -110,6 +115,25 @@ def test_split_step_matches_oracle(pairs, torch_cuda, name):
         ouh, oun = o.split_step(theta, dt, u)
         assert relerr(uh, ouh) <= TOL64, (theta, dt)
         assert relerr(un, oun) <= TOL64, (theta, dt)
+
+
+@pytest.mark.parametrize("rows", [2, 4])
+def test_other_rows_per_thread_match_oracle(torch_cuda, rows):
+    """Fewer rows per thread: more threads per curve, up to T = 1024 (with 2
+    rows per thread every curve of more than 1 024 unknowns is capped at
+    1 024 threads and takes more rows each)."""
+    from paper_2411_11041_gb300 import Solver
+    torch = torch_cuda
+    for name in ("thin_long", "sheared65", "disc_mask"):
+        p = PROBLEMS[name]()
+        o = O.Oracle(p)
+        s = Solver(p, rows_per_thread=rows)
+        u = np.random.default_rng(5).normal(size=(p.ny, p.nx)) * o.interior()
+        uh, un = s.split_step(torch.tensor(u, device="cuda:0"), o.default_dt())
+        ouh, oun = o.split_step(0.5, o.default_dt(), u)
+        assert relerr(uh, ouh) <= TOL64, (name, rows)
+        assert relerr(un, oun) <= TOL64, (name, rows)
+        s.close()
 
 
 @pytest.mark.parametrize("name", ["manufactured33", "L_mask", "sheared65", "data2d", "tiny3",
