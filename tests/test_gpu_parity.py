@@ -69,6 +69,13 @@ PROBLEMS = {
     # (with mu = 0.1 and dt = 0.3 it is 5e5, and the partitioned and the serial
     # eliminations then differ by 2e-12 from rounding alone)
     "thin_long": lambda: _const(5, (1.0, 0.0), nx=4100, mu=1e-4),
+    # lines of m = nx - 2 unknowns at the chunking boundaries (8 rows per
+    # thread): 32 (T = 32, 1 row each), 33, 2 048 (T = 256, 8 rows each, all
+    # full) and 2 049 (the first length that takes T = 512)
+    "thin_m32": lambda: _const(5, (1.0, 0.0), nx=34, mu=1e-3),
+    "thin_m33": lambda: _const(5, (1.0, 0.0), nx=35, mu=1e-3),
+    "thin_m2048": lambda: _const(5, (1.0, 0.0), nx=2050, mu=1e-4),
+    "thin_m2049": lambda: _const(5, (1.0, 0.0), nx=2051, mu=1e-4),
     "perforated129": lambda: _perforated(129, 8),  # 2 560 boundary edges, 257 loops
     "perforated401": lambda: _perforated(401, 4),  # 81 600 boundary edges
 }
