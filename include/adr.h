@@ -290,7 +290,7 @@ adr_status adr_cross_substep_noalloc(int nx, int ny, double mu, double theta, do
 
 /*
  * Learned warm start (no counterpart in the paper; the paper's iteration stays
- * the solver and the judge of convergence, the network only supplies u_0).
+ * the solver and alone decides convergence; the network only supplies u_0).
  *
  * A convolutional network maps a problem on a 256 x 256 node grid, and a
  * first initial state u0 of it (normally the state of eq. u0stationary, from

@@ -2,7 +2,7 @@
 solutions the method generated must cut the iterations to the same tolerance
 on held-out problems (against u_0 = 0; against the paper's own initial state
 it must not lose more than 5 %), and the answers from its initial states must
-be the answers from u_0 = 0 (the iteration stays the judge of convergence)."""
+be the answers from u_0 = 0 (the iteration alone decides convergence)."""
 import numpy as np
 import pytest
 
