@@ -341,7 +341,7 @@ static int build_straight(orc_problem* p, int fam)
  * measure w_e = max(0, -n_e . dir(mid_e)) |e| with dir from the nodal mean of
  * beta over the edge; seeds sit where the cumulative measure reaches
  * (k + 1/2) h_s, linearly inside the edge.  From each seed the curve is traced
- * (eqs. CauchyBeta / CauchyGamma) with RK4 steps of h_s/8 in arc length until
+ * (eqs. CauchyBeta / CauchyGamma) with RK4 steps of h_s/2 in arc length until
  * it leaves the interior of Omega_h; the exit is located by bisection. */
 
 /* boundary edge orientation: +1 / -1 along the axis, 0 = not a boundary edge */
