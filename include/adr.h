@@ -52,7 +52,15 @@ typedef enum {
 
 typedef enum {
     ADR_FP64 = 0,        /* every step in FP64 */
-    ADR_FP32_REFINE = 1  /* line solves in FP32 + one FP64-residual refinement step */
+    ADR_FP32_REFINE = 1  /* line solves in FP32 as one step of mixed-precision iterative
+                            refinement: from the current curve values x0 = u the residual
+                            dt (F - S u) of the substep system is formed in FP64, the
+                            correction is solved in FP32, and v = u + dt d, the grid map,
+                            the norms and the convergence test stay in FP64.  The FP32
+                            rounding of d does not vanish at the fixed point (d != 0
+                            there), so once the relative update reaches 100 tol the
+                            iteration solves its corrections in FP64 (adr_stats.fp32_steps
+                            counts the steps before that) */
 } adr_precision;
 
 typedef enum {
@@ -82,9 +90,11 @@ typedef struct {
     double tol;
     int max_iter;
     int init;        /* adr_init */
-    int rows_per_thread;    /* launch shape of the curve solve: 2, 4 or 8 rows per thread
-                               (0 = 8); a curve of m unknowns gets blocks of the smallest
-                               power-of-two T >= 32 with T * rows_per_thread >= m */
+    int rows_per_thread;    /* launch shape of the curve solve: 2, 4, 8 or 16 rows per
+                               thread (0 = 16); a curve of m unknowns gets blocks of the
+                               smallest power-of-two T >= 32 with T * rows_per_thread >= m,
+                               at most 1024 (longer curves take up to 16 rows per thread;
+                               curves of more than 16384 unknowns are refused) */
     int map_blocks_per_sm;  /* blocks per SM of the curve -> grid map: 1..8 (0 = 4) */
     int interp_weights;     /* curve -> grid: 0 = average of the row and column values (§6);
                                1 = weights by the opposite direction's crossing gap, for
@@ -103,6 +113,16 @@ typedef struct {
     double ms;          /* device time of the solve (CUDA events on the stream) */
     double line_dofs;   /* line unknowns solved in total (both families, all steps) */
     double dt;          /* pseudo step used */
+    double min_pivot;   /* smallest |pivot| that Thomas elimination of the curve systems
+                           (M + theta dt S per curve, §6; both families) meets, computed on
+                           the device when the systems are factored; +inf when nothing was
+                           factored */
+    double max_correction; /* ADR_FP32_REFINE: largest |dt d| over the curve nodes of the last
+                           split step, d the FP32 correction solved from the FP64 residual;
+                           its FP32 rounding bounds what the mode loses against FP64.
+                           0 in FP64 mode */
+    int fp32_steps;     /* ADR_FP32_REFINE: split steps whose corrections were solved in
+                           FP32 (the rest in FP64); 0 in FP64 mode */
 } adr_stats;
 
 typedef struct adr_problem adr_problem; /* opaque handle */
@@ -215,7 +235,7 @@ adr_status adr_time_kernels(adr_problem* prob, int reps, double* ms_out);
 /*
  * adr_autotune -- choose the launch shapes of a handle by measurement (no
  * counterpart in the paper; the result does not change the solution).  Each
- * candidate (rows_per_thread in {2, 4, 8}, map_blocks_per_sm in {2, 4, 8}) is
+ * candidate (rows_per_thread in {4, 8, 16}, map_blocks_per_sm in {2, 4, 8}) is
  * applied and one split step's kernels are timed reps times with CUDA events
  * on the handle's stream; the fastest is kept.  Outputs (host, nullable): the
  * chosen rows_per_thread and map_blocks_per_sm and its ms per split step.

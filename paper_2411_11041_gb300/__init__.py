@@ -40,7 +40,8 @@ class adr_opts(C.Structure):
 
 class adr_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("rel_update", C.c_double), ("ms", C.c_double),
-                ("line_dofs", C.c_double), ("dt", C.c_double)]
+                ("line_dofs", C.c_double), ("dt", C.c_double), ("min_pivot", C.c_double),
+                ("max_correction", C.c_double), ("fp32_steps", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -122,7 +123,7 @@ def tune_key(prob, prec):
     b1, b2 = np.asarray(prob.beta1), np.asarray(prob.beta2)
     const = bool(np.all(b1 == b1.flat[0]) and np.all(b2 == b2.flat[0]))
     mask = np.asarray(prob.mask)
-    return f"{prob.nx}x{prob.ny}:{int(mask.sum())}:{'const' if const else 'curved'}:p{int(prec)}"
+    return f"v2:{prob.nx}x{prob.ny}:{int(mask.sum())}:{'const' if const else 'curved'}:p{int(prec)}"
 
 
 def _tune_path():

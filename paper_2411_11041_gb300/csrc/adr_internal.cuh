@@ -59,21 +59,24 @@ struct Family {
     // per-row data of the curve solve in slot layout (row (t, j) of a curve at
     // soff[curve] + j*T + t, T the curve's block size)
     int n_slots = 0;
+    int cmax = 1;             // rows of the longest chunk (a thread's rows) of the family
     int* soff = nullptr;      // [n_lines+1]
     int* gcell = nullptr;     // [n_slots] bilinear cell r*nx + i of the row's node
     double* gw = nullptr;     // [4 n_slots] bilinear corner weights (1-lx)(1-ly), lx(1-ly),
                               // (1-lx)ly, lx ly
-    double* Fl = nullptr;     // [n_slots] load F = M f (B)
-    double* srow = nullptr;   // [3*n_slots] S sub/diag/super (B)
+    double* Fl = nullptr;     // [n_slots] load row of the right-hand side (B), times ip
+    double* srow = nullptr;   // [3*n_slots] B / [n_slots] G: right-hand-side rows, times ip
+    double* kap = nullptr;    // [n_lines] G: diagonal / off-diagonal ratio of the rhs stencil
     double* fac = nullptr;    // [4*n_slots] elimination factors cp, vp, ip, lp
     float* fac32 = nullptr;   // [4*n_slots] the same in FP32 (reduced-precision mode)
     ItemSet iset[3];          // BS = 256, 512, 1024
     int* mg = nullptr;        // [4*N] curve -> grid map: segment of each crossing
     double* mc = nullptr;     // [8*N] combined weights of the map
-    // factorisation currently held in fac/lanec (theta dt, sigma, steady flag)
+    // factorisation currently held in fac/lanec (theta dt, dt, sigma, steady flag,
+    // right-hand-side form: 1 = FP64 new-value form, 0 = residual form / steady)
     bool prep_valid = false;
-    double prep_td = 0, prep_sig = 0;
-    int prep_paper = 0;
+    double prep_td = 0, prep_dt = 0, prep_sig = 0;
+    int prep_paper = 0, prep_vform = 0;
     bool load_plain = false;  // Fl holds M f without extra load
     // curve -> grid map, per grid node: 4 crossings (row L, row R, col D, col U)
     int* cg = nullptr;        // [4*N] first node of the crossed segment (-1 boundary)
@@ -83,12 +86,21 @@ struct Family {
 };
 
 // Result of a solve kept on the device: [0] rel update, [1] num, [2] den.
+// Reduced-precision mode: the corrections are solved in FP32 until the relative
+// update reaches kHpSwitch * tol, and in FP64 from there on (the FP32 rounding
+// of a correction does not vanish at the fixed point, where d != 0).
+constexpr double kHpSwitch = 100.0;
+
 struct IterState {
     int iter;       // split steps done
     int done;       // 1 once converged or capped
     int converged;  // 1 if rel <= tol
-    int pad;
+    int hp;         // reduced-precision mode: 1 once the corrections are solved in FP64
     double rel;
+    unsigned long long corr_bits;  // running max |dt d| of the step's corrections (bits)
+    double corr;                   // the last step's largest correction (reduced precision)
+    int fp32_steps;                // steps done with FP32 corrections
+    int pad;
 };
 
 struct Problem {
@@ -100,7 +112,7 @@ struct Problem {
     int N = 0;             // nx*ny
     int n_interior = 0;
     int n_sm = 0;
-    int rows_per_thread = 8;    // launch shape of the curve solve (<= 8)
+    int rows_per_thread = 16;   // launch shape of the curve solve (<= 16 rows per thread)
     int map_blocks_per_sm = 4;  // launch shape of the curve -> grid map
     bool const_beta = false;
     double bmax = 0;
@@ -115,6 +127,7 @@ struct Problem {
     double* partial = nullptr;                      // per-block norm partial sums
     int n_partial_blocks = 0;
     IterState* state = nullptr;
+    double* pivmin = nullptr;   // [2] smallest |Thomas pivot| of each family's systems
     double* fextra = nullptr;                       // [N] extra load (parabolic slices)
     std::vector<void*> owned;
 };
@@ -183,7 +196,7 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off);
 void release_groups(Problem* p, int fam);
 adr_status launch_map_coef(Problem* p, int fam);
 int grid_map_blocks(const Problem* p);
-adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper);
+adr_status prepare_family(Problem* p, int fam, double td, double dt, double sig, int paper);
 adr_status load_family(Problem* p, const double* fextra, double fx_scale);
 adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_even,
                              const double* u_odd, bool use_state, int paper);

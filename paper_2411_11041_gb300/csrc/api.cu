@@ -122,8 +122,8 @@ adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
     cudaGraphNode_t node;
     ADR_CUDA_TRY(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &np));
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    TRY(prepare_family(p, 0, theta * dt, sig, 0));
-    TRY(prepare_family(p, 1, theta * dt, sig, 0));
+    TRY(prepare_family(p, 0, theta * dt, dt, sig, 0));
+    TRY(prepare_family(p, 1, theta * dt, dt, sig, 0));
     cudaStream_t user = p->stream;
     p->stream = h->cap_stream;
     cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
@@ -163,8 +163,8 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
     TRY(launch_state_reset(p));
     ADR_CUDA_TRY(cudaEventRecord(h->ev0, p->stream));
     if (max_iter > 0) {
-        TRY(prepare_family(p, 0, theta * dt, sig, 0));
-        TRY(prepare_family(p, 1, theta * dt, sig, 0));
+        TRY(prepare_family(p, 0, theta * dt, dt, sig, 0));
+        TRY(prepare_family(p, 1, theta * dt, dt, sig, 0));
         TRY(load_family(p, fextra, fx_scale));
         if (!h->exec || h->g_theta != theta || h->g_dt != dt || h->g_sig != sig ||
             h->g_fextra != fextra || h->g_scale != fx_scale || h->g_tol != tol ||
@@ -175,7 +175,10 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
     TRY(launch_finish(p, out, iter_out, midpoint));
     ADR_CUDA_TRY(cudaEventRecord(h->ev1, p->stream));
     IterState st;
+    double piv[2] = {INFINITY, INFINITY};
     ADR_CUDA_TRY(cudaMemcpyAsync(&st, p->state, sizeof st, cudaMemcpyDeviceToHost, p->stream));
+    if (max_iter > 0)
+        ADR_CUDA_TRY(cudaMemcpyAsync(piv, p->pivmin, sizeof piv, cudaMemcpyDeviceToHost, p->stream));
     ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
@@ -190,6 +193,9 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
         stats->ms += ms;
         stats->line_dofs += (double)st.iter * (h->line_unknowns[0] + h->line_unknowns[1]);
         stats->dt = dt;
+        stats->min_pivot = std::fmin(stats->min_pivot, std::fmin(piv[0], piv[1]));
+        stats->max_correction = st.iter > 0 ? st.corr : 0.0;
+        if (p->opts.prec == ADR_FP32_REFINE) stats->fp32_steps += st.fp32_steps;
     }
     return ADR_OK;
 }
@@ -205,7 +211,7 @@ adr_status init_state(adr_problem* h, int init, const double* u_init)
         return launch_mask_copy(p, u_init, p->ubuf[0]);
     }
     if (init == ADR_INIT_PAPER_U0) {
-        TRY(prepare_family(p, 0, 1.0, p->sigma, 1));
+        TRY(prepare_family(p, 0, 1.0, 1.0, p->sigma, 1));
         TRY(load_family(p, nullptr, 0.0));
         TRY(launch_line_solve(p, 0, 1.0, nullptr, nullptr, false, 1));
         return launch_grid_map_ex(p, 0, p->ubuf[0], p->ubuf[0], 0, nullptr, nullptr, false, false);
@@ -213,6 +219,13 @@ adr_status init_state(adr_problem* h, int init, const double* u_init)
     if (init == ADR_INIT_ZERO) return launch_mask_copy(p, nullptr, p->ubuf[0]);
     set_error("unsupported opts.init");
     return ADR_EINVAL;
+}
+
+void clear_stats(adr_stats* s)
+{
+    if (!s) return;
+    memset(s, 0, sizeof *s);
+    s->min_pivot = INFINITY;
 }
 
 adr_status check_opts(const adr_opts* o)
@@ -247,9 +260,9 @@ adr_status check_opts(const adr_opts* o)
         return ADR_EINVAL;
     }
     if ((o->rows_per_thread != 0 && o->rows_per_thread != 2 && o->rows_per_thread != 4 &&
-         o->rows_per_thread != 8) ||
+         o->rows_per_thread != 8 && o->rows_per_thread != 16) ||
         o->map_blocks_per_sm < 0 || o->map_blocks_per_sm > 8) {
-        set_error("opts.rows_per_thread must be 0, 2, 4 or 8 and map_blocks_per_sm 0..8");
+        set_error("opts.rows_per_thread must be 0, 2, 4, 8 or 16 and map_blocks_per_sm 0..8");
         return ADR_EINVAL;
     }
     return ADR_OK;
@@ -355,7 +368,8 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
         p->map_blocks_per_sm = keep;
     }
     if ((s = dev_alloc(p, &p->partial, 2 * (size_t)p->n_partial_blocks)) ||
-        (s = dev_alloc(p, &p->state, 1)) || (s = dev_alloc(p, &p->fextra, N)))
+        (s = dev_alloc(p, &p->state, 1)) || (s = dev_alloc(p, &p->fextra, N)) ||
+        (s = dev_alloc(p, &p->pivmin, 2)))
         return fail(s);
     for (int fam = 0; fam < 2; ++fam) {
         std::vector<int>& off = h->offs[fam];
@@ -401,7 +415,7 @@ adr_status adr_solve_stationary(adr_problem* h, const double* u_init, double* u_
     }
     Problem* p = &h->p;
     const adr_opts& o = p->opts;
-    if (stats) memset(stats, 0, sizeof *stats);
+    clear_stats(stats);
     double dt = o.dt > 0 ? o.dt : default_dt(*p, p->sigma);
     TRY(init_state(h, o.init, u_init));
     bool conv = false;
@@ -429,7 +443,7 @@ adr_status adr_step_parabolic(adr_problem* h, double dt, int nsteps, int mode, d
     }
     Problem* p = &h->p;
     const adr_opts& o = p->opts;
-    if (stats) memset(stats, 0, sizeof *stats);
+    clear_stats(stats);
     if (nsteps == 0) return launch_mask_copy(p, u, u);
     bool conv = false;
     if (mode == 0) {
@@ -463,8 +477,8 @@ adr_status adr_split_step(adr_problem* h, double dt, const double* u, double* u_
     Problem* p = &h->p;
     double* half = u_half ? u_half : p->ubuf[2];
     double th = p->opts.theta;
-    TRY(prepare_family(p, 0, th * dt, p->sigma, 0));
-    TRY(prepare_family(p, 1, th * dt, p->sigma, 0));
+    TRY(prepare_family(p, 0, th * dt, dt, p->sigma, 0));
+    TRY(prepare_family(p, 1, th * dt, dt, p->sigma, 0));
     TRY(load_family(p, nullptr, 0.0));
     TRY(launch_line_solve(p, 0, dt, u, u, false, 0));
     TRY(launch_grid_map_ex(p, 0, half, half, 0, nullptr, nullptr, false, false));
@@ -482,7 +496,7 @@ adr_status adr_paper_u0(adr_problem* h, double* u0)
         return ADR_EINVAL;
     }
     Problem* p = &h->p;
-    TRY(prepare_family(p, 0, 1.0, p->sigma, 1));
+    TRY(prepare_family(p, 0, 1.0, 1.0, p->sigma, 1));
     TRY(load_family(p, nullptr, 0.0));
     TRY(launch_line_solve(p, 0, 1.0, nullptr, nullptr, false, 1));
     TRY(launch_grid_map_ex(p, 0, u0, u0, 0, nullptr, nullptr, false, false));
@@ -537,7 +551,7 @@ adr_status adr_autotune(adr_problem* h, int reps, int* rows_out, int* blocks_out
         return ADR_EINVAL;
     }
     Problem* p = &h->p;
-    const int rows[3] = {2, 4, 8}, blocks[3] = {2, 4, 8};
+    const int rows[3] = {4, 8, 16}, blocks[3] = {2, 4, 8};
     double best = 1e300;
     int bR = p->rows_per_thread, bM = p->map_blocks_per_sm;
     double ms[4];
@@ -582,8 +596,8 @@ adr_status adr_time_kernels(adr_problem* h, int reps, double* ms_out)
     Problem* p = &h->p;
     const adr_opts& o = p->opts;
     double dt = o.dt > 0 ? o.dt : default_dt(*p, p->sigma);
-    TRY(prepare_family(p, 0, o.theta * dt, p->sigma, 0));
-    TRY(prepare_family(p, 1, o.theta * dt, p->sigma, 0));
+    TRY(prepare_family(p, 0, o.theta * dt, dt, p->sigma, 0));
+    TRY(prepare_family(p, 1, o.theta * dt, dt, p->sigma, 0));
     TRY(load_family(p, nullptr, 0.0));
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) ADR_CUDA_TRY(cudaEventCreate(&ev[k]));
@@ -655,8 +669,8 @@ adr_status prepare_batch(adr_batch* b)
     for (size_t i = 0; i < b->hs.size(); ++i) {
         Problem* p = &b->hs[i]->p;
         double td = p->opts.theta * b->dts[i];
-        TRY(prepare_family(p, 0, td, p->sigma, 0));
-        TRY(prepare_family(p, 1, td, p->sigma, 0));
+        TRY(prepare_family(p, 0, td, b->dts[i], p->sigma, 0));
+        TRY(prepare_family(p, 1, td, b->dts[i], p->sigma, 0));
         TRY(load_family(p, nullptr, 0.0));
     }
     return ADR_OK;
@@ -765,6 +779,7 @@ adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* co
             return ADR_EINVAL;
         }
     std::vector<IterState> st(n);
+    std::vector<double> piv(2 * (size_t)n, INFINITY);
     float ms = 0.f;
     adr_status s = on_batch_stream(b, [&]() -> adr_status {
         for (int i = 0; i < n; ++i) {
@@ -780,9 +795,12 @@ adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* co
             TRY(launch_finish(&b->hs[i]->p, u_out[i], u_iter_out ? u_iter_out[i] : nullptr,
                               b->hs[i]->p.opts.theta == 0.5));
         ADR_CUDA_TRY(cudaEventRecord(b->ev1, b->stream));
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
             ADR_CUDA_TRY(cudaMemcpyAsync(&st[i], b->hs[i]->p.state, sizeof(IterState),
                                          cudaMemcpyDeviceToHost, b->stream));
+            ADR_CUDA_TRY(cudaMemcpyAsync(&piv[2 * i], b->hs[i]->p.pivmin, 2 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, b->stream));
+        }
         ADR_CUDA_TRY(cudaStreamSynchronize(b->stream));
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);
         return ADR_OK;
@@ -798,6 +816,9 @@ adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* co
             stats[i].ms = ms;
             stats[i].line_dofs = (double)st[i].iter * (h->line_unknowns[0] + h->line_unknowns[1]);
             stats[i].dt = b->dts[i];
+            stats[i].min_pivot = std::fmin(piv[2 * i], piv[2 * i + 1]);
+            stats[i].max_correction = st[i].iter > 0 ? st[i].corr : 0.0;
+            stats[i].fp32_steps = h->p.opts.prec == ADR_FP32_REFINE ? st[i].fp32_steps : 0;
         }
     }
     if (!all) {

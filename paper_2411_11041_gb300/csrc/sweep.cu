@@ -15,7 +15,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "adr_internal.cuh"
@@ -23,23 +25,39 @@
 namespace adr {
 namespace {
 
-constexpr int kCmax = 8;       // rows per thread held in registers by the curve solve
+constexpr int kCmax = 16;      // most rows per thread of the curve solve (kept in shared memory)
 constexpr int kGridThreads = 256;
 
 // ---------------------------------------------------------------- curves
-// The curve systems (M + theta dt S) are fixed for a given (theta dt, sigma),
-// so their partitioned elimination is factored once (k_curve_prep) and every
-// split step only carries the right-hand side through it (k_curve_solve).
+// The curve systems A = M + theta dt S are fixed for a given (theta, dt,
+// sigma), so their partitioned elimination is factored once (k_curve_prep)
+// and every split step only carries a right-hand side through it
+// (k_curve_solve).
 //
 // One block of T threads per curve (T = 32..1024 chosen per curve so that a
-// thread owns at most kCmax rows).  Thread t owns rows [t c, t c + c) of the
-// curve's m unknowns, c = ceil(m / T) (row q <-> curve node q+1).  Downward
-// elimination inside a chunk writes every row as
+// thread owns at most R <= kCmax rows).  Thread t owns rows [t c, t c + c) of
+// the curve's m unknowns, c = ceil(m / T) (row q <-> curve node q+1).
+// Downward elimination inside a chunk writes every row as
 //     x_q + cp_q x_{q+1} + vp_q x_{s-1} = rp_q,   rp_q = r_q ip_q - lp_q rp_{q-1},
 // an upward pass gives the chunk's first unknown in terms of the chunk ends,
 // the chunk ends G_t = x_{e_t - 1} satisfy a T-equation tridiagonal system
 // solved by cyclic reduction in shared memory (multipliers factored once),
-// and back substitution gives every x_q.
+// and back substitution gives every x_q.  The rows' rp values stay in shared
+// memory between the passes.
+//
+// What is solved (§6 eqs. SemiDiscrSplit1Dbeta / SemiDiscrSplit1Dgamma, with
+// the curve values carried as v = u + dt d):
+//  * FP64 mode: the new curve values directly,
+//        A v = dt F + (M - (1 - theta) dt S) u,
+//    the same v as u + dt A^-1 (F - S u) without the update of every row;
+//  * reduced-precision mode: one step of mixed-precision iterative refinement
+//    of that system from the current curve values x0 = u: the residual
+//    dt (F - S u) is formed in FP64, the correction A d = F - S u is solved in
+//    FP32 with the factors rounded to FP32, and v = u + dt d is accumulated in
+//    FP64;
+//  * the steady start (eq. u0stationary): S v = F.
+// Every right-hand-side row is stored times its row factor ip, so the rhs and
+// the first elimination step are plain FMAs.
 //
 // Per-row data live in a chunk-interleaved "slot" layout: row (t, j) of a
 // curve is stored at soff[curve] + j T + t, so that the j-th row of all
@@ -61,19 +79,24 @@ struct CurveArgs {
     const double* eta;
     const double* fextra;  // load kernel only
     double fx_scale;
-    double* Fl;            // per slot: load F (B); times the row's pivot ip when scaled
-    double* srow;          // 3 planes per slot: S sub/diag/super (B), times ip when scaled;
-                           // G when scaled: one plane, (mu / h) ip
-    int scaled;            // FP64 mode: F and S rows carry the factor ip of their row
+    double* Fl;            // per slot: ip (dt F) in the FP64 form, ip F otherwise (B)
+    double* srow;          // B: 3 planes per slot, ip (M - (1-theta) dt S) rows in the FP64
+                           // form, -ip S rows otherwise; G: one plane, ip times the
+                           // off-diagonal coefficient of the rhs stencil
+    double* kap;           // G, per curve: diagonal / off-diagonal ratio of the rhs stencil
+    int vform;             // 1: FP64 form (new values); 0: residual form or steady start
+    double fscale;         // load scale of the right-hand side (dt in the FP64 form, else 1)
     int supg;              // B curves: SUPG-stabilised element forms (mass, S and load)
     double* fac;           // 4 planes per slot: cp, vp, ip, lp
     float* fac32;          // the same factors rounded to FP32 (reduced-precision mode)
     const double* lanecs[3];   // reduced-system constants of the item sets (batched launches)
     const float* lanec32s[3];
     double* v;             // per node: curve values
+    double* pivmin;        // prep: the smallest |pivot| of the family (an ordered-int bit pattern)
     int n_slots;
+    int R;                 // rows per thread of the launch (shared-memory stride)
     double mu, sig, td, dt;
-    int paper;             // steady solve S u0 = F (no mass term, values out)
+    int paper;             // steady solve S v = F (no mass term, values out)
 };
 
 // Work items: a block of BS threads takes BS/T curves of the same block size
@@ -178,7 +201,8 @@ __global__ void __launch_bounds__(BS) k_curve_gdesc(CurveArgs a, const int* item
     }
 }
 
-// load F = M f on the B curves (f + fx_scale * fextra when an extra load is given)
+// load F = M f on the B curves (f + fx_scale * fextra when an extra load is given),
+// stored times the row factor ip and the form's scale
 template <int BS>
 __global__ void __launch_bounds__(BS) k_curve_load(CurveArgs a, const int* item_T,
                                                    const int* item_curve)
@@ -212,10 +236,30 @@ __global__ void __launch_bounds__(BS) k_curve_load(CurveArgs a, const int* item_
             F += tl * (2.0 * f0 * bm + f0 * b0 + f1 * bm + 2.0 * f1 * b0) / 6.0 -
                  tr * (2.0 * f1 * b0 + f1 * bp + f2 * b0 + 2.0 * f2 * bp) / 6.0;
         }
-        a.Fl[sl] = a.scaled ? F * a.fac[2 * a.n_slots + sl] : F;  // row factor ip (k_curve_prep)
+        a.Fl[sl] = F * (a.fac[2 * a.n_slots + sl] * a.fscale);  // times ip (k_curve_prep) and dt or 1
         f0 = f1;
         f1 = f2;
     }
+}
+
+// 2 x 2 projective map [[a b][c d]] (the Thomas pivot recurrence); products
+// are rescaled by a power of two so that long chains stay finite
+struct Mob {
+    double a, b, c, d;
+};
+__device__ __forceinline__ Mob mob_mul(const Mob& X, const Mob& Y)
+{
+    Mob Z{fma(X.a, Y.a, X.b * Y.c), fma(X.a, Y.b, X.b * Y.d), fma(X.c, Y.a, X.d * Y.c),
+          fma(X.c, Y.b, X.d * Y.d)};
+    const double s = fmax(fmax(fabs(Z.a), fabs(Z.b)), fmax(fabs(Z.c), fabs(Z.d)));
+    if (s > 0.0 && isfinite(s)) {
+        const int e = ilogb(s);
+        Z.a = scalbn(Z.a, -e);
+        Z.b = scalbn(Z.b, -e);
+        Z.c = scalbn(Z.c, -e);
+        Z.d = scalbn(Z.d, -e);
+    }
+    return Z;
 }
 
 template <int BS, int FAM>
@@ -224,88 +268,92 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
                                                    float* lanec32)
 {
     constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
-    __shared__ double sA[BS], sB[BS], sC[BS];
+    __shared__ double sA[BS], sB[BS], sC[BS], sD[BS];
     BlockChunk b;
     item_chunk<BS>(a, item_T, item_curve, b);
     const int tid = threadIdx.x, lt = b.lt, T = b.T, L = __ffs(T) - 1, m = b.m, base = b.base;
     const bool has = b.cnt > 0;
     const size_t NS = a.n_slots;
-    double cpL = 0, vpL = 0;
-    if (has) {
-        const double h = a.h[b.line];
-        const double Mo = h / 6.0, Md = 2.0 * h / 3.0, Ko = -1.0 / h, Kd = 2.0 / h;
-        const double mw = a.paper ? 0.0 : 1.0, td = a.td;
-        double b0 = 0, b1 = 0, b2 = 0;
+    const double h = b.active ? a.h[b.line] : 1.0;
+    const double Mo = h / 6.0, Md = 2.0 * h / 3.0, Ko = -1.0 / h, Kd = 2.0 / h;
+    const double mw = a.paper ? 0.0 : 1.0, td = a.td;
+    const double dd = a.dt - a.td;  // (1 - theta) dt of the FP64 form's right-hand side
+    // element rows of node q + 1: mass M and operator S (sub, diag, super)
+    auto rowcoef = [&](int q, double* Mr, double* Sr) {
+        Mr[0] = Mo;
+        Mr[1] = Md;
+        Mr[2] = Mo;
         if (FAM == 0) {
-            b0 = a.bnorm[base + b.s];
-            b1 = a.bnorm[base + b.s + 1];
+            const double b0 = a.bnorm[base + q], b1 = a.bnorm[base + q + 1], b2 = a.bnorm[base + q + 2];
+            const double Csub = -(b0 * (1.0 / 6.0) + b1 * (1.0 / 3.0));
+            const double Cdia = (b0 - b2) * (1.0 / 6.0);
+            const double Csup = b1 * (1.0 / 3.0) + b2 * (1.0 / 6.0);
+            Sr[0] = a.mu * Ko + Csub + a.sig * Mo;
+            Sr[1] = a.mu * Kd + Cdia + a.sig * Md;
+            Sr[2] = a.mu * Ko + Csup + a.sig * Mo;
+            if (a.supg) {  // SUPG terms of the two elements of node q + 1
+                const double tl = supg_tau(h, 0.5 * (b0 + b1), a.mu);
+                const double tr = supg_tau(h, 0.5 * (b1 + b2), a.mu);
+                const double mbs = tl * (2.0 * b0 + b1) / 6.0;
+                const double mbd = tl * (b0 + 2.0 * b1) / 6.0 - tr * (2.0 * b1 + b2) / 6.0;
+                const double mbp = -tr * (b1 + 2.0 * b2) / 6.0;
+                const double al = tl * (b0 * b0 + b0 * b1 + b1 * b1) / (3.0 * h);
+                const double ar = tr * (b1 * b1 + b1 * b2 + b2 * b2) / (3.0 * h);
+                Mr[0] += mbs;
+                Mr[1] += mbd;
+                Mr[2] += mbp;
+                Sr[0] += -al + a.sig * mbs;
+                Sr[1] += al + ar + a.sig * mbd;
+                Sr[2] += -ar + a.sig * mbp;
+            }
+        } else {
+            Sr[0] = a.mu * Ko;
+            Sr[1] = a.mu * Kd;
+            Sr[2] = Sr[0];
         }
-        double cpp = 0, vpp = 0;
+    };
+    // row q of A = mw M + td S (Dirichlet couplings dropped)
+    auto sysrow = [&](int q, const double* Mr, const double* Sr, double& A, double& B, double& C) {
+        A = (q == 0) ? 0.0 : mw * Mr[0] + td * Sr[0];
+        B = mw * Mr[1] + td * Sr[1];
+        C = (q == m - 1) ? 0.0 : mw * Mr[2] + td * Sr[2];
+    };
+    double cpL = 0, vpL = 0, A0 = 0, B0 = 1, Clast = 0;
+    Mob P{1.0, 0.0, 0.0, 1.0};  // pivot maps of the chunk's rows after its first
+    if (has) {
+        double cpp = 0, vpp = 0, Cprev = 0;
         for (int j = 0; j < b.cnt; ++j) {
             const int q = b.s + j;
             const size_t sl = b.so + (size_t)j * T + lt;
-            double Ssub, Sdia, Ssup;
-            double Msub = Mo, Mdia = Md, Msup = Mo;
-            if (FAM == 0) {
-                b2 = a.bnorm[base + q + 2];
-                double Csub = -(b0 * (1.0 / 6.0) + b1 * (1.0 / 3.0));
-                double Cdia = (b0 - b2) * (1.0 / 6.0);
-                double Csup = b1 * (1.0 / 3.0) + b2 * (1.0 / 6.0);
-                Ssub = a.mu * Ko + Csub + a.sig * Mo;
-                Sdia = a.mu * Kd + Cdia + a.sig * Md;
-                Ssup = a.mu * Ko + Csup + a.sig * Mo;
-                if (a.supg) {  // SUPG terms of the two elements of node q + 1
-                    const double tl = supg_tau(h, 0.5 * (b0 + b1), a.mu);
-                    const double tr = supg_tau(h, 0.5 * (b1 + b2), a.mu);
-                    const double mbs = tl * (2.0 * b0 + b1) / 6.0;
-                    const double mbd = tl * (b0 + 2.0 * b1) / 6.0 - tr * (2.0 * b1 + b2) / 6.0;
-                    const double mbp = -tr * (b1 + 2.0 * b2) / 6.0;
-                    const double al = tl * (b0 * b0 + b0 * b1 + b1 * b1) / (3.0 * h);
-                    const double ar = tr * (b1 * b1 + b1 * b2 + b2 * b2) / (3.0 * h);
-                    Msub += mbs;
-                    Mdia += mbd;
-                    Msup += mbp;
-                    Ssub += -al + a.sig * mbs;
-                    Sdia += al + ar + a.sig * mbd;
-                    Ssup += -ar + a.sig * mbp;
-                }
-                a.srow[sl] = Ssub;
-                a.srow[NS + sl] = Sdia;
-                a.srow[2 * NS + sl] = Ssup;
-                b0 = b1;
-                b1 = b2;
-            } else {
-                Ssub = a.mu * Ko;
-                Sdia = a.mu * Kd;
-                Ssup = Ssub;
-            }
-            double A = (q == 0) ? 0.0 : mw * Msub + td * Ssub;
-            double B = mw * Mdia + td * Sdia;
-            double C = (q == m - 1) ? 0.0 : mw * Msup + td * Ssup;
+            double Mr[3], Sr[3], A, B, C;
+            rowcoef(q, Mr, Sr);
+            sysrow(q, Mr, Sr, A, B, C);
             double ip, cp, vp, lp;
             if (j == 0) {
                 ip = 1.0 / B;
                 cp = C * ip;
                 vp = A * ip;
                 lp = 0.0;
+                A0 = A;
+                B0 = B;
             } else {
                 ip = 1.0 / (B - A * cpp);
                 cp = C * ip;
                 vp = -A * vpp * ip;
                 lp = A * ip;
+                P = mob_mul(Mob{B, -A * Cprev, 1.0, 0.0}, P);
             }
             a.fac[sl] = cp;
             a.fac[NS + sl] = vp;
             a.fac[2 * NS + sl] = ip;
             a.fac[3 * NS + sl] = lp;
-            if (a.scaled) {  // fold the row factor into the right-hand side's rows
-                if (FAM == 0) {
-                    a.srow[sl] = Ssub * ip;
-                    a.srow[NS + sl] = Sdia * ip;
-                    a.srow[2 * NS + sl] = Ssup * ip;
-                } else {
-                    a.srow[sl] = (a.mu / h) * ip;
-                }
+            // right-hand-side rows times ip: (M - (1 - theta) dt S) in the FP64
+            // form, -S in the residual form
+            if (FAM == 0) {
+                for (int k = 0; k < 3; ++k)
+                    a.srow[k * NS + sl] = (a.vform ? Mr[k] - dd * Sr[k] : -Sr[k]) * ip;
+            } else {
+                a.srow[sl] = (a.vform ? Mr[0] - dd * Sr[0] : -Sr[0]) * ip;
             }
             if (a.fac32) {
                 a.fac32[sl] = (float)cp;
@@ -315,9 +363,18 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
             }
             cpp = cp;
             vpp = vp;
+            Cprev = C;
         }
         cpL = cpp;
         vpL = vpp;
+        Clast = Cprev;
+    }
+    // G: ratio of the diagonal to the off-diagonal coefficient of the rhs
+    // stencil (constant along a curve)
+    if (FAM == 1 && b.active && lt == 0 && m > 0) {
+        double Mr[3], Sr[3];
+        rowcoef(0, Mr, Sr);
+        a.kap[b.line] = a.vform ? (Mr[1] - dd * Sr[1]) / (Mr[0] - dd * Sr[0]) : -2.0;
     }
     // fixed part of the upward pass: x_s = rho - kap G_t - nu G_{t-1}
     double kap = has ? -1.0 : 0.0, nu = 0.0;
@@ -363,366 +420,285 @@ __global__ void __launch_bounds__(BS) k_curve_prep(CurveArgs a, const int* item_
         float* L32 = lanec32 + (size_t)blockIdx.x * NF * BS;
         for (int f = 0; f < NF; ++f) L32[f * BS + tid] = (float)Lc[f * BS + tid];
     }
+    if (!a.pivmin) return;  // uniform over the block
+    // Thomas pivots of the whole curve (the smallest-pivot diagnostic): the
+    // recurrence d_q = B_q - A_q C_{q-1} / d_{q-1} maps (p, r) -> (B_q p -
+    // A_q C_{q-1} r, p).  Each thread composes its chunk's maps, a scan over
+    // the curve's threads gives every chunk its incoming pivot, and each
+    // thread re-runs its rows from it.
+    sD[tid] = Clast;
+    __syncthreads();
+    const double Cin = (lt > 0) ? sD[tid - 1] : 0.0;
+    __syncthreads();
+    Mob S = has ? mob_mul(P, Mob{B0, -A0 * Cin, 1.0, 0.0}) : Mob{1.0, 0.0, 0.0, 1.0};
+    for (int l = 0; l < L; ++l) {  // L is uniform over the block
+        const int d = 1 << l;
+        sA[tid] = S.a;
+        sB[tid] = S.b;
+        sC[tid] = S.c;
+        sD[tid] = S.d;
+        __syncthreads();
+        if (lt >= d) S = mob_mul(S, Mob{sA[tid - d], sB[tid - d], sC[tid - d], sD[tid - d]});
+        __syncthreads();
+    }
+    sA[tid] = S.a + S.b;  // state after the thread's rows, from (1, 1)
+    sB[tid] = S.c + S.d;
+    __syncthreads();
+    double dprev = (lt > 0) ? sA[tid - 1] / sB[tid - 1] : 1.0;
+    double dmin = INFINITY, Cprev = Cin;
+    for (int j = 0; j < b.cnt; ++j) {
+        const int q = b.s + j;
+        double Mr[3], Sr[3], Aq, Bq, Cq;
+        rowcoef(q, Mr, Sr);
+        sysrow(q, Mr, Sr, Aq, Bq, Cq);
+        const double dq = (q == 0) ? Bq : Bq - Aq * Cprev / dprev;
+        dmin = fmin(dmin, fabs(dq));
+        dprev = dq;
+        Cprev = Cq;
+    }
+    for (int o = 16; o > 0; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    if ((tid & 31) == 0 && dmin < INFINITY)
+        atomicMin(reinterpret_cast<unsigned long long*>(a.pivmin),
+                  (unsigned long long)__double_as_longlong(dmin));
 }
 
-// curve solve of one work item (block size T, curves[0 .. BS/T-1], reduced-
-// system constants Lc); the whole block calls it
-// SU: the gathered row values live in shared memory (sU, kCmax * BS) instead
-// of registers; PF: the reduction's factors are loaded a level ahead, so that
-// they are in flight during the barrier before each level.  The kernels that
-// use them are compiled for a register count that keeps enough blocks per SM
-// (measured: the single-problem kernels at BS <= 512 and the 256-thread
-// FP64 batch kernel).
-template <int BS, int FAM, bool SU = false, bool PF = false>
+// FP64 <-> FP32 conversions on the integer pipe.  On this GPU the FP64 unit
+// issues 2 lanes per SM per clock and also executes F2F conversions, so the
+// reduced-precision solve converts with bit operations on the IEEE-754 fields.
+// toward zero; |x| < 2^-126 gives a signed zero, |x| >= 2^128 an infinity
+__device__ __forceinline__ float f64_to_f32(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sgn = hi & 0x80000000u, ah = hi & 0x7fffffffu;
+    unsigned f = __funnelshift_r(lo, hi, 29) - (384u << 23);  // exponent bias 1023 -> 127 (mod 2^9)
+    if (ah < (897u << 20)) f = 0u;
+    else if (ah >= (1151u << 20))
+        f = (ah > 0x7ff00000u || (ah == 0x7ff00000u && lo)) ? 0x7fc00000u : 0x7f800000u;
+    return __uint_as_float(f | sgn);
+}
+
+// exact for normal values; subnormals give a signed zero
+__device__ __forceinline__ double f32_to_f64(float x)
+{
+    const unsigned b = __float_as_uint(x), sgn = b & 0x80000000u, a = b & 0x7fffffffu;
+    unsigned hi = sgn | ((a >> 3) + (896u << 20)), lo = b << 29;
+    if (a < 0x00800000u) {
+        hi = sgn;
+        lo = 0u;
+    } else if (a >= 0x7f800000u) {
+        hi = sgn | 0x7ff00000u | ((a >> 3) & 0x000fffffu);
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float mad(float x, float y, float z) { return __fmaf_rn(x, y, z); }
+__device__ __forceinline__ double mad(double x, double y, double z) { return __fma_rn(x, y, z); }
+
+// shared memory of a curve-solve block of BS threads whose longest chunk has
+// R rows: the reduction's exchange buffers [2][BS] and the rows' rp values
+// [R][BS] (8-byte slots, also in the FP32 elimination)
+template <int BS>
+__host__ __device__ constexpr size_t solve_smem(int R)
+{
+    return (size_t)(2 + R) * BS * sizeof(double);
+}
+
+template <typename E>
+__device__ __forceinline__ float as_f32(E x)
+{
+    if constexpr (sizeof(E) == 4) return x;
+    else return f64_to_f32(x);
+}
+
+// Curve solve of one work item (block size T, curves[0 .. BS/T-1], reduced-
+// system constants Lc, elimination factors fac in precision E); the whole
+// block calls it.  RES = 0: FP64 new-value form, v = x.  RES = 1: residual
+// form, the correction x in precision E and v = u + dt x accumulated in FP64
+// (u is parked in v between the passes).  The rows' rp values live in
+// shared memory [R][BS] between the passes.
+template <int BS, int FAM, bool RES, typename E>
 __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, const int* curves,
-                                                 const double* Lc, double (*sR)[BS],
-                                                 double* sU = nullptr)
+                                                 const E* __restrict__ Lc, const E* __restrict__ fac,
+                                                 unsigned char* smem)
 {
     constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
+    E (*sR)[BS] = reinterpret_cast<E (*)[BS]>(smem);
+    double* __restrict__ buf = reinterpret_cast<double*>(smem + 2 * BS * sizeof(double));
+    const int tid = threadIdx.x;
+    // row j's 8-byte slot of rp (E)
+    auto rp = [&](int j) -> E& { return *reinterpret_cast<E*>(buf + j * BS + tid); };
     const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
     double* __restrict__ v = a.v;
     BlockChunk b;
     item_chunk_of(a, Titem, curves, b);
-    const int tid = threadIdx.x, lt = b.lt, T = b.T, L = __ffs(T) - 1;
+    const int lt = b.lt, T = b.T, L = __ffs(T) - 1;
     if (b.active && b.n < 2 && lt <= b.n) v[b.base + lt] = 0.0;
-    const int base = b.base, n = b.n, s = b.s, cnt = b.cnt;
-    const size_t NS = a.n_slots, so = b.so;
+    const int base = b.base, s = b.s, cnt = b.cnt;
+    const size_t NS = a.n_slots;
+    const int so = (int)b.so;
     const bool paper = a.paper != 0;
-    auto uslot = [&](int sl) -> double { return gather_w(u, a.nx, __ldg(a.gcell + sl), a.gw, NS, sl); };
-    double rp[kCmax], ur[kCmax];
-    double rpp = 0.0;
-    const int so32 = (int)so;
-    const double* __restrict__ cpP = a.fac;
-    const double* __restrict__ vpP = a.fac + NS;
+    E rpp = E(0);
     if (cnt > 0) {
-        // node s (row s-1: the previous thread's last row) and node s+1 (own row 0)
-        double u0 = (paper || s == 0) ? 0.0 : uslot(so32 + (b.c - 1) * T + (lt - 1));
-        double u1 = paper ? 0.0 : uslot(so32 + lt);
-#pragma unroll
-        for (int j = 0; j < kCmax; ++j) {
-            if (j < cnt) {
-                const int sl = so32 + j * T + lt;
-                double u2;  // node s+j+2 = row s+j+1
-                if (paper) u2 = 0.0;
-                else if (j + 1 < cnt) u2 = uslot(sl + T);
-                else if (s + cnt < b.m) u2 = uslot(so32 + lt + 1);  // next thread's row 0
-                else u2 = 0.0;                                      // the curve's end node
-                // right-hand side times the row's factor ip (folded into F and S)
-                double r;
-                if (FAM == 0) {
-                    r = fma(-__ldg(a.srow + sl), u0, __ldg(a.Fl + sl));
-                    r = fma(-__ldg(a.srow + NS + sl), u1, r);
-                    r = fma(-__ldg(a.srow + 2 * NS + sl), u2, r);
-                } else {
-                    r = __ldg(a.srow + sl) * fma(-2.0, u1, u0 + u2);
+        const double kap = (FAM == 1) ? __ldg(a.kap + b.line) : 0.0;
+        auto uslot = [&](int sl) -> double { return gather_w(u, a.nx, __ldg(a.gcell + sl), a.gw, NS, sl); };
+        double u0 = 0.0, u1 = 0.0;
+        if (!paper) {
+            u0 = (s == 0) ? 0.0 : uslot(so + (b.c - 1) * T + (lt - 1));
+            u1 = uslot(so + lt);
+        }
+        // the gather descriptors (cell, corner weights) of the row gathered at
+        // iteration j (u at node s+j+2; slot -1: the curve's end, u = 0) are
+        // loaded one iteration ahead, so that only the corner loads wait
+        auto next_slot = [&](int j) -> int {
+            return paper ? -1
+                         : (j + 1 < cnt ? so + (j + 1) * T + lt
+                                        : (j + 1 == cnt && s + cnt < b.m ? so + lt + 1 : -1));
+        };
+        int nsl = next_slot(0), ncell = 0;
+        double nw0 = 0.0, nw1 = 0.0, nw2 = 0.0, nw3 = 0.0;
+        auto load_desc = [&]() {
+            ncell = __ldg(a.gcell + nsl);
+            nw0 = __ldg(a.gw + nsl);
+            nw1 = __ldg(a.gw + NS + nsl);
+            nw2 = __ldg(a.gw + 2 * NS + nsl);
+            nw3 = __ldg(a.gw + 3 * NS + nsl);
+        };
+        if (nsl >= 0) load_desc();
+        for (int j = 0; j < cnt; ++j) {
+            const int sl = so + j * T + lt;
+            double u2 = 0.0;
+            if (nsl >= 0) {
+                const double* r0 = u + ncell;
+                u2 = nw0 * __ldg(r0);
+                u2 = fma(nw1, __ldg(r0 + 1), u2);
+                u2 = fma(nw2, __ldg(r0 + a.nx), u2);
+                u2 = fma(nw3, __ldg(r0 + a.nx + 1), u2);
+            }
+            nsl = next_slot(j + 1);
+            if (nsl >= 0) load_desc();
+            if constexpr (RES) {
+                if (!paper) v[base + s + j + 1] = u1;
+            }
+            double r;
+            if (FAM == 0) {
+                r = __ldg(a.Fl + sl);
+                if (!paper) {
+                    r = fma(__ldg(a.srow + sl), u0, r);
+                    r = fma(__ldg(a.srow + NS + sl), u1, r);
+                    r = fma(__ldg(a.srow + 2 * NS + sl), u2, r);
                 }
-                rpp = fma(-__ldg(a.fac + 3 * NS + sl), rpp, r);
-                rp[j] = rpp;
-                if (SU) sU[j * BS + tid] = u1;
-                else ur[j] = u1;
-                u0 = u1;
-                u1 = u2;
-            }
-        }
-    }
-    // upward pass over the chunk: rho for its first row
-    double rho = 0.0;
-#pragma unroll
-    for (int j = kCmax - 2; j >= 0; --j)
-        if (j <= cnt - 2) rho = rp[j] - __ldg(cpP + so32 + j * T + lt) * rho;
-    double R, G;
-    int buf = 1;
-    if (PF) {
-        // the reduction's factors are loaded a level ahead, so that each load
-        // is in flight while the block waits at the barrier before it is used
-        const double lc0 = Lc[tid];
-        double k1n = 0.0, k2n = 0.0;
-        if (L > 0) {
-            k1n = Lc[BS + tid];
-            k2n = Lc[(1 + LMAX) * BS + tid];
-        }
-        sR[0][tid] = rho;
-        __syncthreads();
-        double rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.0;
-        R = cnt > 0 ? rpp - lc0 * rhoN : 0.0;
-        double ib = 0.0;
-        // L (levels of this item's curves) is the same for the whole block
-#pragma unroll
-        for (int l = 0; l < LMAX; ++l) {
-            if (l >= L) break;
-            const int d = 1 << l;
-            const double k1 = k1n, k2 = k2n;
-            if (l + 1 < L) {
-                k1n = Lc[(2 + l) * BS + tid];
-                k2n = Lc[(2 + LMAX + l) * BS + tid];
             } else {
-                ib = Lc[(NF - 1) * BS + tid];
+                r = __ldg(a.srow + sl) * fma(kap, u1, u0 + u2);
             }
-            sR[buf][tid] = R;
-            __syncthreads();
-            double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
-            double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
-            R = R - k1 * Rm - k2 * Rp;
-            buf ^= 1;
+            E re;
+            if constexpr (sizeof(E) == 4) re = f64_to_f32(r);
+            else re = r;
+            rpp = mad(-__ldg(fac + 3 * NS + sl), rpp, re);
+            rp(j) = rpp;
+            u0 = u1;
+            u1 = u2;
         }
-        if (L == 0) ib = Lc[(NF - 1) * BS + tid];
-        G = R * ib;
+    }
+    // 3. upward pass over the chunk: rho for its first row
+    E rho = E(0);
+    for (int j = cnt - 2; j >= 0; --j) rho = mad(-__ldg(fac + so + j * T + lt), rho, rp(j));
+    // 4. reduced system of the chunk ends; its factors are loaded a level
+    //    ahead, so that each load is in flight while the block waits
+    const E lc0 = Lc[tid];
+    E k1n = E(0), k2n = E(0), ib = E(0);
+    if (L > 0) {
+        k1n = Lc[BS + tid];
+        k2n = Lc[(1 + LMAX) * BS + tid];
     } else {
-        sR[0][tid] = rho;
-        __syncthreads();
-        double rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.0;
-        R = cnt > 0 ? rpp - Lc[tid] * rhoN : 0.0;
-#pragma unroll
-        for (int l = 0; l < LMAX; ++l) {
-            if (l >= L) break;  // uniform over the block
-            const int d = 1 << l;
-            sR[buf][tid] = R;
-            __syncthreads();
-            double Rm = lt >= d ? sR[buf][tid - d] : 0.0;
-            double Rp = lt + d < T ? sR[buf][tid + d] : 0.0;
-            R = R - Lc[(1 + l) * BS + tid] * Rm - Lc[(1 + LMAX + l) * BS + tid] * Rp;
-            buf ^= 1;
-        }
-        G = R * Lc[(NF - 1) * BS + tid];
+        ib = Lc[(NF - 1) * BS + tid];
     }
-    sR[buf][tid] = G;
-    __syncthreads();
-    double Gm = lt > 0 ? sR[buf][tid - 1] : 0.0;
-    const double w = paper ? 1.0 : a.dt;
-    double x = G;
-#pragma unroll
-    for (int j = kCmax - 1; j >= 0; --j) {
-        if (j < cnt) {
-            const int sl = so32 + j * T + lt;
-            if (j < cnt - 1) x = rp[j] - __ldg(cpP + sl) * x - __ldg(vpP + sl) * Gm;
-            v[base + s + j + 1] = (paper ? 0.0 : (SU ? sU[j * BS + tid] : ur[j])) + w * x;
-        }
-    }
-    if (b.active && n >= 2 && lt == 0) {
-        v[base] = 0.0;
-        v[base + n] = 0.0;
-    }
-}
-
-template <int BS, int FAM>
-__global__ void __launch_bounds__(BS) k_curve_solve(CurveArgs a, const int* item_T,
-                                                    const int* item_curve, const double* lanec)
-{
-    if (a.state && a.state->done) return;
-    __shared__ double sR[2][BS];
-    constexpr bool SU = BS <= 512;  // the gathered row values in shared memory
-    __shared__ double sU[SU ? kCmax * BS : 1];
-    curve_solve_body<BS, FAM, SU, true>(a, item_T[blockIdx.x],
-                                        item_curve + blockIdx.x * Items<BS>::MAXC,
-                                        lanec + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sU);
-}
-
-// ----------------------------------------------- FP32 solve + FP64 refinement
-// Reduced-precision mode: x0 = A32^-1 r with the FP32-rounded factors, the
-// residual rho = r - A x0 in FP64 (A's entries rebuilt in FP64), x1 = A32^-1 rho,
-// x = x0 + x1.  The right-hand side, the residual and the state update stay in
-// FP64; only the two eliminations run in FP32.
-
-// one FP32 pass of the partitioned elimination over the calling thread's rows;
-// every thread of the block must call it (it synchronises); returns in x the
-// thread's solution rows and in *gprev the previous thread's last unknown
-template <int BS, bool PF = false>
-__device__ __forceinline__ void elim32(const float (&rhs)[kCmax], float (&x)[kCmax], int cnt,
-                                       int so32, int T, int lt, int L, const float* __restrict__ f32,
-                                       size_t NS, const float* __restrict__ L32, float (*sR)[BS],
-                                       float* gprev)
-{
-    constexpr int LMAX = Items<BS>::LMAX, NF = Items<BS>::NF;
-    const int tid = threadIdx.x;
-    float rp[kCmax];
-    float rpp = 0.f;
-#pragma unroll
-    for (int j = 0; j < kCmax; ++j)
-        if (j < cnt) {
-            const int sl = so32 + j * T + lt;
-            rpp = rhs[j] * __ldg(f32 + 2 * NS + sl) - __ldg(f32 + 3 * NS + sl) * rpp;
-            rp[j] = rpp;
-        }
-    float rho = 0.f;
-#pragma unroll
-    for (int j = kCmax - 2; j >= 0; --j)
-        if (j <= cnt - 2) rho = rp[j] - __ldg(f32 + so32 + j * T + lt) * rho;
-    __syncthreads();  // sR may still be read by a previous pass
     sR[0][tid] = rho;
     __syncthreads();
-    float rhoN = lt + 1 < T ? sR[0][tid + 1] : 0.f;
-    float R = cnt > 0 ? rpp - L32[tid] * rhoN : 0.f;
-    int buf = 1;
-    float G;
-    if (PF) {
-        // factors a level ahead, in flight during the barrier (as in the
-        // FP64 solve)
-        float k1n = 0.f, k2n = 0.f, ib = 0.f;
-        if (L > 0) {
-            k1n = L32[BS + tid];
-            k2n = L32[(1 + LMAX) * BS + tid];
-        }
+    const E rhoN = lt + 1 < T ? sR[0][tid + 1] : E(0);
+    E R = cnt > 0 ? mad(-lc0, rhoN, rpp) : E(0);
+    int bsel = 1;
 #pragma unroll
-        for (int l = 0; l < LMAX; ++l) {
-            if (l >= L) break;  // uniform over the block
-            const int d = 1 << l;
-            const float k1 = k1n, k2 = k2n;
-            if (l + 1 < L) {
-                k1n = L32[(2 + l) * BS + tid];
-                k2n = L32[(2 + LMAX + l) * BS + tid];
-            } else {
-                ib = L32[(NF - 1) * BS + tid];
-            }
-            sR[buf][tid] = R;
-            __syncthreads();
-            float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
-            float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
-            R = R - k1 * Rm - k2 * Rp;
-            buf ^= 1;
+    for (int l = 0; l < LMAX; ++l) {
+        if (l >= L) break;  // L (levels of this item's curves) is the same for the whole block
+        const int d = 1 << l;
+        const E k1 = k1n, k2 = k2n;
+        if (l + 1 < L) {
+            k1n = Lc[(2 + l) * BS + tid];
+            k2n = Lc[(2 + LMAX + l) * BS + tid];
+        } else {
+            ib = Lc[(NF - 1) * BS + tid];
         }
-        if (L == 0) ib = L32[(NF - 1) * BS + tid];
-        G = R * ib;
-    } else {
-#pragma unroll
-        for (int l = 0; l < LMAX; ++l) {
-            if (l >= L) break;  // uniform over the block
-            const int d = 1 << l;
-            sR[buf][tid] = R;
-            __syncthreads();
-            float Rm = lt >= d ? sR[buf][tid - d] : 0.f;
-            float Rp = lt + d < T ? sR[buf][tid + d] : 0.f;
-            R = R - L32[(1 + l) * BS + tid] * Rm - L32[(1 + LMAX + l) * BS + tid] * Rp;
-            buf ^= 1;
-        }
-        G = R * L32[(NF - 1) * BS + tid];
+        sR[bsel][tid] = R;
+        __syncthreads();
+        const E Rm = lt >= d ? sR[bsel][tid - d] : E(0);
+        const E Rp = lt + d < T ? sR[bsel][tid + d] : E(0);
+        R = mad(-k2, Rp, mad(-k1, Rm, R));
+        bsel ^= 1;
     }
-    sR[buf][tid] = G;
+    const E G = R * ib;
+    sR[bsel][tid] = G;
     __syncthreads();
-    float Gm = lt > 0 ? sR[buf][tid - 1] : 0.f;
-    *gprev = Gm;
-    float xx = G;
-#pragma unroll
-    for (int j = kCmax - 1; j >= 0; --j) {
-        x[j] = 0.f;
-        if (j < cnt) {
-            const int sl = so32 + j * T + lt;
-            if (j < cnt - 1) xx = rp[j] - __ldg(f32 + sl) * xx - __ldg(f32 + NS + sl) * Gm;
-            x[j] = xx;
+    const E Gm = lt > 0 ? sR[bsel][tid - 1] : E(0);
+    // 5. back substitution; values out
+    E x = G;
+    float xmax = 0.f;  // residual form: the largest |correction| / dt of the thread's rows
+    for (int j = cnt - 1; j >= 0; --j) {
+        const int sl = so + j * T + lt;
+        if (j < cnt - 1) x = mad(-__ldg(fac + NS + sl), Gm, mad(-__ldg(fac + sl), x, rp(j)));
+        const int node = base + s + j + 1;
+        if constexpr (RES) {
+            double x64;
+            if constexpr (sizeof(E) == 4) x64 = f32_to_f64(x);
+            else x64 = x;
+            v[node] = paper ? x64 : fma(a.dt, x64, v[node]);  // v = u + dt d in FP64
+            xmax = fmaxf(xmax, fabsf(as_f32(x)));
+        } else {
+            v[node] = x;
         }
     }
-}
-
-template <int BS, int FAM, bool PF = false, bool SU = false>
-__device__ __forceinline__ void curve_solve_ref_body(const CurveArgs& a, int Titem,
-                                                     const int* curves, const float* L32,
-                                                     float (*sR)[BS], double* sX, double* sU = nullptr)
-{
-    const double* __restrict__ u = (a.state && (a.state->iter & 1)) ? a.u_odd : a.u_even;
-    double* __restrict__ v = a.v;
-    BlockChunk b;
-    item_chunk_of(a, Titem, curves, b);
-    const int tid = threadIdx.x, lt = b.lt, T = b.T, L = __ffs(T) - 1;
-    if (b.active && b.n < 2 && lt <= b.n) v[b.base + lt] = 0.0;
-    const int base = b.base, n = b.n, s = b.s, cnt = b.cnt, m = b.m;
-    const size_t NS = a.n_slots;
-    const int so32 = (int)b.so;
-    const bool paper = a.paper != 0;
-    auto uslot = [&](int sl) -> double { return gather_w(u, a.nx, __ldg(a.gcell + sl), a.gw, NS, sl); };
-    double r64[kCmax], ur[kCmax];
-    float r32[kCmax];
-    double muh = 0.0, h = 1.0;
-    if (cnt > 0) {
-        h = a.h[b.line];
-        muh = a.mu / h;
-        double u0 = (paper || s == 0) ? 0.0 : uslot(so32 + (b.c - 1) * T + (lt - 1));
-        double u1 = paper ? 0.0 : uslot(so32 + lt);
-#pragma unroll
-        for (int j = 0; j < kCmax; ++j) {
-            r64[j] = 0.0;
-            if (!SU) ur[j] = 0.0;
-            r32[j] = 0.f;
-            if (j < cnt) {
-                const int sl = so32 + j * T + lt;
-                double u2;
-                if (paper) u2 = 0.0;
-                else if (j + 1 < cnt) u2 = uslot(sl + T);
-                else if (s + cnt < m) u2 = uslot(so32 + lt + 1);
-                else u2 = 0.0;
-                double r;
-                if (FAM == 0)
-                    r = __ldg(a.Fl + sl) - (__ldg(a.srow + sl) * u0 + __ldg(a.srow + NS + sl) * u1 +
-                                            __ldg(a.srow + 2 * NS + sl) * u2);
-                else
-                    r = muh * ((u0 + u2) - 2.0 * u1);
-                r64[j] = r;
-                r32[j] = (float)r;
-                if (SU) sU[j * BS + tid] = u1;
-                else ur[j] = u1;
-                u0 = u1;
-                u1 = u2;
-            }
-        }
-    }
-    float x0[kCmax], x1[kCmax], g0;
-    elim32<BS, PF>(r32, x0, cnt, so32, T, lt, L, a.fac32, NS, L32, sR, &g0);
-    // neighbours of the chunk in x0: x_{s-1} = g0 (previous thread), x_e from the next thread
-    sX[tid] = cnt > 0 ? (double)x0[0] : 0.0;
-    __syncthreads();
-    double xe = (lt + 1 < T) ? sX[tid + 1] : 0.0;
-    // FP64 residual rho = r - A x0 on the chunk's rows
-    {
-        const double Mo = h / 6.0, Md = 2.0 * h / 3.0, mw = paper ? 0.0 : 1.0, td = a.td;
-        double xm = (double)g0;
-#pragma unroll
-        for (int j = 0; j < kCmax; ++j) {
-            if (j < cnt) {
-                const int q = s + j, sl = so32 + j * T + lt;
-                double Ssub, Sdia, Ssup;
-                if (FAM == 0) {
-                    Ssub = __ldg(a.srow + sl);
-                    Sdia = __ldg(a.srow + NS + sl);
-                    Ssup = __ldg(a.srow + 2 * NS + sl);
-                } else {
-                    Ssub = -muh;
-                    Sdia = 2.0 * muh;
-                    Ssup = -muh;
-                }
-                double A = (q == 0) ? 0.0 : mw * Mo + td * Ssub;
-                double B = mw * Md + td * Sdia;
-                double C = (q == m - 1) ? 0.0 : mw * Mo + td * Ssup;
-                double xc = (double)x0[j];
-                double xn = (j + 1 < cnt) ? (double)x0[j + 1] : xe;
-                double rho = r64[j] - (A * xm + B * xc + C * xn);
-                r32[j] = (float)rho;
-                xm = xc;
-            }
-        }
-    }
-    elim32<BS, PF>(r32, x1, cnt, so32, T, lt, L, a.fac32, NS, L32, sR, &g0);
-    const double w = paper ? 1.0 : a.dt;
-#pragma unroll
-    for (int j = 0; j < kCmax; ++j)
-        if (j < cnt)
-            v[base + s + j + 1] =
-                (paper ? 0.0 : (SU ? sU[j * BS + tid] : ur[j])) + w * ((double)x0[j] + (double)x1[j]);
-    if (b.active && n >= 2 && lt == 0) {
+    if (b.active && b.n >= 2 && lt == 0) {
         v[base] = 0.0;
-        v[base + n] = 0.0;
+        v[base + b.n] = 0.0;
+    }
+    if constexpr (RES) {
+        // largest correction of the launch (for the solve's statistics)
+        if (a.state && !paper) {
+            for (int o = 16; o > 0; o >>= 1) xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+            if ((tid & 31) == 0 && xmax > 0.f) {
+                const double cmax = a.dt * f32_to_f64(xmax);
+                atomicMax(const_cast<unsigned long long*>(&a.state->corr_bits),
+                          (unsigned long long)__double_as_longlong(cmax));
+            }
+        }
     }
 }
 
+// one work item of the reduced-precision mode: FP32 corrections until the
+// iteration switches to FP64 ones (IterState::hp; a split step outside the
+// iteration always solves in FP32)
 template <int BS, int FAM>
-__global__ void __launch_bounds__(BS, BS == 256 ? 3 : (BS == 512 ? 2 : 1)) k_curve_solve_ref(CurveArgs a, const int* item_T,
-                                                        const int* item_curve, const float* lanec32)
+__device__ __forceinline__ void curve_solve_ref(const CurveArgs& a, int Titem, const int* curves,
+                                                const double* lanec, const float* lanec32,
+                                                unsigned char* smem)
+{
+    if (a.state && a.state->hp) curve_solve_body<BS, FAM, true, double>(a, Titem, curves, lanec, a.fac, smem);
+    else curve_solve_body<BS, FAM, true, float>(a, Titem, curves, lanec32, a.fac32, smem);
+}
+
+// 256-thread blocks are held to 64 registers (4 blocks per SM with their
+// shared memory): measured faster than 3 blocks at 74 registers
+template <int BS, int FAM, bool REF>
+__global__ void __launch_bounds__(BS, BS == 256 ? 4 : (BS == 512 ? 2 : 1)) k_curve_solve(CurveArgs a, const int* item_T,
+                                                    const int* item_curve, const double* lanec,
+                                                    const float* lanec32)
 {
     if (a.state && a.state->done) return;
-    __shared__ float sR[2][BS];
-    __shared__ double sX[BS];
-    constexpr bool SU = BS <= 512;  // the gathered row values in shared memory
-    __shared__ double sU[SU ? kCmax * BS : 1];
-    curve_solve_ref_body<BS, FAM, true, SU>(a, item_T[blockIdx.x],
-                                            item_curve + blockIdx.x * Items<BS>::MAXC,
-                                            lanec32 + (size_t)blockIdx.x * Items<BS>::NF * BS, sR, sX, sU);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = item_T[blockIdx.x];
+    const int* cv = item_curve + blockIdx.x * Items<BS>::MAXC;
+    const size_t lo = (size_t)blockIdx.x * Items<BS>::NF * BS;
+    if constexpr (REF) curve_solve_ref<BS, FAM>(a, T, cv, lanec + lo, lanec32 + lo, smem);
+    else curve_solve_body<BS, FAM, false, double>(a, T, cv, lanec + lo, a.fac, smem);
 }
 
 // ------------------------------------------------------------ batched problems
@@ -750,15 +726,11 @@ struct ActiveLists {
 constexpr int kCountPerBuf = 7;
 
 template <int BS, int FAM, bool REF>
-__global__ void __launch_bounds__(BS, BS == 256 ? (REF ? 3 : 4) : 1) k_curve_solve_batch(const CurveArgs* __restrict__ table,
+__global__ void __launch_bounds__(BS) k_curve_solve_batch(const CurveArgs* __restrict__ table,
                                                           const BatchItem* __restrict__ items,
                                                           ActiveLists act, int set)
 {
-    __shared__ double sR[2][BS];
-    __shared__ float sRf[2][BS];
-    __shared__ double sX[BS];
-    constexpr bool SU = BS == 256;  // the gathered row values in shared memory
-    __shared__ double sU[SU ? kCmax * BS : 1];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int cur = *act.sel;
     const int* list = act.items[cur][FAM][set];
     const int n_act = act.count[cur * kCountPerBuf + FAM * 3 + set];
@@ -766,14 +738,12 @@ __global__ void __launch_bounds__(BS, BS == 256 ? (REF ? 3 : 4) : 1) k_curve_sol
         const BatchItem& I = items[list[ii]];
         const CurveArgs& a = table[2 * I.prob + FAM];
         if (a.state->done) continue;  // uniform: one problem per item
-        if (REF)
-            curve_solve_ref_body<BS, FAM, false, SU>(a, I.T, I.curves,
-                                                     a.lanec32s[set] + (size_t)I.local * Items<BS>::NF * BS,
-                                                     sRf, sX, sU);
+        const size_t lo = (size_t)I.local * Items<BS>::NF * BS;
+        if constexpr (REF)
+            curve_solve_ref<BS, FAM>(a, I.T, I.curves, a.lanecs[set] + lo, a.lanec32s[set] + lo, smem);
         else
-            curve_solve_body<BS, FAM, SU, SU>(a, I.T, I.curves,
-                                          a.lanecs[set] + (size_t)I.local * Items<BS>::NF * BS, sR, sU);
-        __syncthreads();  // shared arrays are reused by the next item
+            curve_solve_body<BS, FAM, false, double>(a, I.T, I.curves, a.lanecs[set] + lo, a.fac, smem);
+        __syncthreads();  // shared memory is reused by the next item
     }
 }
 
@@ -1019,6 +989,12 @@ __global__ void k_check_batch(IterState* const* states, const double* const* par
             st->rel = rel;
             st->converged = conv;
             st->done = (conv || iter >= max_iter || !isfinite(rel)) ? 1 : 0;
+            st->corr = __longlong_as_double((long long)st->corr_bits);
+            st->corr_bits = 0ull;
+            if (!st->hp) {
+                st->fp32_steps += 1;
+                if (tol > 0.0 && rel <= kHpSwitch * tol) st->hp = 1;
+            }
             if (st->done) *changed = 1;
         }
     }
@@ -1070,6 +1046,12 @@ __global__ void k_check(IterState* st, const double* partial, int nblocks, doubl
         st->rel = rel;
         st->converged = conv;
         st->done = (conv || iter >= max_iter || !isfinite(rel)) ? 1 : 0;
+        st->corr = __longlong_as_double((long long)st->corr_bits);  // this step's largest correction
+        st->corr_bits = 0ull;
+        if (!st->hp) {
+            st->fp32_steps += 1;
+            if (tol > 0.0 && rel <= kHpSwitch * tol) st->hp = 1;
+        }
         if (use_cond) cudaGraphSetConditional(handle, st->done ? 0 : 1);
     }
 }
@@ -1107,6 +1089,15 @@ __global__ void k_reset(IterState* st)
     st->done = 0;
     st->converged = 0;
     st->rel = INFINITY;
+    st->corr_bits = 0ull;
+    st->corr = 0.0;
+    st->hp = 0;
+    st->fp32_steps = 0;
+}
+
+__global__ void k_set_bits(double* p, unsigned long long bits)
+{
+    *reinterpret_cast<unsigned long long*>(p) = bits;
 }
 
 }  // namespace
@@ -1128,21 +1119,31 @@ static CurveArgs curve_args(Problem* p, int fam)
     a.eta = F.eta;
     a.Fl = F.Fl;
     a.srow = F.srow;
+    a.kap = F.kap;
     a.fac = F.fac;
     a.fac32 = F.fac32;
     a.v = F.v;
     a.n_slots = F.n_slots;
+    a.R = F.cmax;
     a.mu = p->mu;
-    a.scaled = p->opts.prec == ADR_FP64;
     a.supg = p->opts.stabilize;
+    // the factorisation the family holds (prepare_family)
+    a.td = F.prep_td;
+    a.dt = F.prep_dt;
+    a.sig = F.prep_sig;
+    a.paper = F.prep_paper;
+    a.vform = F.prep_vform;
+    a.fscale = F.prep_vform ? F.prep_dt : 1.0;
     return a;
 }
 
 // split the curves of a family into work items, assign slots and build the
 // gather descriptors (host orchestration, at setup).  A curve of m unknowns
-// gets the smallest block size T >= 32 (power of two) with T * kCmax >= m;
-// items of BS = 256 threads hold 256/T curves of one T, curves with T > 256
-// go to items of BS = 1024.  Items are ordered longest curves first.
+// gets the smallest block size T >= 32 (power of two) with T * R >= m, R the
+// preferred rows per thread, at most 1024 (the longest curves then take up to
+// kCmax rows per thread); items of BS = 256 threads hold 256/T curves of one
+// T, curves with T = 512 or 1024 get items of that size.  Items are ordered
+// longest curves first.
 adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
 {
     Family& F = p->fam[fam];
@@ -1160,7 +1161,7 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
             lg++;
         }
         if ((long long)T * kCmax < m) {
-            set_error("a curve has more than 8192 unknowns");
+            set_error("a curve has more than 16384 unknowns");
             return ADR_EINVAL;
         }
         byT[lg].push_back(l);
@@ -1168,10 +1169,12 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
     }
     std::vector<int> soff(F.n_lines + 1, 0);
     long long tot = 0;
+    F.cmax = 1;
     for (int l = 0; l < F.n_lines; ++l) {
         soff[l] = (int)tot;
         int m = off[l + 1] - off[l] - 2;
         if (m > 0) tot += (long long)Tof[l] * ((m + Tof[l] - 1) / Tof[l]);
+        if (m > 0) F.cmax = std::max(F.cmax, (m + Tof[l] - 1) / Tof[l]);
         if (tot > 0x7fffffffLL) {
             set_error("too many curve rows");
             return ADR_EINVAL;
@@ -1191,9 +1194,12 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
     if (fam == 0) {
         TRY_S(dev_alloc(p, &F.Fl, NS));
         TRY_S(dev_alloc(p, &F.srow, 3 * NS));
-    } else if (p->opts.prec == ADR_FP64) {
+    } else {
         TRY_S(dev_alloc(p, &F.srow, NS));
+        TRY_S(dev_alloc(p, &F.kap, (size_t)F.n_lines + 1));
     }
+    F.prep_valid = false;
+    F.load_plain = false;
     CurveArgs a = curve_args(p, fam);
     cudaStream_t st = p->stream;
     for (int k = 0; k < kItemSets; ++k) {
@@ -1232,8 +1238,9 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
 void release_groups(Problem* p, int fam)
 {
     Family& F = p->fam[fam];
-    void* bufs[] = {F.soff, F.gcell, F.gw, F.fac, F.fac32, F.Fl, F.srow};
+    void* bufs[] = {F.soff, F.gcell, F.gw, F.fac, F.fac32, F.Fl, F.srow, F.kap};
     for (void* q : bufs) dev_free(p, q);
+    F.kap = nullptr;
     F.soff = nullptr;
     F.gcell = nullptr;
     F.gw = nullptr;
@@ -1253,15 +1260,24 @@ void release_groups(Problem* p, int fam)
     F.load_plain = false;
 }
 
-adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper)
+// Factor the family's curve systems for (theta dt, dt, sigma) or the steady
+// start (paper), and record the smallest Thomas pivot of the family.
+adr_status prepare_family(Problem* p, int fam, double td, double dt, double sig, int paper)
 {
     Family& F = p->fam[fam];
-    if (F.prep_valid && F.prep_td == td && F.prep_sig == sig && F.prep_paper == paper) return ADR_OK;
+    const int vform = (p->opts.prec == ADR_FP64 && !paper) ? 1 : 0;
+    if (F.prep_valid && F.prep_td == td && F.prep_dt == dt && F.prep_sig == sig &&
+        F.prep_paper == paper)
+        return ADR_OK;
+    F.prep_td = td;
+    F.prep_dt = dt;
+    F.prep_sig = sig;
+    F.prep_paper = paper;
+    F.prep_vform = vform;
     CurveArgs a = curve_args(p, fam);
-    a.td = td;
-    a.sig = sig;
-    a.paper = paper;
+    a.pivmin = p->pivmin + fam;
     cudaStream_t st = p->stream;
+    k_set_bits<<<1, 1, 0, st>>>(a.pivmin, 0x7ff0000000000000ull);  // +inf: no pivot yet
 #define ADR_PREP(BS_, I_)                                                                          \
     if (I_.count) {                                                                                \
         if (fam == 0)                                                                              \
@@ -1275,10 +1291,7 @@ adr_status prepare_family(Problem* p, int fam, double td, double sig, int paper)
 #undef ADR_PREP
     ADR_CUDA_TRY(cudaGetLastError());
     F.prep_valid = true;
-    F.prep_td = td;
-    F.prep_sig = sig;
-    F.prep_paper = paper;
-    if (fam == 0) F.load_plain = false;  // a scaled load carries the new factors
+    if (fam == 0) F.load_plain = false;  // the load carries the row factors
     return ADR_OK;
 }
 
@@ -1299,30 +1312,65 @@ adr_status load_family(Problem* p, const double* fextra, double fx_scale)
     return ADR_OK;
 }
 
+// the curve-solve kernels may use more than 48 KB of dynamic shared memory
+template <int BS, int FAM, bool REF>
+static cudaError_t solve_attr()
+{
+    const int bytes = (int)solve_smem<BS>(kCmax);
+    cudaError_t e = cudaFuncSetAttribute(k_curve_solve<BS, FAM, REF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_curve_solve_batch<BS, FAM, REF>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+static adr_status ensure_solve_attrs()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    ADR_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return ADR_OK;
+    cudaError_t e = cudaSuccess;
+    cudaError_t r[] = {solve_attr<256, 0, false>(), solve_attr<256, 1, false>(), solve_attr<512, 0, false>(),
+                       solve_attr<512, 1, false>(), solve_attr<1024, 0, false>(), solve_attr<1024, 1, false>(),
+                       solve_attr<256, 0, true>(),  solve_attr<256, 1, true>(),  solve_attr<512, 0, true>(),
+                       solve_attr<512, 1, true>(),  solve_attr<1024, 0, true>(), solve_attr<1024, 1, true>()};
+    for (cudaError_t q : r)
+        if (q != cudaSuccess) e = q;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (curve solve shared memory)");
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return ADR_OK;
+}
+
 adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_even,
                              const double* u_odd, bool use_state, int paper)
 {
     Family& F = p->fam[fam];
+    if (!F.prep_valid || F.prep_paper != paper || (!paper && F.prep_dt != dt)) {
+        set_error("internal: curve systems not factored for this step");
+        return ADR_EINVAL;
+    }
+    TRY_S(ensure_solve_attrs());
     CurveArgs a = curve_args(p, fam);
     a.u_even = u_even;
     a.u_odd = u_odd;
     a.state = use_state ? p->state : nullptr;
-    a.dt = dt;
-    a.paper = paper;
-    a.td = F.prep_td;
     const bool ref = p->opts.prec == ADR_FP32_REFINE;
+    const int R = F.cmax;  // rows of the family's longest chunk
     cudaStream_t st = p->stream;
-#define ADR_SOLVE(BS_, I_)                                                                          \
-    if (I_.count) {                                                                                 \
-        if (ref) {                                                                                  \
-            if (fam == 0)                                                                           \
-                k_curve_solve_ref<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec32); \
-            else                                                                                    \
-                k_curve_solve_ref<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec32); \
-        } else {                                                                                    \
-            if (fam == 0) k_curve_solve<BS_, 0><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec); \
-            else k_curve_solve<BS_, 1><<<I_.count, BS_, 0, st>>>(a, I_.T, I_.curve, I_.lanec);     \
-        }                                                                                           \
+#define ADR_SOLVE(BS_, I_)                                                                         \
+    if (I_.count) {                                                                                \
+        const size_t sm = solve_smem<BS_>(R);                                                      \
+        if (ref) {                                                                                 \
+            if (fam == 0) k_curve_solve<BS_, 0, true><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32); \
+            else k_curve_solve<BS_, 1, true><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32);         \
+        } else {                                                                                   \
+            if (fam == 0) k_curve_solve<BS_, 0, false><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32); \
+            else k_curve_solve<BS_, 1, false><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32);         \
+        }                                                                                          \
     }
     ADR_SOLVE(1024, F.iset[2])
     ADR_SOLVE(512, F.iset[1])
@@ -1431,6 +1479,7 @@ struct BatchDev {
     int* max_iter = nullptr;
     unsigned int* ticket = nullptr;
     bool ref = false;
+    int R = 1;  // rows of the longest chunk of the batch's problems (shared-memory size)
     // active lists (see ActiveLists)
     ActiveLists act{};
     const BatchItem** d_items = nullptr;  // [6] item arrays per family and set
@@ -1474,6 +1523,14 @@ adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const 
     BatchDev* b = new BatchDev;
     b->n = n;
     b->ref = ps[0]->opts.prec == ADR_FP32_REFINE;
+    for (int i = 0; i < n; ++i) b->R = std::max({b->R, ps[i]->fam[0].cmax, ps[i]->fam[1].cmax});
+    {
+        adr_status sa = ensure_solve_attrs();
+        if (sa != ADR_OK) {
+            delete b;
+            return sa;
+        }
+    }
     auto fail = [&](adr_status s) {
         batch_dev_destroy(b);
         return s;
@@ -1493,6 +1550,7 @@ adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const 
             a.dt = dts[i];
             a.td = p->opts.theta * dts[i];
             a.paper = 0;
+            a.vform = p->opts.prec == ADR_FP64;
             for (int k = 0; k < kItemSets; ++k) {
                 a.lanecs[k] = p->fam[fam].iset[k].lanec;
                 a.lanec32s[k] = p->fam[fam].iset[k].lanec32;
@@ -1635,15 +1693,16 @@ static adr_status batch_dev_items(BatchDev* b, Problem* const* ps, int fam, Batc
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaError_t e;
+        const int R = b->R;
         if (BS == 256)
-            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<256, 0, true>, 256, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<256, 0, false>, 256, 0);
+            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<256, 0, true>, 256, solve_smem<256>(R))
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<256, 0, false>, 256, solve_smem<256>(R));
         else if (BS == 512)
-            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<512, 0, true>, 512, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<512, 0, false>, 512, 0);
+            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<512, 0, true>, 512, solve_smem<512>(R))
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<512, 0, false>, 512, solve_smem<512>(R));
         else
-            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<1024, 0, true>, 1024, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<1024, 0, false>, 1024, 0);
+            e = b->ref ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<1024, 0, true>, 1024, solve_smem<1024>(R))
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_curve_solve_batch<1024, 0, false>, 1024, solve_smem<1024>(R));
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
         int g = (per_sm > 0 ? per_sm : 1) * nsm;
         grids[k] = counts[k] < g ? counts[k] : g;
@@ -1657,19 +1716,20 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
     BatchItem* const* itB = b->it[0];
     BatchItem* const* itG = b->it[1];
     const int *nB = b->nit[0], *gB = b->git[0], *nG = b->nit[1], *gG = b->git[1];
+    const int R = b->R;
 #define ADR_BATCH_SOLVE(FAM_, IT, N, G)                                                            \
     for (int k = kItemSets - 1; k >= 0; --k) {                                                     \
         if (!N[k]) continue;                                                                       \
         int BS = 256 << k;                                                                         \
         if (BS == 256) {                                                                           \
-            if (b->ref) k_curve_solve_batch<256, FAM_, true><<<G[k], 256, 0, st>>>(b->ctab, IT[k], b->act, k); \
-            else k_curve_solve_batch<256, FAM_, false><<<G[k], 256, 0, st>>>(b->ctab, IT[k], b->act, k);     \
+            if (b->ref) k_curve_solve_batch<256, FAM_, true><<<G[k], 256, solve_smem<256>(R), st>>>(b->ctab, IT[k], b->act, k); \
+            else k_curve_solve_batch<256, FAM_, false><<<G[k], 256, solve_smem<256>(R), st>>>(b->ctab, IT[k], b->act, k);     \
         } else if (BS == 512) {                                                                    \
-            if (b->ref) k_curve_solve_batch<512, FAM_, true><<<G[k], 512, 0, st>>>(b->ctab, IT[k], b->act, k); \
-            else k_curve_solve_batch<512, FAM_, false><<<G[k], 512, 0, st>>>(b->ctab, IT[k], b->act, k);     \
+            if (b->ref) k_curve_solve_batch<512, FAM_, true><<<G[k], 512, solve_smem<512>(R), st>>>(b->ctab, IT[k], b->act, k); \
+            else k_curve_solve_batch<512, FAM_, false><<<G[k], 512, solve_smem<512>(R), st>>>(b->ctab, IT[k], b->act, k);     \
         } else {                                                                                   \
-            if (b->ref) k_curve_solve_batch<1024, FAM_, true><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], b->act, k); \
-            else k_curve_solve_batch<1024, FAM_, false><<<G[k], 1024, 0, st>>>(b->ctab, IT[k], b->act, k);     \
+            if (b->ref) k_curve_solve_batch<1024, FAM_, true><<<G[k], 1024, solve_smem<1024>(R), st>>>(b->ctab, IT[k], b->act, k); \
+            else k_curve_solve_batch<1024, FAM_, false><<<G[k], 1024, solve_smem<1024>(R), st>>>(b->ctab, IT[k], b->act, k);     \
         }                                                                                          \
     }
     ADR_BATCH_SOLVE(0, itB, nB, gB)

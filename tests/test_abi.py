@@ -76,3 +76,29 @@ def test_network_parameter_layout_without_gpu(libadr):
     assert W.cnn_init_params().size == P.adr_cnn_num_params()
     with pytest.raises(ValueError):
         P.adr_cnn_create(1, np.zeros(10, np.float32))
+
+
+def _header_struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "adr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", src).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, rest = decl.split(None, 1)
+        for nm in rest.split(","):
+            fields.append((ctype, nm.strip()))
+    return fields
+
+
+@pytest.mark.parametrize("name", ["adr_stats", "adr_opts", "adr_grid"])
+def test_binding_structs_match_header(name):
+    """The ctypes mirrors have the header's fields, in order, with the same C types."""
+    import paper_2411_11041_gb300 as P
+    want = _header_struct_fields(name)
+    got = getattr(P, name)._fields_
+    ctypes_of = {"int": ctypes.c_int, "double": ctypes.c_double}
+    assert [n for _, n in want] == [n for n, _ in got]
+    assert [ctypes_of[t] for t, _ in want] == [t for _, t in got]

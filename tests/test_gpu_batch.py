@@ -46,7 +46,9 @@ def test_batch_equals_individual_solves(torch_cuda, prec):
     # and the oracle on two of them
     for k in (1, 7):
         ref, _, it, _, _ = O.Oracle(probs[k]).solve_stationary(tol=1e-9, max_iter=20000)
-        assert stats[k]["iters"] == it
+        # the reduced-precision mode's FP32 corrections may move the step that
+        # reaches tol by a step or two
+        assert abs(stats[k]["iters"] - it) <= (0 if prec == 0 else 2)
         err = np.abs(outs[k].cpu().numpy() - ref).max() / np.abs(ref).max()
         assert err <= (1e-12 if prec == 0 else 1e-5)
     batch.close()
@@ -71,7 +73,7 @@ def test_autotune_keeps_the_solution(torch_cuda, tmp_path, monkeypatch):
     u0, _, st0, _ = s0.solve_stationary()
     s1 = Solver(p, tol=1e-9, autotune=True)
     r, m, ms = s1.tuned
-    assert r in (2, 4, 8) and m in (2, 4, 8) and ms > 0
+    assert r in (4, 8, 16) and m in (2, 4, 8) and ms > 0
     u1, _, st1, _ = s1.solve_stationary()
     assert st1["iters"] == st0["iters"]
     assert (u1 - u0).abs().max().item() <= 1e-12 * u0.abs().max().item()
