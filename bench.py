@@ -39,24 +39,25 @@ FALLBACK_HBM_GBS = 6800.0
 # FP64 arithmetic peak of one GB300: 152 SMs x 2 FP64 FMA/clk (4 flop) x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
-# Algorithmic traffic and FP64 work per unit of each sweep kernel (unit = one
-# curve node for the curve solves, one grid node for the maps).  Bytes count
-# every array the kernel must touch once; flops count the kernel's FP64
-# arithmetic per unit (fma = 2, divide = 1).
+# Algorithmic traffic and FP64 work per unit of each sweep kernel in FP64 mode
+# (unit = one curve unknown for the curve solves, one grid node for the maps).
+# Bytes count every array the kernel must touch once; flops count the
+# kernel's FP64 arithmetic per unit (fma = 2).
 KERNELS = ["curve solve B", "curve->grid map B", "curve solve G", "curve->grid map G"]
-#   curve solve B: cell 4 + corner weights 32 + F 8 + S rows 24 + factors 32 + v 8 + u 8 B
-#                  (F and S carry the row factor ip); gather 7 (1 mul + 3 fma) + rhs 6
-#                  (3 fma) + elimination 2 + upward 2 + back 4 + update 2 flop
-#   curve solve G: cell 4 + corner weights 32 + row coefficient 8 + factors 32 + v 8 + u 8 B;
-#                  gather 7 + rhs 4 + elimination 2 + upward 2 + back 4 + update 2 flop
+#   curve solve B: cell 4 + corner weights 32 + load row 8 + rhs rows 24 + factors cp, vp,
+#                  lp 24 + v 8 + u 8 B (load and rhs rows carry the row factor ip);
+#                  gather 7 (1 mul + 3 fma) + rhs 6 (3 fma) + elimination 2 + upward 2 +
+#                  back 4 flop (the new values come out of the solve: no update)
+#   curve solve G: cell 4 + corner weights 32 + rhs coefficient 8 + factors 24 + v 8 + u 8 B;
+#                  gather 7 + rhs 4 (add, fma, mul) + elimination 2 + upward 2 + back 4 flop
 #   maps: crossings 16 + coefficients 64 + type 1 + out 8 (+ u_j 8 for the norms) B, 8 fma
-BYTES_PER_UNIT = [116.0, 81.0, 92.0, 89.0]
-FLOPS_PER_UNIT = [23.0, 16.0, 21.0, 20.0]
-# DRAM bytes per launch (read + write, summed over the block-size launches of a
-# curve solve) from one ncu capture of the 2048^2 sheared workload
-# (profiles/dram_traffic_sweep_sheared2048_fp64.md); None where the kernel has
-# changed since the capture
-NCU_TRAFFIC_SHEARED2048 = [565.2e6, 399.0e6, 499.0e6, 435.3e6]
+#         (+ 1 add and 2 fma for the norms)
+BYTES_PER_UNIT = [108.0, 81.0, 84.0, 89.0]
+FLOPS_PER_UNIT = [21.0, 16.0, 19.0, 21.0]
+# DRAM bytes per launch (read + write) of each kernel in the bench's launch
+# shape, from one ncu capture of the 2048^2 sheared workload; None where the
+# kernel has changed since the capture
+NCU_TRAFFIC_SHEARED2048 = [535.5e6, 399.0e6, 442.6e6, 435.3e6]
 
 
 def parse():
@@ -72,9 +73,13 @@ def parse():
     ap.add_argument("--stabilize", type=int, default=0, choices=[0, 1],
                     help="1: SUPG on the B curves (FP64 only)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the oracle's converged solve (the err_vs_oracle figures)")
     ap.add_argument("--other-prec", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--workload", default="sheared",
-                    choices=["sheared", "batch", "learned", "data2d"])
+                    choices=["sheared", "batch", "learned", "data2d", "parabolic", "manufactured",
+                             "kernels"])
+    ap.add_argument("--time-steps", type=int, default=200, help="parabolic workload: time steps")
     ap.add_argument("--count", type=int, default=256)
     # learned warm start: training set, held-out set, Adam steps, minibatch
     ap.add_argument("--train", type=int, default=2048)
@@ -201,6 +206,56 @@ def job_rate(ws, ms, units, device):
 
 # ------------------------------------------------------------- oracle legs
 
+def _oracle_converged(n, tol, path):
+    """Child process: the oracle's converged stationary solve of the n^2
+    sheared workload from u = 0 (the same Δt and tol as the GPU), saved as
+    path (.npy) with its step count beside it (.json)."""
+    from oracle import oracle as O
+    from paper_2411_11041_gb300 import workloads as W
+    t0 = time.perf_counter()
+    o = O.Oracle(W.sheared(n=n))
+    out, _, it, rel, st = o.solve_stationary(tol=tol, max_iter=200000)
+    np.save(path, out)
+    with open(path + ".json", "w") as fh:
+        json.dump({"iters": it, "status": st, "secs": time.perf_counter() - t0}, fh)
+
+
+class OracleJob:
+    """The oracle's converged solve in a spawned process (one host core), so
+    that every result of the run can be compared with it."""
+
+    def __init__(self, n, tol):
+        import multiprocessing as mp
+        fd, self.path = tempfile.mkstemp(suffix=".npy")
+        os.close(fd)
+        self.proc = mp.get_context("spawn").Process(target=_oracle_converged,
+                                                    args=(n, tol, self.path), daemon=True)
+        self.proc.start()
+
+    def result(self, timeout_s):
+        """(u, info) or (None, reason)."""
+        self.proc.join(timeout_s)
+        if self.proc.is_alive():
+            self.proc.terminate()
+            return None, f"the oracle had not finished after {timeout_s:.0f} s more"
+        try:
+            u = np.load(self.path)
+            with open(self.path + ".json") as fh:
+                info = json.load(fh)
+        except (OSError, ValueError) as e:
+            return None, f"oracle failed: {e}"
+        finally:
+            for q in (self.path, self.path + ".json"):
+                if os.path.exists(q):
+                    os.unlink(q)
+        return u, info
+
+
+def rel_err(u_gpu, u_ref):
+    """max |u - u_oracle| / max |u_oracle| over the grid."""
+    return float(np.abs(u_gpu - u_ref).max() / max(np.abs(u_ref).max(), 1e-300))
+
+
 def oracle_sample(n, budget_s=12.0, min_steps=1):
     """Time split steps of the FP64 CPU oracle on the same workload (setup
     excluded) for about budget_s seconds.  Returns (line-DOF/s, steps, secs)."""
@@ -267,6 +322,7 @@ def run_ours(args):
     from paper_2411_11041_gb300 import ADR_FP32_REFINE, ADR_FP64, Solver
     from paper_2411_11041_gb300 import workloads as W
     ws, rank, local = dist_setup(args)
+    job = OracleJob(args.n, args.tol) if rank == 0 and not args.no_oracle else None
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
@@ -299,23 +355,10 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     ms_max, dofs_all, value = job_rate(ws, ms, dofs, dev)
     # per-kernel device time in the solve's launch configuration (CUDA events)
-    kms = solver.time_kernels(reps=20)
+    roof = kernel_roofline(solver, prob, unknowns)
+    k = KERNELS.index(roof["kernel"])
     units = [unknowns[0], prob.nx * prob.ny, unknowns[1], prob.nx * prob.ny]
-    k = int(np.argmax(kms))
-    hbm, hbm_kind = peaks()
-    gbs = BYTES_PER_UNIT[k] * units[k] / (kms[k] * 1e-3) / 1e9
-    tflops = FLOPS_PER_UNIT[k] * units[k] / (kms[k] * 1e-3) / 1e12
-    if tflops / FP64_PEAK_TFLOPS >= gbs / hbm:
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_kind": "FP64 FMA issue peak derived from 152 SMs x 2 FMA/clk x 2.07 GHz",
-                "hbm_frac": gbs / hbm}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": None, "peak_kind": hbm_kind}
-    roof.update({"kernel": KERNELS[k], "kernel_ms": kms[k], "units_per_launch": units[k],
-                 "all_kernels_ms": dict(zip(KERNELS, kms))})
-    if args.n == 2048 and NCU_TRAFFIC_SHEARED2048[k] is not None:
+    if args.n == 2048 and prec == ADR_FP64 and NCU_TRAFFIC_SHEARED2048[k] is not None:
         roof["traffic"] = NCU_TRAFFIC_SHEARED2048[k]
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture"
         roof["algorithmic_bytes"] = BYTES_PER_UNIT[k] * units[k]
@@ -338,6 +381,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         ms2 = f0.elapsed_time(f1)
         diff = float((u2 - u).abs().max() / u.abs().max())
+        u_other = u2.cpu().numpy()
         other = {"prec": "fp32+refine" if oprec == ADR_FP32_REFINE else "fp64",
                  "ms_per_step": ms2 / reps, "value": d2 / (ms2 / 1e3), "iters_per_solve": it2,
                  "kernels_ms": dict(zip(KERNELS, s2.time_kernels(reps=20))),
@@ -368,6 +412,19 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{nst} split steps of the {args.n}^2 sheared problem "
                                           f"({secs:.1f} s, setup excluded), single thread"}
+    if job is not None:
+        # every result against the oracle's converged solve (same Δt and tol)
+        ref, info = job.result(timeout_s=600)
+        if ref is None:
+            line["err_vs_oracle"] = {"value": None, "why": info}
+        else:
+            ev = {"measure": "max |u - u_oracle| / max |u_oracle| over the grid",
+                  "oracle_iters": info["iters"], "oracle_secs": info["secs"],
+                  args.prec: rel_err(u.cpu().numpy(), ref)}
+            if other:
+                ev["fp32+refine" if other["prec"] == "fp32+refine" else "fp64"] = rel_err(u_other, ref)
+            ev["tolerance"] = {"fp64": 1e-12, "fp32+refine": 1e-5}
+            line["err_vs_oracle"] = ev
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -661,6 +718,174 @@ def run_data2d(args):
     print(json.dumps(line), flush=True)
 
 
+def kernel_roofline(solver, prob, unknowns):
+    """Dominant sweep kernel of a solver, timed with CUDA events in the
+    solve's launch configuration (adr_time_kernels): the roofline object."""
+    kms = solver.time_kernels(reps=20)
+    units = [unknowns[0], prob.nx * prob.ny, unknowns[1], prob.nx * prob.ny]
+    k = int(np.argmax(kms))
+    hbm, hbm_kind = peaks()
+    gbs = BYTES_PER_UNIT[k] * units[k] / (kms[k] * 1e-3) / 1e9
+    tflops = FLOPS_PER_UNIT[k] * units[k] / (kms[k] * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_kind": "FP64 FMA issue peak derived from 152 SMs x 2 FMA/clk x 2.07 GHz",
+            "hbm_frac": gbs / hbm, "kernel": KERNELS[k], "kernel_ms": kms[k],
+            "units_per_launch": units[k], "all_kernels_ms": dict(zip(KERNELS, kms))}
+
+
+def run_parabolic(args):
+    """The parabolic problem (eq. Parabolic1) on n^2 nodes (1024 by default):
+    implicit Euler in time, dt = 1e-3, 200 steps from the Gaussian blob, each
+    time slice solved by the splitting iteration to the tolerance (mode 1: the
+    slice's reaction sigma + 1/dt and load f + u_n/dt).  One timed step = the
+    whole 200-step run."""
+    import torch
+
+    from paper_2411_11041_gb300 import ADR_FP32_REFINE, ADR_FP64, ADR_OK, Solver
+    from paper_2411_11041_gb300 import workloads as W
+    from oracle import oracle as O
+    n = args.n if args.n != 2048 else 1024
+    dt, nsteps = 1e-3, args.time_steps
+    prob = W.parabolic(n=n)
+    dev = torch.device("cuda:0")
+    prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
+    s = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec)
+    unknowns = s.line_unknowns()
+    u0 = torch.tensor(prob.u0, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # the first slices, against the oracle's
+    n_check = 2
+    u = u0.clone()
+    s.step_parabolic(u, dt, n_check, 1)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    o = O.Oracle(prob)
+    ref, ref_iters, ost = o.step_parabolic(prob.u0, dt, n_check, 1, tol=args.tol, max_iter=200000)
+    oracle_check_s = time.perf_counter() - t0
+    err_first = rel_err(u.cpu().numpy(), ref)
+    for _ in range(args.warmup):
+        u = u0.clone()
+        s.step_parabolic(u, dt, nsteps, 1)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, dofs = [], 0.0
+    e0.record(stream)
+    for _ in range(args.steps):
+        u = u0.clone()
+        st, code = s.step_parabolic(u, dt, nsteps, 1)
+        if code != ADR_OK:
+            raise RuntimeError("a time slice did not reach tol")
+        iters.append(st["iters"])
+        dofs += st["line_dofs"]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    roof = kernel_roofline(s, prob, unknowns)
+    line = {"metric": METRIC.replace("time-to-1e-8 relative update",
+                                     f"{nsteps} implicit-Euler steps, each slice to {args.tol:g}"),
+            "value": dofs / args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == ADR_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"parabolic{n}", "nodes": n * n, "dt": dt, "time_steps": nsteps,
+                       "mu": prob.mu, "sigma": prob.sigma, "tol": args.tol, "mode": 1,
+                       "line_unknowns_per_split_step": unknowns,
+                       "split_steps_per_run": iters[-1],
+                       "split_steps_per_slice": iters[-1] / nsteps,
+                       "ms_per_time_step": ms / nsteps,
+                       "step": f"one {nsteps}-step run from the Gaussian blob",
+                       "l2": "working set ~250 MB > 129 MB L2"},
+            "roofline": roof, "gpu_launches": int(iters[-1] * 5 + nsteps * 4), "clocks": clk,
+            "err_vs_oracle": {"measure": "max |u - u_oracle| / max |u_oracle|",
+                              "first_slices": n_check, args.prec: err_first,
+                              "oracle_split_steps": ref_iters, "oracle_secs": oracle_check_s}}
+    if not args.no_cpu_baseline:
+        sig = prob.sigma + 1.0 / dt
+        pdt = o.default_dt(sigma=sig)
+        uo, steps, t0 = prob.u0.copy(), 0, time.perf_counter()
+        while time.perf_counter() - t0 < 10.0:
+            _, uo = o.split_step(0.5, pdt, uo, sigma=sig, f_extra=prob.u0, fx_scale=1.0 / dt)
+            steps += 1
+        secs = time.perf_counter() - t0
+        rate = (unknowns[0] + unknowns[1]) * steps / secs
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{steps} split steps of a {n}^2 time slice ({secs:.1f} s, "
+                                          "setup excluded), single thread; a run takes "
+                                          f"{iters[-1]} of them: {iters[-1] / (rate / (unknowns[0] + unknowns[1])):.0f} s "
+                                          "extrapolated"}
+    print(json.dumps(line), flush=True)
+
+
+def run_manufactured(args):
+    """The manufactured-solution problem on 64^2 nodes (u = sin pi x sin pi y,
+    beta = (1, 0.5), mu = 0.1, sigma = 1) solved to a relative update of 1e-10
+    in FP64.  Fits in L2: a latency case, timed per solve."""
+    import torch
+
+    from paper_2411_11041_gb300 import Solver
+    from paper_2411_11041_gb300 import workloads as W
+    from oracle import oracle as O
+    n = args.n if args.n != 2048 else 64
+    tol = 1e-10
+    prob = W.manufactured(n=n)
+    dev = torch.device("cuda:0")
+    s = Solver(prob, device=dev, tol=tol, max_iter=200000)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        s.solve_stationary()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dofs = 0.0
+    for _ in range(args.steps):
+        u, _, st, _ = s.solve_stationary()
+        dofs += st["line_dofs"]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    o = O.Oracle(prob)
+    t0 = time.perf_counter()
+    ref, _, it, _, _ = o.solve_stationary(tol=tol, max_iter=200000)
+    secs = time.perf_counter() - t0
+    ug = u.cpu().numpy()
+    line = {"metric": METRIC.replace("1e-8", "1e-10"),
+            "value": dofs / args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"manufactured{n}", "nodes": n * n, "tol": tol,
+                       "split_steps": st["iters"], "step": "one stationary solve to tol from u=0",
+                       "l2": "fits in L2: a latency case"},
+            "err_vs_oracle": {"measure": "max |u - u_oracle| / max |u_oracle|", "fp64": rel_err(ug, ref),
+                              "oracle_split_steps": it},
+            "err_vs_exact": float(np.abs(ug - W.exact_manufactured(n)).max()),
+            "cpu_baseline": {"value": dofs / args.steps / secs, "unit": UNIT, "cores": 1,
+                             "kind": "oracle", "sample": f"the same solve ({secs:.2f} s)"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_kernels(args):
+    """Kernel timing only: the n^2 sheared problem's four sweep kernels,
+    args.steps back-to-back launches each in the solve's launch configuration
+    (the command the ncu recipes capture)."""
+    import torch
+
+    from paper_2411_11041_gb300 import ADR_FP32_REFINE, ADR_FP64, Solver
+    from paper_2411_11041_gb300 import workloads as W
+    prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
+    prob = W.sheared(n=args.n)
+    s = Solver(prob, device=torch.device("cuda:0"), tol=args.tol, prec=prec)
+    kms = s.time_kernels(reps=args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": f"sheared{args.n}", "prec": args.prec, "launches_per_kernel": args.steps,
+                      "kernels_ms": dict(zip(KERNELS, kms)), "line_unknowns": s.line_unknowns()}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -671,6 +896,12 @@ def main():
         run_learned(args)
     elif args.workload == "data2d":
         run_data2d(args)
+    elif args.workload == "parabolic":
+        run_parabolic(args)
+    elif args.workload == "manufactured":
+        run_manufactured(args)
+    elif args.workload == "kernels":
+        run_kernels(args)
     else:
         run_ours(args)
 

@@ -285,22 +285,27 @@ adr_status adr_solve_batch(adr_problem* const* probs, int n, double* const* u_ou
  *
  * u_in -> u_out (device double [ny][nx]): u_out = G_G(u^i + dt d) where on
  * every G curve (M + theta dt mu K) d = -mu K u^i, u^i the bilinear samples of
- * u_in.  off[n_lines+1] (device int32, off[n_lines] == n_nodes), h[n_lines],
- * xi/eta[n_nodes]: the family-1 curves as adr_get_lines reports them.
- * seg/t/pos[4*nx*ny]: the family-1 crossings as adr_get_crossings reports them
- * (seg = -2 marks a non-interior node, which gets 0).  stream: cudaStream_t or
- * NULL.  The call only launches work; it returns before the kernels finish.
+ * u_in.  off[n_lines+1] (device int32, non-decreasing from off[0] = 0 to
+ * off[n_lines] == n_nodes), h[n_lines], xi/eta[n_nodes]: the family-1 curves
+ * as adr_get_lines reports them.  seg/t/pos[4*nx*ny]: the family-1 crossings
+ * as adr_get_crossings reports them (seg = -2 marks a non-interior node, which
+ * gets 0).  G_G is the paper's curve -> grid rule with the plain average of
+ * the row and the column value (opts.interp_weights does not apply here).
+ * stream: cudaStream_t or NULL.  The call only launches work; it returns
+ * before the kernels finish.
  *
  * Work space: a fixed array of 4 x 524288 doubles (16 MiB) in device memory,
  * reserved by every GPU that loads the library until the process exits.
- * n_nodes > 524288 is rejected with ADR_EINVAL.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call on a
+ * n_nodes > 524288 is rejected with ADR_EINVAL.  Every call looks up the
+ * array's device address on the current device (cudaGetSymbolAddress, no
+ * allocation); the first call on a device also loads the library's module
+ * there, so make that first call before any stream capture.  Every call on a
  * device shares the one array and it keeps the last call's contents; a call
- * writes every entry it reads, so nothing needs clearing, but calls whose
- * kernels may overlap on the GPU (different streams, no ordering between
- * them) race on it and must be serialised by the caller.  Curves with offsets
- * outside [0, n_nodes] are skipped.  Errors: ADR_EINVAL, ADR_ECUDA.
+ * writes every entry it reads (a curve whose offsets fall outside
+ * [0, n_nodes], or that has fewer than 2 nodes, is skipped and its nodes in
+ * range read as 0), so nothing needs clearing, but calls whose kernels may
+ * overlap on the GPU (different streams, no ordering between them) race on it
+ * and must be serialised by the caller.  Errors: ADR_EINVAL, ADR_ECUDA.
  */
 adr_status adr_cross_substep_noalloc(int nx, int ny, double mu, double theta, double dt,
                                      const double* u_in, int n_lines, int n_nodes, const int* off,

@@ -5,24 +5,20 @@
 // The scratch below is a file-scope __device__ array: every GPU that loads
 // this library holds it (kNoAllocMaxNodes curve nodes x 4 planes of doubles =
 // 16 MiB) until the process exits.  Host code cannot use the array's name as a
-// device address, so its address is looked up once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// device address, so every call looks the address up on the current device
+// with cudaGetSymbolAddress (a lookup, no allocation) and passes it to the
+// kernels.  Looking it up each time keeps the address right even after a
+// context reset has reloaded the module.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "adr_internal.cuh"
 
 namespace {
 
 constexpr int kNoAllocMaxNodes = 1 << 19;  // curve nodes of the G family
-constexpr int kMaxDevices = 64;
 
 // planes: [0] c', [1] v', [2] r' of the partitioned elimination, [3] curve values
 static __device__ __align__(256) double g_noalloc_scratch[4 * (size_t)kNoAllocMaxNodes];
-
-double* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mutex;
 
 __device__ __forceinline__ double gather_u(const double* __restrict__ u, int nx, int ny, double xi,
                                            double eta)
@@ -53,7 +49,13 @@ __global__ void k_cross_curves(int nx, int ny, const double* __restrict__ u, int
     double* rpS = scr + 2 * (size_t)kNoAllocMaxNodes;
     double* v = scr + 3 * (size_t)kNoAllocMaxNodes;
     int base = off[warp], end = off[warp + 1];
-    if (base < 0 || end > n_nodes || end - base < 2) return;  // malformed curve: skipped
+    if (base < 0 || end > n_nodes || end - base < 2) {
+        // malformed curve: skipped, and the nodes of its range that lie in
+        // [0, n_nodes) set to 0, so that no crossing reads an earlier call's value
+        const int lo = base < 0 ? 0 : base, hi = end > n_nodes ? n_nodes : end;
+        for (int k = lo + lane; k < hi; k += 32) v[k] = 0.0;
+        return;
+    }
     int n = end - base - 1;
     if (n < 2) {
         if (lane <= n) v[base + lane] = 0.0;
@@ -188,24 +190,11 @@ extern "C" adr_status adr_cross_substep_noalloc(int nx, int ny, double mu, doubl
         adr::set_error("adr_cross_substep_noalloc: more than 524288 curve nodes (fixed work space)");
         return ADR_EINVAL;
     }
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return adr::cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) {
-        adr::set_error("adr_cross_substep_noalloc: device ordinal out of range");
-        return ADR_EINVAL;
-    }
+    // the array's address on the current device (the first call on a device
+    // also loads the module there)
     double* scr = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_scratch_mutex);
-        if (!g_scratch_addr[dev]) {
-            double* p = nullptr;
-            e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
-            if (e != cudaSuccess) return adr::cuda_fail(e, "cudaGetSymbolAddress");
-            g_scratch_addr[dev] = p;
-        }
-        scr = g_scratch_addr[dev];
-    }
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&scr), g_noalloc_scratch);
+    if (e != cudaSuccess) return adr::cuda_fail(e, "cudaGetSymbolAddress");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_cross_curves<<<(n_lines + 3) / 4, 128, 0, st>>>(nx, ny, u_in, n_lines, n_nodes, off, h, xi,
                                                       eta, mu, theta, dt, scr);

@@ -14,6 +14,7 @@ from paper_2411_11041_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
+TOL_REF = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -238,8 +239,52 @@ def test_sheared_2048_two_steps_match_oracle(torch_cuda):
     assert relerr(u, ref) <= TOL64 and relerr(uit, refit) <= TOL64
 
 
+@pytest.fixture(scope="module")
+def sheared2048_converged():
+    """The oracle's converged solve of the full-size sheared workload (2048^2,
+    traced curves, tol 1e-8; about a minute on one core)."""
+    p = W.sheared(n=2048)
+    ref, refit, it, rel, st = O.Oracle(p).solve_stationary(tol=1e-8, max_iter=200000)
+    assert st == O.OK
+    return p, ref, refit, it
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sheared_2048_converged_solve_matches_oracle(torch_cuda, sheared2048_converged, prec):
+    """The benchmarked solve at full size, to 1e-8, element by element against
+    the oracle's converged solve: FP64 within 1e-12, FP32 + refinement within 1e-5."""
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    p, ref, refit, it = sheared2048_converged
+    s = Solver(p, tol=1e-8, max_iter=200000, prec=prec)
+    u, uit, stats, st = s.solve_stationary(want_iter=True)
+    assert st == ADR_OK
+    if prec == 0:
+        assert stats["iters"] == it
+        assert relerr(u, ref) <= TOL64 and relerr(uit, refit) <= TOL64
+    else:
+        assert abs(stats["iters"] - it) <= 2
+        assert relerr(u, ref) <= TOL_REF
+    s.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_parabolic_1024_first_steps_match_oracle(torch_cuda, mode):
+    """The parabolic workload at full size (1024^2, dt = 1e-3): its first three
+    time steps (mode 1: each slice solved to 1e-8) against the oracle's."""
+    from paper_2411_11041_gb300 import Solver
+    torch = torch_cuda
+    p = W.parabolic(n=1024)
+    o = O.Oracle(p)
+    s = Solver(p, tol=1e-8, max_iter=200000)
+    u = torch.tensor(p.u0, device="cuda:0")
+    stats, st = s.step_parabolic(u, 1e-3, 3, mode)
+    ref, tot, ost = o.step_parabolic(p.u0, 1e-3, 3, mode, tol=1e-8, max_iter=200000)
+    assert ost == O.OK
+    assert stats["iters"] == tot
+    assert relerr(u, ref) <= TOL64
+
+
 # ------------------------------------------------------------ FP32 + FP64 refinement
-TOL_REF = 1e-5
 
 
 @pytest.mark.parametrize("name", ["manufactured33", "L_mask", "disc_mask", "long_lines", "sheared65",
