@@ -67,8 +67,8 @@ typedef enum {
     ADR_INIT_ZERO = 0,     /* u_0 = 0 */
     ADR_INIT_USER = 1,     /* u_0 = caller array (non-interior nodes ignored) */
     ADR_INIT_PAPER_U0 = 2, /* s(u_0, v) = <l, v>  (§5, eq. u0stationary) */
-    ADR_INIT_LEARNED = 3   /* not accepted: pass the network's state with ADR_INIT_USER
-                              (adr_cnn_initial_state) */
+    ADR_INIT_LEARNED = 3   /* the learned warm start: the network attached with
+                              adr_set_warm_start corrects the paper's u_0 (256 x 256 grids) */
 } adr_init;
 
 /* Grid of nx x ny nodes on [x0,x1] x [y0,y1]; nx, ny >= 3. */
@@ -379,6 +379,18 @@ adr_status adr_cnn_loss_grad(adr_cnn* cnn, int batch, const uint16_t* x, const f
  * the update (the call then waits for the stream). */
 adr_status adr_cnn_train_step(adr_cnn* cnn, int batch, const uint16_t* x, const float* t,
                               float lr, double* loss);
+/* adr_cnn_set_wait_limit: bound of the tensor-core kernels' mbarrier waits:
+ * spins > 0 non-blocking polls, or spins = 0 the default bound (about a second
+ * of blocking polls).  A wait that reaches its bound gives up: the kernel lets
+ * the loads and MMAs it issued finish, frees its tensor memory, skips its
+ * output and flags the handle; adr_cnn_sync, or a call that returns the loss,
+ * then reports ADR_ETIMEOUT and clears the flag.  Outputs of the calls since
+ * the last report are then not valid.  A bound of a few polls makes the waits
+ * give up, which is how the timeout path is tested.  Errors: ADR_EINVAL. */
+adr_status adr_cnn_set_wait_limit(adr_cnn* cnn, long long spins);
+/* adr_cnn_sync: wait for the handle's stream; ADR_ETIMEOUT (flag cleared) if a
+ * bounded wait gave up since the last report, else ADR_OK. */
+adr_status adr_cnn_sync(adr_cnn* cnn);
 /* adr_cnn_initial_state: u_out (device double [256][256]) <- u0 + s * v at the
  * interior nodes, 0 elsewhere, v the bilinear interpolation of channel 0 of one
  * prediction y (device float [64][64][8]) with cell centres at node
@@ -388,6 +400,22 @@ adr_status adr_cnn_train_step(adr_cnn* cnn, int batch, const uint16_t* x, const 
  * Errors: ADR_EINVAL (grid not 256 x 256). */
 adr_status adr_cnn_initial_state(adr_problem* prob, const float* y, const double* u0,
                                  const double* scale, double* u_out);
+
+/* adr_set_warm_start -- attach a warm-start network to a problem on a 256 x 256
+ * grid, so that opts.init == ADR_INIT_LEARNED starts adr_solve_stationary (and
+ * adr_batch_solve) from the network's state: the paper's initial state u0 of
+ * §5 eq. u0stationary, the features of the problem and u0 (adr_cnn_features,
+ * with the problem's own mask, mu and sigma), one forward pass, and
+ * adr_cnn_initial_state -- the chain a caller can also run by hand and pass
+ * with ADR_INIT_USER.  The iteration that follows is the paper's, to the same
+ * tolerance.  cnn: a handle from adr_cnn_create, not owned: it must outlive
+ * every solve that uses it; NULL detaches.  The forward pass runs on the
+ * problem's stream, ordered after the network's pending work and before its
+ * later work.  The first attach allocates the chain's buffers (about 0.9 MB)
+ * from the library's pool.  A solve with ADR_INIT_LEARNED and no network
+ * returns ADR_EINVAL.  Errors: ADR_EINVAL (grid not 256 x 256), ADR_ENOMEM,
+ * ADR_ECUDA. */
+adr_status adr_set_warm_start(adr_problem* prob, adr_cnn* cnn);
 
 #ifdef __cplusplus
 }

@@ -104,6 +104,9 @@ def lib():
         L.adr_cnn_loss_grad.argtypes = [vp, C.c_int, vp, vp, vp, dp]
         L.adr_cnn_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, dp]
         L.adr_cnn_initial_state.argtypes = [vp, vp, vp, vp, vp]
+        L.adr_cnn_set_wait_limit.argtypes = [vp, C.c_longlong]
+        L.adr_cnn_sync.argtypes = [vp]
+        L.adr_set_warm_start.argtypes = [vp, vp]
         _lib = L
     return _lib
 
@@ -115,7 +118,8 @@ EXPORTED = ["adr_default_opts", "adr_create", "adr_solve_stationary", "adr_step_
             "adr_solve_batch", "adr_autotune",
             "adr_cnn_num_params", "adr_cnn_create", "adr_cnn_destroy", "adr_cnn_set_params",
             "adr_cnn_get_params", "adr_cnn_features", "adr_cnn_targets", "adr_cnn_forward",
-            "adr_cnn_loss_grad", "adr_cnn_train_step", "adr_cnn_initial_state"]
+            "adr_cnn_loss_grad", "adr_cnn_train_step", "adr_cnn_initial_state",
+            "adr_cnn_set_wait_limit", "adr_cnn_sync", "adr_set_warm_start"]
 
 
 def tune_key(prob, prec):
@@ -340,6 +344,11 @@ class Solver:
         adr_paper_u0(self.h, out)
         return out
 
+    def set_warm_start(self, net):
+        """Attach a Network (adr_set_warm_start) for init=ADR_INIT_LEARNED; None detaches."""
+        _check(lib().adr_set_warm_start(self.h, None if net is None else net.h), "adr_set_warm_start")
+        self.net = net  # kept alive while attached
+
     def time_kernels(self, reps=20):
         """Average device ms of [B solve, B map, G solve, G map] per launch."""
         return adr_time_kernels(self.h, reps)
@@ -538,6 +547,15 @@ class Network:
 
     def train_step(self, x, t, lr, want_loss=True):
         return adr_cnn_train_step(self.h, x.shape[0], x, t, lr, want_loss)
+
+    def set_wait_limit(self, spins):
+        """Bound of the tensor-core kernels' waits in polls (0: the default)."""
+        _check(lib().adr_cnn_set_wait_limit(self.h, int(spins)), "adr_cnn_set_wait_limit")
+
+    def sync(self):
+        """Wait for the network's stream; the status (ADR_ETIMEOUT if a bounded
+        wait gave up since the last report)."""
+        return lib().adr_cnn_sync(self.h)
 
     def initial_state(self, solver, y, u0=None, scale=None):
         """Solver grid initial state u0 + s * bilinear(y[..., 0]) from one

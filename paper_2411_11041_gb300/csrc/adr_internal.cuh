@@ -118,6 +118,7 @@ struct Problem {
     double bmax = 0;
     Family fam[2];
     // owned device buffers
+    uint8_t* mask = nullptr;    // copy of the caller's node mask (warm-start features)
     uint8_t* cell = nullptr;
     uint8_t* ntype = nullptr;
     double* beta1 = nullptr;
@@ -212,5 +213,7 @@ adr_status launch_state_reset(Problem* p);
 // warm-start network (cnn.cu): prediction [64][64][8] -> initial state on the grid
 adr_status launch_cnn_upsample(Problem* p, const float* y, const double* u0, const double* scale,
                                double* u);
+// one network forward on a problem's stream (cnn.cu)
+adr_status cnn_forward_on(adr_cnn* c, int batch, const uint16_t* x, float* y, cudaStream_t st);
 
 }  // namespace adr

@@ -77,6 +77,13 @@ struct adr_problem {
     std::vector<int> offs[2];  // host copies of the curve offsets
     bool diverged = false;     // the last iteration stopped on a non-finite norm
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // learned warm start (adr_set_warm_start): the network (not owned) and the
+    // buffers of its chain
+    adr_cnn* cnn = nullptr;
+    uint16_t* ws_x = nullptr;    // features [64][64][40] (BF16 storage)
+    float* ws_y = nullptr;       // prediction [64][64][8]
+    double* ws_u0 = nullptr;     // the paper's initial state [ny][nx]
+    double* ws_par = nullptr;    // mu, sigma, scale
 };
 
 #define TRY(x)                       \
@@ -217,6 +224,22 @@ adr_status init_state(adr_problem* h, int init, const double* u_init)
         return launch_grid_map_ex(p, 0, p->ubuf[0], p->ubuf[0], 0, nullptr, nullptr, false, false);
     }
     if (init == ADR_INIT_ZERO) return launch_mask_copy(p, nullptr, p->ubuf[0]);
+    if (init == ADR_INIT_LEARNED) {
+        if (!h->cnn) {
+            set_error("opts.init == ADR_INIT_LEARNED needs a network (adr_set_warm_start)");
+            return ADR_EINVAL;
+        }
+        // the paper's initial state (eq. u0stationary), the network's features
+        // of the problem and of it, one forward pass, and the corrected state
+        TRY(prepare_family(p, 0, 1.0, 1.0, p->sigma, 1));
+        TRY(load_family(p, nullptr, 0.0));
+        TRY(launch_line_solve(p, 0, 1.0, nullptr, nullptr, false, 1));
+        TRY(launch_grid_map_ex(p, 0, h->ws_u0, h->ws_u0, 0, nullptr, nullptr, false, false));
+        TRY(adr_cnn_features(1, p->grid.nx, p->f, p->beta1, p->beta2, p->mask, h->ws_par,
+                             h->ws_par + 1, h->ws_u0, h->ws_x, h->ws_par + 2, p->stream));
+        TRY(cnn_forward_on(h->cnn, 1, h->ws_x, h->ws_y, p->stream));
+        return launch_cnn_upsample(p, h->ws_y, h->ws_u0, h->ws_par + 2, p->ubuf[0]);
+    }
     set_error("unsupported opts.init");
     return ADR_EINVAL;
 }
@@ -255,7 +278,7 @@ adr_status check_opts(const adr_opts* o)
         set_error("opts.max_iter must be >= 0 and dt, tol finite");
         return ADR_EINVAL;
     }
-    if (o->init < ADR_INIT_ZERO || o->init > ADR_INIT_PAPER_U0) {
+    if (o->init < ADR_INIT_ZERO || o->init > ADR_INIT_LEARNED) {
         set_error("unsupported opts.init");
         return ADR_EINVAL;
     }
@@ -351,10 +374,11 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
     };
     size_t N = p->N;
     if ((s = dev_alloc(p, &p->beta1, N)) || (s = dev_alloc(p, &p->beta2, N)) ||
-        (s = dev_alloc(p, &p->f, N)))
+        (s = dev_alloc(p, &p->f, N)) || (s = dev_alloc(p, &p->mask, N)))
         return fail(s);
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(p->beta1, beta1, N * 8, cudaMemcpyDeviceToDevice, p->stream)) ||
+    if ((e = cudaMemcpyAsync(p->mask, mask, N, cudaMemcpyDeviceToDevice, p->stream)) ||
+        (e = cudaMemcpyAsync(p->beta1, beta1, N * 8, cudaMemcpyDeviceToDevice, p->stream)) ||
         (e = cudaMemcpyAsync(p->beta2, beta2, N * 8, cudaMemcpyDeviceToDevice, p->stream)) ||
         (e = cudaMemcpyAsync(p->f, f, N * 8, cudaMemcpyDeviceToDevice, p->stream)))
         return fail(cuda_fail(e, "cudaMemcpyAsync"));
@@ -403,6 +427,32 @@ void adr_destroy(adr_problem* h)
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     delete h;
+}
+
+adr_status adr_set_warm_start(adr_problem* h, adr_cnn* cnn)
+{
+    g_err.clear();
+    if (!h) {
+        set_error("adr_set_warm_start: NULL handle");
+        return ADR_EINVAL;
+    }
+    Problem* p = &h->p;
+    if (cnn && (p->grid.nx != 256 || p->grid.ny != 256)) {
+        set_error("adr_set_warm_start: the network predicts 256 x 256 grids");
+        return ADR_EINVAL;
+    }
+    if (cnn && !h->ws_x) {
+        TRY(dev_alloc(p, &h->ws_x, (size_t)64 * 64 * 40));
+        TRY(dev_alloc(p, &h->ws_y, (size_t)64 * 64 * 8));
+        TRY(dev_alloc(p, &h->ws_u0, (size_t)p->N));
+        TRY(dev_alloc(p, &h->ws_par, 3));
+        // mu and sigma of the features, next to the scale the features write
+        const double par[2] = {p->mu, p->sigma};
+        ADR_CUDA_TRY(cudaMemcpyAsync(h->ws_par, par, sizeof par, cudaMemcpyHostToDevice, p->stream));
+        ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    }
+    h->cnn = cnn;
+    return ADR_OK;
 }
 
 adr_status adr_solve_stationary(adr_problem* h, const double* u_init, double* u_out,

@@ -98,6 +98,8 @@ struct ConvArgs {
     bf16* y;            // [B][H][W][Cout] or null
     float* y32;         // [B][H][W][Cout] FP32 output or null
     int relu;
+    long long spin;     // tensor-core kernels: bound of their mbarrier waits in polls
+                        // (0: the default bound)
 };
 
 // implicit GEMM: M = pixels, N = Cout, K = 9 Cin (tap-major); a block computes
@@ -212,10 +214,13 @@ __global__ void __launch_bounds__(256) k_conv_fwd(ConvArgs a)
 // issues the MMAs of a stage and commits them to that stage's mbarrier, which
 // frees the stage for the copies two steps later.  The epilogue reads the
 // accumulator rows back with tcgen05.ld (thread t <-> row t), adds the bias,
-// applies the ReLU and stores BF16.  Every mbarrier wait is bounded; on a
-// timeout the kernel sets *err, skips the epilogue and frees its tensor memory.
+// applies the ReLU and stores BF16.  Every mbarrier wait is bounded; when a
+// wait gives up the kernel sets *err, lets the MMAs it issued finish, skips
+// the epilogue and frees its tensor memory.  The decision to give up is the
+// block's (every thread agrees), so the barriers and the warp-collective
+// tensor-memory loads are never reached by part of a block.
 
-constexpr long long kWaitLimit = 1LL << 22;
+constexpr long long kWaitLimit = 1LL << 22;  // default bound: blocking polls (about a second)
 
 __device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
@@ -233,16 +238,32 @@ __device__ __forceinline__ uint32_t umma_idesc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err)
+// Wait for the phase of parity `parity` of an mbarrier.  spin <= 0: up to
+// kWaitLimit blocking polls (try_wait); spin > 0: up to spin non-blocking
+// polls (test_wait), a bound a caller sets to exercise the give-up path.
+// Gives up by setting *err and returning false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, long long spin = 0)
 {
-    for (long long it = 0; it < kWaitLimit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
+    if (spin > 0) {
+        for (long long it = 0; it < spin; ++it) {
+            uint32_t ok;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(ok)
+                : "r"(bar), "r"(parity)
+                : "memory");
+            if (ok) return true;
+        }
+    } else {
+        for (long long it = 0; it < kWaitLimit; ++it) {
+            uint32_t ok;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(ok)
+                : "r"(bar), "r"(parity)
+                : "memory");
+            if (ok) return true;
+        }
     }
     atomicExch(err, 1);
     return false;
@@ -293,10 +314,15 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, int* err)
     }
     const int nk = (K + BK - 1) / BK;
     bool ok = true;
-    for (int kt = 0; kt < nk && ok; ++kt) {
+    int issued = 0;  // steps whose MMAs were issued and committed
+    for (int kt = 0; kt < nk; ++kt) {
         const int st = kt & 1;
-        if (kt >= 2) ok = mbar_wait(smem_u32(&mbar[st]), ((kt - 2) >> 1) & 1, err);
-        if (!ok) break;
+        if (kt >= 2) {
+            // the stage's previous MMAs (step kt - 2) must be done; the block decides together
+            const bool w = mbar_wait(smem_u32(&mbar[st]), ((kt - 2) >> 1) & 1, err, a.spin);
+            ok = __syncthreads_and(w ? 1 : 0) != 0;
+            if (!ok) break;
+        }
         const uint32_t sa = sbase + st * STAGE, sb = sa + A_BYTES;
         const int k = kt * BK + c * 8;
         const bool kin = k < K;
@@ -337,10 +363,16 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, int* err)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_u32(&mbar[st])));
         }
+        issued = kt + 1;
         __syncthreads();
     }
-    if (ok && nk >= 1) ok = mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1, err);
-    if (ok && nk >= 2) ok = mbar_wait(smem_u32(&mbar[(nk - 2) & 1]), ((nk - 2) >> 1) & 1, err);
+    // the last commit arrives once every MMA the thread issued is done
+    if (issued >= 1) {
+        const uint32_t bar = smem_u32(&mbar[(issued - 1) & 1]), par = ((issued - 1) >> 1) & 1;
+        bool w = ok && mbar_wait(bar, par, err, a.spin);
+        if (!w) mbar_wait(bar, par, err);  // gave up: let the MMAs finish before the memory is freed
+        ok = __syncthreads_and((ok && w) ? 1 : 0) != 0;
+    }
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     if (ok) {
         const long long m = m0 + tid;  // accumulator row = tensor-memory lane
@@ -456,7 +488,7 @@ __global__ void __launch_bounds__(TmaConv<N>::THREADS) k_conv_tma(const __grid_c
         for (int k = 0; k < nk; ++k) {
             const int s = k % S, tap = k / cblocks, cb = k - tap * cblocks;
             // slot s was last read by the MMAs of step k - S
-            if (k >= S && !(ok = mbar_wait(smem_u32(&empty[s]), ((k / S) - 1) & 1, err))) break;
+            if (k >= S && !(ok = mbar_wait(smem_u32(&empty[s]), ((k / S) - 1) & 1, err, a.spin))) break;
             const int dy = (tap / 3 - 1) * a.dil, dx = (tap % 3 - 1) * a.dil;
             const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES, bar = smem_u32(&full[s]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(STAGE)
@@ -479,7 +511,7 @@ __global__ void __launch_bounds__(TmaConv<N>::THREADS) k_conv_tma(const __grid_c
         int k = 0;
         for (; k < nk; ++k) {
             const int s = k % S;
-            if (!(ok = mbar_wait(smem_u32(&full[s]), (k / S) & 1, err))) break;
+            if (!(ok = mbar_wait(smem_u32(&full[s]), (k / S) & 1, err, a.spin))) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n");
             const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES;
 #pragma unroll
@@ -504,12 +536,20 @@ __global__ void __launch_bounds__(TmaConv<N>::THREADS) k_conv_tma(const __grid_c
     const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
     if (!all_ok && tid == 0) {
         // a wait gave up: let the loads this CTA issued and no MMA consumed land
-        // before the shared memory is released (bounded like every wait)
+        // before the shared memory is released (the default bound)
         for (int k = consumed; k < issued; ++k) mbar_wait(smem_u32(&full[k % S]), (k / S) & 1, err);
     }
+    // every MMA issued has finished when the last issued step's commit arrives
+    // (in issue order); after a give-up the MMAs still finish before the
+    // tensor memory is freed
     ok = all_ok;
-    // every MMA has finished when the last step's commit arrives (in issue order)
-    if (ok && nk >= 1) ok = mbar_wait(smem_u32(&empty[(nk - 1) % S]), ((nk - 1) / S) & 1, err);
+    const int nc = consumed;
+    if (nc >= 1) {
+        const uint32_t bar = smem_u32(&empty[(nc - 1) % S]), par = ((nc - 1) / S) & 1;
+        bool w = ok && mbar_wait(bar, par, err, a.spin);
+        if (!w) mbar_wait(bar, par, err);
+        ok = __syncthreads_and((ok && w) ? 1 : 0) != 0;
+    }
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     if (ok) {
         // warp w reads lanes 32 (w % 4) .. of accumulator w / 4; accumulator
@@ -883,6 +923,7 @@ struct adr_cnn {
     float *prm = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     bf16 *wb = nullptr, *wt = nullptr, *wk = nullptr, *wtk = nullptr;
     int* err = nullptr;  // a bounded wait of a tensor-core kernel gave up
+    long long spin = 0;  // bound of those waits (adr_cnn_set_wait_limit; 0: default)
     bf16* act[kLayers] = {};  // post-activation outputs of layers 0..6 (bf16)
     float* y32 = nullptr;     // last layer output (fp32) [M][8]
     bf16 *dA = nullptr, *dB = nullptr, *dpre = nullptr;
@@ -1014,6 +1055,7 @@ adr_status cnn_forward(adr_cnn* c, int batch, const bf16* x)
         a.w = c->wb + c->T.woff[l];
         a.bias = c->prm + c->T.boff[l];
         a.relu = l < kLayers - 1;
+        a.spin = c->spin;
         if (l < kLayers - 1) a.y = c->act[l];
         else a.y32 = c->y32;
         launch_conv(c->stream, a, c->wk + c->T.woff[l], c->err);
@@ -1079,6 +1121,7 @@ adr_status cnn_backward(adr_cnn* c, int batch, const bf16* x, const float* t)
             a.dil = kDil[l];
             a.x = dyp;
             a.w = c->wt + c->T.woff[l];
+            a.spin = c->spin;
             a.y = dy == c->dA ? c->dB : c->dA;
             launch_conv(st, a, c->wtk + c->T.woff[l], c->err);
             dy = a.y;
@@ -1088,11 +1131,42 @@ adr_status cnn_backward(adr_cnn* c, int batch, const bf16* x, const float* t)
     return ADR_OK;
 }
 
+// a bounded wait gave up: clear the flag and report it
+adr_status report_timeout(adr_cnn* c)
+{
+    cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+    adr::set_error("a tensor-core kernel gave up waiting (bounded mbarrier wait); its outputs are not valid");
+    return ADR_ETIMEOUT;
+}
+
 }  // namespace
 
 extern "C" {
 
 long adr_cnn_num_params(void) { return param_offset(kLayers, false); }
+
+adr_status adr_cnn_set_wait_limit(adr_cnn* c, long long spins)
+{
+    if (!c || spins < 0) {
+        adr::set_error("adr_cnn_set_wait_limit: NULL handle or negative bound");
+        return ADR_EINVAL;
+    }
+    c->spin = spins;
+    return ADR_OK;
+}
+
+adr_status adr_cnn_sync(adr_cnn* c)
+{
+    if (!c) {
+        adr::set_error("adr_cnn_sync: NULL handle");
+        return ADR_EINVAL;
+    }
+    int e = 0;
+    ADR_CUDA_TRY(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return e ? report_timeout(c) : ADR_OK;
+}
 
 void adr_cnn_destroy(adr_cnn* c)
 {
@@ -1245,10 +1319,7 @@ adr_status adr_cnn_loss_grad(adr_cnn* c, int batch, const uint16_t* x, const flo
         ADR_CUDA_TRY(cudaMemcpyAsync(loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         ADR_CUDA_TRY(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        if (e) {
-            adr::set_error("a tensor-core kernel gave up waiting for its MMAs");
-            return ADR_ETIMEOUT;
-        }
+        if (e) return report_timeout(c);
     }
     return ADR_OK;
 }
@@ -1275,10 +1346,7 @@ adr_status adr_cnn_train_step(adr_cnn* c, int batch, const uint16_t* x, const fl
         ADR_CUDA_TRY(cudaMemcpyAsync(loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         ADR_CUDA_TRY(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         ADR_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        if (e) {
-            adr::set_error("a tensor-core kernel gave up waiting for its MMAs");
-            return ADR_ETIMEOUT;
-        }
+        if (e) return report_timeout(c);
     }
     return ADR_OK;
 }
@@ -1286,6 +1354,35 @@ adr_status adr_cnn_train_step(adr_cnn* c, int batch, const uint16_t* x, const fl
 }  // extern "C"
 
 namespace adr {
+// forward of a batch on stream st (a problem's stream): ordered after the
+// network's pending work and before its later work by events both ways
+adr_status cnn_forward_on(adr_cnn* c, int batch, const uint16_t* x, float* y, cudaStream_t st)
+{
+    if (!c || batch < 1 || batch > c->max_batch || !x || !y) {
+        set_error("warm start: bad network call");
+        return ADR_EINVAL;
+    }
+    cudaEvent_t ev = nullptr;
+    ADR_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    const cudaStream_t own = c->stream;
+    adr_status s = ADR_OK;
+    cudaError_t e = cudaEventRecord(ev, own);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    if (e != cudaSuccess) s = cuda_fail(e, "warm start: stream order");
+    if (s == ADR_OK) {
+        c->stream = st;
+        s = adr_cnn_forward(c, batch, x, y);
+        c->stream = own;
+    }
+    if (s == ADR_OK) {
+        e = cudaEventRecord(ev, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(own, ev, 0);
+        if (e != cudaSuccess) s = cuda_fail(e, "warm start: stream order");
+    }
+    cudaEventDestroy(ev);
+    return s;
+}
+
 // one prediction [64][64][8] around u0 to the handle's 256 x 256 grid
 adr_status launch_cnn_upsample(Problem* p, const float* y, const double* u0, const double* scale,
                                double* u)

@@ -251,3 +251,34 @@ def test_initial_state_rejects_other_grids(torch_cuda):
     with pytest.raises(AdrError, match="EINVAL"):
         net.initial_state(s, y)
     s.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_the_handle_recovers(torch_cuda):
+    """A bound of one non-blocking poll makes the tensor-core kernels' mbarrier
+    waits give up: each lets the loads and MMAs it issued finish, skips its
+    output and flags the handle, and the calls report ADR_ETIMEOUT, without a
+    fault.  With the default bound restored the same handle computes the
+    forward again, bit for bit as before and against the reference."""
+    torch = torch_cuda
+    from paper_2411_11041_gb300 import ADR_ETIMEOUT, ADR_OK, AdrError, Network
+    p = W.cnn_init_params(5, last_scale=1.0)
+    net = Network(2, p)
+    x, t, xh, _ = _rand_inputs(2, 1, torch)
+    y_ok = net.forward(x).cpu().numpy()
+    assert net.sync() == ADR_OK
+    net.set_wait_limit(1)
+    net.forward(x)
+    assert net.sync() == ADR_ETIMEOUT
+    assert net.sync() == ADR_OK  # the report cleared the flag
+    with pytest.raises(AdrError, match="ETIMEOUT"):
+        net.loss_grad(x, t)
+    net.set_wait_limit(0)
+    y = net.forward(x).cpu().numpy()
+    assert net.sync() == ADR_OK
+    assert np.array_equal(y, y_ok)
+    pb = _bf16(p, torch)
+    for l in range(CNN.LAYERS):  # biases stay FP32 on the GPU
+        pb[CNN.offset(l, True):CNN.offset(l + 1)] = p[CNN.offset(l, True):CNN.offset(l + 1)]
+    ref = CNN.forward(pb, xh[0])
+    assert _rel(y[0], ref) <= 2e-2
+    net.loss_grad(x, t)  # no error left behind

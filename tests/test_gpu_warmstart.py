@@ -55,3 +55,28 @@ def test_trained_network_reduces_iterations_on_held_out_problems(torch_cuda):
     assert stz == ADR_OK and stl == ADR_OK
     for a, b in zip(ul, uz):
         assert (a - b).abs().max().item() <= 1e-6 * b.abs().max().item()
+
+
+def test_init_learned_equals_the_manual_chain(torch_cuda):
+    """ADR_INIT_LEARNED with a network attached by adr_set_warm_start runs the
+    paper's u0, the features, the forward pass and the initial state inside
+    the solve: the same iterations and answer, bit for bit, as the chain run by
+    hand and passed with ADR_INIT_USER.  Without a network it is refused."""
+    torch = torch_cuda
+    from paper_2411_11041_gb300 import ADR_INIT_LEARNED, ADR_OK, AdrError, Network, Solver
+    from paper_2411_11041_gb300 import warmstart as WS
+    probs = W.learned(3, n=256, seed=W.SEED_BASE + 7)
+    net = Network(4, W.cnn_init_params(seed=11, last_scale=1.0))
+    for p in probs:
+        man = Solver(p, init=1, **WS.solver_opts())
+        u0 = WS.initial_states(net, [man], WS.stack([p]))[0]
+        um, _, sm, cm = man.solve_stationary(u_init=u0)
+        lrn = Solver(p, init=ADR_INIT_LEARNED, **WS.solver_opts())
+        lrn.set_warm_start(net)
+        ul, _, sl, cl = lrn.solve_stationary()
+        assert cm == cl == ADR_OK
+        assert sl["iters"] == sm["iters"]
+        assert torch.equal(ul, um)
+    bare = Solver(probs[0], init=ADR_INIT_LEARNED, **WS.solver_opts())
+    with pytest.raises(AdrError, match="EINVAL"):
+        bare.solve_stationary()
