@@ -51,6 +51,10 @@ typedef struct {
     double *xi, *eta, *bnorm, *fval;
     /* four crossings per grid node: row-left, row-right, col-down, col-up */
     crossing* cross;
+    /* direct transfer (built on request): per node of this family, the
+       nearest crossing with the other family's curves before and after it
+       along its own curve (pos in element units along the curve) */
+    crossing* xf;
 } family;
 
 struct orc_problem {
@@ -64,6 +68,7 @@ struct orc_problem {
     double bmax;
     int interp_weights; /* 0: plain average of the row and column values; 1: inverse-gap weights */
     int stabilize;      /* 0: Galerkin on the B lines (the paper); 1: SUPG on the B lines */
+    int transfer;       /* 0: values between the families through the grid (§6); 1: directly */
     family fam[2];
 };
 
@@ -698,6 +703,188 @@ static int build_crossings(orc_problem* p, int fam)
     return uncovered;
 }
 
+/* ------------------------------------ direct transfer between the families
+ * The paper's conclusions propose to carry values between the two sets of
+ * orthogonal curves through the points where they cross, without the
+ * intermediate grid and its bilinear interpolation.  Reading: every crossing
+ * of a target curve's polyline with a source curve's polyline is found (the
+ * two segments share a grid cell: each source segment is listed in the cells
+ * its bounding box covers, and a pair is taken in the cell that holds its
+ * crossing point, so that it counts once).  Along the target curve every
+ * element keeps its crossing of smallest and of largest position (ties: the
+ * smaller source segment, then the smaller position inside it), a crossing on
+ * a node counting for both of its elements.  A target node takes the value
+ * linear in arc length between the nearest crossing at or before it and the
+ * nearest at or after it; an element without a crossing passes the search
+ * on, and the curve's end (on the boundary, u = 0) stands in where a side has
+ * none.  The value at a crossing is linear along the source segment. */
+
+static double cross_value(const crossing* c, const double* v);
+
+/* crossing of the segments A-B and C-D (index coordinates):
+ * A + a (B - A) = C + b (D - C) with 0 <= a, b <= 1; parallel segments give none */
+static int seg_cross(double ax, double ay, double bx, double by, double cx, double cy,
+                     double dx, double dy, double* a, double* b)
+{
+    double ex = bx - ax, ey = by - ay, fx = dx - cx, fy = dy - cy;
+    double det = ex * fy - ey * fx;
+    if (det == 0.0) return 0;
+    double gx = cx - ax, gy = cy - ay;
+    double aa = (gx * fy - gy * fx) / det;
+    double bb = (gx * ey - gy * ex) / det;
+    if (!(aa >= 0.0 && aa <= 1.0 && bb >= 0.0 && bb <= 1.0)) return 0;
+    *a = aa;
+    *b = bb;
+    return 1;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* crossing tables of the target family tf with the source family 1 - tf */
+static int build_transfer(orc_problem* p, int tf)
+{
+    family* T = &p->fam[tf];
+    const family* S = &p->fam[1 - tf];
+    int ncx = p->nx - 1, ncy = p->ny - 1;
+    size_t ncell = (size_t)ncx * ncy;
+    int* cnt = calloc(ncell + 1, sizeof(int));
+    if (!cnt) return -1;
+    /* source segments by cell (CSR), in segment order within a cell */
+    for (int l = 0; l < S->n_lines; ++l)
+        for (int g = S->off[l]; g + 1 < S->off[l + 1]; ++g) {
+            int i0 = clampi((int)floor(fmin(S->xi[g], S->xi[g + 1])), 0, ncx - 1);
+            int i1 = clampi((int)floor(fmax(S->xi[g], S->xi[g + 1])), 0, ncx - 1);
+            int r0 = clampi((int)floor(fmin(S->eta[g], S->eta[g + 1])), 0, ncy - 1);
+            int r1 = clampi((int)floor(fmax(S->eta[g], S->eta[g + 1])), 0, ncy - 1);
+            for (int r = r0; r <= r1; ++r)
+                for (int i = i0; i <= i1; ++i) cnt[(size_t)r * ncx + i + 1]++;
+        }
+    for (size_t c = 0; c < ncell; ++c) cnt[c + 1] += cnt[c];
+    int* fill = malloc(sizeof(int) * (ncell + 1));
+    int* list = malloc(sizeof(int) * ((size_t)cnt[ncell] + 1));
+    if (!fill || !list) {
+        free(cnt);
+        free(fill);
+        free(list);
+        return -1;
+    }
+    memcpy(fill, cnt, sizeof(int) * (ncell + 1));
+    for (int l = 0; l < S->n_lines; ++l)
+        for (int g = S->off[l]; g + 1 < S->off[l + 1]; ++g) {
+            int i0 = clampi((int)floor(fmin(S->xi[g], S->xi[g + 1])), 0, ncx - 1);
+            int i1 = clampi((int)floor(fmax(S->xi[g], S->xi[g + 1])), 0, ncx - 1);
+            int r0 = clampi((int)floor(fmin(S->eta[g], S->eta[g + 1])), 0, ncy - 1);
+            int r1 = clampi((int)floor(fmax(S->eta[g], S->eta[g + 1])), 0, ncy - 1);
+            for (int r = r0; r <= r1; ++r)
+                for (int i = i0; i <= i1; ++i) list[fill[(size_t)r * ncx + i]++] = g;
+        }
+    free(fill);
+    int nmax = 1;
+    for (int l = 0; l < T->n_lines; ++l)
+        if (T->off[l + 1] - T->off[l] > nmax) nmax = T->off[l + 1] - T->off[l];
+    seg_slot* slots = calloc((size_t)nmax, sizeof(seg_slot));
+    free(T->xf);
+    T->xf = calloc((size_t)2 * T->n_nodes + 2, sizeof(crossing));
+    if (!slots || !T->xf) {
+        free(cnt);
+        free(list);
+        free(slots);
+        return -1;
+    }
+    for (int l = 0; l < T->n_lines; ++l) {
+        int base = T->off[l], n = T->off[l + 1] - base - 1; /* n elements */
+        if (n < 2) continue;
+        memset(slots, 0, sizeof(seg_slot) * n);
+        for (int e = 0; e < n; ++e) {
+            int a0 = base + e;
+            double ax = T->xi[a0], ay = T->eta[a0], bx = T->xi[a0 + 1], by = T->eta[a0 + 1];
+            int i0 = clampi((int)floor(fmin(ax, bx)), 0, ncx - 1), i1 = clampi((int)floor(fmax(ax, bx)), 0, ncx - 1);
+            int r0 = clampi((int)floor(fmin(ay, by)), 0, ncy - 1), r1 = clampi((int)floor(fmax(ay, by)), 0, ncy - 1);
+            for (int r = r0; r <= r1; ++r)
+                for (int i = i0; i <= i1; ++i) {
+                    size_t c = (size_t)r * ncx + i;
+                    for (int q = cnt[c]; q < cnt[c + 1]; ++q) {
+                        int g = list[q];
+                        double a, b;
+                        if (!seg_cross(ax, ay, bx, by, S->xi[g], S->eta[g], S->xi[g + 1], S->eta[g + 1], &a, &b))
+                            continue;
+                        double px = ax + a * (bx - ax), py = ay + a * (by - ay);
+                        if (clampi((int)floor(px), 0, ncx - 1) != i || clampi((int)floor(py), 0, ncy - 1) != r)
+                            continue; /* counted in the cell that holds the crossing */
+                        record(slots, n, e + a, g, b);
+                    }
+                }
+        }
+        /* nearest crossing on each side of every interior node of the curve */
+        for (int k = 1; k < n; ++k) {
+            crossing* c = &T->xf[2 * (size_t)(base + k)];
+            crossing bnd = {-1, 0.0, 0.0, 1};
+            c[0] = bnd;
+            c[1] = bnd;
+            c[1].pos = n;
+            for (int e = k - 1; e >= 0; --e)
+                if (slots[e].mx.valid) {
+                    c[0] = slots[e].mx;
+                    break;
+                }
+            for (int e = k; e < n; ++e)
+                if (slots[e].mn.valid) {
+                    c[1] = slots[e].mn;
+                    break;
+                }
+        }
+    }
+    free(cnt);
+    free(list);
+    free(slots);
+    return 0;
+}
+
+int orc_set_transfer(orc_problem* p, int mode)
+{
+    if (mode != 0 && mode != 1) return ORC_EINVAL;
+    if (mode == 1 && (!p->fam[0].xf || !p->fam[1].xf)) {
+        if (build_transfer(p, 0) || build_transfer(p, 1)) return ORC_ENOMEM;
+    }
+    p->transfer = mode;
+    return ORC_OK;
+}
+
+/* values at the nodes of family to_fam from the curve values of the other
+ * family, through the crossing tables (both ends of a curve get 0) */
+void orc_transfer(const orc_problem* p, int to_fam, const double* from_vals, double* to_vals)
+{
+    const family* T = &p->fam[to_fam];
+    for (int l = 0; l < T->n_lines; ++l) {
+        int a = T->off[l], b = T->off[l + 1] - 1;
+        for (int k = a; k <= b; ++k) {
+            if (k == a || k == b || !T->xf) {
+                to_vals[k] = 0.0;
+                continue;
+            }
+            const crossing* c = &T->xf[2 * (size_t)k];
+            double vL = cross_value(&c[0], from_vals), vR = cross_value(&c[1], from_vals);
+            if (c[1].pos == c[0].pos) {
+                to_vals[k] = vL;
+            } else {
+                double w = ((k - a) - c[0].pos) / (c[1].pos - c[0].pos);
+                to_vals[k] = (1.0 - w) * vL + w * vR;
+            }
+        }
+    }
+}
+
+void orc_transfer_table(const orc_problem* p, int fam, int* seg, double* t, double* pos)
+{
+    const family* F = &p->fam[fam];
+    for (size_t k = 0; k < 2 * (size_t)F->n_nodes; ++k) {
+        const crossing* c = F->xf ? &F->xf[k] : NULL;
+        seg[k] = (c && c->valid) ? c->g : -2;
+        t[k] = (c && c->valid) ? c->t : 0.0;
+        pos[k] = (c && c->valid) ? c->pos : 0.0;
+    }
+}
+
 /* ------------------------------------------------------------- create */
 
 int orc_create(int nx, int ny, double x0, double y0, double x1, double y1,
@@ -808,6 +995,7 @@ void orc_destroy(orc_problem* p)
         free(F->bnorm);
         free(F->fval);
         free(F->cross);
+        free(F->xf);
     }
     free(p->beta1);
     free(p->beta2);
@@ -1088,9 +1276,29 @@ int orc_dense_lu_solve(int n, double* A, double* b)
  * (0 at the line ends).  f_extra (nullable, scaled) is added to f on the
  * B lines (the u_n/dt term of an implicit-Euler slice).  Returns the smallest
  * |pivot| met. */
+static double sweep_core(const orc_problem* p, int fam, double theta, double dt,
+                         const double* u_grid, const double* u_vals, double sig,
+                         const double* f_grid, const double* f_extra, double fx_scale, double* d);
+
 double orc_sweep_lines(const orc_problem* p, int fam, double theta, double dt,
                        const double* u_grid, double sig, const double* f_grid,
                        const double* f_extra, double fx_scale, double* d)
+{
+    return sweep_core(p, fam, theta, dt, u_grid, NULL, sig, f_grid, f_extra, fx_scale, d);
+}
+
+/* the same with the state given as values at the line nodes (u_vals) instead
+ * of interpolated from the grid (the direct transfer) */
+double orc_sweep_line_values(const orc_problem* p, int fam, double theta, double dt,
+                             const double* u_vals, double sig, const double* f_extra,
+                             double fx_scale, double* d)
+{
+    return sweep_core(p, fam, theta, dt, NULL, u_vals, sig, p->f, f_extra, fx_scale, d);
+}
+
+static double sweep_core(const orc_problem* p, int fam, double theta, double dt,
+                         const double* u_grid, const double* u_vals, double sig,
+                         const double* f_grid, const double* f_extra, double fx_scale, double* d)
 {
     const family* F = &p->fam[fam];
     int nmax = 0;
@@ -1110,7 +1318,9 @@ double orc_sweep_lines(const orc_problem* p, int fam, double theta, double dt,
         for (int k = 0; k <= n; ++k) d[base + k] = 0.0;
         if (n < 2) continue;
         for (int k = 0; k <= n; ++k) {
-            u[k] = (k == 0 || k == n) ? 0.0 : bilin(p, u_grid, F->xi[base + k], F->eta[base + k]);
+            if (k == 0 || k == n) u[k] = 0.0;
+            else if (u_vals) u[k] = u_vals[base + k];
+            else u[k] = bilin(p, u_grid, F->xi[base + k], F->eta[base + k]);
             double fv = (f_grid == p->f) ? F->fval[base + k]
                                          : bilin(p, f_grid, F->xi[base + k], F->eta[base + k]);
             if (f_extra) fv += fx_scale * bilin(p, f_extra, F->xi[base + k], F->eta[base + k]);
@@ -1150,6 +1360,11 @@ static void substep(const orc_problem* p, int fam, double theta, double dt, doub
 
 /* §5 eq. SemiDiscrSplit: u_j -> u_{j+1/2} (B curves, form s, load l)
  *                        u_{j+1/2} -> u_{j+1} (G curves, form m, no load). */
+static void direct_step(const orc_problem* p, double theta, double dt, double sig,
+                        const double* f_extra, double fx_scale, const double* uB, double* vB,
+                        double* uG, double* vG, double* d);
+static void paper_u0_values(const orc_problem* p, double* v);
+
 void orc_split_step(const orc_problem* p, double theta, double dt, double sig,
                     const double* f_extra, double fx_scale,
                     const double* u, double* u_half, double* u_next)
@@ -1157,10 +1372,112 @@ void orc_split_step(const orc_problem* p, double theta, double dt, double sig,
     int nmax = p->fam[0].n_nodes > p->fam[1].n_nodes ? p->fam[0].n_nodes : p->fam[1].n_nodes;
     double* d = malloc(sizeof(double) * (nmax + 1));
     double* v = malloc(sizeof(double) * (nmax + 1));
-    substep(p, 0, theta, dt, sig, f_extra, fx_scale, u, u_half, d, v);
-    substep(p, 1, theta, dt, sig, NULL, 0.0, u_half, u_next, d, v);
+    if (p->transfer) {
+        /* the grid state onto the B nodes, one direct step, both halves back
+           to the grid for the output */
+        double* uB = malloc(sizeof(double) * (p->fam[0].n_nodes + 1));
+        double* uG = malloc(sizeof(double) * (p->fam[1].n_nodes + 1));
+        double* vG = malloc(sizeof(double) * (p->fam[1].n_nodes + 1));
+        orc_gather(p, 0, u, uB);
+        direct_step(p, theta, dt, sig, f_extra, fx_scale, uB, v, uG, vG, d);
+        orc_map_to_grid(p, 0, v, u_half);
+        orc_map_to_grid(p, 1, vG, u_next);
+        free(uB);
+        free(uG);
+        free(vG);
+    } else {
+        substep(p, 0, theta, dt, sig, f_extra, fx_scale, u, u_half, d, v);
+        substep(p, 1, theta, dt, sig, NULL, 0.0, u_half, u_next, d, v);
+    }
     free(d);
     free(v);
+}
+
+/* one split step with the direct transfer: uB (state on the B nodes) -> vB
+ * (B curve values u + dt d) -> uG (their transfer to the G nodes) -> vG (G
+ * curve values); d is work space */
+static void direct_step(const orc_problem* p, double theta, double dt, double sig,
+                        const double* f_extra, double fx_scale, const double* uB, double* vB,
+                        double* uG, double* vG, double* d)
+{
+    const family *B = &p->fam[0], *G = &p->fam[1];
+    sweep_core(p, 0, theta, dt, NULL, uB, sig, p->f, f_extra, fx_scale, d);
+    for (int k = 0; k < B->n_nodes; ++k) vB[k] = uB[k] + dt * d[k];
+    orc_transfer(p, 1, vB, uG);
+    sweep_core(p, 1, theta, dt, NULL, uG, sig, p->f, NULL, 0.0, d);
+    for (int k = 0; k < G->n_nodes; ++k) vG[k] = uG[k] + dt * d[k];
+}
+
+/* Stationary iteration with the direct transfer: the state lives on the B
+ * nodes (u_j there), each step is direct_step followed by the transfer of the
+ * G curve values back to the B nodes (u_{j+1}); the relative update is taken
+ * over the interior B nodes.  Output: theta = 1/2 the midpoint
+ * (u_j + u_{j+1/2}) / 2 on the B nodes mapped to the grid, otherwise the G
+ * curve values of the last step mapped to the grid (also u_iter_out). */
+static int solve_direct(const orc_problem* p, double theta, double dt, double tol, int max_iter,
+                        int init, const double* u_init, double sig, const double* f_extra,
+                        double fx_scale, double* u_out, double* u_iter_out, int* iters,
+                        double* rel_out)
+{
+    const family *B = &p->fam[0], *G = &p->fam[1];
+    size_t N = (size_t)p->nx * p->ny, nb = (size_t)B->n_nodes + 1, ng = (size_t)G->n_nodes + 1;
+    double *uB = calloc(nb, sizeof(double)), *vB = calloc(nb, sizeof(double)),
+           *uBn = calloc(nb, sizeof(double)), *uG = calloc(ng, sizeof(double)),
+           *vG = calloc(ng, sizeof(double)), *d = calloc(nb > ng ? nb : ng, sizeof(double)),
+           *tmp = calloc(N, sizeof(double));
+    if (!uB || !vB || !uBn || !uG || !vG || !d || !tmp) return ORC_ENOMEM;
+    if (dt <= 0.0) dt = orc_default_dt(p, sig);
+    if (init == 1 && u_init) {
+        for (size_t k = 0; k < N; ++k) tmp[k] = p->ntype[k] == ORC_INTERIOR ? u_init[k] : 0.0;
+        orc_gather(p, 0, tmp, uB);
+    } else if (init == 2) {
+        paper_u0_values(p, uB);
+    }
+    int status = ORC_ENOCONV, j = 0;
+    double rel = INFINITY;
+    for (j = 0; j < max_iter; ++j) {
+        direct_step(p, theta, dt, sig, f_extra, fx_scale, uB, vB, uG, vG, d);
+        orc_transfer(p, 0, vG, uBn);
+        double num = 0.0, den = 0.0;
+        for (int l = 0; l < B->n_lines; ++l)
+            for (int k = B->off[l] + 1; k < B->off[l + 1] - 1; ++k) {
+                double dl = uBn[k] - uB[k];
+                num += dl * dl;
+                den += uBn[k] * uBn[k];
+            }
+        if (!isfinite(num) || !isfinite(den)) rel = INFINITY;
+        else rel = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+        if (tol > 0.0 && rel <= tol) {
+            status = ORC_OK;
+            break;
+        }
+        if (!isfinite(rel)) break; /* diverged */
+        if (j + 1 < max_iter) memcpy(uB, uBn, sizeof(double) * nb);
+    }
+    int done = (j < max_iter) ? j + 1 : max_iter;
+    if (tol <= 0.0 && isfinite(rel)) status = ORC_OK;
+    if (max_iter <= 0) {
+        orc_map_to_grid(p, 0, uB, u_out);
+        if (u_iter_out) memcpy(u_iter_out, u_out, N * sizeof(double));
+    } else {
+        if (theta == 0.5) {
+            for (size_t k = 0; k < nb; ++k) d[k] = 0.5 * (uB[k] + vB[k]);
+            orc_map_to_grid(p, 0, d, u_out);
+        } else {
+            orc_map_to_grid(p, 1, vG, u_out);
+        }
+        if (u_iter_out) orc_map_to_grid(p, 1, vG, u_iter_out);
+    }
+    if (iters) *iters = done;
+    if (rel_out) *rel_out = rel;
+    free(uB);
+    free(vB);
+    free(uBn);
+    free(uG);
+    free(vG);
+    free(d);
+    free(tmp);
+    return status;
 }
 
 /* Pseudo-time step (the paper gives none for the stationary problem): the
@@ -1176,13 +1493,22 @@ double orc_default_dt(const orc_problem* p, double sig)
  * line (mu K + C + sigma M) u0 = F, mapped to the grid as values. */
 void orc_paper_u0(const orc_problem* p, double* u0)
 {
+    double* v = calloc((size_t)p->fam[0].n_nodes + 1, sizeof(double));
+    paper_u0_values(p, v);
+    orc_map_to_grid(p, 0, v, u0);
+    free(v);
+}
+
+/* the B-line solutions of eq. u0stationary (values at the B nodes) */
+static void paper_u0_values(const orc_problem* p, double* v)
+{
     const family* F = &p->fam[0];
     int nmax = 0;
     for (int l = 0; l < F->n_lines; ++l) {
         int n = F->off[l + 1] - F->off[l];
         if (n > nmax) nmax = n;
     }
-    double* v = calloc((size_t)F->n_nodes + 1, sizeof(double));
+    for (int k = 0; k < F->n_nodes; ++k) v[k] = 0.0;
     double* a = malloc(sizeof(double) * (nmax + 1));
     double* b = malloc(sizeof(double) * (nmax + 1));
     double* c = malloc(sizeof(double) * (nmax + 1));
@@ -1201,8 +1527,6 @@ void orc_paper_u0(const orc_problem* p, double* u0)
         }
         orc_thomas(n - 1, a, b, c, r, v + base + 1);
     }
-    orc_map_to_grid(p, 0, v, u0);
-    free(v);
     free(a);
     free(b);
     free(c);
@@ -1237,6 +1561,9 @@ int orc_solve_stationary(const orc_problem* p, double theta, double dt, double t
                          const double* f_extra, double fx_scale, double* u_out,
                          double* u_iter_out, int* iters, double* rel_out)
 {
+    if (p->transfer)
+        return solve_direct(p, theta, dt, tol, max_iter, init, u_init, sig, f_extra, fx_scale, u_out,
+                            u_iter_out, iters, rel_out);
     size_t N = (size_t)p->nx * p->ny;
     double* u = calloc(N, sizeof(double));
     double* uh = calloc(N, sizeof(double));
@@ -1289,7 +1616,15 @@ int orc_step_parabolic(const orc_problem* p, double dt, int nsteps, int mode,
     for (size_t k = 0; k < N; ++k)
         if (p->ntype[k] != ORC_INTERIOR) u[k] = 0.0;
     for (int s = 0; s < nsteps; ++s) {
-        if (mode == 0) {
+        if (mode == 0 && p->transfer) {
+            /* with the direct transfer the state stays on the B nodes: the
+               time steps are the iteration's steps from the gathered u */
+            int r = solve_direct(p, theta, dt, -1.0, nsteps, 1, u, p->sigma, NULL, 0.0, a, b, NULL, NULL);
+            if (r != ORC_OK) st = r;
+            memcpy(u, b, N * sizeof(double));
+            tot += nsteps;
+            break;
+        } else if (mode == 0) {
             orc_split_step(p, theta, dt, p->sigma, NULL, 0.0, u, a, b);
             memcpy(u, b, N * sizeof(double));
             tot += 1;

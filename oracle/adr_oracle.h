@@ -37,6 +37,23 @@ void orc_set_interp_weights(orc_problem* p, int mode);
 /* 1D problems on the B lines: 0 = Galerkin (the paper, default), 1 = SUPG */
 void orc_set_stabilization(orc_problem* p, int mode);
 
+/* values between the families: 0 = through the grid (§6, default),
+   1 = directly through the curves' crossings (the paper's conclusions);
+   builds the crossing tables on first use.  Returns ORC_OK / ORC_EINVAL. */
+int orc_set_transfer(orc_problem* p, int mode);
+/* direct transfer: values at the nodes of to_fam from the other family's
+   curve values */
+void orc_transfer(const orc_problem* p, int to_fam, const double* from_vals, double* to_vals);
+/* the crossing table of fam: per node (left, right) crossings with the other
+   family along its curve: seg[2 n_nodes] (first node of the crossed segment,
+   -1 = the curve's end, -2 = an end node of the curve), t, pos (element units
+   along the curve) */
+void orc_transfer_table(const orc_problem* p, int fam, int* seg, double* t, double* pos);
+/* one substep's increments on family fam from values at its nodes */
+double orc_sweep_line_values(const orc_problem* p, int fam, double theta, double dt,
+                             const double* u_vals, double sig, const double* f_extra,
+                             double fx_scale, double* d);
+
 /* geometry queries */
 int orc_const_beta(const orc_problem* p);
 void orc_node_types(const orc_problem* p, unsigned char* out /* [ny*nx] */);

@@ -74,6 +74,14 @@ def lib():
                                            C.c_int, vp, C.c_double, vp, C.c_double, dp, vp,
                                            C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.orc_paper_u0.argtypes = [vp, dp]
+        L.orc_set_transfer.argtypes = [vp, C.c_int]
+        L.orc_transfer.argtypes = [vp, C.c_int, dp, dp]
+        L.orc_transfer.restype = None
+        L.orc_transfer_table.argtypes = [vp, C.c_int, ip, dp, dp]
+        L.orc_transfer_table.restype = None
+        L.orc_sweep_line_values.argtypes = [vp, C.c_int, C.c_double, C.c_double, dp, C.c_double,
+                                            vp, C.c_double, dp]
+        L.orc_sweep_line_values.restype = C.c_double
         L.orc_step_parabolic.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.c_double,
                                          C.c_double, C.c_double, C.c_int, dp,
                                          C.POINTER(C.c_int)]
@@ -121,7 +129,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """One problem in the oracle.  Mirrors the library's handle."""
 
-    def __init__(self, prob, interp_weights=0, stabilize=0):
+    def __init__(self, prob, interp_weights=0, stabilize=0, transfer=0):
         self.prob = prob
         self.nx, self.ny = prob.nx, prob.ny
         self.mask = _c(prob.mask, np.uint8)
@@ -137,6 +145,10 @@ class Oracle:
             lib().orc_set_interp_weights(h, 1)
         if stabilize:
             lib().orc_set_stabilization(h, 1)
+        if transfer:
+            st = lib().orc_set_transfer(h, int(transfer))
+            if st != OK:
+                raise OracleError(st, "orc_set_transfer")
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -171,6 +183,25 @@ class Oracle:
         lib().orc_crossings(self.h, fam, seg, t, pos)
         s = (self.ny, self.nx, 4)
         return seg.reshape(s), t.reshape(s), pos.reshape(s)
+
+    def transfer_table(self, fam):
+        """Direct-transfer crossings of family fam's nodes: (seg, t, pos), each
+        [n_nodes, 2] (left, right)."""
+        n = 2 * lib().orc_num_line_nodes(self.h, fam)
+        seg, t, pos = np.zeros(n, np.int32), np.zeros(n), np.zeros(n)
+        lib().orc_transfer_table(self.h, fam, seg, t, pos)
+        return seg.reshape(-1, 2), t.reshape(-1, 2), pos.reshape(-1, 2)
+
+    def transfer(self, to_fam, vals):
+        out = np.zeros(lib().orc_num_line_nodes(self.h, to_fam))
+        lib().orc_transfer(self.h, to_fam, _c(vals), out)
+        return out
+
+    def sweep_line_values(self, fam, theta, dt, u_vals, sigma=None):
+        d = np.zeros(lib().orc_num_line_nodes(self.h, fam) + 1)
+        sig = self.prob.sigma if sigma is None else sigma
+        piv = lib().orc_sweep_line_values(self.h, fam, theta, dt, _c(u_vals), sig, None, 0.0, d)
+        return d[:-1], piv
 
     # steps
     def bilinear(self, grid, xi, eta):
