@@ -104,6 +104,18 @@ typedef struct {
                                propose for singularly perturbed problems (test function
                                w + tau |beta| w', tau = h/(2|beta|)(coth Pe - 1/Pe) per element);
                                FP64 mode only */
+    int transfer;           /* how values pass from one curve family to the other:
+                               0 = through the grid (§6: curve values -> grid nodes, then
+                               bilinear samples at the other family's nodes);
+                               1 = directly, the transfer the paper's conclusions propose:
+                               a node takes the value interpolated linearly, along its own
+                               curve, between the nearest crossings with the other family
+                               before and after it (each crossing's value linear along the
+                               crossed segment; no crossing on a side: the curve's end, value
+                               0).  The iteration state then lives at the B curve nodes, the
+                               relative update is taken over them, and the grid is touched only
+                               by the initial state (bilinear samples) and the output (the
+                               curve -> grid map of §6).  FP64 mode only; not in batches */
 } adr_opts;
 
 /* Result statistics (host struct filled by the solve calls). */
@@ -204,6 +216,14 @@ int adr_num_line_nodes(const adr_problem* prob, int fam);
 adr_status adr_get_lines(const adr_problem* prob, int fam, int* off, double* xi, double* eta,
                          double* h);
 adr_status adr_get_crossings(const adr_problem* prob, int fam, int* seg, double* t, double* pos);
+/* adr_get_transfer: the direct transfer's crossings (handles created with
+ * opts.transfer == 1): per node k of family fam, entries 2k (the nearest
+ * crossing at or before the node along its curve) and 2k+1 (at or after it):
+ * seg = global index of the first node of the other family's crossed segment
+ * (-1 none on that side: the curve's end; -2 the node is a curve end), t =
+ * position in that segment, pos = position along the node's own curve in
+ * element units (0 .. n).  Errors: ADR_EINVAL (also for opts.transfer == 0). */
+adr_status adr_get_transfer(const adr_problem* prob, int fam, int* seg, double* t, double* pos);
 
 /*
  * adr_split_step -- one split step u -> (u_half, u_next) of eq. SemiDiscrSplit

@@ -35,7 +35,7 @@ class adr_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("theta", C.c_double), ("dt", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("init", C.c_int),
                 ("rows_per_thread", C.c_int), ("map_blocks_per_sm", C.c_int),
-                ("interp_weights", C.c_int), ("stabilize", C.c_int)]
+                ("interp_weights", C.c_int), ("stabilize", C.c_int), ("transfer", C.c_int)]
 
 
 class adr_stats(C.Structure):
@@ -80,6 +80,7 @@ def lib():
         L.adr_num_line_nodes.argtypes = [vp, C.c_int]
         L.adr_get_lines.argtypes = [vp, C.c_int, ip, dp, dp, dp]
         L.adr_get_crossings.argtypes = [vp, C.c_int, ip, dp, dp]
+        L.adr_get_transfer.argtypes = [vp, C.c_int, ip, dp, dp]
         L.adr_split_step.argtypes = [vp, C.c_double, vp, vp, vp]
         L.adr_paper_u0.argtypes = [vp, vp]
         L.adr_time_kernels.argtypes = [vp, C.c_int, dp]
@@ -113,7 +114,7 @@ def lib():
 
 EXPORTED = ["adr_default_opts", "adr_create", "adr_solve_stationary", "adr_step_parabolic",
             "adr_destroy", "adr_last_error", "adr_num_lines", "adr_num_line_nodes",
-            "adr_get_lines", "adr_get_crossings", "adr_split_step", "adr_paper_u0",
+            "adr_get_lines", "adr_get_crossings", "adr_get_transfer", "adr_split_step", "adr_paper_u0",
             "adr_time_kernels", "adr_batch_create", "adr_batch_solve", "adr_batch_destroy",
             "adr_solve_batch", "adr_autotune",
             "adr_cnn_num_params", "adr_cnn_create", "adr_cnn_destroy", "adr_cnn_set_params",
@@ -122,12 +123,14 @@ EXPORTED = ["adr_default_opts", "adr_create", "adr_solve_stationary", "adr_step_
             "adr_cnn_set_wait_limit", "adr_cnn_sync", "adr_set_warm_start"]
 
 
-def tune_key(prob, prec):
-    """Cache key of a problem's launch shapes: grid, domain, field kind, precision."""
+def tune_key(prob, prec, transfer=0):
+    """Cache key of a problem's launch shapes: grid, domain, field kind, precision
+    (and the direct transfer, which times other kernels)."""
     b1, b2 = np.asarray(prob.beta1), np.asarray(prob.beta2)
     const = bool(np.all(b1 == b1.flat[0]) and np.all(b2 == b2.flat[0]))
     mask = np.asarray(prob.mask)
-    return f"v2:{prob.nx}x{prob.ny}:{int(mask.sum())}:{'const' if const else 'curved'}:p{int(prec)}"
+    key = f"v2:{prob.nx}x{prob.ny}:{int(mask.sum())}:{'const' if const else 'curved'}:p{int(prec)}"
+    return key + (":direct" if transfer else "")
 
 
 def _tune_path():
@@ -280,7 +283,7 @@ class Solver:
         self.device = torch.device(device)
         self.stream = stream
         self.nx, self.ny = int(prob.nx), int(prob.ny)
-        key = tune_key(prob, opts.get("prec", ADR_FP64)) if autotune else None
+        key = tune_key(prob, opts.get("prec", ADR_FP64), opts.get("transfer", 0)) if autotune else None
         cached = _tune_cache().get(key) if key else None
         if cached:
             opts.setdefault("rows_per_thread", cached["rows_per_thread"])
@@ -381,6 +384,17 @@ class Solver:
                "adr_get_crossings")
         s = (self.ny, self.nx, 4)
         return seg.reshape(s), t.reshape(s), pos.reshape(s)
+
+    def transfer_table(self, fam):
+        """The direct transfer's crossings of family fam's nodes (adr_get_transfer):
+        seg, t, pos of shape [n_nodes, 2] (before / after the node)."""
+        nn = lib().adr_num_line_nodes(self.h, fam)
+        seg, t, pos = np.zeros(2 * nn, np.int32), np.zeros(2 * nn), np.zeros(2 * nn)
+        _check(lib().adr_get_transfer(self.h, fam, seg.ctypes.data_as(C.POINTER(C.c_int)),
+                                      t.ctypes.data_as(C.POINTER(C.c_double)),
+                                      pos.ctypes.data_as(C.POINTER(C.c_double))),
+               "adr_get_transfer")
+        return seg.reshape(nn, 2), t.reshape(nn, 2), pos.reshape(nn, 2)
 
 
 class Batch:

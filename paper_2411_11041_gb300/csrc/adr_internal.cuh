@@ -83,6 +83,13 @@ struct Family {
     double* ct = nullptr;     // [4*N] position in that segment
     double* cw = nullptr;     // [2*N] weight of the right / upper crossing
     double* cpos = nullptr;   // [4*N] crossing coordinate (inspection only)
+    // direct transfer (opts.transfer = 1): per node of this family, the
+    // nearest crossing with the other family on each side along its curve
+    int* xseg = nullptr;      // [2*n_nodes] crossed segment (-1 the curve's end, -2 an end node)
+    double* xtt = nullptr;    // [2*n_nodes] position in that segment
+    double* xpos = nullptr;   // [2*n_nodes] position along the curve (element units)
+    int* xg = nullptr;        // [2*n_nodes] the two source segments of the node's value
+    double* xc = nullptr;     // [4*n_nodes] their coefficients
 };
 
 // Result of a solve kept on the device: [0] rel update, [1] num, [2] den.
@@ -130,6 +137,11 @@ struct Problem {
     IterState* state = nullptr;
     double* pivmin = nullptr;   // [2] smallest |Thomas pivot| of each family's systems
     double* fextra = nullptr;                       // [N] extra load (parabolic slices)
+    // direct transfer (opts.transfer = 1): the iteration state at the B nodes
+    double* xu[2] = {nullptr, nullptr};  // u_j / u_{j+1} ping-pong at the B nodes
+    double* xuG = nullptr;               // u_{j+1/2} at the G nodes
+    double* xtmp = nullptr;              // B-node work array (midpoint output)
+    bool xu_set = false;                 // xu[0] already holds the initial state
     std::vector<void*> owned;
 };
 
@@ -191,6 +203,7 @@ adr_status dev_alloc(Problem* p, T** ptr, size_t count)
 
 // setup (geometry.cu)
 adr_status build_geometry(Problem* p, const uint8_t* mask);
+adr_status build_transfer(Problem* p);  // crossing tables of the direct transfer
 
 // sweeps (sweep.cu)
 adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off);
@@ -202,6 +215,15 @@ adr_status load_family(Problem* p, const double* fextra, double fx_scale);
 adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_even,
                              const double* u_odd, bool use_state, int paper);
 adr_status launch_mask_copy(Problem* p, const double* in, double* out);
+// direct transfer between the families (sweep.cu)
+adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u_even,
+                                 const double* u_odd, bool use_state);
+adr_status launch_xfer(Problem* p, int to_fam, const double* v, double* out_even, double* out_odd,
+                       int shift, const double* prev_even, const double* prev_odd, bool use_state,
+                       bool norms);
+adr_status launch_gather_nodes(Problem* p, int fam, const double* u, double* out);
+adr_status launch_node_midpoint(Problem* p, const double* u_even, const double* u_odd, const double* vb,
+                                double* out, bool use_state);
 // batches of problems (sweep.cu)
 struct BatchDev;
 adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const double* tols,

@@ -54,7 +54,7 @@ adr_status cuda_fail(cudaError_t e, const char* what)
 // launchers defined in sweep.cu
 adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out_odd,
                               int parity_shift, const double* prev_even, const double* prev_odd,
-                              bool use_state, bool norms);
+                              bool use_state, bool norms, const double* vin = nullptr);
 adr_status launch_check_ex(Problem* p, double tol, int max_iter,
                            cudaGraphConditionalHandle handle, bool use_cond);
 adr_status launch_finish(Problem* p, double* out, double* iter_out, bool midpoint);
@@ -137,12 +137,23 @@ adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
                                                   cudaStreamCaptureModeRelaxed);
     adr_status s = ADR_OK;
     if (e != cudaSuccess) s = cuda_fail(e, "cudaStreamBeginCaptureToGraph");
-    if (s == ADR_OK) s = launch_line_solve(p, 0, dt, p->ubuf[0], p->ubuf[1], true, 0);
-    if (s == ADR_OK)
-        s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, true, false);
-    if (s == ADR_OK) s = launch_line_solve(p, 1, dt, p->ubuf[2], p->ubuf[2], true, 0);
-    if (s == ADR_OK)
-        s = launch_grid_map_ex(p, 1, p->ubuf[0], p->ubuf[1], 1, p->ubuf[0], p->ubuf[1], true, true);
+    if (p->opts.transfer) {
+        // B solve from the state at the B nodes, B -> G nodes, G solve,
+        // G -> B nodes (u_{j+1}) with the norms of the update
+        if (s == ADR_OK) s = launch_line_solve_dir(p, 0, dt, p->xu[0], p->xu[1], true);
+        if (s == ADR_OK)
+            s = launch_xfer(p, 1, p->fam[0].v, p->xuG, p->xuG, 0, nullptr, nullptr, true, false);
+        if (s == ADR_OK) s = launch_line_solve_dir(p, 1, dt, p->xuG, p->xuG, true);
+        if (s == ADR_OK)
+            s = launch_xfer(p, 0, p->fam[1].v, p->xu[0], p->xu[1], 1, p->xu[0], p->xu[1], true, true);
+    } else {
+        if (s == ADR_OK) s = launch_line_solve(p, 0, dt, p->ubuf[0], p->ubuf[1], true, 0);
+        if (s == ADR_OK)
+            s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, true, false);
+        if (s == ADR_OK) s = launch_line_solve(p, 1, dt, p->ubuf[2], p->ubuf[2], true, 0);
+        if (s == ADR_OK)
+            s = launch_grid_map_ex(p, 1, p->ubuf[0], p->ubuf[1], 1, p->ubuf[0], p->ubuf[1], true, true);
+    }
     if (s == ADR_OK) s = launch_check_ex(p, tol, max_iter, cond, true);
     cudaGraph_t out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &out);
@@ -160,7 +171,28 @@ adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
     return ADR_OK;
 }
 
-// Outer iteration from the state in ubuf[0]; results into out / iter_out.
+// Output of the direct-transfer iteration: theta = 1/2 the midpoint
+// (u_j + u_{j+1/2}) / 2 at the B nodes, otherwise the last G curve values,
+// mapped to the grid (iter_out: the G values); no step run: the initial state.
+adr_status finish_direct(Problem* p, int max_iter, double* out, double* iter_out, bool midpoint)
+{
+    if (max_iter <= 0) {
+        TRY(launch_grid_map_ex(p, 0, out, out, 0, nullptr, nullptr, false, false, p->xu[0]));
+        if (iter_out) TRY(launch_grid_map_ex(p, 0, iter_out, iter_out, 0, nullptr, nullptr, false, false, p->xu[0]));
+        return ADR_OK;
+    }
+    if (midpoint) {
+        TRY(launch_node_midpoint(p, p->xu[0], p->xu[1], p->fam[0].v, p->xtmp, true));
+        TRY(launch_grid_map_ex(p, 0, out, out, 0, nullptr, nullptr, false, false, p->xtmp));
+    } else {
+        TRY(launch_grid_map_ex(p, 1, out, out, 0, nullptr, nullptr, false, false));
+    }
+    if (iter_out) TRY(launch_grid_map_ex(p, 1, iter_out, iter_out, 0, nullptr, nullptr, false, false));
+    return ADR_OK;
+}
+
+// Outer iteration from the state in ubuf[0] (the direct transfer: in xu[0]
+// when xu_set, else gathered from ubuf[0]); results into out / iter_out.
 adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
                          const double* fextra, double fx_scale, double tol, int max_iter,
                          bool midpoint, double* out, double* iter_out, adr_stats* stats,
@@ -169,6 +201,11 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
     Problem* p = &h->p;
     TRY(launch_state_reset(p));
     ADR_CUDA_TRY(cudaEventRecord(h->ev0, p->stream));
+    if (p->opts.transfer) {
+        // the initial state at the B nodes (unless the paper's u_0 put it there)
+        if (!p->xu_set) TRY(launch_gather_nodes(p, 0, p->ubuf[0], p->xu[0]));
+        p->xu_set = false;
+    }
     if (max_iter > 0) {
         TRY(prepare_family(p, 0, theta * dt, dt, sig, 0));
         TRY(prepare_family(p, 1, theta * dt, dt, sig, 0));
@@ -179,7 +216,8 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
             TRY(build_graph(h, theta, dt, sig, fextra, fx_scale, tol, max_iter));
         ADR_CUDA_TRY(cudaGraphLaunch(h->exec, p->stream));
     }
-    TRY(launch_finish(p, out, iter_out, midpoint));
+    if (p->opts.transfer) TRY(finish_direct(p, max_iter, out, iter_out, midpoint));
+    else TRY(launch_finish(p, out, iter_out, midpoint));
     ADR_CUDA_TRY(cudaEventRecord(h->ev1, p->stream));
     IterState st;
     double piv[2] = {INFINITY, INFINITY};
@@ -221,6 +259,13 @@ adr_status init_state(adr_problem* h, int init, const double* u_init)
         TRY(prepare_family(p, 0, 1.0, 1.0, p->sigma, 1));
         TRY(load_family(p, nullptr, 0.0));
         TRY(launch_line_solve(p, 0, 1.0, nullptr, nullptr, false, 1));
+        if (p->opts.transfer) {
+            // the B curve solutions are the state at the B nodes as they stand
+            ADR_CUDA_TRY(cudaMemcpyAsync(p->xu[0], p->fam[0].v, sizeof(double) * p->fam[0].n_nodes,
+                                         cudaMemcpyDeviceToDevice, p->stream));
+            p->xu_set = true;
+            return ADR_OK;
+        }
         return launch_grid_map_ex(p, 0, p->ubuf[0], p->ubuf[0], 0, nullptr, nullptr, false, false);
     }
     if (init == ADR_INIT_ZERO) return launch_mask_copy(p, nullptr, p->ubuf[0]);
@@ -280,6 +325,14 @@ adr_status check_opts(const adr_opts* o)
     }
     if (o->init < ADR_INIT_ZERO || o->init > ADR_INIT_LEARNED) {
         set_error("unsupported opts.init");
+        return ADR_EINVAL;
+    }
+    if (o->transfer != 0 && o->transfer != 1) {
+        set_error("opts.transfer must be 0 or 1");
+        return ADR_EINVAL;
+    }
+    if (o->transfer && o->prec != ADR_FP64) {
+        set_error("opts.transfer == 1 needs opts.prec == ADR_FP64");
         return ADR_EINVAL;
     }
     if ((o->rows_per_thread != 0 && o->rows_per_thread != 2 && o->rows_per_thread != 4 &&
@@ -390,6 +443,15 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
         p->map_blocks_per_sm = 8;
         p->n_partial_blocks = grid_map_blocks(p);
         p->map_blocks_per_sm = keep;
+    }
+    if (p->opts.transfer) {
+        if ((s = build_transfer(p)) || (s = dev_alloc(p, &p->xu[0], p->fam[0].n_nodes)) ||
+            (s = dev_alloc(p, &p->xu[1], p->fam[0].n_nodes)) ||
+            (s = dev_alloc(p, &p->xtmp, p->fam[0].n_nodes)) ||
+            (s = dev_alloc(p, &p->xuG, p->fam[1].n_nodes)))
+            return fail(s);
+        if ((e = cudaMemsetAsync(p->xu[0], 0, sizeof(double) * p->fam[0].n_nodes, p->stream)))
+            return fail(cuda_fail(e, "cudaMemsetAsync"));
     }
     if ((s = dev_alloc(p, &p->partial, 2 * (size_t)p->n_partial_blocks)) ||
         (s = dev_alloc(p, &p->state, 1)) || (s = dev_alloc(p, &p->fextra, N)) ||
@@ -530,10 +592,20 @@ adr_status adr_split_step(adr_problem* h, double dt, const double* u, double* u_
     TRY(prepare_family(p, 0, th * dt, dt, p->sigma, 0));
     TRY(prepare_family(p, 1, th * dt, dt, p->sigma, 0));
     TRY(load_family(p, nullptr, 0.0));
-    TRY(launch_line_solve(p, 0, dt, u, u, false, 0));
-    TRY(launch_grid_map_ex(p, 0, half, half, 0, nullptr, nullptr, false, false));
-    TRY(launch_line_solve(p, 1, dt, half, half, false, 0));
-    TRY(launch_grid_map_ex(p, 1, u_next, u_next, 0, nullptr, nullptr, false, false));
+    if (p->opts.transfer) {
+        // u onto the B nodes, B solve, B -> G nodes, G solve; both halves to the grid
+        TRY(launch_gather_nodes(p, 0, u, p->xtmp));
+        TRY(launch_line_solve_dir(p, 0, dt, p->xtmp, p->xtmp, false));
+        TRY(launch_grid_map_ex(p, 0, half, half, 0, nullptr, nullptr, false, false));
+        TRY(launch_xfer(p, 1, p->fam[0].v, p->xuG, p->xuG, 0, nullptr, nullptr, false, false));
+        TRY(launch_line_solve_dir(p, 1, dt, p->xuG, p->xuG, false));
+        TRY(launch_grid_map_ex(p, 1, u_next, u_next, 0, nullptr, nullptr, false, false));
+    } else {
+        TRY(launch_line_solve(p, 0, dt, u, u, false, 0));
+        TRY(launch_grid_map_ex(p, 0, half, half, 0, nullptr, nullptr, false, false));
+        TRY(launch_line_solve(p, 1, dt, half, half, false, 0));
+        TRY(launch_grid_map_ex(p, 1, u_next, u_next, 0, nullptr, nullptr, false, false));
+    }
     ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
     return ADR_OK;
 }
@@ -590,6 +662,24 @@ adr_status adr_get_crossings(const adr_problem* h, int fam, int* seg, double* t,
     if (seg) ADR_CUDA_TRY(cudaMemcpy(seg, F.cg, sizeof(int) * n, cudaMemcpyDeviceToHost));
     if (t) ADR_CUDA_TRY(cudaMemcpy(t, F.ct, sizeof(double) * n, cudaMemcpyDeviceToHost));
     if (pos) ADR_CUDA_TRY(cudaMemcpy(pos, F.cpos, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return ADR_OK;
+}
+
+adr_status adr_get_transfer(const adr_problem* h, int fam, int* seg, double* t, double* pos)
+{
+    if (!h || (fam != 0 && fam != 1)) {
+        set_error("bad handle or family");
+        return ADR_EINVAL;
+    }
+    const Family& F = h->p.fam[fam];
+    if (!h->p.opts.transfer || !F.xseg) {
+        set_error("adr_get_transfer: the handle was created with opts.transfer == 0");
+        return ADR_EINVAL;
+    }
+    size_t n = 2 * (size_t)F.n_nodes;
+    if (seg) ADR_CUDA_TRY(cudaMemcpy(seg, F.xseg, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    if (t) ADR_CUDA_TRY(cudaMemcpy(t, F.xtt, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (pos) ADR_CUDA_TRY(cudaMemcpy(pos, F.xpos, sizeof(double) * n, cudaMemcpyDeviceToHost));
     return ADR_OK;
 }
 
@@ -655,6 +745,24 @@ adr_status adr_time_kernels(adr_problem* h, int reps, double* ms_out)
     for (int stage = 0; stage < 4 && s == ADR_OK; ++stage) {
         cudaEventRecord(ev[stage], p->stream);
         for (int r = 0; r < reps && s == ADR_OK; ++r) {
+            if (o.transfer) {
+                // B solve, B -> G transfer, G solve, G -> B transfer with norms
+                switch (stage) {
+                case 0:
+                    s = launch_line_solve_dir(p, 0, dt, p->xu[0], p->xu[0], false);
+                    break;
+                case 1:
+                    s = launch_xfer(p, 1, p->fam[0].v, p->xuG, p->xuG, 0, nullptr, nullptr, false, false);
+                    break;
+                case 2:
+                    s = launch_line_solve_dir(p, 1, dt, p->xuG, p->xuG, false);
+                    break;
+                default:
+                    s = launch_xfer(p, 0, p->fam[1].v, p->xu[1], p->xu[1], 0, p->xu[0], p->xu[0], false,
+                                    true);
+                }
+                continue;
+            }
             switch (stage) {
             case 0:
                 s = launch_line_solve(p, 0, dt, p->ubuf[0], p->ubuf[0], false, 0);
@@ -752,11 +860,16 @@ adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_
         return ADR_EINVAL;
     }
     *out = nullptr;
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
         if (!probs[i] || probs[i]->p.opts.prec != probs[0]->p.opts.prec) {
             set_error("adr_batch_create: NULL handle or mixed precision modes");
             return ADR_EINVAL;
         }
+        if (probs[i]->p.opts.transfer) {
+            set_error("adr_batch_create: problems with opts.transfer == 1 are solved one by one");
+            return ADR_EINVAL;
+        }
+    }
     adr_batch* b = new (std::nothrow) adr_batch;
     if (!b) {
         set_error("out of host memory");

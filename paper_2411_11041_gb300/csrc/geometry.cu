@@ -1317,6 +1317,231 @@ __global__ void k_reverse_hist(const int* hist, long long* rev, int maxlen)
 
 // setup temporaries: stream-ordered from the library's pool, freed in stream
 // order when the guard goes out of scope
+// ------------------------------------ direct transfer between the families
+// The crossings of every target curve (family tf) with the polylines of the
+// source family (1 - tf), for carrying values between the families without
+// the grid (the improvement the paper's conclusions propose).  Source segments
+// are listed per grid cell (every cell their bounding box covers).  One thread
+// per target element tests every segment listed in the cells its bounding box
+// covers and takes a crossing in the cell that holds it, so that each counts
+// once.  Each element keeps its crossings of smallest and largest position
+// along the curve and the smallest ones on its two end nodes; every target
+// node then takes its nearest crossing on each side, as a search over all
+// crossings of its curve would.
+
+__device__ __forceinline__ int cell_clamp(double v, int n)
+{
+    int c = (int)floor(v);
+    return c < 0 ? 0 : (c > n - 1 ? n - 1 : c);
+}
+
+// source segments per grid cell: counts
+__global__ void k_xseg_count(int n_nodes, const int* lon, const double* xs, const double* es, int ncx,
+                             int ncy, long long* cnt)
+{
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi + 1 >= n_nodes || lon[gi] != lon[gi + 1]) return;
+    const int i0 = cell_clamp(fmin(xs[gi], xs[gi + 1]), ncx), i1 = cell_clamp(fmax(xs[gi], xs[gi + 1]), ncx);
+    const int r0 = cell_clamp(fmin(es[gi], es[gi + 1]), ncy), r1 = cell_clamp(fmax(es[gi], es[gi + 1]), ncy);
+    for (int r = r0; r <= r1; ++r)
+        for (int i = i0; i <= i1; ++i)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[(size_t)r * ncx + i]), 1ull);
+}
+
+// source segments per grid cell: the lists (order within a cell does not
+// matter: the choices below are keyed)
+__global__ void k_xseg_fill(int n_nodes, const int* lon, const double* xs, const double* es, int ncx,
+                            int ncy, long long* cursor, int* list)
+{
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi + 1 >= n_nodes || lon[gi] != lon[gi + 1]) return;
+    const int i0 = cell_clamp(fmin(xs[gi], xs[gi + 1]), ncx), i1 = cell_clamp(fmax(xs[gi], xs[gi + 1]), ncx);
+    const int r0 = cell_clamp(fmin(es[gi], es[gi + 1]), ncy), r1 = cell_clamp(fmax(es[gi], es[gi + 1]), ncy);
+    for (int r = r0; r <= r1; ++r)
+        for (int i = i0; i <= i1; ++i) {
+            long long q = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[(size_t)r * ncx + i]), 1ull);
+            list[q] = gi;
+        }
+}
+
+// per target element: crossings of smallest / largest position (ties: smaller
+// source segment, then smaller t), and the smallest ones exactly on its first
+// and last node
+struct XSlots {
+    double* mnpos;
+    int* mng;
+    double* mnt;
+    double* mxpos;
+    int* mxg;
+    double* mxt;
+    int* stg;  // on the element's first node (-1: none)
+    double* stt;
+    int* eng;  // on its last node
+    double* ent;
+};
+
+__device__ __forceinline__ bool key_lt(double pa, int ga, double ta, double pb, int gb, double tb, bool max)
+{
+    if (pa != pb) return max ? pa > pb : pa < pb;
+    if (ga != gb) return ga < gb;
+    return ta < tb;
+}
+
+// crossing of A-B and C-D (index coordinates): A + a (B - A) = C + b (D - C)
+// with 0 <= a, b <= 1 (parallel segments give none)
+__device__ __forceinline__ bool seg_cross(double ax, double ay, double bx, double by, double cx, double cy,
+                                          double dx, double dy, double* a, double* b)
+{
+    const double ex = bx - ax, ey = by - ay, fx = dx - cx, fy = dy - cy;
+    const double det = ex * fy - ey * fx;
+    if (det == 0.0) return false;
+    const double gx = cx - ax, gy = cy - ay;
+    const double aa = (gx * fy - gy * fx) / det;
+    const double bb = (gx * ey - gy * ex) / det;
+    if (!(aa >= 0.0 && aa <= 1.0 && bb >= 0.0 && bb <= 1.0)) return false;
+    *a = aa;
+    *b = bb;
+    return true;
+}
+
+__global__ void k_xquery(int nt, const int* lont, const int* offt, const double* xt, const double* et,
+                         const double* xs, const double* es, int ncx, int ncy, const long long* start,
+                         const int* list, XSlots S)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e + 1 >= nt || lont[e] != lont[e + 1]) return;
+    const int el = e - offt[lont[e]];  // element index along its curve
+    const double ax = xt[e], ay = et[e], bx = xt[e + 1], by = et[e + 1];
+    double mnp = 0, mnt_ = 0, mxp = 0, mxt_ = 0, stt_ = 0, ent_ = 0;
+    int mng_ = -1, mxg_ = -1, stg_ = -1, eng_ = -1;
+    const int i0 = cell_clamp(fmin(ax, bx), ncx), i1 = cell_clamp(fmax(ax, bx), ncx);
+    const int r0 = cell_clamp(fmin(ay, by), ncy), r1 = cell_clamp(fmax(ay, by), ncy);
+    for (int r = r0; r <= r1; ++r)
+        for (int i = i0; i <= i1; ++i) {
+            const size_t c = (size_t)r * ncx + i;
+            for (long long q = start[c]; q < start[c + 1]; ++q) {
+                const int sg = list[q];
+                double a, b;
+                if (!seg_cross(ax, ay, bx, by, xs[sg], es[sg], xs[sg + 1], es[sg + 1], &a, &b)) continue;
+                const double px = ax + a * (bx - ax), py = ay + a * (by - ay);
+                if (cell_clamp(px, ncx) != i || cell_clamp(py, ncy) != r) continue;  // counted in its own cell
+                const double pos = el + a;
+                if (mng_ < 0 || key_lt(pos, sg, b, mnp, mng_, mnt_, false)) {
+                    mnp = pos;
+                    mng_ = sg;
+                    mnt_ = b;
+                }
+                if (mxg_ < 0 || key_lt(pos, sg, b, mxp, mxg_, mxt_, true)) {
+                    mxp = pos;
+                    mxg_ = sg;
+                    mxt_ = b;
+                }
+                if (pos == (double)el && (stg_ < 0 || sg < stg_ || (sg == stg_ && b < stt_))) {
+                    stg_ = sg;
+                    stt_ = b;
+                }
+                if (pos == (double)(el + 1) && (eng_ < 0 || sg < eng_ || (sg == eng_ && b < ent_))) {
+                    eng_ = sg;
+                    ent_ = b;
+                }
+            }
+        }
+    S.mnpos[e] = mnp;
+    S.mng[e] = mng_;
+    S.mnt[e] = mnt_;
+    S.mxpos[e] = mxp;
+    S.mxg[e] = mxg_;
+    S.mxt[e] = mxt_;
+    S.stg[e] = stg_;
+    S.stt[e] = stt_;
+    S.eng[e] = eng_;
+    S.ent[e] = ent_;
+}
+
+// the crossings held by element e of a curve whose first node is base and
+// which has n elements, as the oracle's per-element record: its own, the
+// crossing on node e found by element e - 1, the one on node e + 1 found by
+// element e + 1; the one of smallest (max = false) or largest key
+__device__ __forceinline__ bool xslot_pick(const XSlots& S, int base, int n, int e, bool max, double* pos,
+                                           int* sg, double* t)
+{
+    bool ok = false;
+    const int ge = base + e;
+    if (S.mng[ge] >= 0) {
+        ok = true;
+        *pos = max ? S.mxpos[ge] : S.mnpos[ge];
+        *sg = max ? S.mxg[ge] : S.mng[ge];
+        *t = max ? S.mxt[ge] : S.mnt[ge];
+    }
+    if (e >= 1 && S.eng[ge - 1] >= 0) {  // on node e, from element e - 1
+        const double p = (double)e;
+        if (!ok || key_lt(p, S.eng[ge - 1], S.ent[ge - 1], *pos, *sg, *t, max)) {
+            ok = true;
+            *pos = p;
+            *sg = S.eng[ge - 1];
+            *t = S.ent[ge - 1];
+        }
+    }
+    if (e + 1 < n && S.stg[ge + 1] >= 0) {  // on node e + 1, from element e + 1
+        const double p = (double)(e + 1);
+        if (!ok || key_lt(p, S.stg[ge + 1], S.stt[ge + 1], *pos, *sg, *t, max)) {
+            ok = true;
+            *pos = p;
+            *sg = S.stg[ge + 1];
+            *t = S.stt[ge + 1];
+        }
+    }
+    return ok;
+}
+
+// per target node: the nearest crossing on each side along its curve (the
+// curve's end, value 0, where a side has none) and the 4 coefficients of the
+// transfer: value = c0 v[g0] + c1 v[g0 + 1] + c2 v[g1] + c3 v[g1 + 1]
+__global__ void k_xnodes(int nt, const int* lont, const int* offt, XSlots S, int* xseg, double* xtt,
+                         double* xpos, int* xg, double* xc)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const int l = lont[k], base = offt[l], n = offt[l + 1] - 1 - base, kk = k - base;
+    if (kk == 0 || kk == n || n < 2) {  // end node: u = 0
+        for (int q = 0; q < 2; ++q) {
+            xseg[2 * k + q] = -2;
+            xtt[2 * k + q] = 0.0;
+            xpos[2 * k + q] = 0.0;
+            xg[2 * k + q] = 0;
+        }
+        for (int q = 0; q < 4; ++q) xc[4 * k + q] = 0.0;
+        return;
+    }
+    double pl = 0.0, tl = 0.0, pr = (double)n, tr = 0.0;
+    int gl = -1, gr = -1;
+    for (int e = kk - 1; e >= 0; --e)
+        if (xslot_pick(S, base, n, e, true, &pl, &gl, &tl)) break;
+    for (int e = kk; e < n; ++e)
+        if (xslot_pick(S, base, n, e, false, &pr, &gr, &tr)) break;
+    if (gl < 0) {
+        pl = 0.0;
+        tl = 0.0;
+    }
+    if (gr < 0) {
+        pr = (double)n;
+        tr = 0.0;
+    }
+    xseg[2 * k] = gl;
+    xtt[2 * k] = tl;
+    xpos[2 * k] = pl;
+    xseg[2 * k + 1] = gr;
+    xtt[2 * k + 1] = tr;
+    xpos[2 * k + 1] = pr;
+    const double w = (pr == pl) ? 0.0 : ((double)kk - pl) / (pr - pl);
+    xg[2 * k] = gl >= 0 ? gl : 0;
+    xg[2 * k + 1] = gr >= 0 ? gr : 0;
+    xc[4 * k] = gl >= 0 ? (1.0 - w) * (1.0 - tl) : 0.0;
+    xc[4 * k + 1] = gl >= 0 ? (1.0 - w) * tl : 0.0;
+    xc[4 * k + 2] = gr >= 0 ? w * (1.0 - tr) : 0.0;
+    xc[4 * k + 3] = gr >= 0 ? w * tr : 0.0;
+}
+
 struct TmpGuard {
     std::vector<void*> v;
     cudaStream_t st = nullptr;
@@ -1613,6 +1838,68 @@ adr_status build_curved_both(Problem* p, int* status_d, TmpGuard& tg)
 }
 
 }  // namespace
+
+// crossing tables of the direct transfer, both directions (opts.transfer = 1)
+adr_status build_transfer(Problem* p)
+{
+    cudaStream_t st = p->stream;
+    TmpGuard tg;
+    tg.st = st;
+    const int ncx = p->grid.nx - 1, ncy = p->grid.ny - 1;
+    const size_t ncell = (size_t)ncx * ncy;
+    int* lon[2];
+    for (int f = 0; f < 2; ++f) {
+        Family& F = p->fam[f];
+        int* maxlen;
+        TRY(alloc_tmp(tg, &lon[f], F.n_nodes + 1));
+        TRY(alloc_tmp(tg, &maxlen, 1));
+        ADR_CUDA_TRY(cudaMemsetAsync(maxlen, 0, sizeof(int), st));
+        k_line_of_node<<<blocks_for(F.n_lines), kThreads, 0, st>>>(F.n_lines, F.off, lon[f], maxlen);
+    }
+    for (int tf = 0; tf < 2; ++tf) {
+        Family& T = p->fam[tf];
+        const Family& S = p->fam[1 - tf];
+        long long *cnt, *start;
+        TRY(alloc_tmp(tg, &cnt, ncell + 1));
+        TRY(alloc_tmp(tg, &start, ncell + 1));
+        ADR_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(long long) * (ncell + 1), st));
+        k_xseg_count<<<blocks_for(S.n_nodes), kThreads, 0, st>>>(S.n_nodes, lon[1 - tf], S.xi, S.eta, ncx,
+                                                               ncy, cnt);
+        k_scan<<<1, 1024, 0, st>>>(cnt, start, (long long)ncell);
+        long long total = 0;
+        ADR_CUDA_TRY(cudaMemcpyAsync(&total, start + ncell, sizeof total, cudaMemcpyDeviceToHost, st));
+        ADR_CUDA_TRY(cudaStreamSynchronize(st));
+        int* list;
+        TRY(alloc_tmp(tg, &list, (size_t)total + 1));
+        ADR_CUDA_TRY(cudaMemcpyAsync(cnt, start, sizeof(long long) * ncell, cudaMemcpyDeviceToDevice, st));
+        k_xseg_fill<<<blocks_for(S.n_nodes), kThreads, 0, st>>>(S.n_nodes, lon[1 - tf], S.xi, S.eta, ncx, ncy,
+                                                              cnt, list);
+        XSlots X;
+        const size_t nt = (size_t)T.n_nodes + 1;
+        TRY(alloc_tmp(tg, &X.mnpos, nt));
+        TRY(alloc_tmp(tg, &X.mng, nt));
+        TRY(alloc_tmp(tg, &X.mnt, nt));
+        TRY(alloc_tmp(tg, &X.mxpos, nt));
+        TRY(alloc_tmp(tg, &X.mxg, nt));
+        TRY(alloc_tmp(tg, &X.mxt, nt));
+        TRY(alloc_tmp(tg, &X.stg, nt));
+        TRY(alloc_tmp(tg, &X.stt, nt));
+        TRY(alloc_tmp(tg, &X.eng, nt));
+        TRY(alloc_tmp(tg, &X.ent, nt));
+        k_xquery<<<blocks_for(T.n_nodes), kThreads, 0, st>>>(T.n_nodes, lon[tf], T.off, T.xi, T.eta, S.xi,
+                                                           S.eta, ncx, ncy, start, list, X);
+        TRY(dev_alloc(p, &T.xseg, 2 * nt));
+        TRY(dev_alloc(p, &T.xtt, 2 * nt));
+        TRY(dev_alloc(p, &T.xpos, 2 * nt));
+        TRY(dev_alloc(p, &T.xg, 2 * nt));
+        TRY(dev_alloc(p, &T.xc, 4 * nt));
+        k_xnodes<<<blocks_for(T.n_nodes), kThreads, 0, st>>>(T.n_nodes, lon[tf], T.off, X, T.xseg, T.xtt,
+                                                           T.xpos, T.xg, T.xc);
+        ADR_CUDA_TRY(cudaGetLastError());
+        ADR_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return ADR_OK;
+}
 
 adr_status build_geometry(Problem* p, const uint8_t* mask)
 {

@@ -516,7 +516,7 @@ __device__ __forceinline__ float as_f32(E x)
 // form, the correction x in precision E and v = u + dt x accumulated in FP64
 // (u is parked in v between the passes).  The rows' rp values live in
 // shared memory [R][BS] between the passes.
-template <int BS, int FAM, bool RES, typename E>
+template <int BS, int FAM, bool RES, typename E, bool DIR = false>
 __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, const int* curves,
                                                  const E* __restrict__ Lc, const E* __restrict__ fac,
                                                  unsigned char* smem)
@@ -538,7 +538,40 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
     const int so = (int)b.so;
     const bool paper = a.paper != 0;
     E rpp = E(0);
-    if (cnt > 0) {
+    // right-hand side (FP64) of row j from u at its node and the two
+    // neighbours, and the row's downward elimination step
+    auto row = [&](int j, int sl, double kap, double u0, double u1, double u2) {
+        double r;
+        if (FAM == 0) {
+            r = __ldg(a.Fl + sl);
+            if (!paper) {
+                r = fma(__ldg(a.srow + sl), u0, r);
+                r = fma(__ldg(a.srow + NS + sl), u1, r);
+                r = fma(__ldg(a.srow + 2 * NS + sl), u2, r);
+            }
+        } else {
+            r = __ldg(a.srow + sl) * fma(kap, u1, u0 + u2);
+        }
+        E re;
+        if constexpr (sizeof(E) == 4) re = f64_to_f32(r);
+        else re = r;
+        rpp = mad(-__ldg(fac + 3 * NS + sl), rpp, re);
+        rp(j) = rpp;
+    };
+    if constexpr (DIR) {
+        // the state given at the curve's nodes (the direct transfer; 0 at both ends)
+        if (cnt > 0) {
+            const double kap = (FAM == 1) ? __ldg(a.kap + b.line) : 0.0;
+            const double* __restrict__ un = u + base + s;
+            double u0 = paper ? 0.0 : __ldg(un), u1 = paper ? 0.0 : __ldg(un + 1);
+            for (int j = 0; j < cnt; ++j) {
+                const double u2 = paper ? 0.0 : __ldg(un + j + 2);
+                row(j, so + j * T + lt, kap, u0, u1, u2);
+                u0 = u1;
+                u1 = u2;
+            }
+        }
+    } else if (cnt > 0) {
         const double kap = (FAM == 1) ? __ldg(a.kap + b.line) : 0.0;
         auto uslot = [&](int sl) -> double { return gather_w(u, a.nx, __ldg(a.gcell + sl), a.gw, NS, sl); };
         double u0 = 0.0, u1 = 0.0;
@@ -579,22 +612,7 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
             if constexpr (RES) {
                 if (!paper) v[base + s + j + 1] = u1;
             }
-            double r;
-            if (FAM == 0) {
-                r = __ldg(a.Fl + sl);
-                if (!paper) {
-                    r = fma(__ldg(a.srow + sl), u0, r);
-                    r = fma(__ldg(a.srow + NS + sl), u1, r);
-                    r = fma(__ldg(a.srow + 2 * NS + sl), u2, r);
-                }
-            } else {
-                r = __ldg(a.srow + sl) * fma(kap, u1, u0 + u2);
-            }
-            E re;
-            if constexpr (sizeof(E) == 4) re = f64_to_f32(r);
-            else re = r;
-            rpp = mad(-__ldg(fac + 3 * NS + sl), rpp, re);
-            rp(j) = rpp;
+            row(j, sl, kap, u0, u1, u2);
             u0 = u1;
             u1 = u2;
         }
@@ -725,6 +743,18 @@ struct ActiveLists {
 };
 constexpr int kCountPerBuf = 7;
 
+// FP64 curve solve of the direct transfer: the state at the curve's nodes
+template <int BS, int FAM>
+__global__ void __launch_bounds__(BS, BS == 256 ? 4 : (BS == 512 ? 2 : 1)) k_curve_solve_dir(CurveArgs a, const int* item_T,
+                                                    const int* item_curve, const double* lanec)
+{
+    if (a.state && a.state->done) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t lo = (size_t)blockIdx.x * Items<BS>::NF * BS;
+    curve_solve_body<BS, FAM, false, double, true>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
+                                                   lanec + lo, a.fac, smem);
+}
+
 template <int BS, int FAM, bool REF>
 __global__ void __launch_bounds__(BS) k_curve_solve_batch(const CurveArgs* __restrict__ table,
                                                           const BatchItem* __restrict__ items,
@@ -761,6 +791,111 @@ struct GridArgs {
     int parity_shift;  // output buffer = parity(iter + shift)
     double* partial;   // [2 * gridDim.x] sums of (u - u_prev)^2 and u^2
 };
+
+// block sum of (dd, uu) into dst[0..1]
+__device__ __forceinline__ void block_sum2(double dd, double uu, double* dst)
+{
+    __shared__ double sd[kGridThreads / 32], su[kGridThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        dd += __shfl_down_sync(0xffffffffu, dd, o);
+        uu += __shfl_down_sync(0xffffffffu, uu, o);
+    }
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sd[w] = dd;
+        su[w] = uu;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double td = 0, tu = 0;
+        for (int q = 0; q < kGridThreads / 32; ++q) {
+            td += sd[q];
+            tu += su[q];
+        }
+        dst[0] = td;
+        dst[1] = tu;
+    }
+}
+
+// ---------------------------------------------- direct transfer (per step)
+// values at the nodes of the target family from the source family's curve
+// values through the crossing tables: value = c0 v[g0] + c1 v[g0 + 1] +
+// c2 v[g1] + c3 v[g1 + 1] (end nodes have zero coefficients); with NORMS the
+// partial sums of |u - u_prev|^2 and |u|^2 for the convergence test
+struct XferArgs {
+    long long n;              // target nodes
+    const int* xg;            // [2 n]
+    const double* xc;         // [4 n]
+    const double* v;          // source curve values
+    double* out_even;         // output by parity of (iter + parity_shift)
+    double* out_odd;
+    const double* prev_even;  // previous state by parity of iter (NORMS)
+    const double* prev_odd;
+    const IterState* state;
+    int parity_shift;
+    double* partial;
+};
+
+template <bool NORMS>
+__global__ void __launch_bounds__(kGridThreads) k_curve_xfer(XferArgs a)
+{
+    if (a.state && a.state->done) return;
+    const int it = a.state ? a.state->iter : 0;
+    double* __restrict__ out = ((it + a.parity_shift) & 1) ? a.out_odd : a.out_even;
+    const double* __restrict__ prev = (it & 1) ? a.prev_odd : a.prev_even;
+    const double* __restrict__ v = a.v;
+    double dd = 0.0, uu = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < a.n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int2 g = *reinterpret_cast<const int2*>(a.xg + 2 * k);
+        const double2 c0 = *reinterpret_cast<const double2*>(a.xc + 4 * k);
+        const double2 c1 = *reinterpret_cast<const double2*>(a.xc + 4 * k + 2);
+        double val = c0.x * __ldg(v + g.x);
+        val = fma(c0.y, __ldg(v + g.x + 1), val);
+        val = fma(c1.x, __ldg(v + g.y), val);
+        val = fma(c1.y, __ldg(v + g.y + 1), val);
+        out[k] = val;
+        if (NORMS) {
+            const double dl = val - prev[k];
+            dd = fma(dl, dl, dd);
+            uu = fma(val, val, uu);
+        }
+    }
+    if (NORMS) block_sum2(dd, uu, a.partial + 2 * blockIdx.x);
+}
+
+// the grid state at every node of a family (bilinear, §6.1), 0 at both ends
+// of every curve: one warp per curve
+__global__ void k_gather_nodes(int nx, int ny, int n_lines, const int* off, const double* xi,
+                               const double* eta, const double* u, double* out)
+{
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (l >= n_lines) return;
+    const int a0 = off[l], a1 = off[l + 1] - 1;
+    for (int k = a0 + lane; k <= a1; k += 32) {
+        if (k == a0 || k == a1) {
+            out[k] = 0.0;
+            continue;
+        }
+        const double x = xi[k], y = eta[k];
+        int i = (int)floor(x), r = (int)floor(y);
+        i = i > nx - 2 ? nx - 2 : (i < 0 ? 0 : i);
+        r = r > ny - 2 ? ny - 2 : (r < 0 ? 0 : r);
+        out[k] = gather_at(u, nx, r * nx + i, x - i, y - r);
+    }
+}
+
+// midpoint (u_j + u_{j+1/2}) / 2 at the B nodes, u_j the state the last step
+// started from (by its parity)
+__global__ void k_node_midpoint(const IterState* st, const double* u_even, const double* u_odd,
+                                const double* vb, double* out, long long n)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int it = st ? st->iter : 1;
+    const double* uj = ((it - 1) & 1) ? u_odd : u_even;
+    out[k] = 0.5 * (uj[k] + vb[k]);
+}
 
 // combined weights of the curve -> grid map (setup): the row value
 // (1-w) vL + w vR and the column value, each crossing v = (1-t) v[g] + t v[g+1],
@@ -824,31 +959,6 @@ __device__ __forceinline__ void grid_map_body(const GridArgs& a, long long first
             }
         }
         out[k] = val;
-    }
-}
-
-// block sum of (dd, uu) into dst[0..1]
-__device__ __forceinline__ void block_sum2(double dd, double uu, double* dst)
-{
-    __shared__ double sd[kGridThreads / 32], su[kGridThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) {
-        dd += __shfl_down_sync(0xffffffffu, dd, o);
-        uu += __shfl_down_sync(0xffffffffu, uu, o);
-    }
-    int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        sd[w] = dd;
-        su[w] = uu;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double td = 0, tu = 0;
-        for (int q = 0; q < kGridThreads / 32; ++q) {
-            td += sd[q];
-            tu += su[q];
-        }
-        dst[0] = td;
-        dst[1] = tu;
     }
 }
 
@@ -1322,6 +1432,9 @@ static cudaError_t solve_attr()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_curve_solve_batch<BS, FAM, REF>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && !REF)
+        e = cudaFuncSetAttribute(k_curve_solve_dir<BS, FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
     return e;
 }
 
@@ -1380,6 +1493,84 @@ adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_eve
     return ADR_OK;
 }
 
+// the curve solve of the direct transfer: u_even / u_odd are node arrays of
+// the family (selected by the step's parity when use_state)
+adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u_even,
+                                 const double* u_odd, bool use_state)
+{
+    Family& F = p->fam[fam];
+    if (!F.prep_valid || F.prep_paper || F.prep_dt != dt || p->opts.prec != ADR_FP64) {
+        set_error("internal: curve systems not factored for this step");
+        return ADR_EINVAL;
+    }
+    TRY_S(ensure_solve_attrs());
+    CurveArgs a = curve_args(p, fam);
+    a.u_even = u_even;
+    a.u_odd = u_odd;
+    a.state = use_state ? p->state : nullptr;
+    const int R = F.cmax;
+    cudaStream_t st = p->stream;
+#define ADR_SOLVE_DIR(BS_, I_)                                                                     \
+    if (I_.count) {                                                                                \
+        const size_t sm = solve_smem<BS_>(R);                                                      \
+        if (fam == 0) k_curve_solve_dir<BS_, 0><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec); \
+        else k_curve_solve_dir<BS_, 1><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec);         \
+    }
+    ADR_SOLVE_DIR(1024, F.iset[2])
+    ADR_SOLVE_DIR(512, F.iset[1])
+    ADR_SOLVE_DIR(256, F.iset[0])
+#undef ADR_SOLVE_DIR
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+// direct transfer into the nodes of family to_fam from values v of the other
+// family; out by the parity of (iter + shift) when use_state; with norms,
+// against prev (by parity) into the problem's partial sums
+adr_status launch_xfer(Problem* p, int to_fam, const double* v, double* out_even, double* out_odd,
+                       int shift, const double* prev_even, const double* prev_odd, bool use_state,
+                       bool norms)
+{
+    const Family& T = p->fam[to_fam];
+    XferArgs a;
+    a.n = T.n_nodes;
+    a.xg = T.xg;
+    a.xc = T.xc;
+    a.v = v;
+    a.out_even = out_even;
+    a.out_odd = out_odd;
+    a.prev_even = prev_even;
+    a.prev_odd = prev_odd;
+    a.state = use_state ? p->state : nullptr;
+    a.parity_shift = shift;
+    a.partial = p->partial;
+    const int blocks = grid_map_blocks(p);  // the check kernel reads this many partial sums
+    if (norms) k_curve_xfer<true><<<blocks, kGridThreads, 0, p->stream>>>(a);
+    else k_curve_xfer<false><<<blocks, kGridThreads, 0, p->stream>>>(a);
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+adr_status launch_gather_nodes(Problem* p, int fam, const double* u, double* out)
+{
+    const Family& F = p->fam[fam];
+    const int blocks = (int)(((long long)F.n_lines * 32 + 255) / 256);
+    k_gather_nodes<<<blocks > 0 ? blocks : 1, 256, 0, p->stream>>>(p->grid.nx, p->grid.ny, F.n_lines, F.off,
+                                                                  F.xi, F.eta, u, out);
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+adr_status launch_node_midpoint(Problem* p, const double* u_even, const double* u_odd, const double* vb,
+                                double* out, bool use_state)
+{
+    const long long n = p->fam[0].n_nodes;
+    k_node_midpoint<<<(int)((n + 255) / 256), 256, 0, p->stream>>>(use_state ? p->state : nullptr, u_even,
+                                                                   u_odd, vb, out, n);
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
 adr_status launch_map_coef(Problem* p, int fam)
 {
     Family& F = p->fam[fam];
@@ -1392,7 +1583,7 @@ adr_status launch_map_coef(Problem* p, int fam)
 
 adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out_odd,
                               int parity_shift, const double* prev_even, const double* prev_odd,
-                              bool use_state, bool norms)
+                              bool use_state, bool norms, const double* vin)
 {
     Family& F = p->fam[fam];
     GridArgs a;
@@ -1401,7 +1592,7 @@ adr_status launch_grid_map_ex(Problem* p, int fam, double* out_even, double* out
     a.ntype = p->ntype;
     a.mg = F.mg;
     a.mc = F.mc;
-    a.v = F.v;
+    a.v = vin ? vin : F.v;
     a.out_even = out_even;
     a.out_odd = out_odd;
     a.prev_even = prev_even;

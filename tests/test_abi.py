@@ -62,6 +62,15 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(libadr):
     st = P.lib().adr_create(ctypes.byref(g), dummy, 1.0, 1.0, dummy, dummy, dummy, ctypes.byref(o),
                             None, ctypes.byref(h))
     assert st == P.ADR_EINVAL and b"theta" in P.lib().adr_last_error()
+    o.theta = 0.5
+    o.transfer = 2
+    st = P.lib().adr_create(ctypes.byref(g), dummy, 1.0, 1.0, dummy, dummy, dummy, ctypes.byref(o),
+                            None, ctypes.byref(h))
+    assert st == P.ADR_EINVAL and b"transfer" in P.lib().adr_last_error()
+    o.transfer, o.prec = 1, P.ADR_FP32_REFINE  # the direct transfer runs in FP64 only
+    st = P.lib().adr_create(ctypes.byref(g), dummy, 1.0, 1.0, dummy, dummy, dummy, ctypes.byref(o),
+                            None, ctypes.byref(h))
+    assert st == P.ADR_EINVAL and b"transfer" in P.lib().adr_last_error()
 
 
 def test_network_parameter_layout_without_gpu(libadr):
