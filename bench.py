@@ -10,6 +10,8 @@ One step = one such solve.  value = line unknowns solved per second (both curve
 families, every split step) over the timed steps; ms_per_step = time to 1e-8.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32]
+  python bench.py --transfer direct    # values between the curve families through
+                                       # their crossings instead of the grid
   python bench.py --impl reference     # the FP64 CPU oracle on the same workload
 
 With N > 1 (torchrun) every rank solves its own copy of the problem (the
@@ -54,10 +56,23 @@ KERNELS = ["curve solve B", "curve->grid map B", "curve solve G", "curve->grid m
 #         (+ 1 add and 2 fma for the norms)
 BYTES_PER_UNIT = [108.0, 81.0, 84.0, 89.0]
 FLOPS_PER_UNIT = [21.0, 16.0, 19.0, 21.0]
+# The same for the direct curve-to-curve transfer (--transfer direct), whose
+# curve solves read the state at their own nodes and whose transfers replace
+# the maps (unit = one target curve node):
+#   curve solve B: load row 8 + rhs rows 24 + factors 24 + v 8 + u 8 B; rhs 6 +
+#                  elimination 2 + upward 2 + back 4 flop
+#   curve solve G: rhs coefficient 8 + factors 24 + v 8 + u 8 B; rhs 4 + 2 + 2 + 4 flop
+#   transfers: two segment indices 8 + four coefficients 32 + source value 8 + out 8
+#              (+ previous state 8 for the norms) B; 1 mul + 3 fma (+ 1 add, 2 fma) flop
+KERNELS_DIRECT = ["curve solve B (node state)", "transfer B->G", "curve solve G (node state)",
+                  "transfer G->B + norms"]
+BYTES_PER_UNIT_DIRECT = [72.0, 56.0, 48.0, 64.0]
+FLOPS_PER_UNIT_DIRECT = [14.0, 7.0, 12.0, 12.0]
 # DRAM bytes per launch (read + write) of each kernel in the bench's launch
 # shape, from one ncu capture of the 2048^2 sheared workload; None where the
 # kernel has changed since the capture
 NCU_TRAFFIC_SHEARED2048 = [535.5e6, 399.0e6, 442.6e6, 435.3e6]
+NCU_TRAFFIC_DIRECT_SHEARED2048 = [351.2e6, 235.3e6, 263.1e6, 258.9e6]
 
 
 def parse():
@@ -73,6 +88,11 @@ def parse():
     ap.add_argument("--stabilize", type=int, default=0, choices=[0, 1],
                     help="1: SUPG on the B curves (FP64 only)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--transfer", default="grid", choices=["grid", "direct"],
+                    help="values between the curve families through the grid (the paper's "
+                         "section 6) or directly through the curves' crossings")
+    ap.add_argument("--no-direct", action="store_true",
+                    help="skip the direct-transfer solve of the same workload in the default line")
     ap.add_argument("--no-oracle", action="store_true",
                     help="skip the oracle's converged solve (the err_vs_oracle figures)")
     ap.add_argument("--other-prec", action=argparse.BooleanOptionalAction, default=True)
@@ -206,14 +226,14 @@ def job_rate(ws, ms, units, device):
 
 # ------------------------------------------------------------- oracle legs
 
-def _oracle_converged(n, tol, path):
+def _oracle_converged(n, tol, path, transfer=0):
     """Child process: the oracle's converged stationary solve of the n^2
     sheared workload from u = 0 (the same Δt and tol as the GPU), saved as
     path (.npy) with its step count beside it (.json)."""
     from oracle import oracle as O
     from paper_2411_11041_gb300 import workloads as W
     t0 = time.perf_counter()
-    o = O.Oracle(W.sheared(n=n))
+    o = O.Oracle(W.sheared(n=n), transfer=transfer)
     out, _, it, rel, st = o.solve_stationary(tol=tol, max_iter=200000)
     np.save(path, out)
     with open(path + ".json", "w") as fh:
@@ -224,12 +244,12 @@ class OracleJob:
     """The oracle's converged solve in a spawned process (one host core), so
     that every result of the run can be compared with it."""
 
-    def __init__(self, n, tol):
+    def __init__(self, n, tol, transfer=0):
         import multiprocessing as mp
         fd, self.path = tempfile.mkstemp(suffix=".npy")
         os.close(fd)
         self.proc = mp.get_context("spawn").Process(target=_oracle_converged,
-                                                    args=(n, tol, self.path), daemon=True)
+                                                    args=(n, tol, self.path, transfer), daemon=True)
         self.proc.start()
 
     def result(self, timeout_s):
@@ -256,13 +276,13 @@ def rel_err(u_gpu, u_ref):
     return float(np.abs(u_gpu - u_ref).max() / max(np.abs(u_ref).max(), 1e-300))
 
 
-def oracle_sample(n, budget_s=12.0, min_steps=1):
+def oracle_sample(n, budget_s=12.0, min_steps=1, transfer=0):
     """Time split steps of the FP64 CPU oracle on the same workload (setup
     excluded) for about budget_s seconds.  Returns (line-DOF/s, steps, secs)."""
     from oracle import oracle as O
     from paper_2411_11041_gb300 import workloads as W
     prob = W.sheared(n=n)
-    o = O.Oracle(prob)
+    o = O.Oracle(prob, transfer=transfer)
     unknowns = 0
     for fam in (0, 1):
         off = o.lines(fam)["off"]
@@ -285,7 +305,7 @@ def run_reference(args):
     from oracle import oracle as O
     from paper_2411_11041_gb300 import workloads as W
     prob = W.sheared(n=args.n)
-    o = O.Oracle(prob)
+    o = O.Oracle(prob, transfer=int(args.transfer == "direct"))
     unknowns = 0
     for fam in (0, 1):
         off = o.lines(fam)["off"]
@@ -307,6 +327,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": f"sheared{args.n}", "nodes": args.n * args.n,
+                                        "transfer": args.transfer,
                                         "step": "one split step (oracle sample)"},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -322,13 +343,18 @@ def run_ours(args):
     from paper_2411_11041_gb300 import ADR_FP32_REFINE, ADR_FP64, Solver
     from paper_2411_11041_gb300 import workloads as W
     ws, rank, local = dist_setup(args)
-    job = OracleJob(args.n, args.tol) if rank == 0 and not args.no_oracle else None
+    direct = args.transfer == "direct"
+    job = OracleJob(args.n, args.tol, int(direct)) if rank == 0 and not args.no_oracle else None
+    # the same workload with the direct transfer, reported beside the main line
+    also_direct = not direct and not args.no_direct and ws == 1 and args.prec == "fp64" \
+        and not args.stabilize
+    djob = OracleJob(args.n, args.tol, 1) if also_direct and not args.no_oracle else None
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
     prob = W.sheared(n=args.n)
     solver = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec,
-                    stabilize=args.stabilize)
+                    stabilize=args.stabilize, transfer=int(direct))
     tuned = solver.autotune(10)  # launch shapes by measurement (adr_autotune), before timing
     unknowns = solver.line_unknowns()
     stream = torch.cuda.current_stream(dev)
@@ -355,18 +381,22 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     ms_max, dofs_all, value = job_rate(ws, ms, dofs, dev)
     # per-kernel device time in the solve's launch configuration (CUDA events)
-    roof = kernel_roofline(solver, prob, unknowns)
-    k = KERNELS.index(roof["kernel"])
-    units = [unknowns[0], prob.nx * prob.ny, unknowns[1], prob.nx * prob.ny]
-    if args.n == 2048 and prec == ADR_FP64 and NCU_TRAFFIC_SHEARED2048[k] is not None:
-        roof["traffic"] = NCU_TRAFFIC_SHEARED2048[k]
+    roof = kernel_roofline(solver, prob, unknowns, direct)
+    names = KERNELS_DIRECT if direct else KERNELS
+    traffic = NCU_TRAFFIC_DIRECT_SHEARED2048 if direct else NCU_TRAFFIC_SHEARED2048
+    k = names.index(roof["kernel"])
+    if args.n == 2048 and prec == ADR_FP64 and traffic[k] is not None:
+        roof["traffic"] = traffic[k]
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture"
-        roof["algorithmic_bytes"] = BYTES_PER_UNIT[k] * units[k]
-    launches = int(sum(5 * it + 3 for it in iters))
-    # the other precision mode on the same workload: time to tol and agreement
+        roof["algorithmic_bytes"] = roof["algorithmic_bytes_per_launch"]
+    # per split step: B solve, B map / transfer, G solve, G map / transfer, check;
+    # per solve: state reset, output (and the initial gather / midpoint of the direct transfer)
+    launches = int(sum(5 * it + (5 if direct else 3) for it in iters))
+    # the other precision mode on the same workload (the direct transfer: the
+    # transfer through the grid instead): time to tol and agreement
     other = {}
     if args.other_prec and not args.stabilize:  # FP32+refine has no SUPG forms
-        oprec = ADR_FP32_REFINE if prec == ADR_FP64 else ADR_FP64
+        oprec = ADR_FP32_REFINE if prec == ADR_FP64 and not direct else ADR_FP64
         s2 = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=oprec)
         s2.solve_stationary()
         torch.cuda.synchronize(dev)
@@ -383,6 +413,7 @@ def run_ours(args):
         diff = float((u2 - u).abs().max() / u.abs().max())
         u_other = u2.cpu().numpy()
         other = {"prec": "fp32+refine" if oprec == ADR_FP32_REFINE else "fp64",
+                 "transfer": "grid",
                  "ms_per_step": ms2 / reps, "value": d2 / (ms2 / 1e3), "iters_per_solve": it2,
                  "kernels_ms": dict(zip(KERNELS, s2.time_kernels(reps=20))),
                  "max_rel_diff_vs_this_mode": diff}
@@ -394,7 +425,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": f"sheared{args.n}", "nodes": prob.nx * prob.ny,
                    "mu": prob.mu, "sigma": prob.sigma, "tol": args.tol, "prec": args.prec,
-                   "stabilize": args.stabilize,
+                   "stabilize": args.stabilize, "transfer": args.transfer,
                    "line_unknowns_per_step": unknowns, "iters_per_solve": iters,
                    "step": "one stationary solve to tol from u=0",
                    "l2": "working set > 129 MB L2 (curve data and maps ~1 GB)",
@@ -405,10 +436,12 @@ def run_ours(args):
     }
     if other:
         line["other_precision"] = other
+    if also_direct:
+        line["direct_transfer"] = direct_leg(args, prob, dev, stream)
     if not args.no_e2e:
         line["e2e"] = e2e(args, prob, dev, prec)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, nst, secs, unk = oracle_sample(args.n)
+        v, nst, secs, unk = oracle_sample(args.n, transfer=int(direct))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{nst} split steps of the {args.n}^2 sheared problem "
                                           f"({secs:.1f} s, setup excluded), single thread"}
@@ -421,15 +454,60 @@ def run_ours(args):
             ev = {"measure": "max |u - u_oracle| / max |u_oracle| over the grid",
                   "oracle_iters": info["iters"], "oracle_secs": info["secs"],
                   args.prec: rel_err(u.cpu().numpy(), ref)}
-            if other:
+            if other and not direct:
                 ev["fp32+refine" if other["prec"] == "fp32+refine" else "fp64"] = rel_err(u_other, ref)
             ev["tolerance"] = {"fp64": 1e-12, "fp32+refine": 1e-5}
             line["err_vs_oracle"] = ev
+    if djob is not None and "direct_transfer" in line:
+        dl = line["direct_transfer"]
+        ref, info = djob.result(timeout_s=600)
+        if ref is None:
+            dl["err_vs_oracle"] = {"value": None, "why": info}
+        else:
+            dl["err_vs_oracle"] = {"fp64": rel_err(dl.pop("_u"), ref), "oracle_iters": info["iters"],
+                                   "oracle_secs": info["secs"], "tolerance": 1e-12,
+                                   "oracle": "the oracle's converged solve with the direct transfer"}
+    if "direct_transfer" in line:
+        line["direct_transfer"].pop("_u", None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def direct_leg(args, prob, dev, stream, reps=3):
+    """The same stationary solve with the direct curve-to-curve transfer
+    (opts.transfer = 1, FP64): time to tol, iterations, per-kernel roofline."""
+    import torch
+
+    from paper_2411_11041_gb300 import Solver
+    s = Solver(prob, device=dev, tol=args.tol, max_iter=200000, transfer=1)
+    tuned = s.autotune(10)
+    s.solve_stationary()
+    torch.cuda.synchronize(dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    its, dofs = [], 0.0
+    for _ in range(reps):
+        u, _, st, _ = s.solve_stationary()
+        its.append(st["iters"])
+        dofs += st["line_dofs"]
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = f0.elapsed_time(f1)
+    unknowns = s.line_unknowns()
+    roof = kernel_roofline(s, prob, unknowns, True)
+    k = KERNELS_DIRECT.index(roof["kernel"])
+    if args.n == 2048 and NCU_TRAFFIC_DIRECT_SHEARED2048[k] is not None:
+        roof["traffic"] = NCU_TRAFFIC_DIRECT_SHEARED2048[k]
+        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture"
+    out = {"transfer": "direct", "ms_per_step": ms / reps, "value": dofs / (ms / 1e3), "unit": UNIT,
+           "iters_per_solve": its,
+           "launch_shape": {"rows_per_thread": tuned[0], "tuned_ms_per_split_step": tuned[2]},
+           "roofline": roof, "_u": u.cpu().numpy()}
+    s.close()
+    return out
 
 
 def e2e(args, prob, dev, prec):
@@ -453,7 +531,8 @@ def e2e(args, prob, dev, prec):
         q.mu, q.sigma = prob.mu, prob.sigma
         for k, t in pin.items():
             setattr(q, k, t.to(dev, non_blocking=True))
-        s = Solver(q, device=dev, tol=args.tol, max_iter=200000, prec=prec)
+        s = Solver(q, device=dev, tol=args.tol, max_iter=200000, prec=prec,
+                   transfer=int(args.transfer == "direct"))
         u, _, st, _ = s.solve_stationary()
         host_out.copy_(u)
         s.close()
@@ -736,20 +815,35 @@ def run_data2d(args):
     print(json.dumps(line), flush=True)
 
 
-def kernel_roofline(solver, prob, unknowns):
+def kernel_units(solver, prob, unknowns, direct=False):
+    """Units one launch of each sweep kernel processes (curve unknowns for the
+    solves; grid nodes for the maps; target curve nodes for the transfers)."""
+    if direct:
+        nodes = [int(solver.lines(f)["off"][-1]) for f in (0, 1)]
+        return [unknowns[0], nodes[1], unknowns[1], nodes[0]]
+    return [unknowns[0], prob.nx * prob.ny, unknowns[1], prob.nx * prob.ny]
+
+
+def kernel_roofline(solver, prob, unknowns, direct=False):
     """Dominant sweep kernel of a solver, timed with CUDA events in the
     solve's launch configuration (adr_time_kernels): the roofline object."""
     kms = solver.time_kernels(reps=20)
-    units = [unknowns[0], prob.nx * prob.ny, unknowns[1], prob.nx * prob.ny]
+    units = kernel_units(solver, prob, unknowns, direct)
+    names = KERNELS_DIRECT if direct else KERNELS
+    bpu = BYTES_PER_UNIT_DIRECT if direct else BYTES_PER_UNIT
+    fpu = FLOPS_PER_UNIT_DIRECT if direct else FLOPS_PER_UNIT
     k = int(np.argmax(kms))
     hbm, hbm_kind = peaks()
-    gbs = BYTES_PER_UNIT[k] * units[k] / (kms[k] * 1e-3) / 1e9
-    tflops = FLOPS_PER_UNIT[k] * units[k] / (kms[k] * 1e-3) / 1e12
+    gbs = bpu[k] * units[k] / (kms[k] * 1e-3) / 1e9
+    tflops = fpu[k] * units[k] / (kms[k] * 1e-3) / 1e12
     return {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
             "peak_kind": "FP64 FMA issue peak derived from 152 SMs x 2 FMA/clk x 2.07 GHz",
-            "hbm_frac": gbs / hbm, "kernel": KERNELS[k], "kernel_ms": kms[k],
-            "units_per_launch": units[k], "all_kernels_ms": dict(zip(KERNELS, kms))}
+            "hbm_frac": gbs / hbm, "kernel": names[k], "kernel_ms": kms[k],
+            "units_per_launch": units[k], "algorithmic_bytes_per_launch": bpu[k] * units[k],
+            "all_kernels_ms": dict(zip(names, kms)),
+            "all_kernels_hbm_frac": {nm: bpu[i] * units[i] / (kms[i] * 1e-3) / 1e9 / hbm
+                                     for i, nm in enumerate(names)}}
 
 
 def run_parabolic(args):
@@ -896,11 +990,16 @@ def run_kernels(args):
     from paper_2411_11041_gb300 import workloads as W
     prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
     prob = W.sheared(n=args.n)
-    s = Solver(prob, device=torch.device("cuda:0"), tol=args.tol, prec=prec)
+    direct = args.transfer == "direct"
+    s = Solver(prob, device=torch.device("cuda:0"), tol=args.tol, prec=prec, transfer=int(direct))
     kms = s.time_kernels(reps=args.steps)
     torch.cuda.synchronize()
-    print(json.dumps({"workload": f"sheared{args.n}", "prec": args.prec, "launches_per_kernel": args.steps,
-                      "kernels_ms": dict(zip(KERNELS, kms)), "line_unknowns": s.line_unknowns()}),
+    unknowns = s.line_unknowns()
+    print(json.dumps({"workload": f"sheared{args.n}", "prec": args.prec, "transfer": args.transfer,
+                      "launches_per_kernel": args.steps,
+                      "kernels_ms": dict(zip(KERNELS_DIRECT if direct else KERNELS, kms)),
+                      "units_per_launch": kernel_units(s, prob, unknowns, direct),
+                      "line_unknowns": unknowns}),
           flush=True)
 
 

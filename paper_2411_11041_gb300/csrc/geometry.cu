@@ -391,6 +391,32 @@ __global__ void k_scan(const long long* in, long long* out, long long n)
     if (threadIdx.x == 0) out[n] = carry;
 }
 
+// exclusive scan of many counts: every block scans 1024 of them and records
+// its total, one block scans the totals (k_scan), and the block offsets are
+// added back
+__global__ void k_scan_blocks(const long long* in, long long* out, long long n, long long* bsum)
+{
+    __shared__ long long buf[1024];
+    const long long i = blockIdx.x * 1024LL + threadIdx.x;
+    const long long v = i < n ? in[i] : 0;
+    buf[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 1; s < 1024; s <<= 1) {
+        long long add = threadIdx.x >= s ? buf[threadIdx.x - s] : 0;
+        __syncthreads();
+        buf[threadIdx.x] += add;
+        __syncthreads();
+    }
+    if (i < n) out[i] = buf[threadIdx.x] - v;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = buf[1023];
+}
+
+__global__ void k_scan_add(long long* out, long long n, const long long* boff)
+{
+    const long long i = blockIdx.x * 1024LL + threadIdx.x;
+    if (i < n) out[i] += boff[blockIdx.x];
+}
+
 // ---------------------------------------------------- traced curve families
 // Seeds on the inflow part of the boundary (eq. cauchyStartSets): the staircase
 // boundary is walked loop by loop counter-clockwise (domain on the left), each
@@ -1865,7 +1891,17 @@ adr_status build_transfer(Problem* p)
         ADR_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(long long) * (ncell + 1), st));
         k_xseg_count<<<blocks_for(S.n_nodes), kThreads, 0, st>>>(S.n_nodes, lon[1 - tf], S.xi, S.eta, ncx,
                                                                ncy, cnt);
-        k_scan<<<1, 1024, 0, st>>>(cnt, start, (long long)ncell);
+        {
+            const long long nb = ((long long)ncell + 1023) / 1024;
+            long long *bsum, *boff;
+            TRY(alloc_tmp(tg, &bsum, (size_t)nb + 1));
+            TRY(alloc_tmp(tg, &boff, (size_t)nb + 1));
+            k_scan_blocks<<<(unsigned)nb, 1024, 0, st>>>(cnt, start, (long long)ncell, bsum);
+            k_scan<<<1, 1024, 0, st>>>(bsum, boff, nb);
+            k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(start, (long long)ncell, boff);
+            ADR_CUDA_TRY(cudaMemcpyAsync(start + ncell, boff + nb, sizeof(long long), cudaMemcpyDeviceToDevice,
+                                         st));
+        }
         long long total = 0;
         ADR_CUDA_TRY(cudaMemcpyAsync(&total, start + ncell, sizeof total, cudaMemcpyDeviceToHost, st));
         ADR_CUDA_TRY(cudaStreamSynchronize(st));
