@@ -69,6 +69,7 @@ struct orc_problem {
     int interp_weights; /* 0: plain average of the row and column values; 1: inverse-gap weights */
     int stabilize;      /* 0: Galerkin on the B lines (the paper); 1: SUPG on the B lines */
     int transfer;       /* 0: values between the families through the grid (§6); 1: directly */
+    int anderson;       /* 0: plain stationary iteration; m >= 1: Anderson extrapolation, depth m */
     family fam[2];
 };
 
@@ -1408,6 +1409,164 @@ static void direct_step(const orc_problem* p, double theta, double dt, double si
     for (int k = 0; k < G->n_nodes; ++k) vG[k] = uG[k] + dt * d[k];
 }
 
+/* ------------------------------------- accelerated stationary iteration
+ * The multi-parameter pseudo-steps the method's stationary iteration invites
+ * (a cycle of Δt values, as in cyclic ADI) do not keep its fixed point: the
+ * split step's fixed point depends on Δt (only its midpoint does not, and only
+ * for aligned flow), so a cycle converges to another state.  Reading: the
+ * parameters vary per step as Anderson extrapolation weights instead.  With
+ * g_k = Φ(u_k) the split step's output and f_k = g_k - u_k, the next state is
+ * u_{k+1} = g_k - Σ_i γ_i (g_{k-i+1} - g_{k-i}), i = 1..min(m, k), where γ
+ * minimises |f_k - Σ_i γ_i (f_{k-i+1} - f_{k-i})|.  Any γ leaves the fixed
+ * points of Φ in place (f = 0 there gives γ = 0).  γ comes from the normal
+ * equations A γ = b, A_ij = <Δf_i, Δf_j>, b_i = <Δf_i, f_k>, both formed from
+ * the raw products <f_a, f_b> of the last m + 1 residuals, by Cholesky with
+ * the columns newest first; a column whose pivot falls to 1e-12 of its
+ * diagonal entry (or below) ends the factorisation, and only the columns
+ * before it are used. */
+
+#define AA_MAX 8
+
+typedef struct {
+    int m;
+    size_t L;
+    double* f;                          /* [(m+1) L] residuals by slot k mod (m+1) */
+    double* g;                          /* [(m+1) L] map outputs by slot */
+    double R[AA_MAX + 1][AA_MAX + 1];   /* <f_a, f_b> by slot */
+} aa_state;
+
+static int aa_init(aa_state* s, int m, size_t L)
+{
+    memset(s, 0, sizeof *s);
+    s->m = m;
+    s->L = L;
+    s->f = calloc((size_t)(m + 1) * L, sizeof(double));
+    s->g = calloc((size_t)(m + 1) * L, sizeof(double));
+    return (s->f && s->g) ? 0 : -1;
+}
+
+static void aa_free(aa_state* s)
+{
+    free(s->f);
+    free(s->g);
+}
+
+/* the mixing weights c_0..c_m of u_{k+1} = Σ_j c_j g_{k-j} from the raw
+ * products of step k (mk = min(m, k) difference columns) */
+static void aa_weights(const aa_state* s, int k, int mk, double* c)
+{
+    const int ns = s->m + 1;
+#define AA_R(a, b) (s->R[(a) % ns][(b) % ns])
+    double A[AA_MAX][AA_MAX], b[AA_MAX], Lc[AA_MAX][AA_MAX], y[AA_MAX], gam[AA_MAX];
+    for (int i = 1; i <= mk; ++i) {
+        int ai = k - i + 1, bi = k - i;
+        b[i - 1] = AA_R(ai, k) - AA_R(bi, k);
+        for (int j = 1; j <= i; ++j) {
+            int aj = k - j + 1, bj = k - j;
+            A[i - 1][j - 1] = AA_R(ai, aj) - AA_R(ai, bj) - AA_R(bi, aj) + AA_R(bi, bj);
+        }
+    }
+#undef AA_R
+    int use = mk;
+    for (int i = 0; i < mk; ++i) {
+        double d = A[i][i];
+        for (int q = 0; q < i; ++q) d -= Lc[i][q] * Lc[i][q];
+        if (!(A[i][i] > 0.0) || !(d > 1e-12 * A[i][i])) {
+            use = i;
+            break;
+        }
+        Lc[i][i] = sqrt(d);
+        for (int j = i + 1; j < mk; ++j) {
+            double e = A[j][i];
+            for (int q = 0; q < i; ++q) e -= Lc[j][q] * Lc[i][q];
+            Lc[j][i] = e / Lc[i][i];
+        }
+    }
+    for (int i = 0; i < use; ++i) {
+        double e = b[i];
+        for (int q = 0; q < i; ++q) e -= Lc[i][q] * y[q];
+        y[i] = e / Lc[i][i];
+    }
+    for (int i = use - 1; i >= 0; --i) {
+        double e = y[i];
+        for (int q = i + 1; q < use; ++q) e -= Lc[q][i] * gam[q];
+        gam[i] = e / Lc[i][i];
+    }
+    for (int j = 0; j <= s->m; ++j) c[j] = 0.0;
+    c[0] = 1.0;
+    for (int i = 1; i <= use; ++i) {
+        c[i - 1] -= gam[i - 1];
+        c[i] += gam[i - 1];
+    }
+}
+
+/* step k: records f_k = g - u and g_k, then u_next = the extrapolated state */
+static void aa_next(aa_state* s, int k, const double* u, const double* g, double* u_next)
+{
+    const int ns = s->m + 1, sl = k % ns, mk = k < s->m ? k : s->m;
+    double* fk = s->f + (size_t)sl * s->L;
+    double* gk = s->g + (size_t)sl * s->L;
+    for (size_t q = 0; q < s->L; ++q) {
+        fk[q] = g[q] - u[q];
+        gk[q] = g[q];
+    }
+    for (int j = 0; j <= mk; ++j) {
+        const double* fj = s->f + (size_t)((k - j) % ns) * s->L;
+        double acc = 0.0;
+        for (size_t q = 0; q < s->L; ++q) acc += fk[q] * fj[q];
+        s->R[sl][(k - j) % ns] = acc;
+        s->R[(k - j) % ns][sl] = acc;
+    }
+    double c[AA_MAX + 1];
+    aa_weights(s, k, mk, c);
+    for (size_t q = 0; q < s->L; ++q) {
+        double v = 0.0;
+        for (int j = 0; j <= mk; ++j) v += c[j] * s->g[(size_t)((k - j) % ns) * s->L + q];
+        u_next[q] = v;
+    }
+}
+
+int orc_set_anderson(orc_problem* p, int m)
+{
+    if (m < 0 || m > AA_MAX) return ORC_EINVAL;
+    p->anderson = m;
+    return ORC_OK;
+}
+
+int orc_anderson_linear(int n, int m, const double* T, const double* c, double* x, int max_iter,
+                        double tol, double* res)
+{
+    if (n < 1 || m < 0 || m > AA_MAX) return -1;
+    aa_state s;
+    double* g = malloc(sizeof(double) * n);
+    if (!g || aa_init(&s, m, (size_t)n)) {
+        free(g);
+        return -1;
+    }
+    int k = 0;
+    for (; k < max_iter; ++k) {
+        double num = 0.0, den = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double v = c[i];
+            for (int j = 0; j < n; ++j) v += T[(size_t)i * n + j] * x[j];
+            g[i] = v;
+            num += (v - x[i]) * (v - x[i]);
+            den += v * v;
+        }
+        double rel = den > 0.0 ? sqrt(num / den) : 0.0;
+        if (res) res[k] = rel;
+        if (rel <= tol) {
+            ++k;
+            break;
+        }
+        if (m == 0) memcpy(x, g, sizeof(double) * n);
+        else aa_next(&s, k, x, g, x);
+    }
+    aa_free(&s);
+    free(g);
+    return k;
+}
+
 /* Stationary iteration with the direct transfer: the state lives on the B
  * nodes (u_j there), each step is direct_step followed by the transfer of the
  * G curve values back to the B nodes (u_{j+1}); the relative update is taken
@@ -1417,7 +1576,7 @@ static void direct_step(const orc_problem* p, double theta, double dt, double si
 static int solve_direct(const orc_problem* p, double theta, double dt, double tol, int max_iter,
                         int init, const double* u_init, double sig, const double* f_extra,
                         double fx_scale, double* u_out, double* u_iter_out, int* iters,
-                        double* rel_out)
+                        double* rel_out, int accel)
 {
     const family *B = &p->fam[0], *G = &p->fam[1];
     size_t N = (size_t)p->nx * p->ny, nb = (size_t)B->n_nodes + 1, ng = (size_t)G->n_nodes + 1;
@@ -1425,7 +1584,10 @@ static int solve_direct(const orc_problem* p, double theta, double dt, double to
            *uBn = calloc(nb, sizeof(double)), *uG = calloc(ng, sizeof(double)),
            *vG = calloc(ng, sizeof(double)), *d = calloc(nb > ng ? nb : ng, sizeof(double)),
            *tmp = calloc(N, sizeof(double));
-    if (!uB || !vB || !uBn || !uG || !vG || !d || !tmp) return ORC_ENOMEM;
+    aa_state aa;
+    const int m = accel ? p->anderson : 0;
+    if (!uB || !vB || !uBn || !uG || !vG || !d || !tmp || aa_init(&aa, m, nb))
+        return ORC_ENOMEM;
     if (dt <= 0.0) dt = orc_default_dt(p, sig);
     if (init == 1 && u_init) {
         for (size_t k = 0; k < N; ++k) tmp[k] = p->ntype[k] == ORC_INTERIOR ? u_init[k] : 0.0;
@@ -1452,7 +1614,10 @@ static int solve_direct(const orc_problem* p, double theta, double dt, double to
             break;
         }
         if (!isfinite(rel)) break; /* diverged */
-        if (j + 1 < max_iter) memcpy(uB, uBn, sizeof(double) * nb);
+        if (j + 1 < max_iter) {
+            if (m) aa_next(&aa, j, uB, uBn, uB);
+            else memcpy(uB, uBn, sizeof(double) * nb);
+        }
     }
     int done = (j < max_iter) ? j + 1 : max_iter;
     if (tol <= 0.0 && isfinite(rel)) status = ORC_OK;
@@ -1477,6 +1642,7 @@ static int solve_direct(const orc_problem* p, double theta, double dt, double to
     free(vG);
     free(d);
     free(tmp);
+    aa_free(&aa);
     return status;
 }
 
@@ -1563,12 +1729,13 @@ int orc_solve_stationary(const orc_problem* p, double theta, double dt, double t
 {
     if (p->transfer)
         return solve_direct(p, theta, dt, tol, max_iter, init, u_init, sig, f_extra, fx_scale, u_out,
-                            u_iter_out, iters, rel_out);
+                            u_iter_out, iters, rel_out, 1);
     size_t N = (size_t)p->nx * p->ny;
     double* u = calloc(N, sizeof(double));
     double* uh = calloc(N, sizeof(double));
     double* un = calloc(N, sizeof(double));
-    if (!u || !uh || !un) return ORC_ENOMEM;
+    aa_state aa;
+    if (!u || !uh || !un || aa_init(&aa, p->anderson, N)) return ORC_ENOMEM;
     if (dt <= 0.0) dt = orc_default_dt(p, sig);
     if (init == 1 && u_init)
         for (size_t k = 0; k < N; ++k) u[k] = p->ntype[k] == ORC_INTERIOR ? u_init[k] : 0.0;
@@ -1584,7 +1751,10 @@ int orc_solve_stationary(const orc_problem* p, double theta, double dt, double t
             break;
         }
         if (!isfinite(rel)) break; /* diverged */
-        if (j + 1 < max_iter) memcpy(u, un, N * sizeof(double));
+        if (j + 1 < max_iter) {
+            if (p->anderson) aa_next(&aa, j, u, un, u);
+            else memcpy(u, un, N * sizeof(double));
+        }
     }
     int done = (j < max_iter) ? j + 1 : max_iter;
     if (tol <= 0.0 && isfinite(rel)) status = ORC_OK; /* a fixed number of steps was asked for */
@@ -1597,13 +1767,16 @@ int orc_solve_stationary(const orc_problem* p, double theta, double dt, double t
     free(u);
     free(uh);
     free(un);
+    aa_free(&aa);
     return status;
 }
 
 /* Parabolic1 (§2).  mode 0: the paper's scheme, one split step per time step
  * (eq. SemiDiscrSplit with the physical dt and theta).  mode 1: implicit Euler
  * in time, each slice -mu Lap u + beta.grad u + (sigma + 1/dt) u = f + u_n/dt
- * solved by the stationary iteration (theta, pseudo_dt, tol, max_iter). */
+ * solved by the stationary iteration (theta, pseudo_dt, tol, max_iter).  The
+ * Anderson extrapolation, when set, applies to the slices' solves of mode 1,
+ * never to the time steps of mode 0. */
 int orc_step_parabolic(const orc_problem* p, double dt, int nsteps, int mode,
                        double theta, double pseudo_dt, double tol, int max_iter,
                        double* u, int* total_iters)
@@ -1619,7 +1792,8 @@ int orc_step_parabolic(const orc_problem* p, double dt, int nsteps, int mode,
         if (mode == 0 && p->transfer) {
             /* with the direct transfer the state stays on the B nodes: the
                time steps are the iteration's steps from the gathered u */
-            int r = solve_direct(p, theta, dt, -1.0, nsteps, 1, u, p->sigma, NULL, 0.0, a, b, NULL, NULL);
+            int r = solve_direct(p, theta, dt, -1.0, nsteps, 1, u, p->sigma, NULL, 0.0, a, b, NULL, NULL,
+                                 0);
             if (r != ORC_OK) st = r;
             memcpy(u, b, N * sizeof(double));
             tot += nsteps;

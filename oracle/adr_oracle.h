@@ -54,6 +54,17 @@ double orc_sweep_line_values(const orc_problem* p, int fam, double theta, double
                              const double* u_vals, double sig, const double* f_extra,
                              double fx_scale, double* d);
 
+/* acceleration of the stationary iteration: 0 = none (default), 1..8 = the
+   depth m of Anderson extrapolation over the last m steps.  Returns ORC_OK /
+   ORC_EINVAL. */
+int orc_set_anderson(orc_problem* p, int m);
+/* the same extrapolation on a linear fixed-point map g(x) = T x + c of size n
+   (T row-major n*n): iterates from x (overwritten) until |g(x) - x| / |g(x)|
+   <= tol or max_iter maps; returns the number of maps applied, res[k] the
+   relative update at map k */
+int orc_anderson_linear(int n, int m, const double* T, const double* c, double* x, int max_iter,
+                        double tol, double* res);
+
 /* geometry queries */
 int orc_const_beta(const orc_problem* p);
 void orc_node_types(const orc_problem* p, unsigned char* out /* [ny*nx] */);

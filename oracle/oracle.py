@@ -82,6 +82,8 @@ def lib():
         L.orc_sweep_line_values.argtypes = [vp, C.c_int, C.c_double, C.c_double, dp, C.c_double,
                                             vp, C.c_double, dp]
         L.orc_sweep_line_values.restype = C.c_double
+        L.orc_set_anderson.argtypes = [vp, C.c_int]
+        L.orc_anderson_linear.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_double, dp]
         L.orc_step_parabolic.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.c_double,
                                          C.c_double, C.c_double, C.c_int, dp,
                                          C.POINTER(C.c_int)]
@@ -129,7 +131,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """One problem in the oracle.  Mirrors the library's handle."""
 
-    def __init__(self, prob, interp_weights=0, stabilize=0, transfer=0):
+    def __init__(self, prob, interp_weights=0, stabilize=0, transfer=0, anderson=0):
         self.prob = prob
         self.nx, self.ny = prob.nx, prob.ny
         self.mask = _c(prob.mask, np.uint8)
@@ -149,6 +151,10 @@ class Oracle:
             st = lib().orc_set_transfer(h, int(transfer))
             if st != OK:
                 raise OracleError(st, "orc_set_transfer")
+        if anderson:
+            st = lib().orc_set_anderson(h, int(anderson))
+            if st != OK:
+                raise OracleError(st, "orc_set_anderson")
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -268,6 +274,16 @@ class Oracle:
         st = lib().orc_step_parabolic(self.h, dt, nsteps, mode, theta, pseudo_dt, tol, max_iter,
                                       u, C.byref(tot))
         return u, tot.value, st
+
+
+def anderson_linear(T, c, x0, m, max_iter=200, tol=1e-13):
+    """The oracle's Anderson extrapolation (depth m) on g(x) = T x + c from x0.
+    Returns (x, number of maps applied, relative updates per map)."""
+    n = len(c)
+    x = _c(x0).copy()
+    res = np.zeros(max_iter)
+    k = lib().orc_anderson_linear(n, int(m), _c(T), _c(c), x, int(max_iter), float(tol), res)
+    return x, k, res[:max(k, 0)]
 
 
 def thomas(a, b, c, r):
