@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--stabilize", type=int, default=0, choices=[0, 1],
                     help="1: SUPG on the B curves (FP64 only)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--anderson", type=int, default=0,
+                    help="Anderson extrapolation depth of the stationary iteration (0 = none)")
     ap.add_argument("--transfer", default="grid", choices=["grid", "direct"],
                     help="values between the curve families through the grid (the paper's "
                          "section 6) or directly through the curves' crossings")
@@ -98,7 +100,7 @@ def parse():
     ap.add_argument("--other-prec", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--workload", default="sheared",
                     choices=["sheared", "batch", "learned", "data2d", "parabolic", "manufactured",
-                             "kernels"])
+                             "kernels", "anderson"])
     ap.add_argument("--time-steps", type=int, default=200, help="parabolic workload: time steps")
     ap.add_argument("--count", type=int, default=256)
     # learned warm start: training set, held-out set, Adam steps, minibatch
@@ -226,14 +228,14 @@ def job_rate(ws, ms, units, device):
 
 # ------------------------------------------------------------- oracle legs
 
-def _oracle_converged(n, tol, path, transfer=0):
+def _oracle_converged(n, tol, path, transfer=0, anderson=0):
     """Child process: the oracle's converged stationary solve of the n^2
     sheared workload from u = 0 (the same Δt and tol as the GPU), saved as
     path (.npy) with its step count beside it (.json)."""
     from oracle import oracle as O
     from paper_2411_11041_gb300 import workloads as W
     t0 = time.perf_counter()
-    o = O.Oracle(W.sheared(n=n), transfer=transfer)
+    o = O.Oracle(W.sheared(n=n), transfer=transfer, anderson=anderson)
     out, _, it, rel, st = o.solve_stationary(tol=tol, max_iter=200000)
     np.save(path, out)
     with open(path + ".json", "w") as fh:
@@ -244,12 +246,13 @@ class OracleJob:
     """The oracle's converged solve in a spawned process (one host core), so
     that every result of the run can be compared with it."""
 
-    def __init__(self, n, tol, transfer=0):
+    def __init__(self, n, tol, transfer=0, anderson=0):
         import multiprocessing as mp
         fd, self.path = tempfile.mkstemp(suffix=".npy")
         os.close(fd)
         self.proc = mp.get_context("spawn").Process(target=_oracle_converged,
-                                                    args=(n, tol, self.path, transfer), daemon=True)
+                                                    args=(n, tol, self.path, transfer, anderson),
+                                                    daemon=True)
         self.proc.start()
 
     def result(self, timeout_s):
@@ -344,17 +347,21 @@ def run_ours(args):
     from paper_2411_11041_gb300 import workloads as W
     ws, rank, local = dist_setup(args)
     direct = args.transfer == "direct"
-    job = OracleJob(args.n, args.tol, int(direct)) if rank == 0 and not args.no_oracle else None
-    # the same workload with the direct transfer, reported beside the main line
-    also_direct = not direct and not args.no_direct and ws == 1 and args.prec == "fp64" \
-        and not args.stabilize
-    djob = OracleJob(args.n, args.tol, 1) if also_direct and not args.no_oracle else None
+    job = OracleJob(args.n, args.tol, int(direct), args.anderson) \
+        if rank == 0 and not args.no_oracle else None
+    # the same workload with the direct transfer and with the accelerated
+    # iteration, reported beside the main line (each against its own oracle solve)
+    also = not direct and not args.no_direct and ws == 1 and args.prec == "fp64" \
+        and not args.stabilize and not args.anderson
+    variants = [("direct_transfer", 1, 0)] if also else []
+    vjobs = {name: OracleJob(args.n, args.tol, tr, m) for name, tr, m in variants} \
+        if not args.no_oracle else {}
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
     prob = W.sheared(n=args.n)
     solver = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec,
-                    stabilize=args.stabilize, transfer=int(direct))
+                    stabilize=args.stabilize, transfer=int(direct), anderson=args.anderson)
     tuned = solver.autotune(10)  # launch shapes by measurement (adr_autotune), before timing
     unknowns = solver.line_unknowns()
     stream = torch.cuda.current_stream(dev)
@@ -391,11 +398,12 @@ def run_ours(args):
         roof["algorithmic_bytes"] = roof["algorithmic_bytes_per_launch"]
     # per split step: B solve, B map / transfer, G solve, G map / transfer, check;
     # per solve: state reset, output (and the initial gather / midpoint of the direct transfer)
-    launches = int(sum(5 * it + (5 if direct else 3) for it in iters))
+    per_step = 5 + (3 if args.anderson else 0)  # + the extrapolation's 3 kernels
+    launches = int(sum(per_step * it + (5 if direct else 3) for it in iters))
     # the other precision mode on the same workload (the direct transfer: the
     # transfer through the grid instead): time to tol and agreement
     other = {}
-    if args.other_prec and not args.stabilize:  # FP32+refine has no SUPG forms
+    if args.other_prec and not args.stabilize and not args.anderson:  # FP32+refine: no SUPG, no extrapolation
         oprec = ADR_FP32_REFINE if prec == ADR_FP64 and not direct else ADR_FP64
         s2 = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=oprec)
         s2.solve_stationary()
@@ -425,7 +433,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": f"sheared{args.n}", "nodes": prob.nx * prob.ny,
                    "mu": prob.mu, "sigma": prob.sigma, "tol": args.tol, "prec": args.prec,
-                   "stabilize": args.stabilize, "transfer": args.transfer,
+                   "stabilize": args.stabilize, "transfer": args.transfer, "anderson": args.anderson,
                    "line_unknowns_per_step": unknowns, "iters_per_solve": iters,
                    "step": "one stationary solve to tol from u=0",
                    "l2": "working set > 129 MB L2 (curve data and maps ~1 GB)",
@@ -436,8 +444,8 @@ def run_ours(args):
     }
     if other:
         line["other_precision"] = other
-    if also_direct:
-        line["direct_transfer"] = direct_leg(args, prob, dev, stream)
+    for name, tr, m in variants:
+        line[name] = variant_leg(args, prob, dev, stream, tr, m)
     if not args.no_e2e:
         line["e2e"] = e2e(args, prob, dev, prec)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -458,17 +466,17 @@ def run_ours(args):
                 ev["fp32+refine" if other["prec"] == "fp32+refine" else "fp64"] = rel_err(u_other, ref)
             ev["tolerance"] = {"fp64": 1e-12, "fp32+refine": 1e-5}
             line["err_vs_oracle"] = ev
-    if djob is not None and "direct_transfer" in line:
-        dl = line["direct_transfer"]
-        ref, info = djob.result(timeout_s=600)
-        if ref is None:
-            dl["err_vs_oracle"] = {"value": None, "why": info}
-        else:
-            dl["err_vs_oracle"] = {"fp64": rel_err(dl.pop("_u"), ref), "oracle_iters": info["iters"],
-                                   "oracle_secs": info["secs"], "tolerance": 1e-12,
-                                   "oracle": "the oracle's converged solve with the direct transfer"}
-    if "direct_transfer" in line:
-        line["direct_transfer"].pop("_u", None)
+    for name, tr, m in variants:
+        dl = line[name]
+        if name in vjobs:
+            ref, info = vjobs[name].result(timeout_s=600)
+            if ref is None:
+                dl["err_vs_oracle"] = {"value": None, "why": info}
+            else:
+                dl["err_vs_oracle"] = {"fp64": rel_err(dl["_u"], ref), "oracle_iters": info["iters"],
+                                       "oracle_secs": info["secs"], "tolerance": 1e-12,
+                                       "oracle": "the oracle's converged solve with the same options"}
+        dl.pop("_u", None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -476,13 +484,15 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def direct_leg(args, prob, dev, stream, reps=3):
+def variant_leg(args, prob, dev, stream, transfer, anderson, reps=3):
     """The same stationary solve with the direct curve-to-curve transfer
-    (opts.transfer = 1, FP64): time to tol, iterations, per-kernel roofline."""
+    (opts.transfer = 1) and/or the accelerated iteration (opts.anderson),
+    FP64: time to tol, iterations, per-kernel roofline."""
     import torch
 
     from paper_2411_11041_gb300 import Solver
-    s = Solver(prob, device=dev, tol=args.tol, max_iter=200000, transfer=1)
+    direct = bool(transfer)
+    s = Solver(prob, device=dev, tol=args.tol, max_iter=200000, transfer=transfer, anderson=anderson)
     tuned = s.autotune(10)
     s.solve_stationary()
     torch.cuda.synchronize(dev)
@@ -497,12 +507,15 @@ def direct_leg(args, prob, dev, stream, reps=3):
     torch.cuda.synchronize(dev)
     ms = f0.elapsed_time(f1)
     unknowns = s.line_unknowns()
-    roof = kernel_roofline(s, prob, unknowns, True)
-    k = KERNELS_DIRECT.index(roof["kernel"])
-    if args.n == 2048 and NCU_TRAFFIC_DIRECT_SHEARED2048[k] is not None:
-        roof["traffic"] = NCU_TRAFFIC_DIRECT_SHEARED2048[k]
+    roof = kernel_roofline(s, prob, unknowns, direct)
+    names = KERNELS_DIRECT if direct else KERNELS
+    traffic = NCU_TRAFFIC_DIRECT_SHEARED2048 if direct else NCU_TRAFFIC_SHEARED2048
+    k = names.index(roof["kernel"])
+    if args.n == 2048 and traffic[k] is not None:
+        roof["traffic"] = traffic[k]
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture"
-    out = {"transfer": "direct", "ms_per_step": ms / reps, "value": dofs / (ms / 1e3), "unit": UNIT,
+    out = {"transfer": "direct" if direct else "grid", "anderson": anderson,
+           "ms_per_step": ms / reps, "value": dofs / (ms / 1e3), "unit": UNIT,
            "iters_per_solve": its,
            "launch_shape": {"rows_per_thread": tuned[0], "tuned_ms_per_split_step": tuned[2]},
            "roofline": roof, "_u": u.cpu().numpy()}
@@ -532,7 +545,7 @@ def e2e(args, prob, dev, prec):
         for k, t in pin.items():
             setattr(q, k, t.to(dev, non_blocking=True))
         s = Solver(q, device=dev, tol=args.tol, max_iter=200000, prec=prec,
-                   transfer=int(args.transfer == "direct"))
+                   transfer=int(args.transfer == "direct"), anderson=args.anderson)
         u, _, st, _ = s.solve_stationary()
         host_out.copy_(u)
         s.close()
@@ -980,6 +993,42 @@ def run_manufactured(args):
     print(json.dumps(line), flush=True)
 
 
+def run_anderson(args):
+    """The accelerated stationary iteration (opts.anderson) against the plain
+    one on the sheared problem at several sizes, both transfers: split steps
+    and time to tol per solve (CUDA events, 3 solves after one warm-up), and
+    the largest difference between the two answers (the same fixed point)."""
+    import torch
+
+    from paper_2411_11041_gb300 import Solver
+    from paper_2411_11041_gb300 import workloads as W
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for n in (257, 513, 1025, 2048):
+        prob = W.sheared(n=n)
+        for transfer in (0, 1):
+            base = None
+            for m in (0, 1, 3, 5):
+                s = Solver(prob, device=dev, tol=args.tol, max_iter=200000, transfer=transfer, anderson=m)
+                s.solve_stationary()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(3):
+                    u, _, st, code = s.solve_stationary()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                if base is None:
+                    base = u
+                rows.append({"n": n, "transfer": "direct" if transfer else "grid", "anderson": m,
+                             "steps": st["iters"], "ms_per_solve": e0.elapsed_time(e1) / 3,
+                             "max_rel_diff_vs_plain": float((u - base).abs().max() / base.abs().max())})
+                s.close()
+    print(json.dumps({"workload": "anderson_sweep", "problem": "sheared", "tol": args.tol,
+                      "rows": rows}), flush=True)
+
+
 def run_kernels(args):
     """Kernel timing only: the n^2 sheared problem's four sweep kernels,
     args.steps back-to-back launches each in the solve's launch configuration
@@ -1019,6 +1068,8 @@ def main():
         run_manufactured(args)
     elif args.workload == "kernels":
         run_kernels(args)
+    elif args.workload == "anderson":
+        run_anderson(args)
     else:
         run_ours(args)
 

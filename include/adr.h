@@ -116,6 +116,16 @@ typedef struct {
                                relative update is taken over them, and the grid is touched only
                                by the initial state (bilinear samples) and the output (the
                                curve -> grid map of §6).  FP64 mode only; not in batches */
+    int anderson;           /* acceleration of the stationary iteration: 0 = none; m = 1..8 =
+                               Anderson extrapolation over the last m split steps (the
+                               multi-parameter pseudo-steps read as per-step weights: a cycle of
+                               pseudo steps Δt does not keep the split step's fixed point, these
+                               weights do).  With g_k the split step's output from u_k and
+                               f_k = g_k - u_k, u_{k+1} = g_k - Σ_i γ_i (g_{k-i+1} - g_{k-i}),
+                               γ minimising |f_k - Σ_i γ_i (f_{k-i+1} - f_{k-i})|.  The relative
+                               update (tol) is |f_k| / |g_k|, as without it.  Applies to the
+                               stationary solves (also the slices of adr_step_parabolic mode 1),
+                               not to the time steps of mode 0.  FP64 mode only; not in batches */
 } adr_opts;
 
 /* Result statistics (host struct filled by the solve calls). */

@@ -35,7 +35,8 @@ class adr_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("theta", C.c_double), ("dt", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("init", C.c_int),
                 ("rows_per_thread", C.c_int), ("map_blocks_per_sm", C.c_int),
-                ("interp_weights", C.c_int), ("stabilize", C.c_int), ("transfer", C.c_int)]
+                ("interp_weights", C.c_int), ("stabilize", C.c_int), ("transfer", C.c_int),
+                ("anderson", C.c_int)]
 
 
 class adr_stats(C.Structure):

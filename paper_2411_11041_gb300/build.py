@@ -24,6 +24,7 @@ UNITS = {
     "api.cu": [],
     "noalloc.cu": [],
     "cnn.cu": [],
+    "accel.cu": [],
 }
 
 

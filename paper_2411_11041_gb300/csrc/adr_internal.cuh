@@ -110,6 +110,16 @@ struct IterState {
     int pad;
 };
 
+// Anderson extrapolation's small state on the device: the raw products
+// <f_a, f_b> of the last m + 1 residuals by history slot, and the weights of
+// the next state
+struct AaDev {
+    double R[9][9];
+    double c[9];
+    int used;  // difference columns the last weights used
+    int pad;
+};
+
 struct Problem {
     adr_grid grid{};
     adr_opts opts{};
@@ -142,6 +152,11 @@ struct Problem {
     double* xuG = nullptr;               // u_{j+1/2} at the G nodes
     double* xtmp = nullptr;              // B-node work array (midpoint output)
     bool xu_set = false;                 // xu[0] already holds the initial state
+    // Anderson extrapolation (opts.anderson = m): histories of m + 1 state vectors
+    double* aa_f = nullptr;              // residuals f = g - u
+    double* aa_g = nullptr;              // map outputs g
+    AaDev* aa_dev = nullptr;
+    double* aa_partial = nullptr;        // per-block partial products
     std::vector<void*> owned;
 };
 
@@ -215,6 +230,9 @@ adr_status load_family(Problem* p, const double* fextra, double fx_scale);
 adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_even,
                              const double* u_odd, bool use_state, int paper);
 adr_status launch_mask_copy(Problem* p, const double* in, double* out);
+// Anderson extrapolation (accel.cu)
+adr_status launch_anderson(Problem* p);
+adr_status alloc_anderson(Problem* p);
 // direct transfer between the families (sweep.cu)
 adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u_even,
                                  const double* u_odd, bool use_state);

@@ -72,6 +72,7 @@ struct adr_problem {
     // parameters the cached graph was captured with
     double g_theta = 0, g_dt = 0, g_sig = 0, g_scale = 0, g_tol = 0;
     int g_max_iter = -1;
+    bool g_accel = false;
     const double* g_fextra = nullptr;
     double line_unknowns[2] = {0, 0};
     std::vector<int> offs[2];  // host copies of the curve offsets
@@ -114,7 +115,7 @@ void drop_graph(adr_problem* h)
 // the body of a conditional WHILE node; the check kernel clears the
 // condition once the relative update reaches tol or max_iter steps ran.
 adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
-                       const double* fextra, double fx_scale, double tol, int max_iter)
+                       const double* fextra, double fx_scale, double tol, int max_iter, bool accel)
 {
     Problem* p = &h->p;
     drop_graph(h);
@@ -155,6 +156,7 @@ adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
             s = launch_grid_map_ex(p, 1, p->ubuf[0], p->ubuf[1], 1, p->ubuf[0], p->ubuf[1], true, true);
     }
     if (s == ADR_OK) s = launch_check_ex(p, tol, max_iter, cond, true);
+    if (s == ADR_OK && accel) s = launch_anderson(p);  // u_{j+1} extrapolated unless done
     cudaGraph_t out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &out);
     p->stream = user;
@@ -168,6 +170,7 @@ adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
     h->g_scale = fx_scale;
     h->g_tol = tol;
     h->g_max_iter = max_iter;
+    h->g_accel = accel;
     return ADR_OK;
 }
 
@@ -196,9 +199,10 @@ adr_status finish_direct(Problem* p, int max_iter, double* out, double* iter_out
 adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
                          const double* fextra, double fx_scale, double tol, int max_iter,
                          bool midpoint, double* out, double* iter_out, adr_stats* stats,
-                         bool* converged)
+                         bool* converged, bool accel = true)
 {
     Problem* p = &h->p;
+    accel = accel && p->opts.anderson > 0;
     TRY(launch_state_reset(p));
     ADR_CUDA_TRY(cudaEventRecord(h->ev0, p->stream));
     if (p->opts.transfer) {
@@ -212,8 +216,8 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
         TRY(load_family(p, fextra, fx_scale));
         if (!h->exec || h->g_theta != theta || h->g_dt != dt || h->g_sig != sig ||
             h->g_fextra != fextra || h->g_scale != fx_scale || h->g_tol != tol ||
-            h->g_max_iter != max_iter)
-            TRY(build_graph(h, theta, dt, sig, fextra, fx_scale, tol, max_iter));
+            h->g_max_iter != max_iter || h->g_accel != accel)
+            TRY(build_graph(h, theta, dt, sig, fextra, fx_scale, tol, max_iter, accel));
         ADR_CUDA_TRY(cudaGraphLaunch(h->exec, p->stream));
     }
     if (p->opts.transfer) TRY(finish_direct(p, max_iter, out, iter_out, midpoint));
@@ -335,6 +339,14 @@ adr_status check_opts(const adr_opts* o)
         set_error("opts.transfer == 1 needs opts.prec == ADR_FP64");
         return ADR_EINVAL;
     }
+    if (o->anderson < 0 || o->anderson > 8) {
+        set_error("opts.anderson must be 0..8");
+        return ADR_EINVAL;
+    }
+    if (o->anderson && o->prec != ADR_FP64) {
+        set_error("opts.anderson > 0 needs opts.prec == ADR_FP64");
+        return ADR_EINVAL;
+    }
     if ((o->rows_per_thread != 0 && o->rows_per_thread != 2 && o->rows_per_thread != 4 &&
          o->rows_per_thread != 8 && o->rows_per_thread != 16) ||
         o->map_blocks_per_sm < 0 || o->map_blocks_per_sm > 8) {
@@ -453,6 +465,7 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
         if ((e = cudaMemsetAsync(p->xu[0], 0, sizeof(double) * p->fam[0].n_nodes, p->stream)))
             return fail(cuda_fail(e, "cudaMemsetAsync"));
     }
+    if ((s = alloc_anderson(p))) return fail(s);
     if ((s = dev_alloc(p, &p->partial, 2 * (size_t)p->n_partial_blocks)) ||
         (s = dev_alloc(p, &p->state, 1)) || (s = dev_alloc(p, &p->fextra, N)) ||
         (s = dev_alloc(p, &p->pivmin, 2)))
@@ -561,7 +574,7 @@ adr_status adr_step_parabolic(adr_problem* h, double dt, int nsteps, int mode, d
     if (mode == 0) {
         TRY(launch_mask_copy(p, u, p->ubuf[0]));
         TRY(run_iteration(h, o.theta, dt, p->sigma, nullptr, 0.0, -1.0, nsteps, false, u, nullptr,
-                          stats, &conv));
+                          stats, &conv, false));
         return ADR_OK;
     }
     double sig = p->sigma + 1.0 / dt;
@@ -865,8 +878,9 @@ adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_
             set_error("adr_batch_create: NULL handle or mixed precision modes");
             return ADR_EINVAL;
         }
-        if (probs[i]->p.opts.transfer) {
-            set_error("adr_batch_create: problems with opts.transfer == 1 are solved one by one");
+        if (probs[i]->p.opts.transfer || probs[i]->p.opts.anderson) {
+            set_error("adr_batch_create: problems with opts.transfer or opts.anderson set are solved "
+                      "one by one");
             return ADR_EINVAL;
         }
     }

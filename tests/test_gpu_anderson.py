@@ -1,0 +1,117 @@
+"""Anderson extrapolation of the stationary iteration (opts.anderson = m) on
+the GPU against the oracle's: fixed step counts element by element (the
+extrapolation weights come from sums taken in another order, so 1e-11 rather
+than 1e-12), converged solves within 1e-12, the transfer through the grid and
+the direct one, the parabolic slices, and the full-size sheared workload."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_11041_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+TOL_STEPS = 1e-11
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_11041_gb300 import build
+    build.build()
+    return torch
+
+
+def relerr(a, b):
+    a = a.cpu().numpy() if hasattr(a, "cpu") else a
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+PROBLEMS = {
+    "manufactured33": lambda: W.manufactured(n=33),
+    "L_mask": lambda: W.manufactured(n=41, beta=(0.3, 1.0), mask="L"),
+    "sheared65": lambda: W.sheared(n=65),
+    "data2d": lambda: W.data2d(33),
+    "disc_rand": lambda: W.random_problem(np.random.Generator(np.random.PCG64(7)), 97, mask="disc"),
+}
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("transfer", [0, 1])
+@pytest.mark.parametrize("m", [1, 3, 8])
+def test_fixed_step_count_matches_oracle(torch_cuda, name, transfer, m):
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    p = PROBLEMS[name]()
+    iw = 1 if name == "disc_rand" else 0
+    o = O.Oracle(p, interp_weights=iw, transfer=transfer, anderson=m)
+    s = Solver(p, tol=0.0, max_iter=17, interp_weights=iw, transfer=transfer, anderson=m)
+    u, uit, stats, st = s.solve_stationary(want_iter=True)
+    ref, refit, it, rel, ost = o.solve_stationary(tol=0.0, max_iter=17)
+    assert st == ADR_OK and ost == O.OK and stats["iters"] == it == 17
+    assert relerr(u, ref) <= TOL_STEPS and relerr(uit, refit) <= TOL_STEPS
+    assert abs(stats["rel_update"] - rel) <= 1e-8 * rel + 1e-13
+
+
+@pytest.mark.parametrize("name", ["manufactured33", "sheared65", "L_mask"])
+@pytest.mark.parametrize("transfer", [0, 1])
+def test_converged_solve_matches_oracle(torch_cuda, name, transfer):
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    p = PROBLEMS[name]()
+    o = O.Oracle(p, transfer=transfer, anderson=3)
+    s = Solver(p, tol=1e-11, max_iter=20000, transfer=transfer, anderson=3)
+    u, uit, stats, st = s.solve_stationary(want_iter=True)
+    ref, refit, it, rel, ost = o.solve_stationary(tol=1e-11, max_iter=20000)
+    plain, _, itp, _, _ = O.Oracle(p, transfer=transfer).solve_stationary(tol=1e-11, max_iter=20000)
+    assert st == ADR_OK and ost == O.OK
+    assert abs(stats["iters"] - it) <= 1 and stats["iters"] < itp
+    assert relerr(u, ref) <= TOL64
+    assert relerr(u, plain) <= 1e-9  # the plain iteration's fixed point
+
+
+def test_parabolic_slices_are_extrapolated_and_time_steps_are_not(torch_cuda):
+    from paper_2411_11041_gb300 import Solver
+    torch = torch_cuda
+    p = W.parabolic(n=65)
+    for mode in (0, 1):
+        o = O.Oracle(p, anderson=3)
+        s = Solver(p, tol=1e-9, max_iter=5000, anderson=3)
+        u = torch.tensor(p.u0, device="cuda:0")
+        stats, st = s.step_parabolic(u, 1e-3, 3, mode)
+        ref, tot, ost = o.step_parabolic(p.u0, 1e-3, 3, mode, tol=1e-9, max_iter=5000)
+        assert abs(stats["iters"] - tot) <= 3 * (mode == 1)
+        assert relerr(u, ref) <= (TOL64 if mode == 0 else 1e-9)
+
+
+def test_refusals(torch_cuda):
+    from paper_2411_11041_gb300 import ADR_FP32_REFINE, AdrError, Batch, Solver
+    p = W.manufactured(n=17)
+    with pytest.raises(AdrError, match="EINVAL"):
+        Solver(p, anderson=9)
+    with pytest.raises(AdrError, match="EINVAL"):
+        Solver(p, anderson=2, prec=ADR_FP32_REFINE)
+    with pytest.raises(AdrError, match="EINVAL"):
+        Batch([Solver(p, anderson=2), Solver(p)])
+
+
+@pytest.fixture(scope="module")
+def sheared2048_anderson():
+    """The oracle's converged accelerated solve of the full-size sheared
+    workload (2048^2, m = 3, tol 1e-8)."""
+    p = W.sheared(n=2048)
+    ref, refit, it, rel, st = O.Oracle(p, anderson=3).solve_stationary(tol=1e-8, max_iter=200000)
+    assert st == O.OK
+    return p, ref, it
+
+
+def test_sheared_2048_accelerated_solve_matches_oracle(torch_cuda, sheared2048_anderson):
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    p, ref, it = sheared2048_anderson
+    s = Solver(p, tol=1e-8, max_iter=200000, anderson=3)
+    u, _, stats, st = s.solve_stationary()
+    assert st == ADR_OK
+    assert abs(stats["iters"] - it) <= 1
+    assert relerr(u, ref) <= TOL64
+    s.close()
