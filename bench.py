@@ -584,7 +584,8 @@ def run_batch(args):
     parts, loads = PT.lpt_split([PT.work_estimate(p) for p in allp], ws)
     probs = [allp[i] for i in parts[rank]]
     t0 = time.perf_counter()
-    solvers = [Solver(p, device=dev, tol=args.tol, max_iter=200000, prec=prec, interp_weights=1)
+    solvers = [Solver(p, device=dev, tol=args.tol, max_iter=200000, prec=prec, interp_weights=1,
+                      anderson=args.anderson)
                for p in probs]
     setup_s = time.perf_counter() - t0
     batch = Batch(solvers)
@@ -606,17 +607,48 @@ def run_batch(args):
     ms_rank = e0.elapsed_time(e1) / args.steps
     ms_batch, dofs_all, _ = job_rate(ws, ms_rank, dofs / args.steps, dev)
     iters = [x["iters"] for x in stats]
-    # plain: one problem at a time through its own graph
-    for s in solvers[:4]:
-        s.solve_stationary()
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for s in solvers:
-        s.solve_stationary()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_plain = e0.elapsed_time(e1)
-    ms_plain = max_over_ranks(ws, ms_plain, dev)
+    # one problem at a time through its own graph (the same options)
+    def one_by_one(ss):
+        for s in ss[:4]:
+            s.solve_stationary()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        its = []
+        for s in ss:
+            its.append(s.solve_stationary()[2]["iters"])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(ws, e0.elapsed_time(e1), dev), its
+    ms_plain, _ = one_by_one(solvers)
+    # where the batch's time goes: the same batch without its slowest tenth
+    order = np.argsort(iters)[::-1]
+    cut = max(1, len(order) // 10)
+    rest = Batch([solvers[i] for i in sorted(order[cut:])]) if len(order) > cut else None
+    tail = {}
+    if rest is not None:
+        rest.solve()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        rest.solve()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_rest = e0.elapsed_time(e1)
+        tail = {"slowest_tenth": cut, "batch_without_slowest_tenth_ms": ms_rest,
+                "slowest_tenth_share": 1.0 - ms_rest / ms_batch,
+                "active_problems_at_step": {str(k): int(sum(1 for x in iters if x > k))
+                                            for k in (0, 50, 100, 150, 200, 300, 500, 800)}}
+    # the paper's iteration one by one (no extrapolation), when the batch extrapolates
+    unaccel = {}
+    if args.anderson:
+        plain_solvers = [Solver(p, device=dev, tol=args.tol, max_iter=200000, prec=prec, interp_weights=1)
+                         for p in probs]
+        ms_unacc, its_unacc = one_by_one(plain_solvers)
+        unaccel = {"plain_unaccelerated_sequential_ms": ms_unacc,
+                   "unaccelerated_iters_min_median_max": [min(its_unacc), int(np.median(its_unacc)),
+                                                          max(its_unacc)],
+                   "speedup_vs_unaccelerated_sequential": ms_unacc / ms_batch}
+        for s in plain_solvers:
+            s.close()
     line = {"metric": METRIC, "value": dofs_all / (ms_batch / 1e3), "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
@@ -627,7 +659,9 @@ def run_batch(args):
                        "parallelism": f"problems split over {ws} rank(s), LPT on estimated work",
                        "estimated_load_per_rank": loads},
             "plain_sequential_ms": ms_plain, "batched_speedup": ms_plain / ms_batch,
-            "setup_s": setup_s}
+            "setup_s": setup_s, "tail": tail}
+    line["config"]["anderson"] = args.anderson
+    line.update(unaccel)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

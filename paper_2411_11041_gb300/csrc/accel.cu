@@ -23,6 +23,9 @@
 // unknown, so the products run over every entry.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "adr_internal.cuh"
 
 namespace adr {
@@ -48,14 +51,15 @@ struct AaArgs {
 
 __device__ __forceinline__ int step_index(const IterState* st) { return st->iter - 1; }
 
-// every thread loads the same M history vectors whether or not the step
-// has M differences yet (a missing one is read from slot k, a valid vector,
-// and left out of the sums), so that the loads issue back to back
+// Products of one problem over the elements start, start + stride, ...:
+// block partials into a.partial at local block lb.  Every thread loads the
+// same M history vectors whether or not the step has that many differences
+// yet (a missing one is read from slot k, a valid vector, and left out of
+// the sums), so that the loads issue back to back; M >= the problem's depth.
 template <int M>
-__global__ void __launch_bounds__(kAaThreads) k_aa_dots(AaArgs a)
+__device__ __forceinline__ void aa_dots_body(const AaArgs& a, long long start, long long stride, int lb)
 {
-    if (a.state->done || a.state->iter < 1) return;
-    const int k = step_index(a.state), ns = M + 1, mk = k < M ? k : M;
+    const int k = step_index(a.state), ns = a.m + 1, mk = k < a.m ? k : a.m;
     const double* __restrict__ u = (k & 1) ? a.u_odd : a.u_even;
     const double* __restrict__ g = ((k + 1) & 1) ? a.out_odd : a.out_even;
     double* __restrict__ fk = a.fh + (size_t)(k % ns) * a.L;
@@ -66,8 +70,7 @@ __global__ void __launch_bounds__(kAaThreads) k_aa_dots(AaArgs a)
     double acc[M + 1];
 #pragma unroll
     for (int j = 0; j <= M; ++j) acc[j] = 0.0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.L;
-         q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = start; q < a.L; q += stride) {
         double h[M];
 #pragma unroll
         for (int j = 0; j < M; ++j) h[j] = __ldg(fj[j] + q);
@@ -90,13 +93,22 @@ __global__ void __launch_bounds__(kAaThreads) k_aa_dots(AaArgs a)
     if (threadIdx.x <= mk) {
         double t = 0.0;
         for (int q = 0; q < kAaThreads / 32; ++q) t += red[threadIdx.x][q];
-        a.partial[(size_t)blockIdx.x * (kAaMax + 1) + threadIdx.x] = t;
+        a.partial[(size_t)lb * (kAaMax + 1) + threadIdx.x] = t;
     }
 }
 
-__global__ void k_aa_solve(AaArgs a, int nblocks)
+template <int M>
+__global__ void __launch_bounds__(kAaThreads) k_aa_dots(AaArgs a)
 {
     if (a.state->done || a.state->iter < 1) return;
+    aa_dots_body<M>(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x,
+                    blockIdx.x);
+}
+
+// the weights of one problem from its block partials (a block of
+// 32 (kAaMax + 1) threads)
+__device__ void aa_solve_body(const AaArgs& a, int nblocks)
+{
     const int k = step_index(a.state), ns = a.m + 1, mk = k < a.m ? k : a.m;
     __shared__ double sums[kAaMax + 1];
     __shared__ double part[kAaMax + 1][32];
@@ -169,11 +181,16 @@ __global__ void k_aa_solve(AaArgs a, int nblocks)
     d.used = use;
 }
 
-template <int M>
-__global__ void __launch_bounds__(kAaThreads) k_aa_update(AaArgs a)
+__global__ void k_aa_solve(AaArgs a, int nblocks)
 {
     if (a.state->done || a.state->iter < 1) return;
-    const int k = step_index(a.state), ns = M + 1, mk = k < M ? k : M;
+    aa_solve_body(a, nblocks);
+}
+
+template <int M>
+__device__ __forceinline__ void aa_update_body(const AaArgs& a, long long start, long long stride)
+{
+    const int k = step_index(a.state), ns = a.m + 1, mk = k < a.m ? k : a.m;
     double* __restrict__ out = ((k + 1) & 1) ? a.out_odd : a.out_even;
     double c[M + 1];
     const double* gj[M + 1];
@@ -182,8 +199,7 @@ __global__ void __launch_bounds__(kAaThreads) k_aa_update(AaArgs a)
         c[j] = j <= mk ? a.dev->c[j] : 0.0;
         gj[j] = a.gh + (size_t)((k - (j <= mk ? j : 0)) % ns) * a.L;
     }
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.L;
-         q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = start; q < a.L; q += stride) {
         double h[M + 1];
 #pragma unroll
         for (int j = 0; j <= M; ++j) h[j] = __ldg(gj[j] + q);
@@ -194,17 +210,58 @@ __global__ void __launch_bounds__(kAaThreads) k_aa_update(AaArgs a)
     }
 }
 
-}  // namespace
-
-int aa_blocks(const Problem* p) { return grid_map_blocks(p); }
-
-// the three kernels of one extrapolation step (inside the solve's graph)
-adr_status launch_anderson(Problem* p)
+template <int M>
+__global__ void __launch_bounds__(kAaThreads) k_aa_update(AaArgs a)
 {
-    const int m = p->opts.anderson;
-    if (m <= 0) return ADR_OK;
-    AaArgs a;
-    a.m = m;
+    if (a.state->done || a.state->iter < 1) return;
+    aa_update_body<M>(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+// ---------------------------------------------------------------- batches
+// One AaArgs per problem (depth 0: no extrapolation); the dots and update
+// kernels walk the batch's active map blocks (problem, local block), as the
+// batched map does, and the solve kernel takes one block per problem.
+
+template <int M>
+__global__ void __launch_bounds__(kAaThreads) k_aa_dots_batch(const AaArgs* __restrict__ table, AaBatchView v)
+{
+    const int cur = *v.sel;
+    const int* list = v.act_blocks[cur];
+    const int n_act = v.act_count[cur * 7 + 6];
+    for (int ii = blockIdx.x; ii < n_act; ii += gridDim.x) {
+        const int bk = list[ii], p = v.blk_prob[bk], lb = v.blk_local[bk];
+        const AaArgs& a = table[p];
+        if (a.m == 0 || a.state->done || a.state->iter < 1) continue;  // uniform per block
+        aa_dots_body<M>(a, (long long)lb * blockDim.x + threadIdx.x, (long long)v.nblk[p] * blockDim.x, lb);
+        __syncthreads();  // the reduction's shared arrays are reused
+    }
+}
+
+__global__ void k_aa_solve_batch(const AaArgs* __restrict__ table, AaBatchView v)
+{
+    const AaArgs& a = table[blockIdx.x];
+    if (a.m == 0 || a.state->done || a.state->iter < 1) return;
+    aa_solve_body(a, v.nblk[blockIdx.x]);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kAaThreads) k_aa_update_batch(const AaArgs* __restrict__ table, AaBatchView v)
+{
+    const int cur = *v.sel;
+    const int* list = v.act_blocks[cur];
+    const int n_act = v.act_count[cur * 7 + 6];
+    for (int ii = blockIdx.x; ii < n_act; ii += gridDim.x) {
+        const int bk = list[ii], p = v.blk_prob[bk], lb = v.blk_local[bk];
+        const AaArgs& a = table[p];
+        if (a.m == 0 || a.state->done || a.state->iter < 1) continue;
+        aa_update_body<M>(a, (long long)lb * blockDim.x + threadIdx.x, (long long)v.nblk[p] * blockDim.x);
+    }
+}
+
+AaArgs aa_args(Problem* p)
+{
+    AaArgs a{};
+    a.m = p->opts.anderson;
     a.state = p->state;
     if (p->opts.transfer) {
         a.L = p->fam[0].n_nodes;
@@ -223,6 +280,19 @@ adr_status launch_anderson(Problem* p)
     a.gh = p->aa_g;
     a.dev = p->aa_dev;
     a.partial = p->aa_partial;
+    return a;
+}
+
+}  // namespace
+
+int aa_blocks(const Problem* p) { return grid_map_blocks(p); }
+
+// the three kernels of one extrapolation step (inside the solve's graph)
+adr_status launch_anderson(Problem* p)
+{
+    const int m = p->opts.anderson;
+    if (m <= 0) return ADR_OK;
+    const AaArgs a = aa_args(p);
     const int nb = aa_blocks(p);
     cudaStream_t st = p->stream;
     switch (m) {
@@ -264,6 +334,61 @@ adr_status alloc_anderson(Problem* p)
     TRY_S(dev_alloc(p, &p->aa_dev, 1));
     TRY_S(dev_alloc(p, &p->aa_partial, (size_t)nb * (kAaMax + 1)));
     ADR_CUDA_TRY(cudaMemsetAsync(p->aa_dev, 0, sizeof(AaDev), p->stream));
+    return ADR_OK;
+}
+
+}  // namespace adr
+
+namespace adr {
+
+// the batch's table of per-problem arguments (device memory from cudaMalloc,
+// freed by the caller with cudaFree); *mmax = the largest depth (0: none)
+adr_status anderson_batch_table(Problem* const* ps, int n, void** table, int* mmax)
+{
+    *table = nullptr;
+    *mmax = 0;
+    std::vector<AaArgs> t(n);
+    for (int i = 0; i < n; ++i) {
+        t[i] = aa_args(ps[i]);
+        *mmax = std::max(*mmax, t[i].m);
+    }
+    if (*mmax == 0) return ADR_OK;
+    ADR_CUDA_TRY(cudaMalloc(table, sizeof(AaArgs) * n));
+    cudaError_t e = cudaMemcpy(*table, t.data(), sizeof(AaArgs) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(*table);
+        *table = nullptr;
+        return cuda_fail(e, "anderson batch table");
+    }
+    return ADR_OK;
+}
+
+// one extrapolation step of every active problem with a depth (batch graph)
+adr_status launch_anderson_batch(const AaBatchView& v, cudaStream_t st)
+{
+    if (v.mmax <= 0 || !v.table) return ADR_OK;
+    const AaArgs* t = static_cast<const AaArgs*>(v.table);
+    switch (v.mmax) {
+#define ADR_AA_CASE(M_)                                                   \
+    case M_:                                                              \
+        k_aa_dots_batch<M_><<<v.grid, kAaThreads, 0, st>>>(t, v);         \
+        k_aa_solve_batch<<<v.n, 32 * (kAaMax + 1), 0, st>>>(t, v);        \
+        k_aa_update_batch<M_><<<v.grid, kAaThreads, 0, st>>>(t, v);       \
+        break;
+        ADR_AA_CASE(1)
+        ADR_AA_CASE(2)
+        ADR_AA_CASE(3)
+        ADR_AA_CASE(4)
+        ADR_AA_CASE(5)
+        ADR_AA_CASE(6)
+        ADR_AA_CASE(7)
+        ADR_AA_CASE(8)
+#undef ADR_AA_CASE
+    default:
+        set_error("internal: Anderson depth out of range");
+        return ADR_EINVAL;
+    }
+    ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
 }
 

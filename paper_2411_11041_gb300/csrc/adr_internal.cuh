@@ -233,6 +233,20 @@ adr_status launch_mask_copy(Problem* p, const double* in, double* out);
 // Anderson extrapolation (accel.cu)
 adr_status launch_anderson(Problem* p);
 adr_status alloc_anderson(Problem* p);
+// a batch's view for the extrapolation: its per-problem table and the map's
+// active block lists
+struct AaBatchView {
+    const void* table;           // per-problem arguments (anderson_batch_table)
+    int n, mmax, grid;
+    const int* blk_prob;
+    const int* blk_local;
+    const int* nblk;
+    const int* const* act_blocks;
+    const int* act_count;
+    const int* sel;
+};
+adr_status anderson_batch_table(Problem* const* ps, int n, void** table, int* mmax);
+adr_status launch_anderson_batch(const AaBatchView& v, cudaStream_t st);
 // direct transfer between the families (sweep.cu)
 adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u_even,
                                  const double* u_odd, bool use_state);

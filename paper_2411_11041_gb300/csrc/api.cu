@@ -878,9 +878,8 @@ adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_
             set_error("adr_batch_create: NULL handle or mixed precision modes");
             return ADR_EINVAL;
         }
-        if (probs[i]->p.opts.transfer || probs[i]->p.opts.anderson) {
-            set_error("adr_batch_create: problems with opts.transfer or opts.anderson set are solved "
-                      "one by one");
+        if (probs[i]->p.opts.transfer) {
+            set_error("adr_batch_create: problems with opts.transfer == 1 are solved one by one");
             return ADR_EINVAL;
         }
     }

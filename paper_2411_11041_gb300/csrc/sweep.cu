@@ -1680,6 +1680,8 @@ struct BatchDev {
     BatchItem* it[2][kItemSets] = {};
     int nit[2][kItemSets] = {};
     int git[2][kItemSets] = {};
+    void* aa_table = nullptr;  // per-problem Anderson arguments (null: no problem extrapolates)
+    int aa_mmax = 0;
     std::vector<void*> owned;
 };
 
@@ -1833,6 +1835,8 @@ adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const 
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         b->map_grid = std::min(b->n_blk, 8 * nsm);
     }
+    if ((s = anderson_batch_table(ps, n, &b->aa_table, &b->aa_mmax))) return fail(s);
+    if (b->aa_table) b->owned.push_back(b->aa_table);
     *out = b;
     return ADR_OK;
 }
@@ -1934,6 +1938,12 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
 #undef ADR_BATCH_SOLVE
     k_check_batch<<<b->n, 256, 0, st>>>(b->states, (const double* const*)b->partials, b->nblk, b->n,
                                         b->tol, b->max_iter, b->ticket, cond, b->act.changed);
+    if (b->aa_table) {
+        // the extrapolated next states of the problems that go on
+        AaBatchView v{b->aa_table, b->n, b->aa_mmax, b->map_grid, b->blk_prob, b->blk_local, b->nblk,
+                      b->act.blocks_dev, b->act.count, b->act.sel};
+        TRY_S(launch_anderson_batch(v, st));
+    }
     k_batch_compact<<<b->map_grid, 256, 0, st>>>(b->act, b->d_items, b->d_n_items, b->blk_prob,
                                                  b->n_blk, b->states);
     k_batch_flip<<<1, 1, 0, st>>>(b->act);
