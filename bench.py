@@ -703,7 +703,7 @@ def run_learned(args):
     draw_s = time.perf_counter() - t0
     net = Network(max(args.batch_size, args.hold))
     t0 = time.perf_counter()
-    data = WS.generate(net, train, tol=args.tol)
+    data = WS.generate(net, train, tol=args.tol, anderson=3)  # the same fixed points, sooner
     torch.cuda.synchronize(dev)
     gen_s = time.perf_counter() - t0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -713,7 +713,7 @@ def run_learned(args):
     torch.cuda.synchronize(dev)
     train_ms = e0.elapsed_time(e1)
     step_ms = train_ms / args.train_steps
-    hd = WS.generate(net, hold, tol=args.tol)
+    hd = WS.generate(net, hold, tol=args.tol, anderson=3)
     zero_loss = 0.5 * float((hd.t.double() ** 2).mean())
     held_loss = net.loss_grad(hd.x[:args.batch_size].contiguous(),
                               hd.t[:args.batch_size].contiguous())[0]
@@ -728,7 +728,7 @@ def run_learned(args):
     torch.cuda.synchronize(dev)
     fwd_ms = e0.elapsed_time(e1) / 10
     # the timed region: features + network + unpack + batched solve
-    opts = WS.solver_opts(args.tol)
+    opts = WS.solver_opts(args.tol, anderson=args.anderson)
     learned = [Solver(p, device=dev, init=1, **opts) for p in hold]
     zero = [Solver(p, device=dev, **opts) for p in hold]
     paper = [Solver(p, device=dev, init=2, **opts) for p in hold]  # eq. u0stationary
@@ -778,6 +778,20 @@ def run_learned(args):
     itl = np.array([s["iters"] for s in sl])
     itz = np.array([s["iters"] for s in sz])
     itp = np.array([s["iters"] for s in sp])
+    # where the learned start gains or loses against the paper's u0: the
+    # iteration ratio by decade of mu and by half of the sigma range
+    mus = np.array([p.mu for p in hold])
+    sgs = np.array([p.sigma for p in hold])
+    by_mu = {}
+    for lo in (-4, -3, -2):
+        sel = (np.log10(mus) >= lo) & (np.log10(mus) < lo + 1)
+        if sel.any():
+            by_mu[f"1e{lo}..1e{lo + 1}"] = [int(sel.sum()), float(itl[sel].sum() / itp[sel].sum())]
+    by_sigma = {}
+    for lo, hi in ((0.0, 1.05), (1.05, 3.0)):
+        sel = (sgs >= lo) & (sgs < hi)
+        if sel.any():
+            by_sigma[f"{lo}..{hi}"] = [int(sel.sum()), float(itl[sel].sum() / itp[sel].sum())]
     peak, peak_sus, kind = bf16_peak()
     fwd_tf = CNN_FLOPS_FWD * len(hold) / (fwd_ms * 1e-3) / 1e12
     train_tf = 3 * CNN_FLOPS_FWD * args.batch_size / (step_ms * 1e-3) / 1e12
@@ -794,12 +808,17 @@ def run_learned(args):
         "config": {"workload": f"learned256x{args.hold}", "train_problems": args.train,
                    "network_input": "problem data + the paper's initial state (eq. u0stationary)",
                    "train_steps": args.train_steps, "minibatch": args.batch_size, "tol": args.tol,
+                   "anderson": args.anderson,
                    "step": "paper u0 + features + network + initial states + batched solve of the "
                            "held-out set"},
         "iters_mean": {"zero_init": float(itz.mean()), "paper_u0_init": float(itp.mean()),
                        "learned_init": float(itl.mean()),
                        "ratio": float(itl.sum() / itz.sum()),
-                       "share_of_problems_improved": float((itl < itz).mean())},
+                       "ratio_vs_paper_u0": float(itl.sum() / itp.sum()),
+                       "share_of_problems_improved": float((itl < itz).mean()),
+                       "share_improved_vs_paper_u0": float((itl < itp).mean()),
+                       "share_worse_than_paper_u0": float((itl > itp).mean()),
+                       "learned_over_paper_by_mu": by_mu, "learned_over_paper_by_sigma": by_sigma},
         "ms": {"learned_batched": ms_learned, "zero_batched": ms_zero, "paper_u0_batched": ms_paper,
                "plain_sequential": ms_plain},
         "speedup": {"learned_batched_vs_plain": ms_plain / ms_learned,

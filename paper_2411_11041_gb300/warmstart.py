@@ -42,10 +42,11 @@ def stack(probs, device="cuda:0"):
     return f, b1, b2, m, mu, sg
 
 
-def solver_opts(tol=1e-8, prec=0):
+def solver_opts(tol=1e-8, prec=0, anderson=0):
     """Options of every solve of the warm-start workload (curve -> grid weights
-    by crossing gaps: the flow directions are random, some near a grid axis)."""
-    return dict(tol=tol, max_iter=200000, prec=prec, interp_weights=1)
+    by crossing gaps: the flow directions are random, some near a grid axis;
+    anderson: the accelerated iteration's depth, 0 for the plain one)."""
+    return dict(tol=tol, max_iter=200000, prec=prec, interp_weights=1, anderson=anderson)
 
 
 @dataclasses.dataclass
@@ -61,17 +62,18 @@ def paper_states(solvers):
     return torch.stack([s.paper_u0() for s in solvers])
 
 
-def generate(net: Network, probs, chunk=128, tol=1e-8, prec=0, device="cuda:0"):
+def generate(net: Network, probs, chunk=128, tol=1e-8, prec=0, device="cuda:0", anderson=0):
     """Solve every problem with the batched solver from u_0 = 0 and keep the
     network's features (with the paper's u0) and targets: the cell means of
     u_{j+1} - u0 over max |u0|, u_{j+1} the iterate the solve converged to (its
     fixed point; for theta = 1/2 the reported solution is the midpoint of the
-    last step, which differs from it by the splitting error)."""
+    last step, which differs from it by the splitting error).  The accelerated
+    iteration (anderson > 0) reaches the same fixed point in fewer steps."""
     torch = _torch()
     xs, ts, its = [], [], []
     for k in range(0, len(probs), chunk):
         part = probs[k:k + chunk]
-        solvers = [Solver(p, device=device, **solver_opts(tol, prec)) for p in part]
+        solvers = [Solver(p, device=device, **solver_opts(tol, prec, anderson)) for p in part]
         b = Batch(solvers)
         outs, stats, st, its_u = b.solve(want_iter=True)
         if st != ADR_OK:
