@@ -764,15 +764,23 @@ def run_learned(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_paper = e0.elapsed_time(e1) / args.steps
-    for s in zero:
-        s.solve_stationary()
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for s in zero:
-        s.solve_stationary()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_plain = e0.elapsed_time(e1)
+    # the plain method: one problem after another from u = 0, in chunks of
+    # 256 handles (each handle's own solve keeps a graph and a stream)
+    ms_plain = 0.0
+    plain_opts = WS.solver_opts(args.tol)
+    for k in range(0, len(hold), 256):
+        chunk = [Solver(p, device=dev, **plain_opts) for p in hold[k:k + 256]]
+        for s in chunk:
+            s.solve_stationary()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for s in chunk:
+            s.solve_stationary()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_plain += e0.elapsed_time(e1)
+        for s in chunk:
+            s.close()
     if stl != ADR_OK or stz != ADR_OK or stp != ADR_OK:
         raise RuntimeError("a held-out solve did not converge")
     itl = np.array([s["iters"] for s in sl])

@@ -194,6 +194,15 @@ adr_status finish_direct(Problem* p, int max_iter, double* out, double* iter_out
     return ADR_OK;
 }
 
+// the handle's capture stream and timing events, on first use
+adr_status ensure_stream_events(adr_problem* h)
+{
+    if (!h->cap_stream) ADR_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (!h->ev0) ADR_CUDA_TRY(cudaEventCreate(&h->ev0));
+    if (!h->ev1) ADR_CUDA_TRY(cudaEventCreate(&h->ev1));
+    return ADR_OK;
+}
+
 // Outer iteration from the state in ubuf[0] (the direct transfer: in xu[0]
 // when xu_set, else gathered from ubuf[0]); results into out / iter_out.
 adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
@@ -203,6 +212,7 @@ adr_status run_iteration(adr_problem* h, double theta, double dt, double sig,
 {
     Problem* p = &h->p;
     accel = accel && p->opts.anderson > 0;
+    TRY(ensure_stream_events(h));
     TRY(launch_state_reset(p));
     ADR_CUDA_TRY(cudaEventRecord(h->ev0, p->stream));
     if (p->opts.transfer) {
@@ -482,9 +492,9 @@ adr_status adr_create(const adr_grid* grid, const uint8_t* mask, double mu, doub
         h->line_unknowns[fam] = u;
         if ((s = setup_groups(p, fam, off))) return fail(s);
     }
-    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) ||
-        (e = cudaEventCreate(&h->ev0)) || (e = cudaEventCreate(&h->ev1)))
-        return fail(cuda_fail(e, "stream/event create"));
+    // the capture stream and the timing events come with the handle's first
+    // own solve: a handle solved only inside batches never needs them, and
+    // thousands of handles would otherwise hold thousands of streams
     if ((e = cudaStreamSynchronize(p->stream))) return fail(cuda_fail(e, "adr_create"));
     *out = h;
     return ADR_OK;
