@@ -701,7 +701,7 @@ def run_learned(args):
     train = W.learned(args.train, n=256)
     hold = W.learned(args.hold, n=256, seed=W.SEED_BASE + 5)
     draw_s = time.perf_counter() - t0
-    net = Network(max(args.batch_size, args.hold))
+    net = Network(max(args.batch_size, min(args.hold, 512)))
     t0 = time.perf_counter()
     data = WS.generate(net, train, tol=args.tol, anderson=3)  # the same fixed points, sooner
     torch.cuda.synchronize(dev)
@@ -717,8 +717,9 @@ def run_learned(args):
     zero_loss = 0.5 * float((hd.t.double() ** 2).mean())
     held_loss = net.loss_grad(hd.x[:args.batch_size].contiguous(),
                               hd.t[:args.batch_size].contiguous())[0]
-    # forward of the whole held-out set: the tensor-core kernels alone
-    x = hd.x.contiguous()
+    # forward of (up to 512 of) the held-out set: the tensor-core kernels alone
+    n_fwd = min(len(hold), 512)
+    x = hd.x[:n_fwd].contiguous()
     for _ in range(3):
         net.forward(x)
     e0.record(stream)
@@ -727,43 +728,59 @@ def run_learned(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     fwd_ms = e0.elapsed_time(e1) / 10
-    # the timed region: features + network + unpack + batched solve
+    # the timed region: features + network + unpack + batched solve.  The
+    # held-out set is solved in batches of at most 512 problems (each 256^2
+    # handle holds some 40 MB of curve data, maps and factors): the times add up
     opts = WS.solver_opts(args.tol, anderson=args.anderson)
-    learned = [Solver(p, device=dev, init=1, **opts) for p in hold]
-    zero = [Solver(p, device=dev, **opts) for p in hold]
-    paper = [Solver(p, device=dev, init=2, **opts) for p in hold]  # eq. u0stationary
-    fields = WS.stack(hold, dev)
-    bl, bz, bp = Batch(learned), Batch(zero), Batch(paper)
-
-    def learned_step():
-        return bl.solve(WS.initial_states(net, learned, fields))
-
-    for _ in range(args.warmup):
-        learned_step()
-        bz.solve()
-        bp.solve()
-    torch.cuda.synchronize(dev)
+    ms_learned = ms_zero = ms_paper = 0.0
+    sl, sz, sp = [], [], []
+    stl = stz = stp = ADR_OK
     clocks = Clocks(0)
     clocks.start()
-    e0.record(stream)
-    for _ in range(args.steps):
-        _, sl, stl = learned_step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
+    for k in range(0, len(hold), 512):
+        part = hold[k:k + 512]
+        learned = [Solver(p, device=dev, init=1, **opts) for p in part]
+        zero = [Solver(p, device=dev, **opts) for p in part]
+        paper = [Solver(p, device=dev, init=2, **opts) for p in part]  # eq. u0stationary
+        fields = WS.stack(part, dev)
+        bl, bz, bp = Batch(learned), Batch(zero), Batch(paper)
+
+        def learned_step():
+            return bl.solve(WS.initial_states(net, learned, fields))
+
+        for _ in range(args.warmup):
+            learned_step()
+            bz.solve()
+            bp.solve()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, s_l, st_l = learned_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_learned += e0.elapsed_time(e1) / args.steps
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, s_z, st_z = bz.solve()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_zero += e0.elapsed_time(e1) / args.steps
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, s_p, st_p = bp.solve()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_paper += e0.elapsed_time(e1) / args.steps
+        sl += s_l
+        sz += s_z
+        sp += s_p
+        stl, stz, stp = max(stl, st_l), max(stz, st_z), max(stp, st_p)
+        for bb in (bl, bz, bp):
+            bb.close()
+        for s in learned + zero + paper:
+            s.close()
+        del fields
     clk = clocks.stop()
-    ms_learned = e0.elapsed_time(e1) / args.steps
-    e0.record(stream)
-    for _ in range(args.steps):
-        _, sz, stz = bz.solve()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_zero = e0.elapsed_time(e1) / args.steps
-    e0.record(stream)
-    for _ in range(args.steps):
-        _, sp, stp = bp.solve()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_paper = e0.elapsed_time(e1) / args.steps
     # the plain method: one problem after another from u = 0, in chunks of
     # 256 handles (each handle's own solve keeps a graph and a stream)
     ms_plain = 0.0
@@ -801,7 +818,7 @@ def run_learned(args):
         if sel.any():
             by_sigma[f"{lo}..{hi}"] = [int(sel.sum()), float(itl[sel].sum() / itp[sel].sum())]
     peak, peak_sus, kind = bf16_peak()
-    fwd_tf = CNN_FLOPS_FWD * len(hold) / (fwd_ms * 1e-3) / 1e12
+    fwd_tf = CNN_FLOPS_FWD * n_fwd / (fwd_ms * 1e-3) / 1e12
     train_tf = 3 * CNN_FLOPS_FWD * args.batch_size / (step_ms * 1e-3) / 1e12
     # kernels per timed step: the paper's u0 (4 per problem), features, 8
     # convolutions, one unpack per problem, then per batch iteration 2 curve
@@ -818,7 +835,7 @@ def run_learned(args):
                    "train_steps": args.train_steps, "minibatch": args.batch_size, "tol": args.tol,
                    "anderson": args.anderson,
                    "step": "paper u0 + features + network + initial states + batched solve of the "
-                           "held-out set"},
+                           "held-out set (batches of at most 512 problems)"},
         "iters_mean": {"zero_init": float(itz.mean()), "paper_u0_init": float(itp.mean()),
                        "learned_init": float(itl.mean()),
                        "ratio": float(itl.sum() / itz.sum()),
@@ -838,7 +855,7 @@ def run_learned(args):
         "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
                      "frac": fwd_tf / peak, "traffic": None, "peak_kind": kind + " bf16 burst",
                      "kernel": "network forward (8 BF16 convolutions)", "kernel_ms": fwd_ms,
-                     "units_per_launch": len(hold)},
+                     "units_per_launch": n_fwd},
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
