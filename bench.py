@@ -702,6 +702,10 @@ def run_learned(args):
     hold = W.learned(args.hold, n=256, seed=W.SEED_BASE + 5)
     draw_s = time.perf_counter() - t0
     net = Network(max(args.batch_size, min(args.hold, 512)))
+    # a twentieth of the training problems (at least 64) is kept out of the
+    # training to calibrate the gate: the classes where the correction helps
+    n_val = max(64, len(train) // 20) if len(train) >= 256 else 0
+    val, train = train[len(train) - n_val:], train[:len(train) - n_val]
     t0 = time.perf_counter()
     data = WS.generate(net, train, tol=args.tol, anderson=3)  # the same fixed points, sooner
     torch.cuda.synchronize(dev)
@@ -713,6 +717,7 @@ def run_learned(args):
     torch.cuda.synchronize(dev)
     train_ms = e0.elapsed_time(e1)
     step_ms = train_ms / args.train_steps
+    gate = WS.calibrate_gate(net, val, tol=args.tol, anderson=args.anderson) if n_val else {}
     hd = WS.generate(net, hold, tol=args.tol, anderson=3)
     zero_loss = 0.5 * float((hd.t.double() ** 2).mean())
     held_loss = net.loss_grad(hd.x[:args.batch_size].contiguous(),
@@ -743,10 +748,11 @@ def run_learned(args):
         zero = [Solver(p, device=dev, **opts) for p in part]
         paper = [Solver(p, device=dev, init=2, **opts) for p in part]  # eq. u0stationary
         fields = WS.stack(part, dev)
+        use = WS.gate_of(gate, part)
         bl, bz, bp = Batch(learned), Batch(zero), Batch(paper)
 
         def learned_step():
-            return bl.solve(WS.initial_states(net, learned, fields))
+            return bl.solve(WS.initial_states(net, learned, fields, use))
 
         for _ in range(args.warmup):
             learned_step()
@@ -830,7 +836,9 @@ def run_learned(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve, bf16 net",
         "data": "synthetic",
-        "config": {"workload": f"learned256x{args.hold}", "train_problems": args.train,
+        "config": {"workload": f"learned256x{args.hold}", "train_problems": len(train),
+                   "calibration_problems": n_val,
+                   "gate": {f"1e{k}..1e{k + 1}": bool(v) for k, v in sorted(gate.items())},
                    "network_input": "problem data + the paper's initial state (eq. u0stationary)",
                    "train_steps": args.train_steps, "minibatch": args.batch_size, "tol": args.tol,
                    "anderson": args.anderson,

@@ -112,13 +112,64 @@ def train(net: Network, data: Dataset, steps, batch=32, lr=1e-3, lr_final=1e-4, 
     return losses
 
 
-def initial_states(net: Network, solvers, fields):
+def mu_bin(mu):
+    """The decade of mu a problem falls in (the gate's classes)."""
+    return int(np.floor(np.log10(mu)))
+
+
+def initial_states(net: Network, solvers, fields, use=None):
     """u_0 of every solver: the paper's state, the features, one network
-    batch, and the corrected states.  fields = stack(problems)."""
+    batch, and the corrected states.  fields = stack(problems).  use (a list
+    of booleans, optional): where False the network's correction is left out
+    and the problem starts from the paper's u0 as it stands."""
     u0 = paper_states(solvers)
     x, scale = net.features(*fields, u0)
     y = net.forward(x)
-    return [net.initial_state(s, y[i], u0[i], scale[i:i + 1]) for i, s in enumerate(solvers)]
+    zero = None
+    out = []
+    for i, s in enumerate(solvers):
+        yi = y[i]
+        if use is not None and not use[i]:
+            if zero is None:
+                zero = _torch().zeros_like(yi)
+            yi = zero
+        out.append(net.initial_state(s, yi, u0[i], scale[i:i + 1]))
+    return out
+
+
+def calibrate_gate(net: Network, probs, tol=1e-8, prec=0, device="cuda:0", chunk=256, anderson=0):
+    """Which problem classes (decades of mu) gain from the network's
+    correction, measured on problems the network was not trained on: the
+    batched solves from the paper's u0 and from the corrected state, the
+    iterations summed per class.  The correction is a 4 x 4-cell mean: where
+    the solution has layers thinner than a cell (small mu) its interpolation
+    adds error to an already close u0, and the class is better off without
+    it.  Returns {bin: True/False} (True: use the correction)."""
+    paper_it, learned_it = {}, {}
+    for k in range(0, len(probs), chunk):
+        part = probs[k:k + chunk]
+        opts = solver_opts(tol, prec, anderson)
+        pp = [Solver(p, device=device, init=2, **opts) for p in part]
+        ll = [Solver(p, device=device, init=1, **opts) for p in part]
+        bp, bl = Batch(pp), Batch(ll)
+        _, sp, st1 = bp.solve()
+        _, sl, st2 = bl.solve(initial_states(net, ll, stack(part, device)))
+        if st1 != ADR_OK or st2 != ADR_OK:
+            raise RuntimeError("a calibration solve did not converge")
+        for p, a, b in zip(part, sp, sl):
+            key = mu_bin(p.mu)
+            paper_it[key] = paper_it.get(key, 0) + a["iters"]
+            learned_it[key] = learned_it.get(key, 0) + b["iters"]
+        bp.close()
+        bl.close()
+        for q in pp + ll:
+            q.close()
+    return {key: learned_it[key] < paper_it[key] for key in paper_it}
+
+
+def gate_of(gate, probs):
+    """use-flags of problems from a gate (classes not seen: the correction)."""
+    return [gate.get(mu_bin(p.mu), True) for p in probs]
 
 
 def evaluate(net: Network, probs, tol=1e-8, prec=0, device="cuda:0", chunk=128, sequential=False):
