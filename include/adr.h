@@ -247,7 +247,9 @@ adr_status adr_split_step(adr_problem* prob, double dt, const double* u, double*
 /*
  * adr_paper_u0 -- the paper's initial state for advection-dominated problems
  * (§5 eq. u0stationary): one steady solve s_i(u0, w) = <l_i, w> on every B
- * curve, mapped to the grid.  u0: device [ny][nx].  Errors: ADR_ECUDA.
+ * curve, mapped to the grid.  u0: device [ny][nx].  The work is enqueued on
+ * the handle's stream and the call returns without waiting for it (many
+ * handles' states can then be formed back to back).  Errors: ADR_ECUDA.
  */
 adr_status adr_paper_u0(adr_problem* prob, double* u0);
 

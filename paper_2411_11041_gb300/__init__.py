@@ -345,7 +345,9 @@ class Solver:
 
     def paper_u0(self):
         out = self._grid()
-        adr_paper_u0(self.h, out)
+        adr_paper_u0(self.h, out)  # enqueued on the handle's stream
+        if self.stream is not None:
+            self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
         return out
 
     def set_warm_start(self, net):

@@ -42,6 +42,24 @@ struct ItemSet {
     float* lanec32 = nullptr; // the same in FP32 (reduced-precision mode)
 };
 
+// A factorisation of family 0's curve systems that is not the active one:
+// the family keeps the steady start's (eq. u0stationary) and the iteration's
+// side by side, so that switching between them costs no refactorisation.
+// When allocated, its kind (paper) is always the other one than the active.
+struct FacState {
+    bool allocated = false;
+    double* fac = nullptr;
+    float* fac32 = nullptr;
+    double* srow = nullptr;
+    double* Fl = nullptr;
+    double* lanec[3] = {nullptr, nullptr, nullptr};
+    float* lanec32[3] = {nullptr, nullptr, nullptr};
+    bool valid = false;
+    double td = 0, dt = 0, sig = 0;
+    int paper = 0, vform = 0;
+    bool load_plain = false;
+};
+
 // One curve family in structure-of-arrays form.  Curves are stored back to
 // back: curve l owns nodes off[l] .. off[l+1]-1 (both ends on the boundary).
 struct Family {
@@ -78,6 +96,7 @@ struct Family {
     double prep_td = 0, prep_dt = 0, prep_sig = 0;
     int prep_paper = 0, prep_vform = 0;
     bool load_plain = false;  // Fl holds M f without extra load
+    FacState alt;             // family 0: the other factorisation (steady start / iteration)
     // curve -> grid map, per grid node: 4 crossings (row L, row R, col D, col U)
     int* cg = nullptr;        // [4*N] first node of the crossed segment (-1 boundary)
     double* ct = nullptr;     // [4*N] position in that segment
@@ -230,6 +249,9 @@ adr_status load_family(Problem* p, const double* fextra, double fx_scale);
 adr_status launch_line_solve(Problem* p, int fam, double dt, const double* u_even,
                              const double* u_odd, bool use_state, int paper);
 adr_status launch_mask_copy(Problem* p, const double* in, double* out);
+// make the iteration's factorisation family 0's active one (sweep.cu); a
+// batch reads the active buffers once, when it is built
+adr_status ensure_iteration_active(Problem* p);
 // Anderson extrapolation (accel.cu)
 adr_status launch_anderson(Problem* p);
 adr_status alloc_anderson(Problem* p);

@@ -645,8 +645,8 @@ adr_status adr_paper_u0(adr_problem* h, double* u0)
     TRY(load_family(p, nullptr, 0.0));
     TRY(launch_line_solve(p, 0, 1.0, nullptr, nullptr, false, 1));
     TRY(launch_grid_map_ex(p, 0, u0, u0, 0, nullptr, nullptr, false, false));
-    ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
-    return ADR_OK;
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;  // enqueued on the handle's stream
 }
 
 int adr_num_lines(const adr_problem* h, int fam)

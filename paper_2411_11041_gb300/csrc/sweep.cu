@@ -1345,9 +1345,12 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
     return ADR_OK;
 }
 
+static void free_alt(Problem* p, Family& F);
+
 void release_groups(Problem* p, int fam)
 {
     Family& F = p->fam[fam];
+    if (F.alt.allocated) free_alt(p, F);
     void* bufs[] = {F.soff, F.gcell, F.gw, F.fac, F.fac32, F.Fl, F.srow, F.kap};
     for (void* q : bufs) dev_free(p, q);
     F.kap = nullptr;
@@ -1370,11 +1373,83 @@ void release_groups(Problem* p, int fam)
     F.load_plain = false;
 }
 
+// exchange family 0's active factorisation with the one it keeps aside
+static void swap_fac(Family& F)
+{
+    FacState& A = F.alt;
+    std::swap(F.fac, A.fac);
+    std::swap(F.fac32, A.fac32);
+    std::swap(F.srow, A.srow);
+    std::swap(F.Fl, A.Fl);
+    for (int k = 0; k < kItemSets; ++k) {
+        std::swap(F.iset[k].lanec, A.lanec[k]);
+        std::swap(F.iset[k].lanec32, A.lanec32[k]);
+    }
+    std::swap(F.prep_valid, A.valid);
+    std::swap(F.prep_td, A.td);
+    std::swap(F.prep_dt, A.dt);
+    std::swap(F.prep_sig, A.sig);
+    std::swap(F.prep_paper, A.paper);
+    std::swap(F.prep_vform, A.vform);
+    std::swap(F.load_plain, A.load_plain);
+}
+
+// buffers for family 0's second factorisation (kind = paper), sized as the first
+static adr_status alloc_alt(Problem* p, int paper)
+{
+    Family& F = p->fam[0];
+    FacState& A = F.alt;
+    const size_t NS = F.n_slots;
+    const bool ref = p->opts.prec == ADR_FP32_REFINE;
+    TRY_S(dev_alloc(p, &A.fac, 4 * NS));
+    if (ref) TRY_S(dev_alloc(p, &A.fac32, 4 * NS));
+    TRY_S(dev_alloc(p, &A.srow, 3 * NS));
+    TRY_S(dev_alloc(p, &A.Fl, NS));
+    for (int k = 0; k < kItemSets; ++k) {
+        const ItemSet& I = F.iset[k];
+        if (!I.count) continue;
+        const size_t nf = 2 * (8 + k) + 2;
+        TRY_S(dev_alloc(p, &A.lanec[k], (size_t)I.count * nf * I.BS));
+        if (ref) TRY_S(dev_alloc(p, &A.lanec32[k], (size_t)I.count * nf * I.BS));
+    }
+    A.allocated = true;
+    A.valid = false;
+    A.paper = paper;
+    A.load_plain = false;
+    return ADR_OK;
+}
+
+static void free_alt(Problem* p, Family& F)
+{
+    FacState& A = F.alt;
+    void* bufs[] = {A.fac, A.fac32, A.srow, A.Fl};
+    for (void* q : bufs) dev_free(p, q);
+    for (int k = 0; k < kItemSets; ++k) {
+        dev_free(p, A.lanec[k]);
+        dev_free(p, A.lanec32[k]);
+    }
+    A = FacState();
+}
+
+adr_status ensure_iteration_active(Problem* p)
+{
+    Family& F = p->fam[0];
+    if (!F.prep_paper) return ADR_OK;
+    if (!F.alt.allocated) TRY_S(alloc_alt(p, 0));
+    swap_fac(F);
+    return ADR_OK;
+}
+
 // Factor the family's curve systems for (theta dt, dt, sigma) or the steady
-// start (paper), and record the smallest Thomas pivot of the family.
+// start (paper), and record the smallest Thomas pivot of the family.  Family
+// 0 keeps both kinds once both were asked for (see FacState).
 adr_status prepare_family(Problem* p, int fam, double td, double dt, double sig, int paper)
 {
     Family& F = p->fam[fam];
+    if (fam == 0 && F.prep_paper != paper) {
+        if (!F.alt.allocated) TRY_S(alloc_alt(p, paper));
+        swap_fac(F);  // the kept factorisation is the kind asked for
+    }
     const int vform = (p->opts.prec == ADR_FP64 && !paper) ? 1 : 0;
     if (F.prep_valid && F.prep_td == td && F.prep_dt == dt && F.prep_sig == sig &&
         F.prep_paper == paper)
@@ -1385,9 +1460,12 @@ adr_status prepare_family(Problem* p, int fam, double td, double dt, double sig,
     F.prep_paper = paper;
     F.prep_vform = vform;
     CurveArgs a = curve_args(p, fam);
-    a.pivmin = p->pivmin + fam;
     cudaStream_t st = p->stream;
-    k_set_bits<<<1, 1, 0, st>>>(a.pivmin, 0x7ff0000000000000ull);  // +inf: no pivot yet
+    if (!paper) {
+        // the smallest pivot is the iteration's systems' (the steady start's is not scanned)
+        a.pivmin = p->pivmin + fam;
+        k_set_bits<<<1, 1, 0, st>>>(a.pivmin, 0x7ff0000000000000ull);  // +inf: no pivot yet
+    }
 #define ADR_PREP(BS_, I_)                                                                          \
     if (I_.count) {                                                                                \
         if (fam == 0)                                                                              \
@@ -1735,6 +1813,10 @@ adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const 
     std::vector<double*> parts(n);
     for (int i = 0; i < n; ++i) {
         Problem* p = ps[i];
+        {
+            adr_status se = ensure_iteration_active(p);  // the tables hold its buffers
+            if (se != ADR_OK) return fail(se);
+        }
         for (int fam = 0; fam < 2; ++fam) {
             CurveArgs a = curve_args(p, fam);
             a.u_even = fam == 0 ? p->ubuf[0] : p->ubuf[2];
