@@ -146,6 +146,7 @@ def calibrate_gate(net: Network, probs, tol=1e-8, prec=0, device="cuda:0", chunk
     adds error to an already close u0, and the class is better off without
     it.  Returns {bin: True/False} (True: use the correction)."""
     paper_it, learned_it = {}, {}
+    chunk = min(chunk, net.max_batch)  # one network batch per chunk
     for k in range(0, len(probs), chunk):
         part = probs[k:k + chunk]
         opts = solver_opts(tol, prec, anderson)
