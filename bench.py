@@ -961,7 +961,7 @@ def run_parabolic(args):
     prob = W.parabolic(n=n)
     dev = torch.device("cuda:0")
     prec = ADR_FP64 if args.prec == "fp64" else ADR_FP32_REFINE
-    s = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec)
+    s = Solver(prob, device=dev, tol=args.tol, max_iter=200000, prec=prec, anderson=args.anderson)
     unknowns = s.line_unknowns()
     u0 = torch.tensor(prob.u0, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -971,7 +971,7 @@ def run_parabolic(args):
     s.step_parabolic(u, dt, n_check, 1)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    o = O.Oracle(prob)
+    o = O.Oracle(prob, anderson=args.anderson)
     ref, ref_iters, ost = o.step_parabolic(prob.u0, dt, n_check, 1, tol=args.tol, max_iter=200000)
     oracle_check_s = time.perf_counter() - t0
     err_first = rel_err(u.cpu().numpy(), ref)
@@ -1004,13 +1004,15 @@ def run_parabolic(args):
             "dtype": "f64" if prec == ADR_FP64 else "f32+f64", "data": "synthetic",
             "config": {"workload": f"parabolic{n}", "nodes": n * n, "dt": dt, "time_steps": nsteps,
                        "mu": prob.mu, "sigma": prob.sigma, "tol": args.tol, "mode": 1,
+                       "anderson": args.anderson,
                        "line_unknowns_per_split_step": unknowns,
                        "split_steps_per_run": iters[-1],
                        "split_steps_per_slice": iters[-1] / nsteps,
                        "ms_per_time_step": ms / nsteps,
                        "step": f"one {nsteps}-step run from the Gaussian blob",
                        "l2": "working set ~250 MB > 129 MB L2"},
-            "roofline": roof, "gpu_launches": int(iters[-1] * 5 + nsteps * 4), "clocks": clk,
+            "roofline": roof,
+            "gpu_launches": int(iters[-1] * (5 + (3 if args.anderson else 0)) + nsteps * 4), "clocks": clk,
             "err_vs_oracle": {"measure": "max |u - u_oracle| / max |u_oracle|",
                               "first_slices": n_check, args.prec: err_first,
                               "oracle_split_steps": ref_iters, "oracle_secs": oracle_check_s}}
@@ -1044,7 +1046,8 @@ def run_manufactured(args):
     tol = 1e-10
     prob = W.manufactured(n=n)
     dev = torch.device("cuda:0")
-    s = Solver(prob, device=dev, tol=tol, max_iter=200000)
+    s = Solver(prob, device=dev, tol=tol, max_iter=200000, anderson=args.anderson,
+               transfer=int(args.transfer == "direct"))
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         s.solve_stationary()
@@ -1058,7 +1061,7 @@ def run_manufactured(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
-    o = O.Oracle(prob)
+    o = O.Oracle(prob, anderson=args.anderson, transfer=int(args.transfer == "direct"))
     t0 = time.perf_counter()
     ref, _, it, _, _ = o.solve_stationary(tol=tol, max_iter=200000)
     secs = time.perf_counter() - t0
@@ -1069,6 +1072,7 @@ def run_manufactured(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"manufactured{n}", "nodes": n * n, "tol": tol,
+                       "anderson": args.anderson, "transfer": args.transfer,
                        "split_steps": st["iters"], "step": "one stationary solve to tol from u=0",
                        "l2": "fits in L2: a latency case"},
             "err_vs_oracle": {"measure": "max |u - u_oracle| / max |u_oracle|", "fp64": rel_err(ug, ref),
