@@ -589,6 +589,9 @@ def run_batch(args):
                for p in probs]
     setup_s = time.perf_counter() - t0
     batch = Batch(solvers)
+    t0 = time.perf_counter()
+    tuned_rows, tuned_ms = batch.autotune(reps=5)  # rows per thread by measurement, before timing
+    tune_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         batch.solve()
@@ -659,7 +662,9 @@ def run_batch(args):
                        "parallelism": f"problems split over {ws} rank(s), LPT on estimated work",
                        "estimated_load_per_rank": loads},
             "plain_sequential_ms": ms_plain, "batched_speedup": ms_plain / ms_batch,
-            "setup_s": setup_s, "tail": tail}
+            "setup_s": setup_s, "tail": tail,
+            "autotune": {"rows_per_thread": tuned_rows, "ms_per_batched_split_step": tuned_ms,
+                         "tune_s": tune_s}}
     line["config"]["anderson"] = args.anderson
     line.update(unaccel)
     if rank == 0:

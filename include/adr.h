@@ -283,7 +283,9 @@ adr_status adr_autotune(adr_problem* prob, int reps, int* rows_per_thread,
  * whole outer loop of the batch is one CUDA graph whose WHILE condition stays
  * set while any problem is active.  Each problem keeps its own options (dt,
  * theta, tol, max_iter, init) and convergence test; a converged problem drops
- * out of the later launches.  All handles must share the precision mode.
+ * out of the later launches.  All handles must share the precision mode;
+ * handles with opts.transfer == 1 are refused; opts.anderson may differ per
+ * handle (0: that problem is not extrapolated).
  *
  * adr_batch_create: probs (host array of n handles, not owned; they must
  * outlive the batch and must not be used concurrently with it).  stream: the
@@ -294,6 +296,12 @@ adr_status adr_autotune(adr_problem* prob, int reps, int* rows_per_thread,
  * nullable device grids <- u_{j+1}, the iterate, as in adr_solve_stationary),
  * stats (nullable host array of n; ms = device time of the whole batch).  Returns ADR_ENOCONV if a problem hit
  * max_iter (all outputs written).
+ * adr_batch_autotune: times reps batched split steps from u = 0 for 4, 8 and
+ * 16 rows per thread (every handle of the batch regrouped each time: the
+ * handles' own cached solve graphs are dropped) and keeps the fastest; the
+ * batch is then rebuilt with its handles' options.  rows_out, ms_out
+ * (nullable): the choice and its device time per split step.  Errors:
+ * ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA.
  * adr_solve_batch: create, solve from the handles' initial states, destroy.
  */
 typedef struct adr_batch adr_batch;
@@ -301,6 +309,7 @@ adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_
 adr_status adr_batch_solve(adr_batch* batch, const double* const* u_init, double* const* u_out,
                            double* const* u_iter_out, adr_stats* stats);
 void adr_batch_destroy(adr_batch* batch);
+adr_status adr_batch_autotune(adr_batch* batch, int reps, int* rows_out, double* ms_out);
 adr_status adr_solve_batch(adr_problem* const* probs, int n, double* const* u_out,
                            adr_stats* stats);
 

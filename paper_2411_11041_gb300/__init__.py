@@ -91,6 +91,7 @@ def lib():
                                       C.POINTER(adr_stats)]
         L.adr_batch_destroy.argtypes = [vp]
         L.adr_batch_destroy.restype = None
+        L.adr_batch_autotune.argtypes = [vp, C.c_int, ip, dp]
         L.adr_solve_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(adr_stats)]
         fp = C.POINTER(C.c_float)
         L.adr_cnn_num_params.argtypes = []
@@ -117,7 +118,7 @@ EXPORTED = ["adr_default_opts", "adr_create", "adr_solve_stationary", "adr_step_
             "adr_destroy", "adr_last_error", "adr_num_lines", "adr_num_line_nodes",
             "adr_get_lines", "adr_get_crossings", "adr_get_transfer", "adr_split_step", "adr_paper_u0",
             "adr_time_kernels", "adr_batch_create", "adr_batch_solve", "adr_batch_destroy",
-            "adr_solve_batch", "adr_autotune",
+            "adr_solve_batch", "adr_autotune", "adr_batch_autotune",
             "adr_cnn_num_params", "adr_cnn_create", "adr_cnn_destroy", "adr_cnn_set_params",
             "adr_cnn_get_params", "adr_cnn_features", "adr_cnn_targets", "adr_cnn_forward",
             "adr_cnn_loss_grad", "adr_cnn_train_step", "adr_cnn_initial_state",
@@ -417,6 +418,14 @@ class Batch:
         if want_iter:
             return outs, stats, st, its
         return outs, stats, st
+
+    def autotune(self, reps=5):
+        """Rows per thread of the batch's curve solves by measurement
+        (adr_batch_autotune): (rows, ms per batched split step)."""
+        r, ms = C.c_int(0), C.c_double(0)
+        _check(lib().adr_batch_autotune(self.b, int(reps), C.byref(r), C.byref(ms)),
+               "adr_batch_autotune")
+        return r.value, ms.value
 
     def close(self):
         if getattr(self, "b", None):

@@ -845,6 +845,10 @@ adr_status on_batch_stream(adr_batch* b, F f)
     return s;
 }
 
+// the batch's device tables and its loop graph: WHILE(any problem active)
+// { batched split step }; an earlier build of them is released first
+adr_status build_batch(adr_batch* b, const double* tols, const int* maxit);
+
 adr_status prepare_batch(adr_batch* b)
 {
     for (size_t i = 0; i < b->hs.size(); ++i) {
@@ -854,6 +858,45 @@ adr_status prepare_batch(adr_batch* b)
         TRY(prepare_family(p, 1, td, b->dts[i], p->sigma, 0));
         TRY(load_family(p, nullptr, 0.0));
     }
+    return ADR_OK;
+}
+
+adr_status build_batch(adr_batch* b, const double* tols, const int* maxit)
+{
+    const int n = (int)b->hs.size();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    if (b->dev) {
+        cudaStreamSynchronize(b->stream);
+        batch_dev_destroy(b->dev);
+        b->dev = nullptr;
+    }
+    std::vector<Problem*> ps(n);
+    for (int i = 0; i < n; ++i) ps[i] = &b->hs[i]->p;
+    TRY(batch_dev_create(ps.data(), n, b->dts.data(), tols, maxit, &b->dev));
+    TRY(on_batch_stream(b, [&] { return prepare_batch(b); }));
+    ADR_CUDA_TRY(cudaGraphCreate(&b->graph, 0));
+    cudaGraphConditionalHandle cond;
+    ADR_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, b->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    ADR_CUDA_TRY(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ADR_CUDA_TRY(cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeRelaxed));
+    adr_status s = batch_dev_step(b->dev, b->cap_stream, cond);
+    cudaGraph_t cap = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &cap);
+    if (s) return s;
+    if (e) return cuda_fail(e, "cudaStreamEndCapture");
+    ADR_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    ADR_CUDA_TRY(cudaStreamSynchronize(b->stream));
     return ADR_OK;
 }
 
@@ -916,36 +959,8 @@ adr_status adr_batch_create(adr_problem* const* probs, int n, void* stream, adr_
     if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) ||
         (e = cudaEventCreate(&b->ev0)) || (e = cudaEventCreate(&b->ev1)))
         return fail(cuda_fail(e, "batch stream/events"));
-    std::vector<Problem*> ps(n);
-    for (int i = 0; i < n; ++i) ps[i] = &probs[i]->p;
-    adr_status s = batch_dev_create(ps.data(), n, b->dts.data(), tols.data(), maxit.data(), &b->dev);
+    adr_status s = build_batch(b, tols.data(), maxit.data());
     if (s) return fail(s);
-    s = on_batch_stream(b, [&] { return prepare_batch(b); });
-    if (s) return fail(s);
-    // the batch loop as one graph: WHILE(any problem active) { batched split step }
-    if ((e = cudaGraphCreate(&b->graph, 0))) return fail(cuda_fail(e, "cudaGraphCreate"));
-    cudaGraphConditionalHandle cond;
-    if ((e = cudaGraphConditionalHandleCreate(&cond, b->graph, 1, cudaGraphCondAssignDefault)))
-        return fail(cuda_fail(e, "cudaGraphConditionalHandleCreate"));
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = cond;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    if ((e = cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &np)))
-        return fail(cuda_fail(e, "cudaGraphAddNode"));
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    if ((e = cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeRelaxed)))
-        return fail(cuda_fail(e, "cudaStreamBeginCaptureToGraph"));
-    s = batch_dev_step(b->dev, b->cap_stream, cond);
-    cudaGraph_t cap = nullptr;
-    e = cudaStreamEndCapture(b->cap_stream, &cap);
-    if (s) return fail(s);
-    if (e) return fail(cuda_fail(e, "cudaStreamEndCapture"));
-    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0))) return fail(cuda_fail(e, "cudaGraphInstantiate"));
-    if ((e = cudaStreamSynchronize(b->stream))) return fail(cuda_fail(e, "adr_batch_create"));
     *out = b;
     return ADR_OK;
 }
@@ -1011,6 +1026,67 @@ adr_status adr_batch_solve(adr_batch* b, const double* const* u_init, double* co
         set_error("a problem of the batch reached max_iter before tol");
         return ADR_ENOCONV;
     }
+    return ADR_OK;
+}
+
+adr_status adr_batch_autotune(adr_batch* b, int reps, int* rows_out, double* ms_out)
+{
+    g_err.clear();
+    if (!b || reps < 1) {
+        set_error("bad arguments to adr_batch_autotune");
+        return ADR_EINVAL;
+    }
+    const int n = (int)b->hs.size();
+    // every candidate runs exactly reps batched split steps from u = 0
+    std::vector<double> tol0(n, 0.0), tols(n);
+    std::vector<int> capped(n, reps), maxit(n);
+    for (int i = 0; i < n; ++i) {
+        tols[i] = b->hs[i]->p.opts.tol;
+        maxit[i] = b->hs[i]->p.opts.max_iter;
+    }
+    auto set_rows = [&](int R) -> adr_status {
+        for (adr_problem* h : b->hs) {
+            Problem* p = &h->p;
+            if (p->rows_per_thread == R && p->fam[0].iset[0].BS) continue;
+            p->rows_per_thread = R;
+            drop_graph(h);
+            for (int fam = 0; fam < 2; ++fam) {
+                release_groups(p, fam);
+                TRY(setup_groups(p, fam, h->offs[fam]));
+            }
+        }
+        return ADR_OK;
+    };
+    const int rows[3] = {4, 8, 16};
+    int best_r = b->hs[0]->p.rows_per_thread;
+    double best = 1e300;
+    for (int R : rows) {
+        TRY(set_rows(R));
+        TRY(build_batch(b, tol0.data(), capped.data()));
+        float ms = 0.f;
+        adr_status s = on_batch_stream(b, [&]() -> adr_status {
+            for (adr_problem* h : b->hs) {
+                TRY(init_state(h, ADR_INIT_ZERO, nullptr));
+                TRY(launch_state_reset(&h->p));
+            }
+            TRY(batch_dev_reset(b->dev, b->stream));
+            ADR_CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
+            ADR_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+            ADR_CUDA_TRY(cudaEventRecord(b->ev1, b->stream));
+            ADR_CUDA_TRY(cudaStreamSynchronize(b->stream));
+            cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+            return ADR_OK;
+        });
+        TRY(s);
+        if (ms < best) {
+            best = ms;
+            best_r = R;
+        }
+    }
+    TRY(set_rows(best_r));
+    TRY(build_batch(b, tols.data(), maxit.data()));
+    if (rows_out) *rows_out = best_r;
+    if (ms_out) *ms_out = best / reps;
     return ADR_OK;
 }
 

@@ -144,3 +144,67 @@ def test_sheared_2048_accelerated_solve_matches_oracle(torch_cuda, sheared2048_a
     assert abs(stats["iters"] - it) <= 1
     assert relerr(u, ref) <= (TOL64 if stats["iters"] == it else 1e-7)
     s.close()
+
+
+def test_direct_transfer_with_paper_start_and_extrapolation(torch_cuda):
+    """The three options together: the direct transfer, the paper's initial
+    state (the B-curve solutions as they stand) and the extrapolation."""
+    from paper_2411_11041_gb300 import ADR_OK, Solver
+    p = W.sheared(n=65)
+    o = O.Oracle(p, transfer=1, anderson=3)
+    for max_iter, tol in ((11, 0.0), (20000, 1e-11)):
+        s = Solver(p, tol=tol, max_iter=max_iter, init=2, transfer=1, anderson=3)
+        u, uit, stats, st = s.solve_stationary(want_iter=True)
+        ref, refit, it, _, ost = o.solve_stationary(tol=tol, max_iter=max_iter, init=2)
+        assert st == ADR_OK and ost == O.OK and abs(stats["iters"] - it) <= (0 if tol == 0.0 else 1)
+        assert relerr(u, ref) <= (TOL_STEPS if stats["iters"] == it else 1e-10)
+
+
+def test_extrapolation_from_a_caller_state_and_in_a_batch_with_paper_starts(torch_cuda):
+    """ADR_INIT_USER and ADR_INIT_PAPER_U0 with the extrapolation, one by one
+    and as one batch: the same steps and answers."""
+    from paper_2411_11041_gb300 import ADR_OK, Batch, Solver
+    torch = torch_cuda
+    rng = np.random.Generator(np.random.PCG64(41))
+    probs = [W.random_problem(rng, int(n), mask="square") for n in (49, 73, 88)]
+    u0 = [torch.tensor(np.random.default_rng(i).normal(size=(p.ny, p.nx)), device="cuda:0")
+          for i, p in enumerate(probs)]
+    for init in (1, 2):
+        solo = []
+        for p, ui in zip(probs, u0):
+            s = Solver(p, tol=1e-10, max_iter=20000, interp_weights=1, anderson=4, init=init)
+            u, _, st, code = s.solve_stationary(u_init=ui if init == 1 else None)
+            assert code == ADR_OK
+            ref, _, it, _, _ = O.Oracle(p, interp_weights=1, anderson=4).solve_stationary(
+                tol=1e-10, max_iter=20000, init=init, u_init=ui.cpu().numpy() if init == 1 else None)
+            assert abs(st["iters"] - it) <= 1
+            assert relerr(u, ref) <= (TOL64 if st["iters"] == it else 1e-9)
+            solo.append((u, st["iters"]))
+        b = Batch([Solver(p, tol=1e-10, max_iter=20000, interp_weights=1, anderson=4, init=init)
+                   for p in probs])
+        outs, stats, code = b.solve(u0 if init == 1 else None)
+        assert code == ADR_OK
+        for (u, it), o_, s_ in zip(solo, outs, stats):
+            assert s_["iters"] == it
+            assert (o_ - u).abs().max().item() <= 1e-13 * u.abs().max().item()
+
+
+def test_extrapolation_caps_and_single_step(torch_cuda):
+    """max_iter = 1 (no extrapolation happens), a cap reached before tol
+    (ADR_ENOCONV, the state of the last step reported), and max_iter = 0."""
+    from paper_2411_11041_gb300 import ADR_ENOCONV, ADR_OK, Solver
+    p = W.sheared(n=65)
+    o = O.Oracle(p, anderson=3)
+    plain = O.Oracle(p)
+    s1 = Solver(p, tol=0.0, max_iter=1, anderson=3)
+    u1, _, st1, c1 = s1.solve_stationary()
+    r1 = plain.solve_stationary(tol=0.0, max_iter=1)[0]
+    assert c1 == ADR_OK and st1["iters"] == 1 and relerr(u1, r1) <= TOL64
+    s2 = Solver(p, tol=1e-14, max_iter=9, anderson=3)
+    u2, _, st2, c2 = s2.solve_stationary()
+    r2, _, it2, _, oc2 = o.solve_stationary(tol=1e-14, max_iter=9)
+    assert c2 == ADR_ENOCONV and oc2 == O.ENOCONV and st2["iters"] == it2 == 9
+    assert relerr(u2, r2) <= TOL_STEPS
+    s3 = Solver(p, tol=1e-10, max_iter=0, anderson=3)
+    u3, _, st3, c3 = s3.solve_stationary()
+    assert st3["iters"] == 0 and float(u3.abs().max()) == 0.0

@@ -82,3 +82,22 @@ def test_autotune_keeps_the_solution(torch_cuda, tmp_path, monkeypatch):
     assert s2.tuned is None and s2.opts.rows_per_thread == r
     u2, _, _, _ = s2.solve_stationary()
     assert (u2 - u1).abs().max().item() <= 1e-12 * u0.abs().max().item()
+
+
+def test_batch_autotune_keeps_the_answers(torch_cuda):
+    """adr_batch_autotune regroups every handle for each candidate and
+    rebuilds the batch; the solve after it takes the same steps to the same
+    answers (the partitioned eliminations of other chunk sizes round
+    differently, nothing more)."""
+    from paper_2411_11041_gb300 import ADR_OK, Batch, Solver
+    rng = np.random.Generator(np.random.PCG64(51))
+    probs = [W.random_problem(rng, int(n)) for n in (70, 130, 257, 96)]
+    b = Batch([Solver(p, tol=1e-10, max_iter=20000, interp_weights=1) for p in probs])
+    before, sb, cb = b.solve()
+    rows, ms = b.autotune(reps=3)
+    assert rows in (4, 8, 16) and ms > 0
+    after, sa, ca = b.solve()
+    assert cb == ca == ADR_OK
+    for x, y, s0, s1 in zip(before, after, sb, sa):
+        assert abs(s0["iters"] - s1["iters"]) <= 1
+        assert (x - y).abs().max().item() <= 1e-9 * y.abs().max().item()
