@@ -45,17 +45,22 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # (unit = one curve unknown for the curve solves, one grid node for the maps).
 # Bytes count every array the kernel must touch once; flops count the
 # kernel's FP64 arithmetic per unit (fma = 2).
-KERNELS = ["curve solve B", "curve->grid map B", "curve solve G", "curve->grid map G"]
-#   curve solve B: cell 4 + corner weights 32 + load row 8 + rhs rows 24 + factors cp, vp,
-#                  lp 24 + v 8 + u 8 B (load and rhs rows carry the row factor ip);
-#                  gather 7 (1 mul + 3 fma) + rhs 6 (3 fma) + elimination 2 + upward 2 +
-#                  back 4 flop (the new values come out of the solve: no update)
-#   curve solve G: cell 4 + corner weights 32 + rhs coefficient 8 + factors 24 + v 8 + u 8 B;
-#                  gather 7 + rhs 4 (add, fma, mul) + elimination 2 + upward 2 + back 4 flop
-#   maps: crossings 16 + coefficients 64 + type 1 + out 8 (+ u_j 8 for the norms) B, 8 fma
-#         (+ 1 add and 2 fma for the norms)
-BYTES_PER_UNIT = [108.0, 81.0, 84.0, 89.0]
-FLOPS_PER_UNIT = [21.0, 16.0, 19.0, 21.0]
+KERNELS = ["gather B", "curve solve B", "curve->grid map B", "gather G", "curve solve G",
+           "curve->grid map G"]
+#   gathers (unit = curve node): cell 4 + corner weights 32 + grid value 8 + node value out 8 B;
+#                  1 mul + 3 fma = 7 flop
+#   curve solve B (unit = curve unknown): load row 8 + rhs rows 24 + factors cp, vp, lp 24 +
+#                  v 8 + u 8 B (load and rhs rows carry the row factor ip); rhs 6 (3 fma) +
+#                  elimination 2 + upward 2 + back 4 flop (the new values come out of the
+#                  solve: no update)
+#   curve solve G: rhs coefficient 8 + factors 24 + v 8 + u 8 B; rhs 4 (add, fma, mul) +
+#                  elimination 2 + upward 2 + back 4 flop
+#   maps (unit = grid node): crossings 16 + coefficients 64 + type 1 + out 8 (+ u_j 8 for
+#         the norms) B, 8 fma (+ 1 add and 2 fma for the norms)
+# In the reduced-precision mode the solves gather themselves (the gather stages
+# read 0 time) and their figures are the gather's plus the solve's.
+BYTES_PER_UNIT = [52.0, 72.0, 81.0, 52.0, 48.0, 89.0]
+FLOPS_PER_UNIT = [7.0, 14.0, 16.0, 7.0, 12.0, 21.0]
 # The same for the direct curve-to-curve transfer (--transfer direct), whose
 # curve solves read the state at their own nodes and whose transfers replace
 # the maps (unit = one target curve node):
@@ -64,15 +69,15 @@ FLOPS_PER_UNIT = [21.0, 16.0, 19.0, 21.0]
 #   curve solve G: rhs coefficient 8 + factors 24 + v 8 + u 8 B; rhs 4 + 2 + 2 + 4 flop
 #   transfers: two segment indices 8 + four coefficients 32 + source value 8 + out 8
 #              (+ previous state 8 for the norms) B; 1 mul + 3 fma (+ 1 add, 2 fma) flop
-KERNELS_DIRECT = ["curve solve B (node state)", "transfer B->G", "curve solve G (node state)",
-                  "transfer G->B + norms"]
-BYTES_PER_UNIT_DIRECT = [72.0, 56.0, 48.0, 64.0]
-FLOPS_PER_UNIT_DIRECT = [14.0, 7.0, 12.0, 12.0]
+KERNELS_DIRECT = ["(none)", "curve solve B (node state)", "transfer B->G", "(none)",
+                  "curve solve G (node state)", "transfer G->B + norms"]
+BYTES_PER_UNIT_DIRECT = [0.0, 72.0, 56.0, 0.0, 48.0, 64.0]
+FLOPS_PER_UNIT_DIRECT = [0.0, 14.0, 7.0, 0.0, 12.0, 12.0]
 # DRAM bytes per launch (read + write) of each kernel in the bench's launch
 # shape, from one ncu capture of the 2048^2 sheared workload; None where the
 # kernel has changed since the capture
-NCU_TRAFFIC_SHEARED2048 = [535.5e6, 399.0e6, 442.6e6, 435.3e6]
-NCU_TRAFFIC_DIRECT_SHEARED2048 = [351.2e6, 235.3e6, 263.1e6, 258.9e6]
+NCU_TRAFFIC_SHEARED2048 = [None, None, 399.0e6, None, None, 435.3e6]
+NCU_TRAFFIC_DIRECT_SHEARED2048 = [None, 351.2e6, 235.3e6, None, 263.1e6, 258.9e6]
 
 
 def parse():
@@ -920,12 +925,13 @@ def run_data2d(args):
 
 
 def kernel_units(solver, prob, unknowns, direct=False):
-    """Units one launch of each sweep kernel processes (curve unknowns for the
-    solves; grid nodes for the maps; target curve nodes for the transfers)."""
+    """Units one launch of each sweep kernel processes (curve nodes for the
+    gathers and the transfers' targets, curve unknowns for the solves, grid
+    nodes for the maps)."""
+    nodes = [int(solver.lines(f)["off"][-1]) for f in (0, 1)]
     if direct:
-        nodes = [int(solver.lines(f)["off"][-1]) for f in (0, 1)]
-        return [unknowns[0], nodes[1], unknowns[1], nodes[0]]
-    return [unknowns[0], prob.nx * prob.ny, unknowns[1], prob.nx * prob.ny]
+        return [0, unknowns[0], nodes[1], 0, unknowns[1], nodes[0]]
+    return [nodes[0], unknowns[0], prob.nx * prob.ny, nodes[1], unknowns[1], prob.nx * prob.ny]
 
 
 def kernel_roofline(solver, prob, unknowns, direct=False):
@@ -945,9 +951,10 @@ def kernel_roofline(solver, prob, unknowns, direct=False):
             "peak_kind": "FP64 FMA issue peak derived from 152 SMs x 2 FMA/clk x 2.07 GHz",
             "hbm_frac": gbs / hbm, "kernel": names[k], "kernel_ms": kms[k],
             "units_per_launch": units[k], "algorithmic_bytes_per_launch": bpu[k] * units[k],
-            "all_kernels_ms": dict(zip(names, kms)),
+            "all_kernels_ms": {nm: kms[i] for i, nm in enumerate(names) if kms[i] > 0},
             "all_kernels_hbm_frac": {nm: bpu[i] * units[i] / (kms[i] * 1e-3) / 1e9 / hbm
-                                     for i, nm in enumerate(names)}}
+                                     for i, nm in enumerate(names) if kms[i] > 0},
+            "split_step_ms": float(sum(kms))}
 
 
 def run_parabolic(args):

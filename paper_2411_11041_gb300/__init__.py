@@ -225,7 +225,7 @@ def adr_paper_u0(h, u0):
 
 
 def adr_time_kernels(h, reps):
-    ms = (C.c_double * 4)()
+    ms = (C.c_double * 6)()
     _check(lib().adr_time_kernels(h, int(reps), ms), "adr_time_kernels")
     return list(ms)
 
@@ -357,7 +357,8 @@ class Solver:
         self.net = net  # kept alive while attached
 
     def time_kernels(self, reps=20):
-        """Average device ms of [B solve, B map, G solve, G map] per launch."""
+        """Average device ms per launch of [B gather, B solve, B map, G gather,
+        G solve, G map] (0 where a stage has no kernel of its own)."""
         return adr_time_kernels(self.h, reps)
 
     def line_unknowns(self):

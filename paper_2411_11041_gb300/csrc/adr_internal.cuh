@@ -79,6 +79,10 @@ struct Family {
     int n_slots = 0;
     int cmax = 1;             // rows of the longest chunk (a thread's rows) of the family
     int* soff = nullptr;      // [n_lines+1]
+    int* ncell = nullptr;     // [n_nodes] the same cells in node order (-1 at the curves' ends;
+                              // FP64 through the grid: the separate gather pass)
+    double* nw = nullptr;     // [4*n_nodes] the same corner weights in node order
+    double* ug = nullptr;     // [n_nodes] the gathered grid state at the nodes
     int* gcell = nullptr;     // [n_slots] bilinear cell r*nx + i of the row's node
     double* gw = nullptr;     // [4 n_slots] bilinear corner weights (1-lx)(1-ly), lx(1-ly),
                               // (1-lx)ly, lx ly
@@ -269,6 +273,12 @@ struct AaBatchView {
 };
 adr_status anderson_batch_table(Problem* const* ps, int n, void** table, int* mmax);
 adr_status launch_anderson_batch(const AaBatchView& v, cudaStream_t st);
+// the curve solve of one substep through the grid (gather pass + solve in
+// FP64, the solve's own gather otherwise), and its two passes apart
+adr_status launch_substep_solve(Problem* p, int fam, double dt, const double* u_even, const double* u_odd,
+                                bool use_state);
+adr_status launch_gather_pass(Problem* p, int fam, const double* u);
+adr_status launch_solve_pass(Problem* p, int fam, double dt, const double* u);
 // direct transfer between the families (sweep.cu)
 adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u_even,
                                  const double* u_odd, bool use_state);

@@ -148,10 +148,10 @@ adr_status build_graph(adr_problem* h, double theta, double dt, double sig,
         if (s == ADR_OK)
             s = launch_xfer(p, 0, p->fam[1].v, p->xu[0], p->xu[1], 1, p->xu[0], p->xu[1], true, true);
     } else {
-        if (s == ADR_OK) s = launch_line_solve(p, 0, dt, p->ubuf[0], p->ubuf[1], true, 0);
+        if (s == ADR_OK) s = launch_substep_solve(p, 0, dt, p->ubuf[0], p->ubuf[1], true);
         if (s == ADR_OK)
             s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, true, false);
-        if (s == ADR_OK) s = launch_line_solve(p, 1, dt, p->ubuf[2], p->ubuf[2], true, 0);
+        if (s == ADR_OK) s = launch_substep_solve(p, 1, dt, p->ubuf[2], p->ubuf[2], true);
         if (s == ADR_OK)
             s = launch_grid_map_ex(p, 1, p->ubuf[0], p->ubuf[1], 1, p->ubuf[0], p->ubuf[1], true, true);
     }
@@ -624,9 +624,9 @@ adr_status adr_split_step(adr_problem* h, double dt, const double* u, double* u_
         TRY(launch_line_solve_dir(p, 1, dt, p->xuG, p->xuG, false));
         TRY(launch_grid_map_ex(p, 1, u_next, u_next, 0, nullptr, nullptr, false, false));
     } else {
-        TRY(launch_line_solve(p, 0, dt, u, u, false, 0));
+        TRY(launch_substep_solve(p, 0, dt, u, u, false));
         TRY(launch_grid_map_ex(p, 0, half, half, 0, nullptr, nullptr, false, false));
-        TRY(launch_line_solve(p, 1, dt, half, half, false, 0));
+        TRY(launch_substep_solve(p, 1, dt, half, half, false));
         TRY(launch_grid_map_ex(p, 1, u_next, u_next, 0, nullptr, nullptr, false, false));
     }
     ADR_CUDA_TRY(cudaStreamSynchronize(p->stream));
@@ -717,7 +717,7 @@ adr_status adr_autotune(adr_problem* h, int reps, int* rows_out, int* blocks_out
     const int rows[3] = {4, 8, 16}, blocks[3] = {2, 4, 8};
     double best = 1e300;
     int bR = p->rows_per_thread, bM = p->map_blocks_per_sm;
-    double ms[4];
+    double ms[6];
     for (int R : rows) {
         p->rows_per_thread = R;
         drop_graph(h);
@@ -728,7 +728,7 @@ adr_status adr_autotune(adr_problem* h, int reps, int* rows_out, int* blocks_out
         for (int M : blocks) {
             p->map_blocks_per_sm = M;
             TRY(adr_time_kernels(h, reps, ms));
-            double t = ms[0] + ms[1] + ms[2] + ms[3];
+            double t = ms[0] + ms[1] + ms[2] + ms[3] + ms[4] + ms[5];
             if (t < best) {
                 best = t;
                 bR = R;
@@ -762,39 +762,52 @@ adr_status adr_time_kernels(adr_problem* h, int reps, double* ms_out)
     TRY(prepare_family(p, 0, o.theta * dt, dt, p->sigma, 0));
     TRY(prepare_family(p, 1, o.theta * dt, dt, p->sigma, 0));
     TRY(load_family(p, nullptr, 0.0));
-    cudaEvent_t ev[5];
-    for (int k = 0; k < 5; ++k) ADR_CUDA_TRY(cudaEventCreate(&ev[k]));
+    // stages: B gather, B solve, B map (or transfer), G gather, G solve, G map
+    // (or transfer) with the norms; a stage without a kernel of its own (the
+    // gathers inside the solves of the other modes) reads 0
+    const bool split = p->fam[0].ug != nullptr;
+    cudaEvent_t ev[7];
+    for (int k = 0; k < 7; ++k) ADR_CUDA_TRY(cudaEventCreate(&ev[k]));
     adr_status s = ADR_OK;
-    for (int stage = 0; stage < 4 && s == ADR_OK; ++stage) {
+    for (int stage = 0; stage < 6 && s == ADR_OK; ++stage) {
         cudaEventRecord(ev[stage], p->stream);
         for (int r = 0; r < reps && s == ADR_OK; ++r) {
             if (o.transfer) {
                 // B solve, B -> G transfer, G solve, G -> B transfer with norms
                 switch (stage) {
-                case 0:
+                case 1:
                     s = launch_line_solve_dir(p, 0, dt, p->xu[0], p->xu[0], false);
                     break;
-                case 1:
+                case 2:
                     s = launch_xfer(p, 1, p->fam[0].v, p->xuG, p->xuG, 0, nullptr, nullptr, false, false);
                     break;
-                case 2:
+                case 4:
                     s = launch_line_solve_dir(p, 1, dt, p->xuG, p->xuG, false);
                     break;
-                default:
+                case 5:
                     s = launch_xfer(p, 0, p->fam[1].v, p->xu[1], p->xu[1], 0, p->xu[0], p->xu[0], false,
                                     true);
+                    break;
+                default:
+                    break;
                 }
                 continue;
             }
             switch (stage) {
             case 0:
-                s = launch_line_solve(p, 0, dt, p->ubuf[0], p->ubuf[0], false, 0);
+                if (split) s = launch_gather_pass(p, 0, p->ubuf[0]);
                 break;
             case 1:
-                s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, false, false);
+                s = launch_solve_pass(p, 0, dt, p->ubuf[0]);
                 break;
             case 2:
-                s = launch_line_solve(p, 1, dt, p->ubuf[2], p->ubuf[2], false, 0);
+                s = launch_grid_map_ex(p, 0, p->ubuf[2], p->ubuf[2], 0, nullptr, nullptr, false, false);
+                break;
+            case 3:
+                if (split) s = launch_gather_pass(p, 1, p->ubuf[2]);
+                break;
+            case 4:
+                s = launch_solve_pass(p, 1, dt, p->ubuf[2]);
                 break;
             default:
                 s = launch_grid_map_ex(p, 1, p->ubuf[1], p->ubuf[1], 0, p->ubuf[0], p->ubuf[0], false,
@@ -802,15 +815,16 @@ adr_status adr_time_kernels(adr_problem* h, int reps, double* ms_out)
             }
         }
     }
-    cudaEventRecord(ev[4], p->stream);
-    cudaError_t e = cudaEventSynchronize(ev[4]);
+    cudaEventRecord(ev[6], p->stream);
+    cudaError_t e = cudaEventSynchronize(ev[6]);
     if (s == ADR_OK && e != cudaSuccess) s = cuda_fail(e, "adr_time_kernels");
-    for (int k = 0; k < 4 && s == ADR_OK; ++k) {
+    const bool has[6] = {split && !o.transfer, true, true, split && !o.transfer, true, true};
+    for (int k = 0; k < 6 && s == ADR_OK; ++k) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-        ms_out[k] = ms / reps;
+        ms_out[k] = has[k] ? ms / reps : 0.0;
     }
-    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
     return s;
 }
 

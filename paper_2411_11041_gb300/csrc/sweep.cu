@@ -73,6 +73,8 @@ struct CurveArgs {
     const double* h;
     int* gcell;            // per slot: bilinear cell r*nx + i of the row's node
     double* gw;            // 4 planes per slot: the cell's corner weights of the row's node
+    int* ncell;            // per node: the same cell (setup; -1 at the curves' ends)
+    double* nw;            // 4 per node: the same weights (setup)
     const double* bnorm;   // per node
     const double* fval;    // per node
     const double* xi;      // per node (setup of the gather descriptors)
@@ -193,11 +195,47 @@ __global__ void __launch_bounds__(BS) k_curve_gdesc(CurveArgs a, const int* item
         size_t sl = b.so + (size_t)j * b.T + b.lt;
         const size_t NS = a.n_slots;
         const double lx = x - i, ly = y - r;
+        const double w0 = (1.0 - lx) * (1.0 - ly), w1 = lx * (1.0 - ly), w2 = (1.0 - lx) * ly, w3 = lx * ly;
         a.gcell[sl] = r * a.nx + i;
-        a.gw[sl] = (1.0 - lx) * (1.0 - ly);
-        a.gw[NS + sl] = lx * (1.0 - ly);
-        a.gw[2 * NS + sl] = (1.0 - lx) * ly;
-        a.gw[3 * NS + sl] = lx * ly;
+        a.gw[sl] = w0;
+        a.gw[NS + sl] = w1;
+        a.gw[2 * NS + sl] = w2;
+        a.gw[3 * NS + sl] = w3;
+        if (a.ncell) {  // the same descriptor in node order (the separate gather pass)
+            a.ncell[node] = r * a.nx + i;
+            a.nw[4 * (size_t)node] = w0;
+            a.nw[4 * (size_t)node + 1] = w1;
+            a.nw[4 * (size_t)node + 2] = w2;
+            a.nw[4 * (size_t)node + 3] = w3;
+        }
+    }
+}
+
+// the grid state at every node of a family from the node-order descriptors
+// (the same corner products, in the same order, as the solve's own gather);
+// 0 at the curves' ends.  The grid by the step's parity when state is given.
+__global__ void __launch_bounds__(256) k_gather_grid(long long n, const int* __restrict__ ncell,
+                                                     const double* __restrict__ nw, int nx,
+                                                     const double* u_even, const double* u_odd,
+                                                     const IterState* state, double* __restrict__ out)
+{
+    if (state && state->done) return;
+    const double* __restrict__ u = (state && (state->iter & 1)) ? u_odd : u_even;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int c = __ldg(ncell + k);
+        double v = 0.0;
+        if (c >= 0) {
+            const double2 wa = *reinterpret_cast<const double2*>(nw + 4 * k);
+            const double2 wb = *reinterpret_cast<const double2*>(nw + 4 * k + 2);
+            const double* r0 = u + c;
+            const double p11 = __ldg(r0), p12 = __ldg(r0 + 1), p21 = __ldg(r0 + nx), p22 = __ldg(r0 + nx + 1);
+            v = wa.x * p11;
+            v = fma(wa.y, p12, v);
+            v = fma(wb.x, p21, v);
+            v = fma(wb.y, p22, v);
+        }
+        out[k] = v;
     }
 }
 
@@ -1223,6 +1261,8 @@ static CurveArgs curve_args(Problem* p, int fam)
     a.h = F.h;
     a.gcell = F.gcell;
     a.gw = F.gw;
+    a.ncell = F.ncell;
+    a.nw = F.nw;
     a.bnorm = F.bnorm;
     a.fval = F.fval;
     a.xi = F.xi;
@@ -1299,6 +1339,14 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
                                  p->stream));
     TRY_S(dev_alloc(p, &F.gcell, NS));
     TRY_S(dev_alloc(p, &F.gw, 4 * NS));
+    if (p->opts.prec == ADR_FP64 && !p->opts.transfer) {
+        // node-order gather descriptors and node values of the separate gather pass
+        const size_t nn = (size_t)F.n_nodes + 1;
+        TRY_S(dev_alloc(p, &F.ncell, nn));
+        TRY_S(dev_alloc(p, &F.nw, 4 * nn));
+        TRY_S(dev_alloc(p, &F.ug, nn));
+        ADR_CUDA_TRY(cudaMemsetAsync(F.ncell, 0xff, sizeof(int) * nn, p->stream));  // -1: curve ends
+    }
     TRY_S(dev_alloc(p, &F.fac, 4 * NS));
     if (p->opts.prec == ADR_FP32_REFINE) TRY_S(dev_alloc(p, &F.fac32, 4 * NS));
     if (fam == 0) {
@@ -1351,8 +1399,11 @@ void release_groups(Problem* p, int fam)
 {
     Family& F = p->fam[fam];
     if (F.alt.allocated) free_alt(p, F);
-    void* bufs[] = {F.soff, F.gcell, F.gw, F.fac, F.fac32, F.Fl, F.srow, F.kap};
+    void* bufs[] = {F.soff, F.gcell, F.gw, F.fac, F.fac32, F.Fl, F.srow, F.kap, F.ncell, F.nw, F.ug};
     for (void* q : bufs) dev_free(p, q);
+    F.ncell = nullptr;
+    F.nw = nullptr;
+    F.ug = nullptr;
     F.kap = nullptr;
     F.soff = nullptr;
     F.gcell = nullptr;
@@ -1600,6 +1651,41 @@ adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u
 #undef ADR_SOLVE_DIR
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
+}
+
+// one curve solve through the grid in FP64: the gather pass into the
+// family's node values, then the curve solve from them (the same arithmetic
+// as the solve's own gather, split so that the gathers' latency does not
+// hold up the elimination chain); other modes keep the gather in the solve
+adr_status launch_substep_solve(Problem* p, int fam, double dt, const double* u_even, const double* u_odd,
+                                bool use_state)
+{
+    Family& F = p->fam[fam];
+    if (!F.ug) return launch_line_solve(p, fam, dt, u_even, u_odd, use_state, 0);
+    const long long n = F.n_nodes;
+    const int blocks = grid_map_blocks(p);
+    k_gather_grid<<<blocks, 256, 0, p->stream>>>(n, F.ncell, F.nw, p->grid.nx, u_even, u_odd,
+                                                 use_state ? p->state : nullptr, F.ug);
+    ADR_CUDA_TRY(cudaGetLastError());
+    return launch_line_solve_dir(p, fam, dt, F.ug, F.ug, use_state);
+}
+
+// the two passes apart (kernel timing): the gather alone, the solve alone
+adr_status launch_gather_pass(Problem* p, int fam, const double* u)
+{
+    Family& F = p->fam[fam];
+    if (!F.ug) return ADR_OK;
+    k_gather_grid<<<grid_map_blocks(p), 256, 0, p->stream>>>(F.n_nodes, F.ncell, F.nw, p->grid.nx, u, u,
+                                                             nullptr, F.ug);
+    ADR_CUDA_TRY(cudaGetLastError());
+    return ADR_OK;
+}
+
+adr_status launch_solve_pass(Problem* p, int fam, double dt, const double* u)
+{
+    Family& F = p->fam[fam];
+    if (!F.ug) return launch_line_solve(p, fam, dt, u, u, false, 0);
+    return launch_line_solve_dir(p, fam, dt, F.ug, F.ug, false);
 }
 
 // direct transfer into the nodes of family to_fam from values v of the other
