@@ -76,7 +76,7 @@ FLOPS_PER_UNIT_DIRECT = [0.0, 14.0, 7.0, 0.0, 12.0, 12.0]
 # DRAM bytes per launch (read + write) of each kernel in the bench's launch
 # shape, from one ncu capture of the 2048^2 sheared workload; None where the
 # kernel has changed since the capture
-NCU_TRAFFIC_SHEARED2048 = [None, None, 399.0e6, None, None, 435.3e6]
+NCU_TRAFFIC_SHEARED2048 = [204.3e6, 350.9e6, 398.9e6, 215.5e6, 262.4e6, 435.3e6]
 NCU_TRAFFIC_DIRECT_SHEARED2048 = [None, 351.2e6, 235.3e6, None, 263.1e6, 258.9e6]
 
 
@@ -401,6 +401,9 @@ def run_ours(args):
         roof["traffic"] = traffic[k]
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture"
         roof["algorithmic_bytes"] = roof["algorithmic_bytes_per_launch"]
+    if args.n == 2048 and prec == ADR_FP64 and all(t is not None for t, m in
+                                                   zip(traffic, roof["all_kernels_ms_list"]) if m > 0):
+        roof["split_step"] = step_hbm(roof, traffic)
     # per split step: B solve, B map / transfer, G solve, G map / transfer, check;
     # per solve: state reset, output (and the initial gather / midpoint of the direct transfer)
     per_step = 5 + (3 if args.anderson else 0)  # + the extrapolation's 3 kernels
@@ -519,6 +522,8 @@ def variant_leg(args, prob, dev, stream, transfer, anderson, reps=3):
     if args.n == 2048 and traffic[k] is not None:
         roof["traffic"] = traffic[k]
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture"
+    if args.n == 2048 and all(t is not None for t, m in zip(traffic, roof["all_kernels_ms_list"]) if m > 0):
+        roof["split_step"] = step_hbm(roof, traffic)
     out = {"transfer": "direct" if direct else "grid", "anderson": anderson,
            "ms_per_step": ms / reps, "value": dofs / (ms / 1e3), "unit": UNIT,
            "iters_per_solve": its,
@@ -954,7 +959,23 @@ def kernel_roofline(solver, prob, unknowns, direct=False):
             "all_kernels_ms": {nm: kms[i] for i, nm in enumerate(names) if kms[i] > 0},
             "all_kernels_hbm_frac": {nm: bpu[i] * units[i] / (kms[i] * 1e-3) / 1e9 / hbm
                                      for i, nm in enumerate(names) if kms[i] > 0},
-            "split_step_ms": float(sum(kms))}
+            "split_step_ms": float(sum(kms)), "all_kernels_ms_list": [float(x) for x in kms],
+            "algorithmic_bytes_list": [bpu[i] * units[i] for i in range(len(kms))]}
+
+
+def step_hbm(roof, traffic):
+    """The whole split step against the HBM peak: the DRAM bytes of every
+    sweep kernel (one ncu capture each) and their algorithmic bytes over the
+    kernels' CUDA-event times back to back."""
+    hbm, hbm_kind = peaks()
+    kms = roof["all_kernels_ms_list"]
+    ms = float(sum(kms))
+    dram = float(sum(t for t, m in zip(traffic, kms) if m > 0))
+    alg = float(sum(b for b, m in zip(roof["algorithmic_bytes_list"], kms) if m > 0))
+    return {"ms": ms, "dram_bytes": dram, "algorithmic_bytes": alg,
+            "dram_gbs": dram / (ms * 1e-3) / 1e9, "dram_frac": dram / (ms * 1e-3) / 1e9 / hbm,
+            "algorithmic_frac": alg / (ms * 1e-3) / 1e9 / hbm, "peak_gbs": hbm,
+            "peak_kind": "measured copy peak" if hbm_kind == "measured" else "fallback copy peak"}
 
 
 def run_parabolic(args):

@@ -1653,6 +1653,14 @@ adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u
     return ADR_OK;
 }
 
+// the gather pass runs one node per thread: every node's loads are in flight
+// at once instead of behind a grid-stride loop
+static int gather_blocks(const Family& F)
+{
+    const long long b = ((long long)F.n_nodes + 255) / 256;
+    return (int)(b > 0 ? (b < 0x7fffffffLL ? b : 0x7fffffff) : 1);
+}
+
 // one curve solve through the grid in FP64: the gather pass into the
 // family's node values, then the curve solve from them (the same arithmetic
 // as the solve's own gather, split so that the gathers' latency does not
@@ -1663,7 +1671,7 @@ adr_status launch_substep_solve(Problem* p, int fam, double dt, const double* u_
     Family& F = p->fam[fam];
     if (!F.ug) return launch_line_solve(p, fam, dt, u_even, u_odd, use_state, 0);
     const long long n = F.n_nodes;
-    const int blocks = grid_map_blocks(p);
+    const int blocks = gather_blocks(F);
     k_gather_grid<<<blocks, 256, 0, p->stream>>>(n, F.ncell, F.nw, p->grid.nx, u_even, u_odd,
                                                  use_state ? p->state : nullptr, F.ug);
     ADR_CUDA_TRY(cudaGetLastError());
@@ -1675,7 +1683,7 @@ adr_status launch_gather_pass(Problem* p, int fam, const double* u)
 {
     Family& F = p->fam[fam];
     if (!F.ug) return ADR_OK;
-    k_gather_grid<<<grid_map_blocks(p), 256, 0, p->stream>>>(F.n_nodes, F.ncell, F.nw, p->grid.nx, u, u,
+    k_gather_grid<<<gather_blocks(F), 256, 0, p->stream>>>(F.n_nodes, F.ncell, F.nw, p->grid.nx, u, u,
                                                              nullptr, F.ug);
     ADR_CUDA_TRY(cudaGetLastError());
     return ADR_OK;
