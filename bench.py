@@ -406,7 +406,10 @@ def run_ours(args):
         roof["split_step"] = step_hbm(roof, traffic)
     # per split step: B solve, B map / transfer, G solve, G map / transfer, check;
     # per solve: state reset, output (and the initial gather / midpoint of the direct transfer)
-    per_step = 5 + (3 if args.anderson else 0)  # + the extrapolation's 3 kernels
+    # per split step: (gather,) solve, map or transfer for each family, the check;
+    # the gathers are passes of their own in FP64 through the grid; + the
+    # extrapolation's 3 kernels
+    per_step = (7 if prec == ADR_FP64 and not direct else 5) + (3 if args.anderson else 0)
     launches = int(sum(per_step * it + (5 if direct else 3) for it in iters))
     # the other precision mode on the same workload (the direct transfer: the
     # transfer through the grid instead): time to tol and agreement
