@@ -1048,7 +1048,8 @@ def run_parabolic(args):
                        "step": f"one {nsteps}-step run from the Gaussian blob",
                        "l2": "working set ~250 MB > 129 MB L2"},
             "roofline": roof,
-            "gpu_launches": int(iters[-1] * (5 + (3 if args.anderson else 0)) + nsteps * 4), "clocks": clk,
+            "gpu_launches": int(iters[-1] * ((7 if prec == ADR_FP64 else 5) + (3 if args.anderson else 0))
+                                + nsteps * 4), "clocks": clk,
             "err_vs_oracle": {"measure": "max |u - u_oracle| / max |u_oracle|",
                               "first_slices": n_check, args.prec: err_first,
                               "oracle_split_steps": ref_iters, "oracle_secs": oracle_check_s}}
