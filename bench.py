@@ -57,8 +57,6 @@ KERNELS = ["gather B", "curve solve B", "curve->grid map B", "gather G", "curve 
 #                  elimination 2 + upward 2 + back 4 flop
 #   maps (unit = grid node): crossings 16 + coefficients 64 + type 1 + out 8 (+ u_j 8 for
 #         the norms) B, 8 fma (+ 1 add and 2 fma for the norms)
-# In the reduced-precision mode the solves gather themselves (the gather stages
-# read 0 time) and their figures are the gather's plus the solve's.
 BYTES_PER_UNIT = [52.0, 72.0, 81.0, 52.0, 48.0, 89.0]
 FLOPS_PER_UNIT = [7.0, 14.0, 16.0, 7.0, 12.0, 21.0]
 # The same for the direct curve-to-curve transfer (--transfer direct), whose
@@ -409,7 +407,7 @@ def run_ours(args):
     # per split step: (gather,) solve, map or transfer for each family, the check;
     # the gathers are passes of their own in FP64 through the grid; + the
     # extrapolation's 3 kernels
-    per_step = (7 if prec == ADR_FP64 and not direct else 5) + (3 if args.anderson else 0)
+    per_step = (5 if direct else 7) + (3 if args.anderson else 0)
     launches = int(sum(per_step * it + (5 if direct else 3) for it in iters))
     # the other precision mode on the same workload (the direct transfer: the
     # transfer through the grid instead): time to tol and agreement
@@ -1048,7 +1046,7 @@ def run_parabolic(args):
                        "step": f"one {nsteps}-step run from the Gaussian blob",
                        "l2": "working set ~250 MB > 129 MB L2"},
             "roofline": roof,
-            "gpu_launches": int(iters[-1] * ((7 if prec == ADR_FP64 else 5) + (3 if args.anderson else 0))
+            "gpu_launches": int(iters[-1] * (7 + (3 if args.anderson else 0))
                                 + nsteps * 4), "clocks": clk,
             "err_vs_oracle": {"measure": "max |u - u_oracle| / max |u_oracle|",
                               "first_slices": n_check, args.prec: err_first,

@@ -258,9 +258,9 @@ adr_status adr_paper_u0(adr_problem* prob, double* u0);
  * launched reps times back to back on the handle's stream in the launch
  * configuration of the solve, timed with CUDA events on that stream: B gather,
  * B curve solve, B curve->grid map, G gather, G curve solve, G map (+ norms).
- * The gathers are passes of their own in FP64 mode through the grid; in the
- * reduced-precision mode the solves gather themselves and the gather entries
- * read 0.  With opts.transfer = 1: 0, B solve, B -> G transfer, 0, G solve,
+ * The gathers are passes of their own through the grid (both precision
+ * modes; batches keep the gathers inside their solves).  With
+ * opts.transfer = 1: 0, B solve, B -> G transfer, 0, G solve,
  * G -> B transfer (+ norms).  They run on the handle's current state (work
  * buffers only; no caller memory is touched).  ms_out: host double[6],
  * average milliseconds per launch.  Errors: ADR_EINVAL, ADR_ECUDA.

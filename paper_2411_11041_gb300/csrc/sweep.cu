@@ -706,7 +706,9 @@ __device__ __forceinline__ void curve_solve_body(const CurveArgs& a, int Titem, 
             double x64;
             if constexpr (sizeof(E) == 4) x64 = f32_to_f64(x);
             else x64 = x;
-            v[node] = paper ? x64 : fma(a.dt, x64, v[node]);  // v = u + dt d in FP64
+            // v = u + dt d in FP64 (u parked in v, or the node values themselves)
+            const double ub = DIR ? __ldg(u + node) : v[node];
+            v[node] = paper ? x64 : fma(a.dt, x64, ub);
             xmax = fmaxf(xmax, fabsf(as_f32(x)));
         } else {
             v[node] = x;
@@ -739,6 +741,17 @@ __device__ __forceinline__ void curve_solve_ref(const CurveArgs& a, int Titem, c
 {
     if (a.state && a.state->hp) curve_solve_body<BS, FAM, true, double>(a, Titem, curves, lanec, a.fac, smem);
     else curve_solve_body<BS, FAM, true, float>(a, Titem, curves, lanec32, a.fac32, smem);
+}
+
+// the same from the state at the curve's nodes (the gather pass before it)
+template <int BS, int FAM>
+__device__ __forceinline__ void curve_solve_ref_dir(const CurveArgs& a, int Titem, const int* curves,
+                                                    const double* lanec, const float* lanec32,
+                                                    unsigned char* smem)
+{
+    if (a.state && a.state->hp)
+        curve_solve_body<BS, FAM, true, double, true>(a, Titem, curves, lanec, a.fac, smem);
+    else curve_solve_body<BS, FAM, true, float, true>(a, Titem, curves, lanec32, a.fac32, smem);
 }
 
 // 256-thread blocks are held to 64 registers (4 blocks per SM with their
@@ -781,16 +794,20 @@ struct ActiveLists {
 };
 constexpr int kCountPerBuf = 7;
 
-// FP64 curve solve of the direct transfer: the state at the curve's nodes
-template <int BS, int FAM>
+// curve solve from the state at the curve's nodes (the direct transfer, or
+// after the gather pass): FP64 new values, or (REF) the reduced-precision
+// mode's correction added in FP64
+template <int BS, int FAM, bool REF = false>
 __global__ void __launch_bounds__(BS, BS == 256 ? 4 : (BS == 512 ? 2 : 1)) k_curve_solve_dir(CurveArgs a, const int* item_T,
-                                                    const int* item_curve, const double* lanec)
+                                                    const int* item_curve, const double* lanec,
+                                                    const float* lanec32)
 {
     if (a.state && a.state->done) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t lo = (size_t)blockIdx.x * Items<BS>::NF * BS;
-    curve_solve_body<BS, FAM, false, double, true>(a, item_T[blockIdx.x], item_curve + blockIdx.x * Items<BS>::MAXC,
-                                                   lanec + lo, a.fac, smem);
+    const int* cv = item_curve + blockIdx.x * Items<BS>::MAXC;
+    if constexpr (REF) curve_solve_ref_dir<BS, FAM>(a, item_T[blockIdx.x], cv, lanec + lo, lanec32 + lo, smem);
+    else curve_solve_body<BS, FAM, false, double, true>(a, item_T[blockIdx.x], cv, lanec + lo, a.fac, smem);
 }
 
 template <int BS, int FAM, bool REF>
@@ -1339,7 +1356,7 @@ adr_status setup_groups(Problem* p, int fam, const std::vector<int>& off)
                                  p->stream));
     TRY_S(dev_alloc(p, &F.gcell, NS));
     TRY_S(dev_alloc(p, &F.gw, 4 * NS));
-    if (p->opts.prec == ADR_FP64 && !p->opts.transfer) {
+    if (!p->opts.transfer) {
         // node-order gather descriptors and node values of the separate gather pass
         const size_t nn = (size_t)F.n_nodes + 1;
         TRY_S(dev_alloc(p, &F.ncell, nn));
@@ -1561,8 +1578,8 @@ static cudaError_t solve_attr()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_curve_solve_batch<BS, FAM, REF>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess && !REF)
-        e = cudaFuncSetAttribute(k_curve_solve_dir<BS, FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_curve_solve_dir<BS, FAM, REF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  bytes);
     return e;
 }
@@ -1628,10 +1645,11 @@ adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u
                                  const double* u_odd, bool use_state)
 {
     Family& F = p->fam[fam];
-    if (!F.prep_valid || F.prep_paper || F.prep_dt != dt || p->opts.prec != ADR_FP64) {
+    if (!F.prep_valid || F.prep_paper || F.prep_dt != dt) {
         set_error("internal: curve systems not factored for this step");
         return ADR_EINVAL;
     }
+    const bool ref = p->opts.prec == ADR_FP32_REFINE;
     TRY_S(ensure_solve_attrs());
     CurveArgs a = curve_args(p, fam);
     a.u_even = u_even;
@@ -1642,8 +1660,13 @@ adr_status launch_line_solve_dir(Problem* p, int fam, double dt, const double* u
 #define ADR_SOLVE_DIR(BS_, I_)                                                                     \
     if (I_.count) {                                                                                \
         const size_t sm = solve_smem<BS_>(R);                                                      \
-        if (fam == 0) k_curve_solve_dir<BS_, 0><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec); \
-        else k_curve_solve_dir<BS_, 1><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec);         \
+        if (ref) {                                                                                 \
+            if (fam == 0) k_curve_solve_dir<BS_, 0, true><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32); \
+            else k_curve_solve_dir<BS_, 1, true><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32);         \
+        } else {                                                                                   \
+            if (fam == 0) k_curve_solve_dir<BS_, 0><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32); \
+            else k_curve_solve_dir<BS_, 1><<<I_.count, BS_, sm, st>>>(a, I_.T, I_.curve, I_.lanec, I_.lanec32);         \
+        }                                                                                          \
     }
     ADR_SOLVE_DIR(1024, F.iset[2])
     ADR_SOLVE_DIR(512, F.iset[1])
