@@ -810,7 +810,9 @@ __global__ void __launch_bounds__(BS, BS == 256 ? 4 : (BS == 512 ? 2 : 1)) k_cur
     else curve_solve_body<BS, FAM, false, double, true>(a, item_T[blockIdx.x], cv, lanec + lo, a.fac, smem);
 }
 
-template <int BS, int FAM, bool REF>
+// DIR: the table's u pointers are the families' node values (the batched
+// gather pass before the solve fills them)
+template <int BS, int FAM, bool REF, bool DIR = false>
 __global__ void __launch_bounds__(BS) k_curve_solve_batch(const CurveArgs* __restrict__ table,
                                                           const BatchItem* __restrict__ items,
                                                           ActiveLists act, int set)
@@ -824,10 +826,12 @@ __global__ void __launch_bounds__(BS) k_curve_solve_batch(const CurveArgs* __res
         const CurveArgs& a = table[2 * I.prob + FAM];
         if (a.state->done) continue;  // uniform: one problem per item
         const size_t lo = (size_t)I.local * Items<BS>::NF * BS;
-        if constexpr (REF)
+        if constexpr (REF && DIR)
+            curve_solve_ref_dir<BS, FAM>(a, I.T, I.curves, a.lanecs[set] + lo, a.lanec32s[set] + lo, smem);
+        else if constexpr (REF)
             curve_solve_ref<BS, FAM>(a, I.T, I.curves, a.lanecs[set] + lo, a.lanec32s[set] + lo, smem);
         else
-            curve_solve_body<BS, FAM, false, double>(a, I.T, I.curves, a.lanecs[set] + lo, a.fac, smem);
+            curve_solve_body<BS, FAM, false, double, DIR>(a, I.T, I.curves, a.lanecs[set] + lo, a.fac, smem);
         __syncthreads();  // shared memory is reused by the next item
     }
 }
@@ -1049,6 +1053,52 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_map_batch(const GridArgs*
                              (long long)nblk[p] * blockDim.x, dd, uu);
         if (NORMS) block_sum2(dd, uu, a.partial + 2 * lb);
         __syncthreads();  // block_sum2's shared arrays are reused
+    }
+}
+
+// batched gather pass: the grid state at the nodes of one family of every
+// active problem, over the batch's map blocks (problem, local block)
+struct GatherArgs {
+    long long n;         // curve nodes of the family
+    const int* ncell;
+    const double* nw;
+    int nx;
+    const double* u_even;
+    const double* u_odd;
+    const IterState* state;
+    double* out;
+};
+
+__global__ void __launch_bounds__(256) k_gather_batch(const GatherArgs* __restrict__ table, int fam,
+                                                      const int* blk_prob, const int* blk_local,
+                                                      const int* nblk, const int* const* act_blocks,
+                                                      const int* act_count, const int* sel)
+{
+    const int cur = *sel;
+    const int* list = act_blocks[cur];
+    const int n_act = act_count[cur * 7 + 6];
+    for (int ii = blockIdx.x; ii < n_act; ii += gridDim.x) {
+        const int bk = list[ii], pr = blk_prob[bk], lb = blk_local[bk];
+        const GatherArgs& g = table[2 * pr + fam];
+        if (g.state->done) continue;
+        const double* __restrict__ u = (g.state->iter & 1) ? g.u_odd : g.u_even;
+        const long long stride = (long long)nblk[pr] * blockDim.x;
+        for (long long k = (long long)lb * blockDim.x + threadIdx.x; k < g.n; k += stride) {
+            const int c = __ldg(g.ncell + k);
+            double v = 0.0;
+            if (c >= 0) {
+                const double2 wa = *reinterpret_cast<const double2*>(g.nw + 4 * k);
+                const double2 wb = *reinterpret_cast<const double2*>(g.nw + 4 * k + 2);
+                const double* r0 = u + c;
+                const double p11 = __ldg(r0), p12 = __ldg(r0 + 1), p21 = __ldg(r0 + g.nx),
+                             p22 = __ldg(r0 + g.nx + 1);
+                v = wa.x * p11;
+                v = fma(wa.y, p12, v);
+                v = fma(wb.x, p21, v);
+                v = fma(wb.y, p22, v);
+            }
+            g.out[k] = v;
+        }
     }
 }
 
@@ -1579,6 +1629,9 @@ static cudaError_t solve_attr()
         e = cudaFuncSetAttribute(k_curve_solve_batch<BS, FAM, REF>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_curve_solve_batch<BS, FAM, REF, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_curve_solve_dir<BS, FAM, REF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  bytes);
     return e;
@@ -1875,6 +1928,7 @@ struct BatchDev {
     BatchItem* it[2][kItemSets] = {};
     int nit[2][kItemSets] = {};
     int git[2][kItemSets] = {};
+    GatherArgs* gath = nullptr;  // [2n] gather passes (null: the solves gather themselves)
     void* aa_table = nullptr;  // per-problem Anderson arguments (null: no problem extrapolates)
     int aa_mmax = 0;
     std::vector<void*> owned;
@@ -1925,6 +1979,9 @@ adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const 
     };
     std::vector<CurveArgs> ct(2 * n);
     std::vector<GridArgs> gt(2 * n);
+    std::vector<GatherArgs> ga(2 * n);
+    bool split = true;  // every problem has its gather pass
+    for (int i = 0; i < n; ++i) split = split && ps[i]->fam[0].ug && ps[i]->fam[1].ug;
     std::vector<int> bp, bl, nb(n);
     std::vector<IterState*> sts(n);
     std::vector<double*> parts(n);
@@ -1939,6 +1996,12 @@ adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const 
             a.u_even = fam == 0 ? p->ubuf[0] : p->ubuf[2];
             a.u_odd = fam == 0 ? p->ubuf[1] : p->ubuf[2];
             a.state = p->state;
+            if (split) {
+                const Family& F = p->fam[fam];
+                GatherArgs g{F.n_nodes, F.ncell, F.nw, p->grid.nx, a.u_even, a.u_odd, p->state, F.ug};
+                ga[2 * i + fam] = g;
+                a.u_even = a.u_odd = F.ug;  // the solve reads the node values
+            }
             a.dt = dts[i];
             a.td = p->opts.theta * dts[i];
             a.paper = 0;
@@ -1982,6 +2045,11 @@ adr_status batch_dev_create(Problem* const* ps, int n, const double* dts, const 
     }
     b->n_blk = (int)bp.size();
     adr_status s;
+    if (split) {
+        if ((s = bdev_alloc(b, &b->gath, 2 * n))) return fail(s);
+        cudaError_t eg = cudaMemcpy(b->gath, ga.data(), sizeof(GatherArgs) * ga.size(), cudaMemcpyHostToDevice);
+        if (eg != cudaSuccess) return fail(cuda_fail(eg, "batch tables"));
+    }
     if ((s = bdev_alloc(b, &b->ctab, 2 * n)) || (s = bdev_alloc(b, &b->gtab, 2 * n)) ||
         (s = bdev_alloc(b, &b->blk_prob, b->n_blk)) || (s = bdev_alloc(b, &b->blk_local, b->n_blk)) ||
         (s = bdev_alloc(b, &b->nblk, n)) || (s = bdev_alloc(b, &b->states, n)) ||
@@ -2111,19 +2179,28 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
     BatchItem* const* itG = b->it[1];
     const int *nB = b->nit[0], *gB = b->git[0], *nG = b->nit[1], *gG = b->git[1];
     const int R = b->R;
+    const bool dir = b->gath != nullptr;  // gather passes, then solves from the node values
+#define ADR_BATCH_SOLVE_BS(BS_, FAM_, IT, G)                                                        \
+    if (b->ref) {                                                                                  \
+        if (dir) k_curve_solve_batch<BS_, FAM_, true, true><<<G[k], BS_, solve_smem<BS_>(R), st>>>(b->ctab, IT[k], b->act, k); \
+        else k_curve_solve_batch<BS_, FAM_, true><<<G[k], BS_, solve_smem<BS_>(R), st>>>(b->ctab, IT[k], b->act, k);          \
+    } else {                                                                                       \
+        if (dir) k_curve_solve_batch<BS_, FAM_, false, true><<<G[k], BS_, solve_smem<BS_>(R), st>>>(b->ctab, IT[k], b->act, k); \
+        else k_curve_solve_batch<BS_, FAM_, false><<<G[k], BS_, solve_smem<BS_>(R), st>>>(b->ctab, IT[k], b->act, k);          \
+    }
 #define ADR_BATCH_SOLVE(FAM_, IT, N, G)                                                            \
+    if (dir)                                                                                       \
+        k_gather_batch<<<b->map_grid, 256, 0, st>>>(b->gath, FAM_, b->blk_prob, b->blk_local, b->nblk, \
+                                                    b->act.blocks_dev, b->act.count, b->act.sel);    \
     for (int k = kItemSets - 1; k >= 0; --k) {                                                     \
         if (!N[k]) continue;                                                                       \
         int BS = 256 << k;                                                                         \
         if (BS == 256) {                                                                           \
-            if (b->ref) k_curve_solve_batch<256, FAM_, true><<<G[k], 256, solve_smem<256>(R), st>>>(b->ctab, IT[k], b->act, k); \
-            else k_curve_solve_batch<256, FAM_, false><<<G[k], 256, solve_smem<256>(R), st>>>(b->ctab, IT[k], b->act, k);     \
+            ADR_BATCH_SOLVE_BS(256, FAM_, IT, G)                                                   \
         } else if (BS == 512) {                                                                    \
-            if (b->ref) k_curve_solve_batch<512, FAM_, true><<<G[k], 512, solve_smem<512>(R), st>>>(b->ctab, IT[k], b->act, k); \
-            else k_curve_solve_batch<512, FAM_, false><<<G[k], 512, solve_smem<512>(R), st>>>(b->ctab, IT[k], b->act, k);     \
+            ADR_BATCH_SOLVE_BS(512, FAM_, IT, G)                                                   \
         } else {                                                                                   \
-            if (b->ref) k_curve_solve_batch<1024, FAM_, true><<<G[k], 1024, solve_smem<1024>(R), st>>>(b->ctab, IT[k], b->act, k); \
-            else k_curve_solve_batch<1024, FAM_, false><<<G[k], 1024, solve_smem<1024>(R), st>>>(b->ctab, IT[k], b->act, k);     \
+            ADR_BATCH_SOLVE_BS(1024, FAM_, IT, G)                                                  \
         }                                                                                          \
     }
     ADR_BATCH_SOLVE(0, itB, nB, gB)
@@ -2135,6 +2212,7 @@ adr_status batch_dev_step(BatchDev* b, cudaStream_t st, cudaGraphConditionalHand
                                                                 b->nblk, b->act.blocks_dev, b->act.count,
                                                                 b->act.sel);
 #undef ADR_BATCH_SOLVE
+#undef ADR_BATCH_SOLVE_BS
     k_check_batch<<<b->n, 256, 0, st>>>(b->states, (const double* const*)b->partials, b->nblk, b->n,
                                         b->tol, b->max_iter, b->ticket, cond, b->act.changed);
     if (b->aa_table) {
