@@ -259,7 +259,7 @@ adr_status adr_paper_u0(adr_problem* prob, double* u0);
  * configuration of the solve, timed with CUDA events on that stream: B gather,
  * B curve solve, B curve->grid map, G gather, G curve solve, G map (+ norms).
  * The gathers are passes of their own through the grid (both precision
- * modes; batches keep the gathers inside their solves).  With
+ * modes, single handles and batches).  With
  * opts.transfer = 1: 0, B solve, B -> G transfer, 0, G solve,
  * G -> B transfer (+ norms).  They run on the handle's current state (work
  * buffers only; no caller memory is touched).  ms_out: host double[6],
@@ -274,7 +274,10 @@ adr_status adr_time_kernels(adr_problem* prob, int reps, double* ms_out);
  * applied and one split step's kernels are timed reps times with CUDA events
  * on the handle's stream; the fastest is kept.  Outputs (host, nullable): the
  * chosen rows_per_thread and map_blocks_per_sm and its ms per split step.
- * Errors: ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA.
+ * The handle's curve groups are rebuilt for every candidate, so a batch built
+ * over the handle before the call must be destroyed and built again (or
+ * tuned with adr_batch_autotune, which rebuilds its own).  Errors:
+ * ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA.
  */
 adr_status adr_autotune(adr_problem* prob, int reps, int* rows_per_thread,
                         int* map_blocks_per_sm, double* ms_per_step);
